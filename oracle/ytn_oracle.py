@@ -1,0 +1,515 @@
+"""CPU FP64 oracle for abelian-symmetric block-sparse tensors.
+
+TEST INFRASTRUCTURE. This module is the plain, slow, reference statement of what the
+library computes. Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import it. It shares no code with the CUDA
+library and imports nothing from it; the library never calls it.
+
+It follows the paper "YASTN: Yet another symmetric tensor networks" (arXiv 2405.12196):
+
+* Sec. II.A -- a tensor is a set of dense blocks, one per tuple of charge sectors
+  (rho_1..rho_N), one sector per leg V(s, t, D); stored blocks satisfy
+  sum_i s_i rho_i = n (block form of Eq. ``elemchargecon``), component-wise and modulo
+  m for Z_m components (charges of U(1) live in Z, of Z_m in Z_m, of product groups in
+  products of these).
+* Sec. II.B -- fusion: fused charge nu = s_r (s_i rho + s_j rho') and fused dimension
+  D_nu = sum of D_rho D_rho' over the pairs that give nu; fusion is lazy (only charges
+  of blocks that exist); the fused tensor records the original structure so that the
+  fusion can be undone.
+* Sec. II.B, contraction equation -- tensordot = fuse into matrices, multiply, unfuse;
+  the result is, by definition, the sum over the contracted indices of the products of
+  the elements, which for block-sparse tensors is a sum over matching block pairs.
+
+Readings where the paper is silent (each is listed in the design notes):
+contraction compatibility = opposite signatures and equal dimensions of every charge
+present on both legs; n_C = n_A + n_B; output legs = A's free legs then B's; blocks in
+ascending lexicographic order of their charge tuple, row-major elements; fused signature
+= signature of the group's first leg; fused sub-blocks ordered by ascending constituent
+charge tuple; fusion records of contracted fused legs must be conjugate of one another
+(else an error); trace over leg pairs sums the diagonals of blocks whose paired charges
+are equal.
+
+Pins (``tests/test_oracle_*.py``): brute force against the dense embedding on random
+U(1), Z2, Z3 and U(1)xU(1) tensors, the trivial-symmetry special case, the closed form
+(S1.S2)^2 = 3/16 - S1.S2/2 on the paper's two-spin example, hand-derived structure
+counts, fuse/unfuse round trips and singular-value invariance of fused matrices.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+__all__ = [
+    "OTensor", "OracleError", "SignatureError", "DimMismatchError", "FusionMismatchError",
+    "ChargeError", "InvalidError", "UnsupportedError",
+    "from_record", "to_record", "conj", "tensordot", "fuse", "unfuse", "trace",
+    "to_dense", "leg_sectors", "useful_flops", "tensordot_block",
+]
+
+
+class OracleError(Exception):
+    pass
+
+
+class InvalidError(OracleError):
+    pass
+
+
+class SignatureError(OracleError):
+    pass
+
+
+class DimMismatchError(OracleError):
+    pass
+
+
+class FusionMismatchError(OracleError):
+    pass
+
+
+class ChargeError(OracleError):
+    pass
+
+
+class UnsupportedError(OracleError):
+    pass
+
+
+def _red(q, mods):
+    """Reduce a charge tuple: Z components as they are, Z_m components modulo m."""
+    return tuple((int(c) % m) if m else int(c) for c, m in zip(q, mods))
+
+
+def _add(q1, q2, mods):
+    return _red(tuple(a + b for a, b in zip(q1, q2)), mods)
+
+
+def _scale(s, q, mods):
+    return _red(tuple(s * c for c in q), mods)
+
+
+class FusionRecord:
+    """What a fused leg remembers about its origin (Sec. II.B: the fused tensor records
+    the original structure).
+
+    ``sig``: signatures of the constituent legs. ``entries``: for each fused charge nu,
+    the list of (constituent charges, constituent dims) that were present, in ascending
+    order of the constituent charge tuple; each occupies prod(dims) consecutive indices
+    of the fused sector, in that order."""
+
+    def __init__(self, sig, entries):
+        self.sig = tuple(int(s) for s in sig)
+        self.entries = {nu: sorted(lst) for nu, lst in entries.items()}
+
+    def dim(self, nu):
+        return sum(int(np.prod(d)) for _, d in self.entries[nu])
+
+    def offsets(self, nu):
+        out, off = [], 0
+        for ch, d in self.entries[nu]:
+            out.append((ch, d, off))
+            off += int(np.prod(d))
+        return out
+
+    def conj(self):
+        return FusionRecord(tuple(-s for s in self.sig), self.entries)
+
+    def key(self):
+        return (self.sig, tuple(sorted((nu, tuple(l)) for nu, l in self.entries.items())))
+
+
+class OTensor:
+    """A block-sparse symmetric tensor: ``blocks`` maps a tuple of per-leg charge tuples
+    to a dense FP64 array whose shape is the per-leg sector dimensions."""
+
+    def __init__(self, mods, sig, n, blocks=None, fus=None):
+        self.mods = tuple(int(m) for m in mods)
+        self.sig = tuple(int(s) for s in sig)
+        self.n = _red(n, self.mods)
+        self.blocks = {} if blocks is None else blocks
+        self.fus = list(fus) if fus is not None else [None] * len(self.sig)
+
+    @property
+    def rank(self):
+        return len(self.sig)
+
+    @property
+    def nsym(self):
+        return len(self.mods)
+
+    def keys(self):
+        """Block keys in canonical order: ascending lexicographic charge tuples."""
+        return sorted(self.blocks)
+
+    def validate(self):
+        """Check the block conservation rule and that a charge has one dimension per leg."""
+        dims = [dict() for _ in range(self.rank)]
+        for key, blk in self.blocks.items():
+            if len(key) != self.rank or blk.ndim != self.rank:
+                raise InvalidError("block rank does not match the tensor rank")
+            tot = tuple([0] * self.nsym)
+            for s, q in zip(self.sig, key):
+                tot = _add(tot, _scale(s, q, self.mods), self.mods)
+            if tot != self.n:
+                raise ChargeError(f"block {key} violates charge conservation")
+            for a, (q, d) in enumerate(zip(key, blk.shape)):
+                if dims[a].setdefault(q, d) != d:
+                    raise DimMismatchError(f"leg {a} charge {q} has two dimensions")
+                if self.fus[a] is not None:
+                    if q not in self.fus[a].entries or self.fus[a].dim(q) != d:
+                        raise InvalidError("fused leg block does not match its record")
+        return self
+
+
+def leg_sectors(T, axis):
+    """Charge -> dimension map of one leg, read from the stored blocks (and, for a fused
+    leg, from its record)."""
+    out = {}
+    for key, blk in T.blocks.items():
+        out[key[axis]] = blk.shape[axis]
+    if T.fus[axis] is not None:
+        for nu in T.fus[axis].entries:
+            out.setdefault(nu, T.fus[axis].dim(nu))
+    return out
+
+
+# ------------------------------------------------------------------ plain-array records
+
+def from_record(rec):
+    """Build an OTensor from the plain-array record of ``workloads`` (canonical order,
+    packed row-major blocks); ``rec['fus']`` (optional) holds per-leg fusion records in
+    plain-array form."""
+    mods = tuple(rec["mods"])
+    t = np.asarray(rec["t"])
+    D = np.asarray(rec["D"])
+    data = np.asarray(rec["data"], dtype=np.float64)
+    blocks = {}
+    off = 0
+    for b in range(len(t)):
+        key = tuple(tuple(int(c) for c in t[b, a]) for a in range(t.shape[1]))
+        shape = tuple(int(d) for d in D[b])
+        sz = int(np.prod(shape))
+        if key in blocks:
+            raise InvalidError("duplicate block")
+        blocks[key] = data[off:off + sz].reshape(shape).copy()
+        off += sz
+    if off != data.size:
+        raise InvalidError("data size does not match the block dimensions")
+    fus = None
+    if rec.get("fus") is not None:
+        fus = [None if f is None else _record_from_plain(f) for f in rec["fus"]]
+    return OTensor(mods, rec["sig"], rec["n"], blocks, fus).validate()
+
+
+def _record_from_plain(f):
+    entries = {}
+    nu = np.asarray(f["nu"])
+    ct = np.asarray(f["t"])
+    cd = np.asarray(f["D"])
+    for e in range(len(nu)):
+        key = tuple(int(c) for c in nu[e])
+        ch = tuple(tuple(int(c) for c in ct[e, i]) for i in range(ct.shape[1]))
+        dd = tuple(int(d) for d in cd[e])
+        entries.setdefault(key, []).append((ch, dd))
+    return FusionRecord(f["sig"], entries)
+
+
+def _record_to_plain(fr, nsym):
+    rows = [(nu, ch, d) for nu in sorted(fr.entries) for ch, d in fr.entries[nu]]
+    m = len(fr.sig)
+    nu = np.array([r[0] for r in rows], dtype=np.int32).reshape(len(rows), nsym)
+    t = np.array([r[1] for r in rows], dtype=np.int32).reshape(len(rows), m, nsym)
+    D = np.array([r[2] for r in rows], dtype=np.int64).reshape(len(rows), m)
+    return {"sig": fr.sig, "nu": nu, "t": t, "D": D}
+
+
+def to_record(T):
+    """Plain-array record of an OTensor (canonical block order, packed data)."""
+    keys = T.keys()
+    nb = len(keys)
+    t = np.zeros((nb, T.rank, T.nsym), dtype=np.int32)
+    D = np.zeros((nb, T.rank), dtype=np.int64)
+    parts = []
+    for b, key in enumerate(keys):
+        for a in range(T.rank):
+            t[b, a, :] = key[a]
+        D[b, :] = T.blocks[key].shape
+        parts.append(np.ascontiguousarray(T.blocks[key]).ravel())
+    data = np.concatenate(parts) if parts else np.zeros(0)
+    fus = [None if f is None else _record_to_plain(f, T.nsym) for f in T.fus]
+    return {"mods": T.mods, "sig": T.sig, "n": T.n, "t": t, "D": D, "data": data,
+            "fus": fus if any(f is not None for f in fus) else None}
+
+
+# ------------------------------------------------------------------ basic operations
+
+def conj(T):
+    """Conjugate: every leg's signature flips (Sec. II.A footnote), so the total charge
+    becomes -n; real data is unchanged."""
+    fus = [None if f is None else f.conj() for f in T.fus]
+    return OTensor(T.mods, tuple(-s for s in T.sig), _scale(-1, T.n, T.mods),
+                   {k: v.copy() for k, v in T.blocks.items()}, fus)
+
+
+def _check_pairs(rankA, rankB, axa, axb):
+    axa, axb = tuple(int(a) for a in axa), tuple(int(b) for b in axb)
+    if len(axa) != len(axb):
+        raise InvalidError("axes lists differ in length")
+    if len(set(axa)) != len(axa) or len(set(axb)) != len(axb):
+        raise InvalidError("repeated axis")
+    if any(a < 0 or a >= rankA for a in axa) or any(b < 0 or b >= rankB for b in axb):
+        raise InvalidError("axis out of range")
+    return axa, axb
+
+
+def _check_compatible(A, a, B, b):
+    """Contracted legs must be compatible: opposite signatures, equal dimension for each
+    charge present on both, conjugate fusion records (Sec. II.B footnote)."""
+    if A.sig[a] != -B.sig[b]:
+        raise SignatureError(f"leg {a} of A and leg {b} of B have equal signatures")
+    da, db = leg_sectors(A, a), leg_sectors(B, b)
+    for q in set(da) & set(db):
+        if da[q] != db[q]:
+            raise DimMismatchError(f"charge {q}: dimension {da[q]} vs {db[q]}")
+    fa, fb = A.fus[a], B.fus[b]
+    if (fa is None) != (fb is None):
+        raise FusionMismatchError("a fused leg is contracted with a plain leg")
+    if fa is not None and fa.key() != fb.conj().key():
+        raise FusionMismatchError("fusion records of contracted legs differ")
+
+
+def tensordot(A, B, axa, axb):
+    """C = sum over the contracted indices of A * B (Sec. II.B, contraction equation).
+
+    Every pair (alpha, beta) of stored blocks whose charges agree on all contracted legs
+    contributes tensordot(A_alpha, B_beta) to the C block keyed by A's free charges
+    followed by B's free charges. Blocks of C exist when at least one pair contributed
+    (lazy storage, Sec. II.A)."""
+    if A.mods != B.mods:
+        raise InvalidError("tensors have different symmetries")
+    axa, axb = _check_pairs(A.rank, B.rank, axa, axb)
+    for a, b in zip(axa, axb):
+        _check_compatible(A, a, B, b)
+    freeA = [i for i in range(A.rank) if i not in axa]
+    freeB = [i for i in range(B.rank) if i not in axb]
+    C = OTensor(A.mods, tuple(A.sig[i] for i in freeA) + tuple(B.sig[i] for i in freeB),
+                _add(A.n, B.n, A.mods),
+                fus=[A.fus[i] for i in freeA] + [B.fus[i] for i in freeB])
+    byx = {}
+    for kb in B.keys():
+        byx.setdefault(tuple(kb[b] for b in axb), []).append(kb)
+    for ka in A.keys():
+        x = tuple(ka[a] for a in axa)
+        for kb in byx.get(x, []):
+            kc = tuple(ka[i] for i in freeA) + tuple(kb[i] for i in freeB)
+            prod = np.tensordot(A.blocks[ka], B.blocks[kb], axes=(axa, axb))
+            if kc in C.blocks:
+                C.blocks[kc] = C.blocks[kc] + prod
+            else:
+                C.blocks[kc] = np.array(prod, dtype=np.float64)
+    return C
+
+
+def tensordot_block(A, B, axa, axb, kc):
+    """One output block of tensordot(A, B), summed over its matching pairs in canonical
+    order -- the same definition as ``tensordot``, evaluated for one key (used to check
+    sampled outputs of large contractions)."""
+    axa, axb = tuple(axa), tuple(axb)
+    freeA = [i for i in range(A.rank) if i not in axa]
+    freeB = [i for i in range(B.rank) if i not in axb]
+    ia, ib = kc[:len(freeA)], kc[len(freeA):]
+    out = None
+    for ka in A.keys():
+        if tuple(ka[i] for i in freeA) != ia:
+            continue
+        x = tuple(ka[a] for a in axa)
+        for kb in B.keys():
+            if tuple(kb[i] for i in freeB) != ib or tuple(kb[b] for b in axb) != x:
+                continue
+            prod = np.tensordot(A.blocks[ka], B.blocks[kb], axes=(axa, axb))
+            out = prod if out is None else out + prod
+    return out
+
+
+def useful_flops(A, B, axa, axb):
+    """FLOPs of the block-sparse contraction: 2 |I| |x| |J| per matching block pair."""
+    axa, axb = tuple(axa), tuple(axb)
+    byx = {}
+    for kb, blk in B.blocks.items():
+        byx.setdefault(tuple(kb[b] for b in axb), []).append(blk.size)
+    total = 0
+    for ka, blk in A.blocks.items():
+        x = tuple(ka[a] for a in axa)
+        kx = int(np.prod([blk.shape[a] for a in axa])) if axa else 1
+        for szb in byx.get(x, []):
+            total += 2 * (blk.size // kx) * kx * (szb // kx)
+    return total
+
+
+# ------------------------------------------------------------------ fusion
+
+def _normalise_groups(groups, rank):
+    gs = [tuple(g) if isinstance(g, (tuple, list)) else (int(g),) for g in groups]
+    flat = [a for g in gs for a in g]
+    if sorted(flat) != list(range(rank)):
+        raise InvalidError("fusion groups must list every leg exactly once")
+    if any(len(g) == 0 for g in gs):
+        raise InvalidError("empty fusion group")
+    return gs
+
+
+def fuse(A, groups):
+    """Fuse groups of legs into single legs (Sec. II.B).
+
+    For a group of legs i..j the fused leg gets the signature of the group's first leg
+    s_r, charges nu = s_r * sum_i s_i rho_i, and dimension D_nu = sum over the charge
+    tuples present in some stored block of prod_i D_rho_i (lazy fusion). Sub-blocks sit
+    in ascending order of their constituent charge tuple, each row-major over the group's
+    legs. Every stored block is transposed to the group order and copied to its place in
+    the fused block; fused-block entries with no stored block are zero."""
+    gs = _normalise_groups(groups, A.rank)
+    mods = A.mods
+    # a single leg passes through; a group of two or more legs must consist of plain legs
+    for g in gs:
+        if len(g) > 1 and any(A.fus[a] is not None for a in g):
+            raise UnsupportedError("fusing an already fused leg")
+    rec = []
+    for g in gs:
+        if len(g) == 1:
+            rec.append(None)
+            continue
+        entries = {}
+        seen = set()
+        for key, blk in A.blocks.items():
+            ch = tuple(key[a] for a in g)
+            if ch in seen:
+                continue
+            seen.add(ch)
+            tot = tuple([0] * A.nsym)
+            for a in g:
+                tot = _add(tot, _scale(A.sig[a], key[a], mods), mods)
+            nu = _scale(A.sig[g[0]], tot, mods)
+            entries.setdefault(nu, []).append((ch, tuple(blk.shape[a] for a in g)))
+        rec.append(FusionRecord(tuple(A.sig[a] for a in g), entries))
+    sig = tuple(A.sig[g[0]] for g in gs)
+    fus = [A.fus[g[0]] if len(g) == 1 else rec[i] for i, g in enumerate(gs)]
+    out = OTensor(mods, sig, A.n, fus=fus)
+    order = [a for g in gs for a in g]
+    for key in A.keys():
+        blk = A.blocks[key]
+        newkey, shape, box = [], [], []
+        for i, g in enumerate(gs):
+            if len(g) == 1:
+                newkey.append(key[g[0]])
+                shape.append(blk.shape[g[0]])
+                box.append((0, blk.shape[g[0]]))
+            else:
+                ch = tuple(key[a] for a in g)
+                tot = tuple([0] * A.nsym)
+                for a in g:
+                    tot = _add(tot, _scale(A.sig[a], key[a], mods), mods)
+                nu = _scale(A.sig[g[0]], tot, mods)
+                newkey.append(nu)
+                shape.append(rec[i].dim(nu))
+                for c, d, off in rec[i].offsets(nu):
+                    if c == ch:
+                        box.append((off, int(np.prod(d))))
+                        break
+        newkey = tuple(newkey)
+        if newkey not in out.blocks:
+            out.blocks[newkey] = np.zeros(shape)
+        sub = np.transpose(blk, order).reshape([b[1] for b in box])
+        out.blocks[newkey][tuple(slice(o, o + n) for o, n in box)] = sub
+    return out
+
+
+def unfuse(A, axes):
+    """Undo the fusion of the given fused legs using their records (Sec. II.B).
+
+    Every fused block is cut into its recorded sub-blocks; each sub-block is reshaped to
+    the constituent dimensions and stored under the constituent charges. All recorded
+    sub-blocks of stored fused blocks are emitted, including ones that are zero."""
+    axes = sorted(set(int(a) for a in axes))
+    for a in axes:
+        if a < 0 or a >= A.rank or A.fus[a] is None:
+            raise InvalidError(f"leg {a} is not a fused leg")
+    sig, fus = [], []
+    for a in range(A.rank):
+        if a in axes:
+            sig.extend(A.fus[a].sig)
+            fus.extend([None] * len(A.fus[a].sig))
+        else:
+            sig.append(A.sig[a])
+            fus.append(A.fus[a])
+    out = OTensor(A.mods, tuple(sig), A.n, fus=fus)
+    for key in A.keys():
+        blk = A.blocks[key]
+        choices = []
+        for a in range(A.rank):
+            if a in axes:
+                choices.append(A.fus[a].offsets(key[a]))
+            else:
+                choices.append([((key[a],), (blk.shape[a],), 0)])
+        for combo in itertools.product(*choices):
+            sl = tuple(slice(off, off + int(np.prod(d))) for _, d, off in combo)
+            newkey = tuple(q for ch, _, _ in combo for q in ch)
+            shape = tuple(x for _, d, _ in combo for x in d)
+            out.blocks[newkey] = np.array(blk[sl]).reshape(shape)
+    return out
+
+
+# ------------------------------------------------------------------ trace
+
+def trace(A, ax1, ax2):
+    """Sum over the diagonals of leg pairs (ax1[k], ax2[k]).
+
+    The paper does not describe a trace; this follows from the block structure: a pair
+    of legs is traced when its signatures are opposite; a block contributes when its two
+    charges of every pair are equal, and adds sum_d block[..d..d..] to the output block
+    keyed by its remaining charges. The total charge is unchanged."""
+    ax1, ax2 = tuple(int(a) for a in ax1), tuple(int(b) for b in ax2)
+    if len(ax1) != len(ax2) or len(set(ax1 + ax2)) != 2 * len(ax1):
+        raise InvalidError("trace axes must be disjoint pairs")
+    if any(a < 0 or a >= A.rank for a in ax1 + ax2):
+        raise InvalidError("axis out of range")
+    for a, b in zip(ax1, ax2):
+        _check_compatible(A, a, A, b)
+    rest = [i for i in range(A.rank) if i not in ax1 + ax2]
+    out = OTensor(A.mods, tuple(A.sig[i] for i in rest), A.n, fus=[A.fus[i] for i in rest])
+    for key in A.keys():
+        if any(key[a] != key[b] for a, b in zip(ax1, ax2)):
+            continue
+        blk = A.blocks[key]
+        P = int(np.prod([blk.shape[a] for a in ax1])) if ax1 else 1
+        R = [blk.shape[i] for i in rest]
+        m = np.transpose(blk, rest + list(ax1) + list(ax2)).reshape(int(np.prod(R)) if R else 1, P, P)
+        val = np.trace(m, axis1=1, axis2=2).reshape(R)
+        kc = tuple(key[i] for i in rest)
+        out.blocks[kc] = out.blocks[kc] + val if kc in out.blocks else np.array(val, dtype=np.float64)
+    return out
+
+
+# ------------------------------------------------------------------ dense embedding
+
+def to_dense(T, legs=None):
+    """Dense embedding: each leg's index runs over its sectors concatenated in ascending
+    charge order; a block sits at its sectors' offsets; everything else is zero.
+
+    ``legs``: optional list of charge -> dim maps (one per leg), to embed several tensors
+    in a common basis; defaults to ``leg_sectors``."""
+    if legs is None:
+        legs = [leg_sectors(T, a) for a in range(T.rank)]
+    offs, dims = [], []
+    for lg in legs:
+        o, acc = {}, 0
+        for q in sorted(lg):
+            o[q] = acc
+            acc += lg[q]
+        offs.append(o)
+        dims.append(acc)
+    out = np.zeros(dims)
+    for key, blk in T.blocks.items():
+        sl = tuple(slice(offs[a][key[a]], offs[a][key[a]] + blk.shape[a]) for a in range(T.rank))
+        out[sl] = blk
+    return out

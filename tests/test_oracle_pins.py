@@ -1,0 +1,359 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the mathematics.
+
+Each test names the passage it pins. A plausible mistake in the oracle (a dropped
+pair, a wrong sign in charge matching, a transposed operand, a misplaced fused
+sub-block, a wrong trace pairing) fails at least one of these.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import leg_map, random_legs, random_pair
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _tensor_from_golden(g, key="blocks"):
+    blocks = {}
+    for charges, val in g[key]:
+        k = tuple(tuple(c) for c in charges)
+        blocks[k] = np.array(val, dtype=np.float64).reshape([1] * len(k))
+    return O.OTensor(tuple(g["mods"]), tuple(g["sig"]), tuple(g["n"]), blocks).validate()
+
+
+# ---------------------------------------------------------------- the paper's example
+
+def test_heisenberg_structure_and_closed_form():
+    """Sec. II.A/II.B example: H = S1.S2 on legs [l, l, lc, lc]; (S1.S2)^2 = 3/16 - H/2."""
+    g = _golden("heisenberg_two_site.json")
+    H = _tensor_from_golden(g)
+    assert len(H.blocks) == 6
+    # the generator's allowed blocks for these legs are exactly the 6 of the example
+    l = W.Leg(1, [(-1,), (1,)], [1, 1])
+    rec = W.random_tensor((0,), [l, l, l.conj(), l.conj()], (0,), 0)
+    assert sorted(O.from_record(rec).blocks) == sorted(H.blocks)
+    H2 = O.tensordot(H, H, (2, 3), (0, 1))
+    want = _tensor_from_golden(g, "H2_blocks")
+    assert sorted(H2.blocks) == sorted(want.blocks)
+    for k in want.blocks:
+        assert H2.blocks[k].shape == (1, 1, 1, 1)
+        assert H2.blocks[k][0, 0, 0, 0] == pytest.approx(want.blocks[k][0, 0, 0, 0], abs=1e-15)
+
+
+def test_heisenberg_traces():
+    g = _golden("heisenberg_two_site.json")
+    H = _tensor_from_golden(g)
+    trH = O.trace(H, (0, 1), (2, 3))
+    assert trH.rank == 0 and list(trH.blocks) == [()]
+    assert float(trH.blocks[()]) == pytest.approx(g["trace_H"], abs=1e-15)
+    H2 = O.tensordot(H, H, (2, 3), (0, 1))
+    assert float(O.trace(H2, (0, 1), (2, 3)).blocks[()]) == pytest.approx(g["trace_H2"], abs=1e-15)
+
+
+def test_heisenberg_fused_matrix_and_two_routes():
+    """Sec. II.B: H_mat sectors nu in {-2,0,2} with dims {1,2,1}; tensordot(H,H) equals
+    (H_mat @ H_mat).unfuse_legs((0,1)) in structure and values."""
+    g = _golden("heisenberg_two_site.json")
+    H = _tensor_from_golden(g)
+    Hm = O.fuse(H, ((0, 1), (2, 3)))
+    assert Hm.sig == (1, -1)
+    for leg, key in ((0, "H_mat_leg0_sectors"), (1, "H_mat_leg1_sectors")):
+        want = {tuple(q): d for q, d in g[key]}
+        assert O.leg_sectors(Hm, leg) == want
+    want_blocks = {tuple(tuple(c) for c in k): np.array(v) for k, v in g["H_mat_blocks"]}
+    assert sorted(Hm.blocks) == sorted(want_blocks)
+    for k, v in want_blocks.items():
+        np.testing.assert_array_equal(Hm.blocks[k], v)
+    route1 = O.tensordot(H, H, (2, 3), (0, 1))
+    route2 = O.unfuse(O.tensordot(Hm, Hm, (1,), (0,)), (0, 1))
+    assert sorted(route1.blocks) == sorted(route2.blocks)
+    for k in route1.blocks:
+        np.testing.assert_allclose(route2.blocks[k], route1.blocks[k], atol=1e-15)
+
+
+# ---------------------------------------------------------------- hand-derived counts
+
+def test_config1_structure_counts():
+    """Hand-derived block/element/sector counts of the U(1) rank-3 workload."""
+    g = _golden("config1_structure.json")
+    cfg = W.config1()
+    A, B = O.from_record(cfg["A"]), O.from_record(cfg["B"])
+    assert len(A.blocks) == g["A_blocks"]
+    assert sum(b.size for b in A.blocks.values()) == g["A_elements"]
+    C = O.tensordot(A, B, cfg["axa"], cfg["axb"])
+    assert len(C.blocks) == g["C_blocks"]
+    assert sum(b.size for b in C.blocks.values()) == g["C_elements"]
+    assert O.useful_flops(A, B, cfg["axa"], cfg["axb"]) == g["useful_flops"]
+    # sector view: rows/cols of each contracted charge x
+    for x, M, N, K in g["sectors"]:
+        rows = {k[:2] for k in A.blocks if k[2] == (x,)}
+        cols = {k[1:] for k in B.blocks if k[0] == (x,)}
+        assert sum(A.blocks[next(k for k in A.blocks if k[:2] == r)].shape[0] for r in rows) == M
+        assert sum(B.blocks[next(k for k in B.blocks if k[1:] == c)].shape[2] for c in cols) == N
+        assert cfg["A"]["D"][[i for i, k in enumerate(sorted(A.blocks)) if k[2] == (x,)][0], 2] == K
+
+
+# ---------------------------------------------------------------- brute force
+
+SYMS = {"U1": (0,), "Z2": (2,), "Z3": (3,), "U1xU1": (0, 0)}
+
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(12))
+def test_tensordot_equals_dense_brute_force(sym, case):
+    """Symmetric contraction == dense contraction of the block-embedded tensors, and the
+    dense result vanishes outside C's blocks (Sec. II.A block form, Sec. II.B contraction)."""
+    mods = SYMS[sym]
+    rng = np.random.default_rng(1000 * case + len(sym))
+    rankA = int(rng.integers(1, 5))
+    rankB = int(rng.integers(1, 5))
+    ncon = int(rng.integers(0, min(rankA, rankB) + 1))
+    A, B, axa, axb, legsA, legsB = random_pair(rng, mods, rankA, rankB, ncon)
+    oA, oB = O.from_record(A), O.from_record(B)
+    C = O.tensordot(oA, oB, axa, axb)
+    dA = O.to_dense(oA, [leg_map(l) for l in legsA])
+    dB = O.to_dense(oB, [leg_map(l) for l in legsB])
+    want = np.tensordot(dA, dB, axes=(axa, axb))
+    freeA = [i for i in range(rankA) if i not in axa]
+    freeB = [i for i in range(rankB) if i not in axb]
+    legsC = [leg_map(legsA[i]) for i in freeA] + [leg_map(legsB[i]) for i in freeB]
+    got = O.to_dense(C, legsC)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    # every C block conserves charge n_A + n_B
+    C.validate()
+    assert C.n == tuple((a + b) % m if m else a + b for a, b, m in zip(A["n"], B["n"], mods))
+
+
+def test_trivial_symmetry_is_dense_tensordot():
+    """All charges zero: one block per tensor, the result is numpy.tensordot itself."""
+    rng = np.random.default_rng(7)
+    legs = [W.Leg(1, [(0,)], [d]) for d in (3, 4, 5)]
+    legsB = [W.Leg(-1, [(0,)], [5]), W.Leg(1, [(0,)], [2])]
+    A = O.from_record(W.random_tensor((0,), legs, (0,), 11))
+    B = O.from_record(W.random_tensor((0,), legsB, (0,), 12))
+    C = O.tensordot(A, B, (2,), (0,))
+    assert list(C.blocks) == [((0,), (0,), (0,))]
+    want = np.tensordot(A.blocks[((0,), (0,), (0,))], B.blocks[((0,), (0,))], axes=((2,), (0,)))
+    np.testing.assert_array_equal(C.blocks[((0,), (0,), (0,))], want)
+    del rng
+
+
+def test_full_contraction_is_rank0_dot_product():
+    """Contracting every leg gives a rank-0 tensor holding the dense inner product."""
+    rng = np.random.default_rng(3)
+    legs = random_legs(rng, (0,), 3)
+    A = O.from_record(W.random_tensor((0,), legs, (0,), 21))
+    B = O.from_record(W.random_tensor((0,), [l.conj() for l in legs], (0,), 22))
+    C = O.tensordot(A, B, (0, 1, 2), (0, 1, 2))
+    dA = O.to_dense(A, [leg_map(l) for l in legs])
+    dB = O.to_dense(B, [leg_map(l) for l in legs])
+    if A.blocks:
+        assert C.rank == 0 and list(C.blocks) == [()]
+        assert float(C.blocks[()]) == pytest.approx(float(np.sum(dA * dB)), rel=1e-13)
+
+
+def test_no_matching_pair_gives_empty_result():
+    """Contracted charges present on one side only contribute nothing (not an error)."""
+    la = W.Leg(1, [(0,), (1,)], [2, 2])
+    A = O.from_record(W.random_tensor((0,), [la, W.Leg(-1, [(0,), (1,)], [2, 2])], (0,), 1))
+    lb = W.Leg(1, [(5,)], [3])
+    B = O.from_record(W.random_tensor((0,), [lb, W.Leg(-1, [(5,)], [1])], (0,), 2))
+    assert len(B.blocks) == 1
+    C = O.tensordot(A, B, (1,), (0,))
+    assert C.blocks == {}
+
+
+# ---------------------------------------------------------------- errors (compatibility)
+
+def test_incompatible_legs_raise():
+    l = W.Leg(1, [(0,), (1,)], [2, 3])
+    A = O.from_record(W.random_tensor((0,), [l, l.conj()], (0,), 1))
+    with pytest.raises(O.SignatureError):
+        O.tensordot(A, A, (0,), (0,))
+    lb = W.Leg(-1, [(0,), (1,)], [2, 4])
+    B = O.from_record(W.random_tensor((0,), [lb, W.Leg(1, [(0,), (1,)], [2, 4])], (0,), 2))
+    with pytest.raises(O.DimMismatchError):
+        O.tensordot(A, B, (1,), (1,))
+    F = O.fuse(A, ((0, 1),))
+    with pytest.raises(O.FusionMismatchError):
+        O.tensordot(F, O.from_record(W.random_tensor((0,), [W.Leg(-1, [(0,)], [13])], (0,), 3)), (0,), (0,))
+    with pytest.raises(O.InvalidError):
+        O.tensordot(A, A, (0, 0), (1, 1))
+
+
+def test_charge_conservation_is_checked():
+    rec = W.random_tensor((0,), [W.Leg(1, [(0,), (1,)], [1, 1]), W.Leg(-1, [(0,), (1,)], [1, 1])], (0,), 5)
+    rec = dict(rec)
+    rec["t"] = rec["t"].copy()
+    rec["t"][0, 0, 0] = 7
+    with pytest.raises(O.ChargeError):
+        O.from_record(rec)
+
+
+# ---------------------------------------------------------------- fusion
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(6))
+def test_fuse_unfuse_roundtrip_and_sizes(sym, case):
+    """unfuse(fuse(T)) == T for fully populated T; sum_nu D_nu <= prod D with equality
+    when every charge combination occurs (Sec. II.B, fused dimension)."""
+    mods = SYMS[sym]
+    rng = np.random.default_rng(77 + case)
+    rank = int(rng.integers(2, 6))
+    legs = random_legs(rng, mods, rank)
+    T = O.from_record(W.random_tensor(mods, legs, tuple([0] * len(mods)), 100 + case))
+    if not T.blocks:
+        return
+    perm = [int(a) for a in rng.permutation(rank)]
+    cut = int(rng.integers(1, rank))
+    groups = (tuple(perm[:cut]), tuple(perm[cut:]))
+    F = O.fuse(T, groups)
+    F.validate()
+    assert sum(b.size for b in F.blocks.values()) >= sum(b.size for b in T.blocks.values())
+    for gi, g in enumerate(groups):
+        if len(g) > 1:
+            dsum = sum(O.leg_sectors(F, gi).values())
+            assert dsum <= int(np.prod([legs[a].dim for a in g]))
+    U = O.unfuse(F, [i for i, g in enumerate(groups) if len(g) > 1])
+    # unfuse restores the legs in group order: permute T's keys the same way
+    order = [a for g in groups for a in g]
+    want = {tuple(k[a] for a in order): np.transpose(v, order) for k, v in T.blocks.items()}
+    for k, v in want.items():
+        np.testing.assert_array_equal(U.blocks[k], v)
+    # extra blocks of U (zero-filled sub-blocks) must be exactly zero
+    for k in set(U.blocks) - set(want):
+        assert not np.any(U.blocks[k])
+
+
+def test_full_product_leg_dimension_equality():
+    """Every charge combination present: sum_nu D_nu = prod D exactly."""
+    l1 = W.Leg(1, [(-1,), (0,), (1,)], [2, 1, 3])
+    l2 = W.Leg(1, [(0,), (2,)], [2, 2])
+    # a third dummy leg absorbs any total charge, so every (rho1, rho2) pair is stored
+    l3 = W.Leg(-1, [(q,) for q in range(-1, 4)], [1] * 5)
+    T = O.from_record(W.random_tensor((0,), [l1, l2, l3], (0,), 4))
+    F = O.fuse(T, ((0, 1), (2,)))
+    assert sum(O.leg_sectors(F, 0).values()) == l1.dim * l2.dim
+    assert O.leg_sectors(F, 0) == {(-1,): 4, (0,): 2, (1,): 10, (2,): 2, (3,): 6}
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_fused_matrix_has_same_singular_values(case):
+    """Fusion only reorders rows and columns of the matricised dense tensor: the dense
+    embedding of fuse(T, ((0,1),(2,3))) has the singular values of dense(T) reshaped."""
+    rng = np.random.default_rng(500 + case)
+    mods = [(0,), (2,), (0, 0)][case % 3]
+    legs = random_legs(rng, mods, 4)
+    T = O.from_record(W.random_tensor(mods, legs, tuple([0] * len(mods)), 900 + case))
+    if not T.blocks:
+        return
+    dense = O.to_dense(T, [leg_map(l) for l in legs])
+    F = O.fuse(T, ((0, 1), (2, 3)))
+    dF = O.to_dense(F)
+    sv1 = np.linalg.svd(dense.reshape(dense.shape[0] * dense.shape[1], -1), compute_uv=False)
+    sv2 = np.linalg.svd(dF, compute_uv=False)
+    k = min(len(sv1), len(sv2))
+    np.testing.assert_allclose(sv2[:k], sv1[:k], rtol=1e-12, atol=1e-12)
+    assert np.all(np.abs(sv1[k:]) < 1e-12) and np.all(np.abs(sv2[k:]) < 1e-12)
+
+
+def test_fused_charge_rule():
+    """nu = s_r (s_i rho + s_j rho') with s_r the first leg's signature (Sec. II.B)."""
+    l1 = W.Leg(-1, [(0,), (1,), (2,)], [1, 1, 1])
+    l2 = W.Leg(1, [(0,), (3,)], [1, 2])
+    l3 = W.Leg(1, [(q,) for q in range(-6, 7)], [1] * 13)
+    T = O.from_record(W.random_tensor((0,), [l1, l2, l3], (0,), 9))
+    F = O.fuse(T, ((0, 1), (2,)))
+    # s_r = -1: nu = -(-rho + rho') = rho - rho'
+    want = {}
+    for q1, d1 in zip(l1.t, l1.D):
+        for q2, d2 in zip(l2.t, l2.D):
+            nu = (q1[0] - q2[0],)
+            want[nu] = want.get(nu, 0) + d1 * d2
+    assert O.leg_sectors(F, 0) == want
+
+
+def test_fused_contraction_matches_unfused():
+    """Contracting fused legs gives the unfused contraction after unfusing (Sec. II.B)."""
+    rng = np.random.default_rng(42)
+    legs = random_legs(rng, (0,), 4, max_sectors=3, max_dim=3)
+    A = O.from_record(W.random_tensor((0,), legs, (0,), 1))
+    # B's legs (l2*, l3*, l0*, l1*) allow exactly the (rho2, rho3) combinations that A
+    # allows, so the lazy fusion records of the contracted fused legs are conjugate.
+    B = O.from_record(W.random_tensor((0,), [legs[2].conj(), legs[3].conj(), legs[0].conj(), legs[1].conj()], (0,), 2))
+    direct = O.tensordot(A, B, (2, 3), (0, 1))
+    Am = O.fuse(A, ((0, 1), (2, 3)))
+    Bm = O.fuse(B, ((0, 1), (2, 3)))
+    via = O.unfuse(O.tensordot(Am, Bm, (1,), (0,)), (0, 1))
+    dl = [leg_map(legs[0]), leg_map(legs[1]), leg_map(legs[0]), leg_map(legs[1])]
+    np.testing.assert_allclose(O.to_dense(via, dl), O.to_dense(direct, dl), rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- trace
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(5))
+def test_trace_equals_dense_trace(sym, case):
+    mods = SYMS[sym]
+    rng = np.random.default_rng(300 + case)
+    base = random_legs(rng, mods, 2)
+    other = random_legs(rng, mods, int(rng.integers(0, 3)))
+    legs = [base[0], base[1], base[0].conj(), base[1].conj()] + other
+    npair = int(rng.integers(1, 3))
+    ax1, ax2 = (0, 1)[:npair], (2, 3)[:npair]
+    T = O.from_record(W.random_tensor(mods, legs, tuple([0] * len(mods)), 40 + case))
+    R = O.trace(T, ax1, ax2)
+    dense = O.to_dense(T, [leg_map(l) for l in legs])
+    sub = "abcdefgh"[:len(legs)]
+    sub_l = list(sub)
+    for a, b in zip(ax1, ax2):
+        sub_l[b] = sub_l[a]
+    out = "".join(c for i, c in enumerate(sub_l) if i not in ax1 + ax2)
+    want = np.einsum("".join(sub_l) + "->" + out, dense)
+    rest = [i for i in range(len(legs)) if i not in ax1 + ax2]
+    got = O.to_dense(R, [leg_map(legs[i]) for i in rest])
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+def test_trace_signature_rule():
+    l = W.Leg(1, [(0,), (1,)], [2, 2])
+    T = O.from_record(W.random_tensor((0,), [l, l, W.Leg(-1, [(q,) for q in range(3)], [1, 1, 1])], (0,), 3))
+    with pytest.raises(O.SignatureError):
+        O.trace(T, (0,), (1,))
+
+
+def test_fuse_sub_block_order_convention():
+    """Hand-worked fusion with unequal sub-block sizes: fixes the sub-block order
+    (ascending constituent charges) and the row-major placement inside a sector."""
+    g = _golden("fuse_order_example.json")
+    legs = [W.Leg(s, [tuple(q) for q in t], D) for s, t, D in g["legs"]]
+    rec = W.random_tensor((0,), legs, (0,), 0, fill="ones")
+    rec["data"] = np.array(g["data"], dtype=np.float64)
+    T = O.from_record(rec)
+    F = O.fuse(T, ((0, 1), (2,)))
+    want = {tuple(tuple(c) for c in k): np.array(v, dtype=np.float64) for k, v in g["fused_blocks"]}
+    assert sorted(F.blocks) == sorted(want)
+    for k, v in want.items():
+        np.testing.assert_array_equal(F.blocks[k], v)
+
+
+@pytest.mark.parametrize("mods,n,want", [((0,), (1,), (-1,)), ((3,), (1,), (2,)), ((0, 2), (2, 1), (-2, 1))])
+def test_conj_flips_signatures_and_charge(mods, n, want):
+    """Conjugation flips every signature (Sec. II.A footnote); the blocks then conserve
+    -n, so the total charge of the conjugate is -n."""
+    rng = np.random.default_rng(sum(n) + len(mods))
+    legs = random_legs(rng, mods, 3)
+    T = O.from_record(W.random_tensor(mods, legs, n, 8))
+    Tc = O.conj(T)
+    Tc.validate()
+    assert Tc.sig == tuple(-s for s in T.sig)
+    assert Tc.n == want
