@@ -1,0 +1,399 @@
+"""Benchmark: block-sparse tensordot useful TFLOP/s on one GB300 (or N, one process each).
+
+Workload (default): the large U(1)xU(1) Hubbard-like iPEPS environment contraction
+X2 . a over two legs -- bond dimension D = 20 split over 13 charge sectors, chi = D^2 =
+400 over 61 sectors, 103,725 + 103,725 blocks, 225 charge sectors up to 4648^3, 1.86e12
+useful FLOPs per contraction. Synthetic N(0,1) data (seeded), every allowed block
+stored. A step is one full contraction through the C ABI (gather the blocks into sector
+matrices, grouped GEMM over all sectors, scatter into the output blocks), plan cached.
+Inputs (2.7 GB each) are larger than L2, so no flush is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|split]
+python bench.py --impl reference ...   (the CPU oracle, timed on host cores)
+
+Multi-GPU (torchrun, one rank per GPU): every rank contracts its own independent
+problem (its own seed); there is no data-path collective. value = all ranks' useful
+FLOPs / max-over-ranks time ("scaling": "weak").
+"""
+import os
+
+# The oracle's CPU timing runs numpy with one BLAS thread; set before numpy loads.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "block-sparse tensordot useful TFLOP/s, FP64 vs split-precision at ≤1e-10; p50/p99"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# Nominal GB300 dense rates (TFLOP/s) used to scale the measured BF16 peak to other
+# operand types.
+NOMINAL = {"bf16": 2250.0, "fp64": 1.25}
+
+
+def read_traffic(kernel, workload):
+    """DRAM bytes per launch of a kernel, from the committed ncu summary (or None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[1] == workload:
+                try:
+                    return float(parts[2])
+                except ValueError:
+                    return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name, rank):
+    seed_shift = 100 * rank
+    if name == "cfg5":
+        return W.config5(seed=5001 + seed_shift)
+    if name == "cfg5b":
+        return W.config5b(seed=5101 + seed_shift)
+    if name == "cfg3":
+        c = W.config3(seed=3001 + seed_shift)
+        dl = c["dleg"]
+        a = W.random_tensor((0, 0), [W.Leg(-1, dl.t, dl.D), W.Leg(1, dl.t, dl.D), W.Leg(1, dl.t, dl.D),
+                                     W.Leg(-1, dl.t, dl.D)], (0, 0), 3999 + seed_shift)
+        return {"A": c["X2"], "B": a, "axa": (1, 2), "axb": (0, 1), "dleg": dl, "name": c["name"]}
+    raise ValueError(name)
+
+
+WORKLOAD_DESC = {
+    "cfg5": "U(1)xU(1) iPEPS environment contraction X2.a, D=20 (13 sectors), chi=400 (61 sectors)",
+    "cfg5b": "U(1)xU(1) iPEPS environment contraction X2.a, D=20 (9 sectors, 25-sector D^2 legs), chi=400",
+    "cfg3": "U(1)xU(1) CTMRG X2.a, D=12, chi=144",
+}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+def oracle_sample(cfg, budget_s, seed=0):
+    """Time the CPU oracle on a bounded sample of the workload: the contraction restricted
+    to a random subset of the contracted charge tuples x (every block pair of those x).
+    Returns (useful FLOPs, seconds, description)."""
+    import oracle as O
+    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
+    ta, tb = A["t"], B["t"]
+    xa = [tuple(map(tuple, ta[b, list(axa)])) for b in range(ta.shape[0])]
+    xb = [tuple(map(tuple, tb[b, list(axb)])) for b in range(tb.shape[0])]
+    xs = sorted(set(xa) & set(xb))
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(xs))
+    offa = W.block_offsets(A["D"])
+    offb = W.block_offsets(B["D"])
+    sza = np.prod(A["D"], axis=1)
+    szb = np.prod(B["D"], axis=1)
+    byxa, byxb = {}, {}
+    for b, x in enumerate(xa):
+        byxa.setdefault(x, []).append(b)
+    for b, x in enumerate(xb):
+        byxb.setdefault(x, []).append(b)
+
+    def sub(rec, idx, off, sz):
+        idx = sorted(idx)
+        return {"mods": rec["mods"], "sig": rec["sig"], "n": rec["n"], "t": rec["t"][idx], "D": rec["D"][idx],
+                "data": np.concatenate([rec["data"][off[i]:off[i] + sz[i]] for i in idx]) if idx else np.zeros(0)}
+
+    flops, secs, nx, npairs = 0, 0.0, 0, 0
+    chunk = 8
+    i = 0
+    while secs < budget_s and i < len(order):
+        pick = [xs[j] for j in order[i:i + chunk]]
+        i += chunk
+        ia = [b for x in pick for b in byxa[x]]
+        ib = [b for x in pick for b in byxb[x]]
+        sa, sb = sub(A, ia, offa, sza), sub(B, ib, offb, szb)
+        oA, oB = O.from_record(sa), O.from_record(sb)
+        t0 = time.perf_counter()
+        O.tensordot(oA, oB, axa, axb)
+        secs += time.perf_counter() - t0
+        flops += O.useful_flops(oA, oB, axa, axb)
+        nx += len(pick)
+        npairs += sum(len(byxa[x]) * len(byxb[x]) for x in pick)
+    desc = (f"oracle tensordot over {nx} of {len(xs)} contracted charge tuples "
+            f"({npairs} block pairs, {flops:.3e} useful FLOPs), numpy with 1 BLAS thread")
+    return flops, secs, desc
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = make_workload(args.workload, 0)
+    times, flops_all, desc = [], [], ""
+    for step in range(args.warmup + args.steps):
+        f, s, desc = oracle_sample(cfg, args.ref_budget, seed=step)
+        if step >= args.warmup:
+            times.append(s)
+            flops_all.append(f)
+    tflops = sum(flops_all) / sum(times) / 1e12
+    line = {
+        "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_DESC[args.workload]},
+        "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2405_12196_gb300 import ytn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}[args.precision]
+
+    t_gen = time.perf_counter()
+    cfg = make_workload(args.workload, rank)
+    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
+    t_gen = time.perf_counter() - t_gen
+    ctx = ytn.ytn_ctx_create(local)
+    t_plan = time.perf_counter()
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    t_plan = time.perf_counter() - t_plan
+    t_plan_cached = time.perf_counter()
+    plan2 = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    t_plan_cached = time.perf_counter() - t_plan_cached
+    assert plan2.handle == plan.handle
+    flops = plan.info["useful_flops"]
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        da = torch.from_numpy(A["data"]).to(dev)
+        db = torch.from_numpy(B["data"]).to(dev)
+        dc = torch.empty(plan.out["size"], dtype=torch.float64, device=dev)
+        ws_bytes = ytn.ytn_workspace_size(plan, prec, args.rtol)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream.synchronize()
+
+    def step():
+        return ytn.ytn_tensordot(plan, da, db, dc, prec=prec, rtol=args.rtol, workspace=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        res = step()
+    stream.synchronize()
+
+    # ---- timed region: K device-resident steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ytn.ytn_profile_enable(ctx, True)
+    ytn.ytn_profile_read(ctx)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        res = step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = ytn.ytn_profile_read(ctx)
+    ytn.ytn_profile_enable(ctx, False)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * flops * args.steps / (total_ms * 1e-3) / 1e12
+
+    # ---- end to end through the C ABI: pinned host inputs in, result out, every step
+    ha = torch.from_numpy(A["data"]).pin_memory()
+    hb = torch.from_numpy(B["data"]).pin_memory()
+    hc = torch.empty(plan.out["size"], dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            da.copy_(ha, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+            step()
+            hc.copy_(dc, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * flops * e2e_steps / (float(te.item()) * 1e-3) / 1e12
+
+    # ---- roofline of the dominant kernel (the grouped GEMM), timed live on its stream
+    peaks, peak_src = load_peaks()
+    gemm_calls, gemm_ms = prof.get("gemm", (0, 0.0))
+    kernel_ms = gemm_ms / max(1, gemm_calls)
+    if prec == ytn.YTN_FP64:
+        kernel = "gemm_fp64_kernel"
+        peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+        peak_note = (f"{peak_src} dense BF16 burst ({peaks['bf16_tflops']} TFLOP/s) x nominal FP64/BF16 "
+                     f"ratio {NOMINAL['fp64']}/{NOMINAL['bf16']}")
+        dtype = "f64"
+    else:
+        kernel = "gemm_split_kernel"
+        peak = peaks["bf16_tflops"]
+        peak_note = f"{peak_src} dense BF16 burst"
+        dtype = "bf16-slices/f32-acc/f64-recombine"
+    slices = res.get("slices", 0) if isinstance(res, dict) else 0
+    # algorithmic work of the dominant kernel per launch: useful FLOPs (FP64 path) or
+    # the BF16 slice-product FLOPs (split path: s(s+1)/2 slice products per useful FLOP)
+    kernel_flops = flops if prec == ytn.YTN_FP64 else flops * slices * (slices + 1) / 2
+    achieved = kernel_flops / (kernel_ms * 1e-3) / 1e12 if kernel_ms > 0 else None
+    traffic = read_traffic(kernel, args.workload)
+    roofline = {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_source": peak_note}
+    phases = {k: {"calls": v[0], "ms_per_call": v[1] / max(1, v[0])} for k, v in prof.items() if k != "dropped"}
+    moved_bytes = 16.0 * plan.info["moved_elems"]
+    mover_ms = sum(phases[k]["ms_per_call"] for k in ("gather_a", "gather_b", "scatter") if k in phases)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "precision": args.precision,
+        "config": {"workload": WORKLOAD_DESC[args.workload], "useful_flops_per_step": flops,
+                   "blocks": [int(A["t"].shape[0]), int(B["t"].shape[0]), int(plan.out["t"].shape[0])],
+                   "sectors": plan.info["nsectors"], "max_mnk": [plan.info["max_m"], plan.info["max_n"],
+                                                                 plan.info["max_k"]],
+                   "l2": "inputs larger than L2 (no flush)", "rtol": args.rtol if prec != ytn.YTN_FP64 else None},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "steps": e2e_steps,
+                "h2d_bytes_per_step": int(8 * (A["data"].size + B["data"].size)),
+                "d2h_bytes_per_step": int(8 * plan.out["size"])},
+        "gpu_launches": int(sum(v[0] for k, v in prof.items() if k != "dropped")),
+        "roofline": roofline,
+        "phases_ms": phases,
+        "data_movers": {"bytes_per_step": moved_bytes, "ms_per_step": mover_ms,
+                        "GB_per_s": moved_bytes / (mover_ms * 1e-3) / 1e9 if mover_ms else None,
+                        "peak_GB_per_s": peaks["hbm_gbs"]},
+        "host": {"generate_s": t_gen, "plan_s": t_plan, "plan_cached_s": t_plan_cached},
+    }
+    if prec != ytn.YTN_FP64:
+        line["split"] = {"slices": slices, "err_bound": res.get("err_bound")}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        f, s, desc = oracle_sample(cfg, args.cpu_budget)
+        line["cpu_baseline"] = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                                "sample": desc}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--workload", default="cfg5", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

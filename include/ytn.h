@@ -1,0 +1,261 @@
+/*
+ * ytn.h -- C ABI of a single-GPU (GB300, sm_103a) library that contracts
+ * abelian-symmetric block-sparse tensors.
+ *
+ * The operations follow "YASTN: Yet another symmetric tensor networks"
+ * (arXiv 2405.12196):
+ *   - Sec. II.A: a leg V(s, t, D) has a signature s = +-1, charge sectors t and
+ *     their dimensions D; a rank-N tensor stores dense blocks keyed by one
+ *     sector per leg, and a stored block (rho_1..rho_N) satisfies
+ *     sum_i s_i rho_i = n (block form of Eq. elemchargecon). Charges of U(1) are
+ *     integers, of Z_m integers modulo m, of product groups tuples of these.
+ *   - Sec. II.A (storage): blocks are serialised into one 1-D array.
+ *   - Sec. II.B: fusion of legs (fused charge nu = s_r (s_i rho + s_j rho'),
+ *     fused dimension D_nu = sum D_rho D_rho'), its inverse (unfusion, from the
+ *     recorded original structure), and contraction = fuse into matrices,
+ *     multiply per charge sector, unfuse (the contraction equation), with the
+ *     non-zero blocks precomputed before any dense work.
+ *
+ * Model of use: describe the tensors' block structure on the host (ytn_struct),
+ * call ytn_plan once per structure (pure host integer work plus one upload of
+ * job tables to the device; cached), then run the plan on device data as often
+ * as needed (ytn_tensordot / ytn_fuse / ytn_unfuse / ytn_trace). Execution
+ * calls are asynchronous on the given stream and allocate nothing.
+ *
+ * Conventions for every tensor in this API
+ *   - data are FP64, one device buffer per tensor; block b occupies
+ *     [off[b], off[b] + prod_i D[b][i]) of it, row-major (C order);
+ *   - blocks are listed in canonical order: strictly ascending lexicographic
+ *     order of the flattened (rank x nsym) charge tuple;
+ *   - Z_m charge components are given reduced, in [0, m).
+ *
+ * Ownership
+ *   - every host array passed in (ytn_struct, ytn_fusion) belongs to the
+ *     caller and is read only during the call; the plan keeps its own copies;
+ *   - plans and the output structure they describe belong to the library
+ *     (release with ytn_plan_release);
+ *   - device buffers (inputs, outputs, workspace) belong to the caller.
+ *
+ * Errors: every call returns a ytn_status; nothing is thrown across the ABI.
+ * Structural errors are found by ytn_plan, before any device work. A short
+ * message for the last error of the calling thread is in ytn_last_error().
+ */
+#ifndef YTN_H
+#define YTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define YTN_MAX_RANK 16
+#define YTN_MAX_SYM 4
+
+typedef enum {
+  YTN_OK = 0,
+  YTN_E_INVALID = 1,          /* malformed descriptor, axes, order or sizes      */
+  YTN_E_SIGNATURE = 2,        /* contracted/traced legs with equal signatures    */
+  YTN_E_DIM_MISMATCH = 3,     /* one charge with two dimensions on paired legs   */
+  YTN_E_FUSION_MISMATCH = 4,  /* contracted fused legs with different histories  */
+  YTN_E_NOMEM = 5,            /* host or device allocation failed                */
+  YTN_E_CUDA = 6,             /* a CUDA runtime call failed                      */
+  YTN_E_TIMEOUT = 7,          /* a bounded device wait ran out                   */
+  YTN_E_UNSUPPORTED = 8,      /* valid request outside what this build handles   */
+  YTN_E_TOLERANCE = 9,        /* requested accuracy cannot be guaranteed         */
+  YTN_E_CHARGE = 10,          /* a block violates charge conservation            */
+  YTN_E_WORKSPACE = 11        /* workspace missing or too small                  */
+} ytn_status;
+
+typedef enum {
+  YTN_FP64 = 0,        /* FP64 operands, FP64 tensor-core (DMMA) products        */
+  YTN_SPLIT_BF16 = 1   /* FP64 operands split into BF16 slices, tcgen05 products  *
+                        * with exact FP32 accumulation, recombined to FP64        */
+} ytn_precision;
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *ytn_stream;
+
+typedef struct ytn_ctx ytn_ctx;
+typedef struct ytn_plan_s ytn_plan_t;
+
+/* Abelian group: nsym components; mod[c] == 0 is U(1), mod[c] == m > 1 is Z_m. */
+typedef struct {
+  int32_t nsym;
+  int32_t mod[YTN_MAX_SYM];
+} ytn_sym;
+
+/* What a fused leg remembers of its origin (Sec. II.B: "records the original
+ * structure"). For each fused charge nu, in ascending order of nu, the
+ * constituent charge tuples present in the tensor in ascending order, each
+ * with its constituent dimensions; sub-block e of sector nu occupies
+ * prod_i D[e][i] consecutive indices of the fused sector, row-major over the
+ * constituent legs, after the sub-blocks listed before it. */
+typedef struct {
+  int32_t nlegs;              /* m: constituent legs (2..YTN_MAX_RANK)        */
+  int8_t sig[YTN_MAX_RANK];   /* constituent signatures                       */
+  int64_t nentries;           /* rows of the record                           */
+  const int32_t *nu;          /* [nentries][nsym] fused charge of each row    */
+  const int32_t *t;           /* [nentries][nlegs][nsym] constituent charges  */
+  const int64_t *D;           /* [nentries][nlegs] constituent dimensions     */
+} ytn_fusion;
+
+/* Block structure of one tensor (host memory, caller-owned). */
+typedef struct {
+  ytn_sym sym;
+  int32_t rank;               /* 0..YTN_MAX_RANK                              */
+  int8_t sig[YTN_MAX_RANK];   /* leg signatures, +1 or -1                     */
+  int32_t n[YTN_MAX_SYM];     /* total charge                                 */
+  int64_t nblocks;
+  const int32_t *t;           /* [nblocks][rank][nsym] block charges          */
+  const int64_t *D;           /* [nblocks][rank] block dimensions (>= 1)      */
+  const int64_t *off;         /* [nblocks] element offsets into the data
+                                 buffer; NULL means packed in block order     */
+  int64_t size;               /* elements in the data buffer                  */
+  const ytn_fusion *fus[YTN_MAX_RANK]; /* per leg; NULL for a plain leg       */
+} ytn_struct;
+
+typedef enum {
+  YTN_OP_TENSORDOT = 1,  /* C = sum_x A B over pairs (axa[k], axb[k]), Sec. II.B */
+  YTN_OP_FUSE = 2,       /* fuse groups of legs, Sec. II.B                        */
+  YTN_OP_UNFUSE = 3,     /* undo the fusion of legs axa[0..naxes), Sec. II.B      */
+  YTN_OP_TRACE = 4       /* sum the diagonals of leg pairs (axa[k], axb[k]) of a  */
+} ytn_op_kind;
+
+/* A planned operation.
+ *  TENSORDOT: a, b, naxes pairs (axa[k] of a, axb[k] of b). Output legs: the
+ *             free legs of a in order, then those of b; n_C = n_A + n_B.
+ *  FUSE:      a, ngroups groups; order[] lists the legs group by group
+ *             (group g has group_size[g] legs); every leg exactly once. A
+ *             group of one leg passes through; a group of >= 2 legs must
+ *             consist of plain legs. The fused leg takes the signature of its
+ *             group's first leg.
+ *  UNFUSE:    a, naxes fused legs axa[]; each is replaced by its constituents.
+ *  TRACE:     a, naxes pairs (axa[k], axb[k]) of legs of a, with opposite
+ *             signatures (the paper has no trace; this is the block-diagonal
+ *             sum that the block structure implies). */
+typedef struct {
+  ytn_op_kind kind;
+  const ytn_struct *a;
+  const ytn_struct *b;
+  int32_t naxes;
+  int32_t axa[YTN_MAX_RANK];
+  int32_t axb[YTN_MAX_RANK];
+  int32_t ngroups;
+  int32_t group_size[YTN_MAX_RANK];
+  int32_t order[YTN_MAX_RANK];
+} ytn_op;
+
+/* Sizes of a plan. */
+typedef struct {
+  double useful_flops;       /* sum over matching block pairs of 2|I||x||J|     */
+  int64_t nsectors;          /* charge sectors with at least one product        */
+  int64_t max_m, max_n, max_k;
+  int64_t a_elems, b_elems, c_elems; /* elements of the sector matrices        */
+  int64_t moved_elems;       /* elements read (= written) by the data movers    */
+  int64_t out_size;          /* elements of the output data buffer              */
+  int64_t njobs;             /* copy jobs of all data movers                    */
+} ytn_plan_info;
+
+/* Per-call result of ytn_tensordot. */
+typedef struct {
+  double useful_flops;
+  int32_t precision;         /* ytn_precision used                              */
+  int32_t slices;            /* split path: BF16 slices per operand, else 0     */
+  double err_bound;          /* split path: a-priori bound on the relative
+                                Frobenius error of the result; 0 for FP64     */
+} ytn_result;
+
+/* Context bound to one CUDA device; allocates a device status word.
+ * device < 0 creates a host-only context: ytn_plan then builds plans (output
+ * structure, sizes, job tables) without uploading them, and the execution
+ * calls on such plans return YTN_E_INVALID. */
+ytn_status ytn_ctx_create(ytn_ctx **ctx, int device);
+void ytn_ctx_destroy(ytn_ctx *ctx);
+
+/* Plan an operation: validates the structures (conservation, canonical order,
+ * one dimension per charge and leg, compatibility of paired legs), matches
+ * blocks by charge, groups them into sectors, builds the output structure and
+ * the job tables, and uploads the tables to the context's device (synchronous
+ * cudaMalloc + copy). Plans are cached by the full integer structure and the
+ * operation: an identical request returns the cached plan with one more
+ * reference. Errors: YTN_E_INVALID, YTN_E_CHARGE, YTN_E_SIGNATURE,
+ * YTN_E_DIM_MISMATCH, YTN_E_FUSION_MISMATCH, YTN_E_UNSUPPORTED, YTN_E_NOMEM,
+ * YTN_E_CUDA. */
+ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan);
+
+/* Output structure of a plan (library-owned, valid until the plan is released). */
+const ytn_struct *ytn_plan_output(const ytn_plan_t *plan);
+ytn_status ytn_plan_get_info(const ytn_plan_t *plan, ytn_plan_info *info);
+void ytn_plan_release(ytn_plan_t *plan);
+
+/* Device workspace (bytes) a ytn_tensordot call needs for this precision and
+ * tolerance; 0 for the other operations. */
+ytn_status ytn_workspace_size(const ytn_plan_t *plan, ytn_precision prec, double rtol,
+                              size_t *bytes);
+
+/* C = tensordot(A, B) (Sec. II.B contraction equation): gather the blocks of A
+ * and B into one matrix per charge sector, multiply the sectors in one grouped
+ * launch, scatter the products into the blocks of C. a, b, c: device buffers
+ * of sizes a->size, b->size and ytn_plan_output(plan)->size; every element of
+ * c is written. prec/rtol select the product precision (rtol is the target
+ * relative Frobenius error of the split path, ignored for FP64).
+ * workspace: device buffer of at least ytn_workspace_size bytes, 256-byte
+ * aligned. res (optional, host): filled before return. Asynchronous on stream.
+ * Errors: YTN_E_INVALID (wrong plan kind), YTN_E_WORKSPACE, YTN_E_TOLERANCE
+ * (rtol below what the split path can guarantee), YTN_E_CUDA (launch). */
+ytn_status ytn_tensordot(ytn_plan_t *plan, const double *a, const double *b, double *c,
+                         ytn_precision prec, double rtol, void *workspace,
+                         size_t workspace_bytes, ytn_result *res, ytn_stream stream);
+
+/* out = fuse(a) / unfuse(a) (Sec. II.B). a: device buffer of the planned
+ * input's size; out: device buffer of ytn_plan_output(plan)->size elements,
+ * every element written (fused entries with no stored block are zero).
+ * Asynchronous on stream. Errors: YTN_E_INVALID (wrong plan kind), YTN_E_CUDA. */
+ytn_status ytn_fuse(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
+ytn_status ytn_unfuse(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
+
+/* out = trace of a over the planned leg pairs. Same buffer rules as ytn_fuse. */
+ytn_status ytn_trace(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
+
+/* Wait for the stream (at most timeout_ms; < 0 waits without limit) and report
+ * the context's device status word: YTN_E_TIMEOUT if a bounded device wait
+ * ran out since the last call (the word is then cleared), YTN_E_CUDA if the
+ * stream reported an error. */
+ytn_status ytn_sync(ytn_ctx *ctx, ytn_stream stream, int64_t timeout_ms);
+
+/* Phase timing. While enabled on a context, every execution call on its plans
+ * records a CUDA event pair on the call's stream around each kernel phase
+ * (events come from a pool created by ytn_profile_enable; when the pool is
+ * used up, further phases are counted in `dropped` and not timed).
+ * ytn_profile_read waits for the recorded events, adds their durations per
+ * phase into *out and clears the record. Phases: */
+enum {
+  YTN_PHASE_GATHER_A = 0,   /* blocks of A -> sector matrices                 */
+  YTN_PHASE_GATHER_B = 1,   /* blocks of B -> sector matrices                 */
+  YTN_PHASE_GEMM = 2,       /* grouped GEMM (FP64 or split-precision)         */
+  YTN_PHASE_SCATTER = 3,    /* sector matrices -> blocks of C                 */
+  YTN_PHASE_SPLIT = 4,      /* FP64 -> BF16 slices (split path)               */
+  YTN_PHASE_MOVE = 5,       /* fuse / unfuse / trace                          */
+  YTN_NPHASES = 8
+};
+typedef struct {
+  int64_t calls[YTN_NPHASES];
+  double ms[YTN_NPHASES];
+  int64_t dropped;
+} ytn_profile;
+ytn_status ytn_profile_enable(ytn_ctx *ctx, int enable);
+ytn_status ytn_profile_read(ytn_ctx *ctx, ytn_profile *out);
+
+/* Message of the last failed call on this thread (empty if none). */
+const char *ytn_last_error(void);
+
+/* Library version string. */
+const char *ytn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* YTN_H */

@@ -179,7 +179,7 @@ def leg_sectors(T, axis):
 def from_record(rec):
     """Build an OTensor from the plain-array record of ``workloads`` (canonical order,
     packed row-major blocks); ``rec['fus']`` (optional) holds per-leg fusion records in
-    plain-array form."""
+    plain-array form. Blocks are views of ``rec['data']``."""
     mods = tuple(rec["mods"])
     t = np.asarray(rec["t"])
     D = np.asarray(rec["D"])
@@ -192,7 +192,7 @@ def from_record(rec):
         sz = int(np.prod(shape))
         if key in blocks:
             raise InvalidError("duplicate block")
-        blocks[key] = data[off:off + sz].reshape(shape).copy()
+        blocks[key] = data[off:off + sz].reshape(shape)  # a view: inputs are never modified
         off += sz
     if off != data.size:
         raise InvalidError("data size does not match the block dimensions")
@@ -319,16 +319,18 @@ def tensordot_block(A, B, axa, axb, kc):
     freeA = [i for i in range(A.rank) if i not in axa]
     freeB = [i for i in range(B.rank) if i not in axb]
     ia, ib = kc[:len(freeA)], kc[len(freeA):]
+    rowsA = [ka for ka in A.keys() if tuple(ka[i] for i in freeA) == ia]
+    colsB = {}
+    for kb in B.keys():
+        if tuple(kb[i] for i in freeB) == ib:
+            colsB[tuple(kb[b] for b in axb)] = kb
     out = None
-    for ka in A.keys():
-        if tuple(ka[i] for i in freeA) != ia:
+    for ka in rowsA:
+        kb = colsB.get(tuple(ka[a] for a in axa))
+        if kb is None:
             continue
-        x = tuple(ka[a] for a in axa)
-        for kb in B.keys():
-            if tuple(kb[i] for i in freeB) != ib or tuple(kb[b] for b in axb) != x:
-                continue
-            prod = np.tensordot(A.blocks[ka], B.blocks[kb], axes=(axa, axb))
-            out = prod if out is None else out + prod
+        prod = np.tensordot(A.blocks[ka], B.blocks[kb], axes=(axa, axb))
+        out = prod if out is None else out + prod
     return out
 
 

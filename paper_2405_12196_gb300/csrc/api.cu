@@ -1,0 +1,479 @@
+// C ABI of the library (include/ytn.h): contexts, planning with a plan cache,
+// upload of the job tables, and the execution entry points that launch the
+// device kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "kernels.hpp"
+
+namespace ytn {
+
+static thread_local std::string g_last_error;
+
+ytn_status fail(ytn_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+static ytn_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(YTN_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Makes ctx->device current for the scope of an entry point and restores the
+// caller's device afterwards.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    ok_ = cudaGetDevice(&prev_) == cudaSuccess;
+    if (ok_ && prev_ != dev) ok_ = cudaSetDevice(dev) == cudaSuccess, changed_ = true;
+  }
+  ~DeviceGuard() {
+    if (changed_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = 0;
+  bool ok_ = false, changed_ = false;
+};
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+template <class T>
+static void put_table(std::vector<char> &buf, const std::vector<T> &v, size_t &off) {
+  off = align256(buf.size());
+  buf.resize(off + v.size() * sizeof(T));
+  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+}
+
+static ytn_status upload(ytn_plan_t *p) {
+  std::vector<char> buf;
+  size_t o_jobs, o_items, o_sec, o_tiles, o_tro, o_trc;
+  put_table(buf, p->jobs, o_jobs);
+  put_table(buf, p->items, o_items);
+  put_table(buf, p->sectors_dev, o_sec);
+  put_table(buf, p->tiles, o_tiles);
+  put_table(buf, p->tr_out, o_tro);
+  put_table(buf, p->tr_contrib, o_trc);
+  p->dev_bytes = align256(buf.size()) + 256;
+  cudaError_t e = cudaMalloc(&p->dev, p->dev_bytes);
+  if (e != cudaSuccess) {
+    p->dev = nullptr;
+    return e == cudaErrorMemoryAllocation ? fail(YTN_E_NOMEM, "cudaMalloc of plan tables failed")
+                                          : cuda_fail(e, "cudaMalloc");
+  }
+  if (!buf.empty()) {
+    e = cudaMemcpy(p->dev, buf.data(), buf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy of plan tables");
+  }
+  char *d = static_cast<char *>(p->dev);
+  p->d_jobs = reinterpret_cast<const CopyJob *>(d + o_jobs);
+  p->d_items = reinterpret_cast<const CopyItem *>(d + o_items);
+  p->d_sectors = reinterpret_cast<const SectorDev *>(d + o_sec);
+  p->d_tiles = reinterpret_cast<const GemmTile *>(d + o_tiles);
+  p->d_tr_out = reinterpret_cast<const TraceOut *>(d + o_tro);
+  p->d_tr_contrib = reinterpret_cast<const TraceContrib *>(d + o_trc);
+  return YTN_OK;
+}
+
+static void destroy_plan(ytn_plan_t *p) {
+  if (!p) return;
+  if (p->dev) {
+    DeviceGuard g(p->ctx->device);
+    cudaFree(p->dev);
+  }
+  delete p;
+}
+
+// Records a CUDA event pair around one kernel phase when profiling is on.
+class PhaseTimer {
+ public:
+  PhaseTimer(ytn_ctx *ctx, int phase, cudaStream_t st) : ctx_(ctx), st_(st) {
+    if (!ctx_->prof) return;
+    std::lock_guard<std::mutex> lk(ctx_->prof_mu);
+    if (ctx_->ev_next + 2 > ctx_->ev_pool.size()) {
+      ctx_->dropped++;
+      return;
+    }
+    idx_ = (int)ctx_->ev_next;
+    ctx_->ev_next += 2;
+    ctx_->pending.push_back({phase, idx_});
+    cudaEventRecord(static_cast<cudaEvent_t>(ctx_->ev_pool[idx_]), st_);
+  }
+  ~PhaseTimer() {
+    if (idx_ >= 0) cudaEventRecord(static_cast<cudaEvent_t>(ctx_->ev_pool[idx_ + 1]), st_);
+  }
+
+ private:
+  ytn_ctx *ctx_;
+  cudaStream_t st_;
+  int idx_ = -1;
+};
+
+// FP64 workspace: WA | WB | WC, each 256-byte aligned.
+static size_t fp64_workspace(const ytn_plan_t *p, size_t &ob, size_t &oc) {
+  ob = align256((size_t)p->a_elems * 8);
+  oc = ob + align256((size_t)p->b_elems * 8);
+  return oc + align256((size_t)p->c_elems * 8);
+}
+
+}  // namespace ytn
+
+using namespace ytn;
+
+extern "C" {
+
+const char *ytn_version(void) { return "ytn 0.1 (sm_103a)"; }
+
+const char *ytn_last_error(void) { return g_last_error.c_str(); }
+
+ytn_status ytn_ctx_create(ytn_ctx **ctx, int device) {
+  if (!ctx) return fail(YTN_E_INVALID, "null ctx pointer");
+  *ctx = nullptr;
+  if (device < 0) {  // host-only context: plans without device tables
+    ytn_ctx *c = new (std::nothrow) ytn_ctx;
+    if (!c) return fail(YTN_E_NOMEM, "host allocation failed");
+    c->device = -1;
+    *ctx = c;
+    return YTN_OK;
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(YTN_E_INVALID, "device out of range");
+  ytn_ctx *c = new (std::nothrow) ytn_ctx;
+  if (!c) return fail(YTN_E_NOMEM, "host allocation failed");
+  c->device = device;
+  DeviceGuard g(device);
+  if (!g.ok()) {
+    delete c;
+    return fail(YTN_E_CUDA, "cannot select device");
+  }
+  e = cudaMalloc(&c->status_dev, sizeof(int) * 4);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaMalloc status word");
+  }
+  e = cudaMemset(c->status_dev, 0, sizeof(int) * 4);
+  if (e != cudaSuccess) {
+    cudaFree(c->status_dev);
+    delete c;
+    return cuda_fail(e, "cudaMemset status word");
+  }
+  *ctx = c;
+  return YTN_OK;
+}
+
+void ytn_ctx_destroy(ytn_ctx *ctx) {
+  if (!ctx) return;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto &kv : ctx->cache) {
+      ytn_plan_t *p = kv.second;
+      if (--p->refs == 0) destroy_plan(p);
+    }
+    ctx->cache.clear();
+  }
+  if (ctx->device >= 0) {
+    DeviceGuard g(ctx->device);
+    for (void *ev : ctx->ev_pool) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
+    if (ctx->status_dev) cudaFree(ctx->status_dev);
+  }
+  delete ctx;
+}
+
+ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
+  if (!ctx || !op || !plan) return fail(YTN_E_INVALID, "null argument");
+  *plan = nullptr;
+  std::string key;
+  try {
+    key = plan_key(op);
+  } catch (...) {
+    return fail(YTN_E_NOMEM, "host allocation failed");
+  }
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->cache.find(key);
+    if (it != ctx->cache.end()) {
+      it->second->refs++;
+      *plan = it->second;
+      return YTN_OK;
+    }
+  }
+  ytn_plan_t *p = new (std::nothrow) ytn_plan_t;
+  if (!p) return fail(YTN_E_NOMEM, "host allocation failed");
+  p->ctx = ctx;
+  p->key = key;
+  std::string err;
+  ytn_status st = YTN_OK;
+  try {
+    Tensor A, B;
+    st = load_struct(op->a, A, err);
+    if (st == YTN_OK) {
+      switch (op->kind) {
+        case YTN_OP_TENSORDOT:
+          st = load_struct(op->b, B, err);
+          if (st == YTN_OK) st = plan_tensordot(p, A, B, op->naxes, op->axa, op->axb, err);
+          break;
+        case YTN_OP_FUSE:
+          st = plan_fuse(p, A, op->ngroups, op->group_size, op->order, err);
+          break;
+        case YTN_OP_UNFUSE:
+          if (op->naxes < 1 || op->naxes > YTN_MAX_RANK) {
+            st = YTN_E_INVALID;
+            err = "naxes out of range";
+          } else {
+            st = plan_unfuse(p, A, op->naxes, op->axa, err);
+          }
+          break;
+        case YTN_OP_TRACE:
+          if (op->naxes < 1 || op->naxes > YTN_MAX_RANK) {
+            st = YTN_E_INVALID;
+            err = "naxes out of range";
+          } else {
+            st = plan_trace(p, A, op->naxes, op->axa, op->axb, err);
+          }
+          break;
+        default:
+          st = YTN_E_INVALID;
+          err = "unknown operation";
+      }
+    }
+    if (st == YTN_OK) finish_output_view(p);
+  } catch (const std::bad_alloc &) {
+    st = YTN_E_NOMEM;
+    err = "host allocation failed";
+  }
+  if (st != YTN_OK) {
+    delete p;
+    return fail(st, err);
+  }
+  if (ctx->device >= 0) {
+    DeviceGuard g(ctx->device);
+    if (!g.ok()) {
+      delete p;
+      return fail(YTN_E_CUDA, "cannot select device");
+    }
+    st = upload(p);
+  }
+  if (st != YTN_OK) {
+    destroy_plan(p);
+    return st;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->cache.find(key);
+  if (it != ctx->cache.end()) {  // planned concurrently by another thread
+    destroy_plan(p);
+    it->second->refs++;
+    *plan = it->second;
+    return YTN_OK;
+  }
+  p->refs = 2;  // the caller's reference and the cache's
+  ctx->cache[key] = p;
+  *plan = p;
+  return YTN_OK;
+}
+
+const ytn_struct *ytn_plan_output(const ytn_plan_t *plan) { return plan ? &plan->out_view : nullptr; }
+
+ytn_status ytn_plan_get_info(const ytn_plan_t *p, ytn_plan_info *info) {
+  if (!p || !info) return fail(YTN_E_INVALID, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->useful_flops = p->flops;
+  info->nsectors = (int64_t)p->sectors.size();
+  info->max_m = p->max_m;
+  info->max_n = p->max_n;
+  info->max_k = p->max_k;
+  info->a_elems = p->a_elems;
+  info->b_elems = p->b_elems;
+  info->c_elems = p->c_elems;
+  info->moved_elems = p->moved;
+  info->out_size = p->out.size;
+  info->njobs = (int64_t)p->jobs.size();
+  return YTN_OK;
+}
+
+void ytn_plan_release(ytn_plan_t *plan) {
+  if (!plan) return;
+  ytn_ctx *ctx = plan->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (--plan->refs == 0) destroy_plan(plan);
+}
+
+ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rtol, size_t *bytes) {
+  if (!p || !bytes) return fail(YTN_E_INVALID, "null argument");
+  *bytes = 0;
+  if (p->kind != Kind::Tensordot) return YTN_OK;
+  size_t ob, oc;
+  if (prec == YTN_FP64) {
+    *bytes = fp64_workspace(p, ob, oc);
+    return YTN_OK;
+  }
+  (void)rtol;
+  return fail(YTN_E_UNSUPPORTED, "precision not available in this build");
+}
+
+ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, ytn_precision prec,
+                         double rtol, void *workspace, size_t workspace_bytes, ytn_result *res,
+                         ytn_stream stream) {
+  if (!p) return fail(YTN_E_INVALID, "null plan");
+  if (p->kind != Kind::Tensordot) return fail(YTN_E_INVALID, "plan is not a tensordot plan");
+  if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
+  if ((p->a_size && !a) || (p->b_size && !b) || (p->out.size && !c))
+    return fail(YTN_E_INVALID, "null data buffer");
+  if (prec != YTN_FP64) return fail(YTN_E_UNSUPPORTED, "precision not available in this build");
+  (void)rtol;
+  size_t ob, oc;
+  const size_t need = fp64_workspace(p, ob, oc);
+  if (need && (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)))
+    return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
+  DeviceGuard g(p->ctx->device);
+  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char *ws = static_cast<char *>(workspace);
+  double *wa = reinterpret_cast<double *>(ws), *wb = reinterpret_cast<double *>(ws + ob),
+         *wc = reinterpret_cast<double *>(ws + oc);
+  cudaError_t e;
+  if (p->zero_a && (e = cudaMemsetAsync(wa, 0, (size_t)p->a_elems * 8, st)) != cudaSuccess)
+    return cuda_fail(e, "memset A workspace");
+  if (p->zero_b && (e = cudaMemsetAsync(wb, 0, (size_t)p->b_elems * 8, st)) != cudaSuccess)
+    return cuda_fail(e, "memset B workspace");
+  {
+    PhaseTimer t(p->ctx, YTN_PHASE_GATHER_A, st);
+    e = launch_copy(p->d_jobs, p->d_items + p->items_a_begin, p->items_a_end - p->items_a_begin, a, wa, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "gather A");
+  {
+    PhaseTimer t(p->ctx, YTN_PHASE_GATHER_B, st);
+    e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, b, wb, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "gather B");
+  {
+    PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
+    e = launch_gemm_fp64(p->d_sectors, p->d_tiles, (int64_t)p->tiles.size(), wa, wb, wc, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "grouped FP64 GEMM");
+  {
+    PhaseTimer t(p->ctx, YTN_PHASE_SCATTER, st);
+    e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, wc, c, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "scatter C");
+  if (res) {
+    res->useful_flops = p->flops;
+    res->precision = YTN_FP64;
+    res->slices = 0;
+    res->err_bound = 0.0;
+  }
+  return YTN_OK;
+}
+
+static ytn_status run_move(ytn_plan_t *p, Kind k, const double *a, double *out, ytn_stream stream,
+                           const char *what) {
+  if (!p) return fail(YTN_E_INVALID, "null plan");
+  if (p->kind != k) return fail(YTN_E_INVALID, std::string("plan is not a ") + what + " plan");
+  if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
+  if ((p->a_size && !a) || (p->out.size && !out)) return fail(YTN_E_INVALID, "null data buffer");
+  DeviceGuard g(p->ctx->device);
+  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (p->zero_out && (e = cudaMemsetAsync(out, 0, (size_t)p->out.size * 8, st)) != cudaSuccess)
+    return cuda_fail(e, "memset output");
+  PhaseTimer t(p->ctx, YTN_PHASE_MOVE, st);
+  if (k == Kind::Trace) {
+    if ((e = launch_trace(p->d_tr_out, (int64_t)p->tr_out.size(), p->d_tr_contrib, a, out, st)) != cudaSuccess)
+      return cuda_fail(e, "trace");
+    return YTN_OK;
+  }
+  if ((e = launch_copy(p->d_jobs, p->d_items + p->items_a_begin, p->items_a_end - p->items_a_begin, a, out, st)) !=
+      cudaSuccess)
+    return cuda_fail(e, what);
+  return YTN_OK;
+}
+
+ytn_status ytn_fuse(ytn_plan_t *p, const double *a, double *out, ytn_stream stream) {
+  return run_move(p, Kind::Fuse, a, out, stream, "fuse");
+}
+
+ytn_status ytn_unfuse(ytn_plan_t *p, const double *a, double *out, ytn_stream stream) {
+  return run_move(p, Kind::Unfuse, a, out, stream, "unfuse");
+}
+
+ytn_status ytn_trace(ytn_plan_t *p, const double *a, double *out, ytn_stream stream) {
+  return run_move(p, Kind::Trace, a, out, stream, "trace");
+}
+
+ytn_status ytn_profile_enable(ytn_ctx *ctx, int enable) {
+  if (!ctx) return fail(YTN_E_INVALID, "null ctx");
+  if (ctx->device < 0) return fail(YTN_E_INVALID, "host-only context");
+  std::lock_guard<std::mutex> lk(ctx->prof_mu);
+  if (enable && ctx->ev_pool.empty()) {
+    DeviceGuard g(ctx->device);
+    for (int i = 0; i < 8192; i++) {
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+      ctx->ev_pool.push_back(ev);
+    }
+  }
+  ctx->prof = enable != 0;
+  return YTN_OK;
+}
+
+ytn_status ytn_profile_read(ytn_ctx *ctx, ytn_profile *out) {
+  if (!ctx || !out) return fail(YTN_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->prof_mu);
+  if (ctx->device < 0) return YTN_OK;
+  DeviceGuard g(ctx->device);
+  for (auto &pe : ctx->pending) {
+    cudaEvent_t e0 = static_cast<cudaEvent_t>(ctx->ev_pool[pe.second]);
+    cudaEvent_t e1 = static_cast<cudaEvent_t>(ctx->ev_pool[pe.second + 1]);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    if (pe.first >= 0 && pe.first < YTN_NPHASES) {
+      out->calls[pe.first]++;
+      out->ms[pe.first] += ms;
+    }
+  }
+  out->dropped += ctx->dropped;
+  ctx->pending.clear();
+  ctx->ev_next = 0;
+  ctx->dropped = 0;
+  return YTN_OK;
+}
+
+ytn_status ytn_sync(ytn_ctx *ctx, ytn_stream stream, int64_t timeout_ms) {
+  if (!ctx) return fail(YTN_E_INVALID, "null ctx");
+  if (ctx->device < 0) return YTN_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "stream");
+    if (timeout_ms >= 0 &&
+        std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count() >
+            timeout_ms)
+      return fail(YTN_E_TIMEOUT, "stream did not finish within the timeout");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  int word[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpy(word, ctx->status_dev, sizeof(word), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status word");
+  if (word[0] != 0) {
+    cudaMemset(ctx->status_dev, 0, sizeof(word));
+    return fail(YTN_E_TIMEOUT, "a bounded device wait ran out (status " + std::to_string(word[0]) + ")");
+  }
+  return YTN_OK;
+}
+
+}  // extern "C"

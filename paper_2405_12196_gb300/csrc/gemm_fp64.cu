@@ -1,0 +1,152 @@
+// Grouped FP64 GEMM over the charge sectors of a contraction (Sec. II.B: the
+// fused matrices are multiplied sector by sector, C_q = A_q B_q), on the FP64
+// tensor cores (DMMA, mma.sync m8n8k4 f64).
+//
+// One launch covers every sector: the grid is the host-built tile list
+// (sector, m-tile, n-tile), largest K first so that long tiles start early.
+// Each CTA computes one 64x64 tile of C_q over the full K (no split-K), so every
+// output element has one fixed summation order: results do not depend on the
+// schedule or on what else runs on the GPU.
+//
+// On GB300 the FP64 rate (DMMA and DFMA alike, about 1 TFLOP/s for the whole
+// GPU) is low enough that this kernel is bound by the FP64 pipe even at 64x64
+// tiles; operands are staged through padded shared memory with a register
+// prefetch of the next K step.
+#include <cuda_runtime.h>
+
+#include "kernels.hpp"
+
+namespace ytn {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, PAD = 4;
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(c[0]), "+d"(c[1])
+               : "d"(a), "d"(b));
+}
+
+// Load one BK-slice of the A (or B) tile into registers: 64 x 16 elements, 8 per
+// thread. kmajor: element (r, k) at base[r * ld + k]; else at base[k * ld + r].
+__device__ __forceinline__ void load_tile(double (&v)[8], const double *__restrict__ base, int ld,
+                                          bool kmajor, int rows, int r0, int k0, int K) {
+  const int t = threadIdx.x;
+  if (kmajor) {
+    const int k = t & 15;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const int r = (t >> 4) + 8 * i;
+      const int gr = r0 + r, gk = k0 + k;
+      v[i] = (gr < rows && gk < K) ? __ldg(base + (int64_t)gr * ld + gk) : 0.0;
+    }
+  } else {
+    const int r = t & 63;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const int k = (t >> 6) + 2 * i;
+      const int gr = r0 + r, gk = k0 + k;
+      v[i] = (gr < rows && gk < K) ? __ldg(base + (int64_t)gk * ld + gr) : 0.0;
+    }
+  }
+}
+
+__device__ __forceinline__ void store_tile(double (*s)[BM + PAD], const double (&v)[8], bool kmajor) {
+  const int t = threadIdx.x;
+  if (kmajor) {
+    const int k = t & 15;
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[k][(t >> 4) + 8 * i] = v[i];
+  } else {
+    const int r = t & 63;
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[(t >> 6) + 2 * i][r] = v[i];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) gemm_fp64_kernel(const SectorDev *__restrict__ sectors,
+                                                             const GemmTile *__restrict__ tiles,
+                                                             const double *__restrict__ wa,
+                                                             const double *__restrict__ wb,
+                                                             double *__restrict__ wc) {
+  __shared__ double As[2][BK][BM + PAD];
+  __shared__ double Bs[2][BK][BN + PAD];
+  const GemmTile tl = tiles[blockIdx.x];
+  const SectorDev s = sectors[tl.sector];
+  const int M = s.M, N = s.N, K = s.K;
+  const int m0 = tl.mt * BM, n0 = tl.nt * BN;
+  const double *A = wa + s.a_off;
+  const double *B = wb + s.b_off;
+  const int lda = s.a_kmajor ? K : M;
+  const int ldb = s.b_kmajor ? K : N;
+  const bool akm = s.a_kmajor != 0, bkm = s.b_kmajor != 0;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  double acc[4][4][2];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+  double ra[8], rb[8];
+  const int nk = (K + BK - 1) / BK;
+  if (nk > 0) {
+    load_tile(ra, A, lda, akm, M, m0, 0, K);
+    load_tile(rb, B, ldb, bkm, N, n0, 0, K);
+    store_tile(As[0], ra, akm);
+    store_tile(Bs[0], rb, bkm);
+  }
+  __syncthreads();
+  for (int kt = 0; kt < nk; kt++) {
+    const int cur = kt & 1;
+    const bool more = kt + 1 < nk;
+    if (more) {
+      load_tile(ra, A, lda, akm, M, m0, (kt + 1) * BK, K);
+      load_tile(rb, B, ldb, bkm, N, n0, (kt + 1) * BK, K);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 4) {
+      double af[4], bf[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) af[i] = As[cur][kk + (lane & 3)][wm + i * 8 + (lane >> 2)];
+#pragma unroll
+      for (int j = 0; j < 4; j++) bf[j] = Bs[cur][kk + (lane & 3)][wn + j * 8 + (lane >> 2)];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) dmma(acc[i][j], af[i], bf[j]);
+    }
+    if (more) {
+      store_tile(As[cur ^ 1], ra, akm);
+      store_tile(Bs[cur ^ 1], rb, bkm);
+    }
+    __syncthreads();
+  }
+  double *C = wc + s.c_off;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int m = m0 + wm + i * 8 + (lane >> 2);
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int n = n0 + wn + j * 8 + 2 * (lane & 3);
+      if (n < N) C[(int64_t)m * N + n] = acc[i][j][0];
+      if (n + 1 < N) C[(int64_t)m * N + n + 1] = acc[i][j][1];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_fp64(const SectorDev *sectors, const GemmTile *tiles, int64_t ntiles,
+                             const double *wa, const double *wb, double *wc, cudaStream_t stream) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (ntiles > INT32_MAX) return cudaErrorInvalidValue;
+  gemm_fp64_kernel<<<(unsigned)ntiles, kThreads, 0, stream>>>(sectors, tiles, wa, wb, wc);
+  return cudaGetLastError();
+}
+
+}  // namespace ytn

@@ -1,0 +1,1159 @@
+// Host-side planner: pure integer structure work. Validates block structures,
+// matches blocks by charge, groups them into charge sectors, builds the output
+// structure in canonical order and the job tables that the device kernels run.
+//
+// Sec. II.A (block conservation rule sum_i s_i rho_i = n, lazy storage in one
+// 1-D array) and Sec. II.B (fusion: nu = s_r (s_i rho + s_j rho'), D_nu =
+// sum D_rho D_rho'; contraction = fuse -> multiply per sector -> unfuse, with
+// the non-zero blocks precomputed) define what is planned here.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <set>
+#include <sstream>
+
+#include "ytn_internal.hpp"
+
+namespace ytn {
+
+using Key = std::vector<int32_t>;
+
+static inline int32_t reduce(int64_t v, int m) {
+  if (m == 0) return (int32_t)v;
+  int64_t r = v % m;
+  return (int32_t)(r < 0 ? r + m : r);
+}
+
+static std::string keystr(const Key &k) {
+  std::ostringstream os;
+  os << "(";
+  for (size_t i = 0; i < k.size(); i++) os << (i ? "," : "") << k[i];
+  os << ")";
+  return os.str();
+}
+
+// ---------------------------------------------------------------------------
+// Loading and validating a ytn_struct
+// ---------------------------------------------------------------------------
+
+ytn_status load_struct(const ytn_struct *s, Tensor &T, std::string &err) {
+  if (!s) { err = "null structure"; return YTN_E_INVALID; }
+  if (s->sym.nsym < 1 || s->sym.nsym > YTN_MAX_SYM) { err = "nsym out of range"; return YTN_E_INVALID; }
+  if (s->rank < 0 || s->rank > YTN_MAX_RANK) { err = "rank out of range"; return YTN_E_INVALID; }
+  if (s->nblocks < 0 || s->size < 0) { err = "negative sizes"; return YTN_E_INVALID; }
+  if (s->nblocks > 0 && s->rank > 0 && (!s->t || !s->D)) { err = "null block arrays"; return YTN_E_INVALID; }
+  T = Tensor();
+  T.nsym = s->sym.nsym;
+  T.rank = s->rank;
+  for (int c = 0; c < T.nsym; c++) {
+    if (s->sym.mod[c] < 0 || s->sym.mod[c] == 1) { err = "modulus must be 0 (U(1)) or >= 2"; return YTN_E_INVALID; }
+    T.mod[c] = s->sym.mod[c];
+  }
+  for (int c = 0; c < T.nsym; c++) T.n[c] = reduce(s->n[c], T.mod[c]);
+  for (int i = 0; i < T.rank; i++) {
+    if (s->sig[i] != 1 && s->sig[i] != -1) { err = "signature must be +1 or -1"; return YTN_E_INVALID; }
+    T.sig[i] = s->sig[i];
+  }
+  T.nblocks = s->nblocks;
+  const size_t nt = (size_t)T.nblocks * T.rank * T.nsym;
+  const size_t nd = (size_t)T.nblocks * T.rank;
+  T.t.assign(s->t ? s->t : nullptr, s->t ? s->t + nt : nullptr);
+  T.D.assign(s->D ? s->D : nullptr, s->D ? s->D + nd : nullptr);
+  T.size = s->size;
+  T.off.resize(T.nblocks);
+  int64_t acc = 0;
+  for (int64_t b = 0; b < T.nblocks; b++) {
+    int64_t e = 1;
+    for (int i = 0; i < T.rank; i++) {
+      int64_t d = T.dim(b, i);
+      if (d < 1 || d > (int64_t)1 << 30) { err = "block dimension out of range"; return YTN_E_INVALID; }
+      e *= d;
+      if (e > ((int64_t)1 << 40)) { err = "block too large"; return YTN_E_INVALID; }
+    }
+    T.off[b] = s->off ? s->off[b] : acc;
+    if (T.off[b] < 0 || T.off[b] + e > T.size) { err = "block outside the data buffer"; return YTN_E_INVALID; }
+    acc += e;
+  }
+  // Z_m charges reduced; conservation; canonical order; one dimension per charge and leg.
+  std::vector<std::map<Key, int64_t>> legdim(T.rank);
+  for (int64_t b = 0; b < T.nblocks; b++) {
+    int64_t tot[YTN_MAX_SYM] = {0};
+    for (int i = 0; i < T.rank; i++) {
+      const int32_t *q = T.charge(b, i);
+      for (int c = 0; c < T.nsym; c++) {
+        if (T.mod[c] && (q[c] < 0 || q[c] >= T.mod[c])) { err = "Z_m charge not reduced"; return YTN_E_INVALID; }
+        tot[c] += (int64_t)T.sig[i] * q[c];
+      }
+      Key k(q, q + T.nsym);
+      auto it = legdim[i].find(k);
+      if (it == legdim[i].end()) legdim[i][k] = T.dim(b, i);
+      else if (it->second != T.dim(b, i)) {
+        err = "leg " + std::to_string(i) + " charge " + keystr(k) + " has two dimensions";
+        return YTN_E_DIM_MISMATCH;
+      }
+    }
+    for (int c = 0; c < T.nsym; c++)
+      if (reduce(tot[c], T.mod[c]) != T.n[c]) {
+        err = "block " + std::to_string(b) + " violates charge conservation";
+        return YTN_E_CHARGE;
+      }
+    if (b > 0) {
+      const int32_t *p = &T.t[(size_t)(b - 1) * T.rank * T.nsym];
+      const int32_t *q = &T.t[(size_t)b * T.rank * T.nsym];
+      if (!std::lexicographical_compare(p, p + T.rank * T.nsym, q, q + T.rank * T.nsym)) {
+        err = "blocks not in strictly ascending canonical order";
+        return YTN_E_INVALID;
+      }
+    }
+  }
+  if (T.rank == 0 && T.nblocks > 1) { err = "rank-0 tensor with more than one block"; return YTN_E_INVALID; }
+  for (int i = 0; i < T.rank; i++) {
+    const ytn_fusion *f = s->fus[i];
+    if (!f) continue;
+    if (f->nlegs < 2 || f->nlegs > YTN_MAX_RANK || f->nentries < 1 || !f->nu || !f->t || !f->D) {
+      err = "malformed fusion record";
+      return YTN_E_INVALID;
+    }
+    auto F = std::make_shared<Fusion>();
+    F->nlegs = f->nlegs;
+    for (int j = 0; j < f->nlegs; j++) {
+      if (f->sig[j] != 1 && f->sig[j] != -1) { err = "fusion record signature"; return YTN_E_INVALID; }
+      F->sig[j] = f->sig[j];
+    }
+    F->nentries = f->nentries;
+    F->nu.assign(f->nu, f->nu + f->nentries * T.nsym);
+    F->t.assign(f->t, f->t + f->nentries * f->nlegs * T.nsym);
+    F->D.assign(f->D, f->D + f->nentries * f->nlegs);
+    // entries sorted by (nu, constituent charges); each row consistent with F2
+    std::map<Key, int64_t> dnu;
+    for (int64_t e = 0; e < F->nentries; e++) {
+      int64_t tot[YTN_MAX_SYM] = {0};
+      for (int j = 0; j < F->nlegs; j++)
+        for (int c = 0; c < T.nsym; c++) tot[c] += (int64_t)F->sig[j] * F->t[(e * F->nlegs + j) * T.nsym + c];
+      int64_t sz = 1;
+      for (int j = 0; j < F->nlegs; j++) {
+        if (F->D[e * F->nlegs + j] < 1) { err = "fusion record dimension"; return YTN_E_INVALID; }
+        sz *= F->D[e * F->nlegs + j];
+      }
+      for (int c = 0; c < T.nsym; c++)
+        if (reduce((int64_t)T.sig[i] * tot[c], T.mod[c]) != F->nu[e * T.nsym + c]) {
+          err = "fusion record charge does not follow nu = s_r sum_i s_i rho_i";
+          return YTN_E_INVALID;
+        }
+      Key k(&F->nu[e * T.nsym], &F->nu[e * T.nsym] + T.nsym);
+      dnu[k] += sz;
+      if (e > 0) {
+        Key a(&F->nu[(e - 1) * T.nsym], &F->nu[(e - 1) * T.nsym] + T.nsym);
+        a.insert(a.end(), &F->t[(e - 1) * F->nlegs * T.nsym], &F->t[e * F->nlegs * T.nsym]);
+        Key bk = k;
+        bk.insert(bk.end(), &F->t[e * F->nlegs * T.nsym], &F->t[(e + 1) * F->nlegs * T.nsym]);
+        if (!(a < bk)) { err = "fusion record rows not in ascending order"; return YTN_E_INVALID; }
+      }
+    }
+    for (auto &kv : legdim[i]) {
+      auto it = dnu.find(kv.first);
+      if (it == dnu.end() || it->second != kv.second) {
+        err = "fused leg " + std::to_string(i) + " block dimension does not match its record";
+        return YTN_E_INVALID;
+      }
+    }
+    T.fus[i] = F;
+  }
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Helpers
+// ---------------------------------------------------------------------------
+
+static Key sub_charges(const Tensor &T, int64_t b, const std::vector<int> &legs) {
+  Key k;
+  k.reserve(legs.size() * T.nsym);
+  for (int l : legs) {
+    const int32_t *q = T.charge(b, l);
+    k.insert(k.end(), q, q + T.nsym);
+  }
+  return k;
+}
+
+static int64_t sub_elems(const Tensor &T, int64_t b, const std::vector<int> &legs) {
+  int64_t e = 1;
+  for (int l : legs) e *= T.dim(b, l);
+  return e;
+}
+
+static std::map<Key, int64_t> leg_dims(const Tensor &T, int leg) {
+  std::map<Key, int64_t> m;
+  for (int64_t b = 0; b < T.nblocks; b++) {
+    const int32_t *q = T.charge(b, leg);
+    m[Key(q, q + T.nsym)] = T.dim(b, leg);
+  }
+  if (T.fus[leg]) {
+    const Fusion &F = *T.fus[leg];
+    std::map<Key, int64_t> dnu;
+    for (int64_t e = 0; e < F.nentries; e++) {
+      int64_t sz = 1;
+      for (int j = 0; j < F.nlegs; j++) sz *= F.D[e * F.nlegs + j];
+      dnu[Key(&F.nu[e * T.nsym], &F.nu[e * T.nsym] + T.nsym)] += sz;
+    }
+    for (auto &kv : dnu) m.emplace(kv.first, kv.second);
+  }
+  return m;
+}
+
+static bool fusion_conj_equal(const Fusion &a, const Fusion &b) {
+  if (a.nlegs != b.nlegs || a.nentries != b.nentries) return false;
+  for (int j = 0; j < a.nlegs; j++)
+    if (a.sig[j] != -b.sig[j]) return false;
+  return a.nu == b.nu && a.t == b.t && a.D == b.D;
+}
+
+// Paired legs (contraction or trace) must be compatible: opposite signatures,
+// one dimension per charge present on both, conjugate fusion records.
+static ytn_status check_pair(const Tensor &A, int a, const Tensor &B, int b, std::string &err) {
+  if (A.sig[a] != -B.sig[b]) {
+    err = "paired legs " + std::to_string(a) + "/" + std::to_string(b) + " have equal signatures";
+    return YTN_E_SIGNATURE;
+  }
+  auto da = leg_dims(A, a), db = leg_dims(B, b);
+  for (auto &kv : da) {
+    auto it = db.find(kv.first);
+    if (it != db.end() && it->second != kv.second) {
+      err = "charge " + keystr(kv.first) + " has dimension " + std::to_string(kv.second) + " vs " +
+            std::to_string(it->second) + " on paired legs";
+      return YTN_E_DIM_MISMATCH;
+    }
+  }
+  const bool fa = (bool)A.fus[a], fb = (bool)B.fus[b];
+  if (fa != fb) { err = "a fused leg is paired with a plain leg"; return YTN_E_FUSION_MISMATCH; }
+  if (fa && !fusion_conj_equal(*A.fus[a], *B.fus[b])) {
+    err = "fusion records of paired legs differ";
+    return YTN_E_FUSION_MISMATCH;
+  }
+  return YTN_OK;
+}
+
+// Row-major element strides of block b.
+static std::vector<int64_t> block_strides(const Tensor &T, int64_t b) {
+  std::vector<int64_t> st(T.rank);
+  int64_t acc = 1;
+  for (int i = T.rank - 1; i >= 0; i--) {
+    st[i] = acc;
+    acc *= T.dim(b, i);
+  }
+  return st;
+}
+
+struct Dim {
+  int64_t ext, sst, dst;
+};
+
+// Normalise a copy (dims outer -> inner in destination order): drop unit dims,
+// merge dims contiguous in both layouts, pick rows or tile mode.
+static ytn_status make_job(std::vector<Dim> dims, int64_t src_off, int64_t dst_off, CopyJob &J,
+                           std::string &err) {
+  std::vector<Dim> v;
+  for (auto &d : dims)
+    if (d.ext != 1) v.push_back(d);
+  std::vector<Dim> m;
+  for (auto &d : v) {
+    if (!m.empty() && m.back().sst == d.sst * d.ext && m.back().dst == d.dst * d.ext) {
+      m.back().ext *= d.ext;
+      m.back().sst = d.sst;
+      m.back().dst = d.dst;
+    } else {
+      m.push_back(d);
+    }
+  }
+  if (m.empty()) m.push_back({1, 1, 1});
+  // put the destination-contiguous dim innermost when it is not already
+  if (m.back().dst != 1) {
+    for (size_t i = 0; i + 1 < m.size(); i++)
+      if (m[i].dst == 1) {
+        Dim d = m[i];
+        m.erase(m.begin() + i);
+        m.push_back(d);
+        break;
+      }
+  }
+  if ((int)m.size() > kMaxCopyDims) { err = "copy job needs more than 8 dimensions"; return YTN_E_UNSUPPORTED; }
+  std::memset(&J, 0, sizeof(J));
+  J.src_off = src_off;
+  J.dst_off = dst_off;
+  J.nd = (int)m.size();
+  for (int i = 0; i < J.nd; i++) {
+    if (m[i].ext > INT32_MAX || m[i].sst > INT32_MAX || m[i].dst > INT32_MAX) {
+      err = "copy job stride exceeds 32 bits";
+      return YTN_E_UNSUPPORTED;
+    }
+    J.ext[i] = (int32_t)m[i].ext;
+    J.sst[i] = (int32_t)m[i].sst;
+    J.dst[i] = (int32_t)m[i].dst;
+  }
+  const int q = J.nd - 1;
+  int64_t tot = 1;
+  for (int i = 0; i < J.nd; i++) tot *= J.ext[i];
+  if (tot > INT32_MAX) { err = "copy job larger than 2^31 elements"; return YTN_E_UNSUPPORTED; }
+  J.mode = 0;
+  J.p = q;
+  if (J.sst[q] != 1 && J.dst[q] == 1) {
+    for (int i = 0; i < q; i++)
+      if (J.sst[i] == 1 && J.ext[i] >= 8 && J.ext[q] >= 8) {
+        J.mode = 1;
+        J.p = i;
+      }
+  }
+  J.nchunk = J.mode == 0 ? (J.ext[q] + kRowChunk - 1) / kRowChunk : 0;
+  return YTN_OK;
+}
+
+static int64_t job_units(const CopyJob &J) {
+  int64_t u = 1;
+  if (J.mode == 0) {
+    for (int i = 0; i + 1 < J.nd; i++) u *= J.ext[i];
+    return u * J.nchunk;
+  }
+  for (int i = 0; i < J.nd; i++) {
+    if (i == J.p || i == J.nd - 1) u *= (J.ext[i] + kTile - 1) / kTile;
+    else u *= J.ext[i];
+  }
+  return u;
+}
+
+// Split jobs [j0, j1) into CTA work items of about 8K elements.
+static void make_items(ytn_plan_t *p, size_t j0, size_t j1) {
+  for (size_t j = j0; j < j1; j++) {
+    const CopyJob &J = p->jobs[j];
+    const int64_t units = job_units(J);
+    int64_t per_unit;
+    if (J.mode == 0) per_unit = std::min<int64_t>(J.ext[J.nd - 1], kRowChunk);
+    else per_unit = kTile * kTile;
+    int64_t per_item = std::max<int64_t>(1, 8192 / std::max<int64_t>(1, per_unit));
+    per_item = std::min<int64_t>(per_item, 1 << 20);
+    for (int64_t u = 0; u < units; u += per_item) {
+      CopyItem it;
+      it.job = (int32_t)j;
+      it.begin = u;
+      it.count = (int32_t)std::min<int64_t>(per_item, units - u);
+      p->items.push_back(it);
+    }
+  }
+}
+
+static void copy_fusion(const Fusion *f, std::shared_ptr<Fusion> &dst) {
+  dst = f ? std::make_shared<Fusion>(*f) : nullptr;
+}
+
+// Sort output blocks canonically and assign packed offsets.
+struct OutBlock {
+  Key key;                  // flattened charges, rank * nsym
+  std::vector<int64_t> D;   // rank
+  int64_t id;               // caller's handle
+};
+
+static void finalize_out(Tensor &C, std::vector<OutBlock> &blocks, std::vector<int64_t> &offset_of_id) {
+  std::sort(blocks.begin(), blocks.end(), [](const OutBlock &a, const OutBlock &b) { return a.key < b.key; });
+  C.nblocks = (int64_t)blocks.size();
+  C.t.clear();
+  C.D.clear();
+  C.off.clear();
+  int64_t acc = 0;
+  offset_of_id.assign(blocks.size(), 0);
+  for (auto &ob : blocks) {
+    C.t.insert(C.t.end(), ob.key.begin(), ob.key.end());
+    C.D.insert(C.D.end(), ob.D.begin(), ob.D.end());
+    C.off.push_back(acc);
+    offset_of_id[ob.id] = acc;
+    int64_t e = 1;
+    for (auto d : ob.D) e *= d;
+    acc += e;
+  }
+  C.size = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Tensordot
+// ---------------------------------------------------------------------------
+
+ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int naxes,
+                          const int *axa_in, const int *axb_in, std::string &err) {
+  if (A.nsym != B.nsym || std::memcmp(A.mod, B.mod, sizeof(A.mod)) != 0) {
+    err = "tensors have different symmetries";
+    return YTN_E_INVALID;
+  }
+  if (naxes < 0 || naxes > A.rank || naxes > B.rank) { err = "naxes out of range"; return YTN_E_INVALID; }
+  std::vector<int> axa(axa_in, axa_in + naxes), axb(axb_in, axb_in + naxes);
+  {
+    std::set<int> sa(axa.begin(), axa.end()), sb(axb.begin(), axb.end());
+    if ((int)sa.size() != naxes || (int)sb.size() != naxes) { err = "repeated axis"; return YTN_E_INVALID; }
+    for (int k = 0; k < naxes; k++)
+      if (axa[k] < 0 || axa[k] >= A.rank || axb[k] < 0 || axb[k] >= B.rank) {
+        err = "axis out of range";
+        return YTN_E_INVALID;
+      }
+  }
+  if (A.rank + B.rank - 2 * naxes > YTN_MAX_RANK) { err = "output rank too large"; return YTN_E_UNSUPPORTED; }
+  for (int k = 0; k < naxes; k++) {
+    ytn_status st = check_pair(A, axa[k], B, axb[k], err);
+    if (st != YTN_OK) return st;
+  }
+  const int nsym = A.nsym;
+  std::vector<int> freeA, freeB;
+  for (int i = 0; i < A.rank; i++)
+    if (std::find(axa.begin(), axa.end(), i) == axa.end()) freeA.push_back(i);
+  for (int i = 0; i < B.rank; i++)
+    if (std::find(axb.begin(), axb.end(), i) == axb.end()) freeB.push_back(i);
+
+  // Output tensor: A's free legs then B's; n_C = n_A + n_B.
+  Tensor &C = p->out;
+  C = Tensor();
+  C.nsym = nsym;
+  std::memcpy(C.mod, A.mod, sizeof(C.mod));
+  C.rank = (int)(freeA.size() + freeB.size());
+  for (size_t i = 0; i < freeA.size(); i++) {
+    C.sig[i] = A.sig[freeA[i]];
+    copy_fusion(A.fus[freeA[i]].get(), C.fus[i]);
+  }
+  for (size_t i = 0; i < freeB.size(); i++) {
+    C.sig[freeA.size() + i] = B.sig[freeB[i]];
+    copy_fusion(B.fus[freeB[i]].get(), C.fus[freeA.size() + i]);
+  }
+  for (int c = 0; c < nsym; c++) C.n[c] = reduce((int64_t)A.n[c] + B.n[c], A.mod[c]);
+
+  // Match blocks on the contracted charges x (in the order of axa / axb).
+  std::map<Key, std::vector<int64_t>> Ax, Bx;
+  for (int64_t b = 0; b < A.nblocks; b++) Ax[sub_charges(A, b, axa)].push_back(b);
+  for (int64_t b = 0; b < B.nblocks; b++) Bx[sub_charges(B, b, axb)].push_back(b);
+
+  // Sector key q = sum_k s_A[axa_k] x_k (reduced): every x, every row I of A and
+  // every column J of B belongs to exactly one sector.
+  struct SB {
+    std::map<Key, int64_t> xs;                      // x -> |x|
+    std::map<Key, std::pair<int64_t, int64_t>> rows; // I -> (|I|, any A block)
+    std::map<Key, std::pair<int64_t, int64_t>> cols; // J -> (|J|, any B block)
+  };
+  std::map<Key, SB> secs;
+  double flops = 0;
+  for (auto &kv : Ax) {
+    auto itb = Bx.find(kv.first);
+    if (itb == Bx.end()) continue;
+    Key q(nsym, 0);
+    for (int k = 0; k < naxes; k++)
+      for (int c = 0; c < nsym; c++)
+        q[c] = reduce((int64_t)q[c] + (int64_t)A.sig[axa[k]] * kv.first[k * nsym + c], A.mod[c]);
+    SB &s = secs[q];
+    const int64_t b0 = kv.second[0];
+    const int64_t kx = sub_elems(A, b0, axa);
+    s.xs[kv.first] = kx;
+    double si = 0, sj = 0;
+    for (int64_t a : kv.second) {
+      const int64_t ni = sub_elems(A, a, freeA);
+      s.rows.emplace(sub_charges(A, a, freeA), std::make_pair(ni, a));
+      si += (double)ni;
+    }
+    for (int64_t b : itb->second) {
+      const int64_t nj = sub_elems(B, b, freeB);
+      s.cols.emplace(sub_charges(B, b, freeB), std::make_pair(nj, b));
+      sj += (double)nj;
+    }
+    flops += 2.0 * si * (double)kx * sj;
+  }
+  p->flops = flops;
+
+  // Sector geometry: rows, K and columns in ascending charge order.
+  struct SG {
+    std::map<Key, int64_t> row_off, col_off, x_off;
+    int64_t M = 0, N = 0, K = 0;
+  };
+  std::vector<SG> geo;
+  std::vector<const SB *> sbs;
+  for (auto &kv : secs) {
+    SG g;
+    for (auto &r : kv.second.rows) { g.row_off[r.first] = g.M; g.M += r.second.first; }
+    for (auto &c : kv.second.cols) { g.col_off[c.first] = g.N; g.N += c.second.first; }
+    for (auto &x : kv.second.xs) { g.x_off[x.first] = g.K; g.K += x.second; }
+    if (g.M > INT32_MAX || g.N > INT32_MAX || g.K > INT32_MAX) { err = "sector too large"; return YTN_E_UNSUPPORTED; }
+    geo.push_back(std::move(g));
+    sbs.push_back(&kv.second);
+  }
+
+  // Operand layouts: choose, per operand, the sector-matrix orientation in which
+  // most gathered elements keep their source-contiguous dimension innermost.
+  auto count_contig = [&](const Tensor &T, const std::vector<int> &first, const std::vector<int> &second) {
+    // elements whose innermost destination dim is the source's innermost leg
+    double same = 0, total = 0;
+    for (int64_t b = 0; b < T.nblocks; b++) {
+      const double e = (double)T.elems(b);
+      total += e;
+      int last_src = -1;
+      for (int i = T.rank - 1; i >= 0; i--)
+        if (T.dim(b, i) != 1) { last_src = i; break; }
+      int last_dst = -1;
+      for (int i = (int)second.size() - 1; i >= 0 && last_dst < 0; i--)
+        if (T.dim(b, second[i]) != 1) last_dst = second[i];
+      for (int i = (int)first.size() - 1; i >= 0 && last_dst < 0; i--)
+        if (T.dim(b, first[i]) != 1) last_dst = first[i];
+      if (last_src == last_dst) same += e;
+    }
+    return same;
+  };
+  {
+    const double a_mk = count_contig(A, freeA, axa), a_km = count_contig(A, axa, freeA);
+    const double b_nk = count_contig(B, freeB, axb), b_kn = count_contig(B, axb, freeB);
+    p->a_kmajor = a_mk >= a_km;
+    p->b_kmajor = b_nk > b_kn;
+  }
+
+  // Workspace offsets of the sector matrices (256-byte aligned per sector).
+  auto align32 = [](int64_t e) { return (e + 31) / 32 * 32; };
+  p->sectors.clear();
+  p->sectors_dev.clear();
+  int64_t ao = 0, bo = 0, co = 0;
+  int64_t a_cov = 0, b_cov = 0;
+  p->max_m = p->max_n = p->max_k = 0;
+  for (auto &g : geo) {
+    HostSector h;
+    h.M = g.M; h.N = g.N; h.K = g.K;
+    h.a_off = ao; h.b_off = bo; h.c_off = co;
+    ao += align32(g.M * g.K);
+    bo += align32(g.K * g.N);
+    co += align32(g.M * g.N);
+    p->sectors.push_back(h);
+    SectorDev d{};
+    d.a_off = h.a_off; d.b_off = h.b_off; d.c_off = h.c_off;
+    d.M = (int32_t)g.M; d.N = (int32_t)g.N; d.K = (int32_t)g.K;
+    d.a_kmajor = p->a_kmajor; d.b_kmajor = p->b_kmajor;
+    p->sectors_dev.push_back(d);
+    p->max_m = std::max(p->max_m, g.M);
+    p->max_n = std::max(p->max_n, g.N);
+    p->max_k = std::max(p->max_k, g.K);
+  }
+  p->a_elems = ao;
+  p->b_elems = bo;
+  p->c_elems = co;
+
+  p->jobs.clear();
+  p->items.clear();
+  p->moved = 0;
+  // Gather A: block (I, x) -> A_q[row_off(I) + i, x_off(x) + k].
+  // isA: gather A (free part = rows M) else B (free part = columns N).
+  auto gather = [&](const Tensor &T, const std::vector<int> &freeL, const std::vector<int> &conL,
+                    bool isA, bool kmajor, int64_t &covered) -> ytn_status {
+    for (size_t si = 0; si < geo.size(); si++) {
+      const SG &g = geo[si];
+      const HostSector &h = p->sectors[si];
+      for (auto &xk : g.x_off) {
+        const auto &blist = isA ? Ax[xk.first] : Bx[xk.first];
+        for (int64_t b : blist) {
+          Key fk = sub_charges(T, b, freeL);
+          const auto &offmap = isA ? g.row_off : g.col_off;
+          auto it = offmap.find(fk);
+          if (it == offmap.end()) continue;
+          const int64_t foff = it->second, xoff = xk.second;
+          const int64_t F = isA ? g.M : g.N;  // free extent of the sector
+          const int64_t base = isA ? h.a_off : h.b_off;
+          auto st = block_strides(T, b);
+          // strides of the free and contracted sub-indices inside their fused index
+          std::vector<Dim> dims;
+          std::vector<int64_t> fstr(freeL.size()), cstr(conL.size());
+          int64_t acc = 1;
+          for (int i = (int)freeL.size() - 1; i >= 0; i--) { fstr[i] = acc; acc *= T.dim(b, freeL[i]); }
+          acc = 1;
+          for (int i = (int)conL.size() - 1; i >= 0; i--) { cstr[i] = acc; acc *= T.dim(b, conL[i]); }
+          // kmajor: matrix is (free rows) x (K cols), ld = K; else (K rows) x (free cols), ld = F.
+          const int64_t ldk = kmajor ? g.K : F;
+          int64_t dst_off;
+          if (kmajor) {
+            for (size_t i = 0; i < freeL.size(); i++) dims.push_back({T.dim(b, freeL[i]), st[freeL[i]], fstr[i] * ldk});
+            for (size_t i = 0; i < conL.size(); i++) dims.push_back({T.dim(b, conL[i]), st[conL[i]], cstr[i]});
+            dst_off = base + foff * ldk + xoff;
+          } else {
+            for (size_t i = 0; i < conL.size(); i++) dims.push_back({T.dim(b, conL[i]), st[conL[i]], cstr[i] * ldk});
+            for (size_t i = 0; i < freeL.size(); i++) dims.push_back({T.dim(b, freeL[i]), st[freeL[i]], fstr[i]});
+            dst_off = base + xoff * ldk + foff;
+          }
+          CopyJob J;
+          ytn_status s = make_job(dims, T.off[b], dst_off, J, err);
+          if (s != YTN_OK) return s;
+          p->jobs.push_back(J);
+          covered += T.elems(b);
+          p->moved += T.elems(b);
+        }
+      }
+    }
+    return YTN_OK;
+  };
+  size_t j0 = p->jobs.size();
+  ytn_status s = gather(A, freeA, axa, true, p->a_kmajor, a_cov);
+  if (s != YTN_OK) return s;
+  size_t j1 = p->jobs.size();
+  p->items_a_begin = (int64_t)p->items.size();
+  make_items(p, j0, j1);
+  p->items_a_end = (int64_t)p->items.size();
+  s = gather(B, freeB, axb, false, p->b_kmajor, b_cov);
+  if (s != YTN_OK) return s;
+  size_t j2 = p->jobs.size();
+  p->items_b_begin = (int64_t)p->items.size();
+  make_items(p, j1, j2);
+  p->items_b_end = (int64_t)p->items.size();
+  int64_t a_need = 0, b_need = 0;
+  for (auto &g : geo) { a_need += g.M * g.K; b_need += g.K * g.N; }
+  p->zero_a = a_cov < a_need;
+  p->zero_b = b_cov < b_need;
+
+  // Output blocks: (I, J) exists when some x has both A(I, x) and B(x, J).
+  std::vector<OutBlock> outb;
+  struct Src { int64_t sector; int64_t roff, coff; int64_t nI, nJ; int64_t a_blk, b_blk; };
+  std::vector<Src> srcs;
+  for (size_t si = 0; si < geo.size(); si++) {
+    const SG &g = geo[si];
+    const SB &sb = *sbs[si];
+    // x index per sector
+    std::map<Key, int> xidx;
+    for (auto &x : g.x_off) xidx.emplace(x.first, (int)xidx.size());
+    const int nw = ((int)xidx.size() + 63) / 64;
+    std::map<Key, std::vector<uint64_t>> rowx, colx;
+    for (auto &x : g.x_off) {
+      const int xi = xidx[x.first];
+      for (int64_t a : Ax[x.first]) {
+        auto &v = rowx[sub_charges(A, a, freeA)];
+        v.resize(nw, 0);
+        v[xi / 64] |= 1ull << (xi % 64);
+      }
+      for (int64_t b : Bx[x.first]) {
+        auto &v = colx[sub_charges(B, b, freeB)];
+        v.resize(nw, 0);
+        v[xi / 64] |= 1ull << (xi % 64);
+      }
+    }
+    for (auto &r : sb.rows) {
+      const auto &rv = rowx[r.first];
+      for (auto &c : sb.cols) {
+        const auto &cv = colx[c.first];
+        bool hit = false;
+        for (int w = 0; w < nw && !hit; w++) hit = (rv[w] & cv[w]) != 0;
+        if (!hit) continue;
+        OutBlock ob;
+        ob.key = r.first;
+        ob.key.insert(ob.key.end(), c.first.begin(), c.first.end());
+        for (int l : freeA) ob.D.push_back(A.dim(r.second.second, l));
+        for (int l : freeB) ob.D.push_back(B.dim(c.second.second, l));
+        ob.id = (int64_t)srcs.size();
+        outb.push_back(ob);
+        srcs.push_back({(int64_t)si, g.row_off.at(r.first), g.col_off.at(c.first), r.second.first,
+                        c.second.first, r.second.second, c.second.second});
+      }
+    }
+  }
+  std::vector<int64_t> off_of_id;
+  finalize_out(C, outb, off_of_id);
+  // Scatter C: block (I, J) = C_q[row_off(I) + i, col_off(J) + j], row-major per leg.
+  for (size_t id = 0; id < srcs.size(); id++) {
+    const Src &sr = srcs[id];
+    const HostSector &h = p->sectors[sr.sector];
+    std::vector<Dim> dims;
+    std::vector<int64_t> ds(C.rank);
+    // destination: the C block, row-major over its legs
+    std::vector<int64_t> cd;
+    for (int l : freeA) cd.push_back(A.dim(sr.a_blk, l));
+    for (int l : freeB) cd.push_back(B.dim(sr.b_blk, l));
+    int64_t acc = 1;
+    for (int i = C.rank - 1; i >= 0; i--) { ds[i] = acc; acc *= cd[i]; }
+    // source: inside I the legs are row-major, times ldc = N; inside J row-major
+    std::vector<int64_t> ss(C.rank);
+    acc = 1;
+    for (int i = (int)freeA.size() - 1; i >= 0; i--) { ss[i] = acc * h.N; acc *= cd[i]; }
+    acc = 1;
+    for (int i = C.rank - 1; i >= (int)freeA.size(); i--) { ss[i] = acc; acc *= cd[i]; }
+    for (int i = 0; i < C.rank; i++) dims.push_back({cd[i], ss[i], ds[i]});
+    CopyJob J;
+    s = make_job(dims, h.c_off + sr.roff * h.N + sr.coff, off_of_id[id], J, err);
+    if (s != YTN_OK) return s;
+    p->jobs.push_back(J);
+    p->moved += acc;
+  }
+  size_t j3 = p->jobs.size();
+  p->items_c_begin = (int64_t)p->items.size();
+  make_items(p, j2, j3);
+  p->items_c_end = (int64_t)p->items.size();
+
+  // Grouped-GEMM tiles (64 x 64), largest K first.
+  p->tiles.clear();
+  for (size_t si = 0; si < geo.size(); si++) {
+    const int64_t mt = (geo[si].M + 63) / 64, nt = (geo[si].N + 63) / 64;
+    for (int64_t i = 0; i < mt; i++)
+      for (int64_t j = 0; j < nt; j++) p->tiles.push_back({(int32_t)si, (int32_t)i, (int32_t)j, 0});
+  }
+  std::stable_sort(p->tiles.begin(), p->tiles.end(), [&](const GemmTile &x, const GemmTile &y) {
+    return geo[x.sector].K > geo[y.sector].K;
+  });
+  p->kind = Kind::Tensordot;
+  p->a_size = A.size;
+  p->b_size = B.size;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Fuse
+// ---------------------------------------------------------------------------
+
+ytn_status plan_fuse(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size,
+                     const int *order, std::string &err) {
+  if (ngroups < 1 || ngroups > YTN_MAX_RANK) { err = "ngroups out of range"; return YTN_E_INVALID; }
+  std::vector<std::vector<int>> groups;
+  std::vector<int> seen(A.rank, 0);
+  int pos = 0;
+  for (int g = 0; g < ngroups; g++) {
+    if (group_size[g] < 1 || pos + group_size[g] > A.rank) { err = "bad group sizes"; return YTN_E_INVALID; }
+    std::vector<int> grp;
+    for (int i = 0; i < group_size[g]; i++) {
+      const int l = order[pos++];
+      if (l < 0 || l >= A.rank || seen[l]) { err = "fusion groups must list every leg once"; return YTN_E_INVALID; }
+      seen[l] = 1;
+      grp.push_back(l);
+    }
+    groups.push_back(grp);
+  }
+  if (pos != A.rank) { err = "fusion groups must list every leg once"; return YTN_E_INVALID; }
+  for (auto &g : groups)
+    if (g.size() > 1)
+      for (int l : g)
+        if (A.fus[l]) { err = "fusing an already fused leg"; return YTN_E_UNSUPPORTED; }
+  const int nsym = A.nsym;
+  const int G = ngroups;
+  // fused charge of block b for group g: nu = s_r sum_i s_i rho_i (s_r: first leg)
+  auto nu_of = [&](int64_t b, const std::vector<int> &g) {
+    Key nu(nsym, 0);
+    for (int c = 0; c < nsym; c++) {
+      int64_t tot = 0;
+      for (int l : g) tot += (int64_t)A.sig[l] * A.charge(b, l)[c];
+      nu[c] = reduce((int64_t)A.sig[g[0]] * tot, A.mod[c]);
+    }
+    return nu;
+  };
+  // Records: per group, nu -> ascending constituent tuples with dims (lazy).
+  std::vector<std::map<Key, std::map<Key, std::vector<int64_t>>>> rec(G);
+  for (int g = 0; g < G; g++) {
+    if (groups[g].size() < 2) continue;
+    for (int64_t b = 0; b < A.nblocks; b++) {
+      Key ch = sub_charges(A, b, groups[g]);
+      std::vector<int64_t> d;
+      for (int l : groups[g]) d.push_back(A.dim(b, l));
+      rec[g][nu_of(b, groups[g])].emplace(ch, d);
+    }
+  }
+  // offsets of each constituent tuple inside its fused sector, and D_nu
+  std::vector<std::map<Key, std::map<Key, int64_t>>> suboff(G);
+  std::vector<std::map<Key, int64_t>> dnu(G);
+  for (int g = 0; g < G; g++)
+    for (auto &kv : rec[g]) {
+      int64_t acc = 0;
+      for (auto &e : kv.second) {
+        suboff[g][kv.first][e.first] = acc;
+        int64_t sz = 1;
+        for (auto d : e.second) sz *= d;
+        acc += sz;
+      }
+      dnu[g][kv.first] = acc;
+    }
+  Tensor &C = p->out;
+  C = Tensor();
+  C.nsym = nsym;
+  std::memcpy(C.mod, A.mod, sizeof(C.mod));
+  std::memcpy(C.n, A.n, sizeof(C.n));
+  C.rank = G;
+  for (int g = 0; g < G; g++) {
+    C.sig[g] = A.sig[groups[g][0]];
+    if (groups[g].size() == 1) {
+      copy_fusion(A.fus[groups[g][0]].get(), C.fus[g]);
+      continue;
+    }
+    auto F = std::make_shared<Fusion>();
+    F->nlegs = (int)groups[g].size();
+    for (int j = 0; j < F->nlegs; j++) F->sig[j] = A.sig[groups[g][j]];
+    for (auto &kv : rec[g])
+      for (auto &e : kv.second) {
+        F->nu.insert(F->nu.end(), kv.first.begin(), kv.first.end());
+        F->t.insert(F->t.end(), e.first.begin(), e.first.end());
+        F->D.insert(F->D.end(), e.second.begin(), e.second.end());
+        F->nentries++;
+      }
+    C.fus[g] = F;
+  }
+  // New blocks.
+  std::map<Key, int64_t> newid;
+  std::vector<OutBlock> outb;
+  std::vector<int64_t> blk_new(A.nblocks);
+  for (int64_t b = 0; b < A.nblocks; b++) {
+    Key k;
+    std::vector<int64_t> D;
+    for (int g = 0; g < G; g++) {
+      if (groups[g].size() == 1) {
+        const int32_t *q = A.charge(b, groups[g][0]);
+        k.insert(k.end(), q, q + nsym);
+        D.push_back(A.dim(b, groups[g][0]));
+      } else {
+        Key nu = nu_of(b, groups[g]);
+        k.insert(k.end(), nu.begin(), nu.end());
+        D.push_back(dnu[g][nu]);
+      }
+    }
+    auto it = newid.find(k);
+    if (it == newid.end()) {
+      const int64_t id = (int64_t)outb.size();
+      newid[k] = id;
+      outb.push_back({k, D, id});
+      blk_new[b] = id;
+    } else {
+      blk_new[b] = it->second;
+    }
+  }
+  std::vector<OutBlock> sorted = outb;
+  std::vector<int64_t> off_of_id;
+  finalize_out(C, sorted, off_of_id);
+  // Copy jobs: old block, legs in group order -> its sub-box of the new block.
+  p->jobs.clear();
+  p->items.clear();
+  p->moved = 0;
+  for (int64_t b = 0; b < A.nblocks; b++) {
+    const OutBlock &ob = outb[blk_new[b]];
+    std::vector<int64_t> nst(G);
+    int64_t acc = 1;
+    for (int g = G - 1; g >= 0; g--) { nst[g] = acc; acc *= ob.D[g]; }
+    auto st = block_strides(A, b);
+    std::vector<Dim> dims;
+    int64_t dst_off = off_of_id[ob.id];
+    for (int g = 0; g < G; g++) {
+      const auto &grp = groups[g];
+      int64_t in = 1;
+      std::vector<int64_t> gs(grp.size());
+      for (int i = (int)grp.size() - 1; i >= 0; i--) { gs[i] = in; in *= A.dim(b, grp[i]); }
+      for (size_t i = 0; i < grp.size(); i++) dims.push_back({A.dim(b, grp[i]), st[grp[i]], gs[i] * nst[g]});
+      if (grp.size() > 1) {
+        Key nu = nu_of(b, grp);
+        dst_off += suboff[g][nu][sub_charges(A, b, grp)] * nst[g];
+      }
+    }
+    CopyJob J;
+    ytn_status s = make_job(dims, A.off[b], dst_off, J, err);
+    if (s != YTN_OK) return s;
+    p->jobs.push_back(J);
+    p->moved += A.elems(b);
+  }
+  make_items(p, 0, p->jobs.size());
+  p->items_a_begin = 0;
+  p->items_a_end = (int64_t)p->items.size();
+  p->zero_out = p->moved < C.size;
+  p->kind = Kind::Fuse;
+  p->a_size = A.size;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Unfuse
+// ---------------------------------------------------------------------------
+
+ytn_status plan_unfuse(ytn_plan_t *p, const Tensor &A, int naxes, const int *axes_in, std::string &err) {
+  std::vector<int> isun(A.rank, 0);
+  if (naxes < 1) { err = "no legs to unfuse"; return YTN_E_INVALID; }
+  for (int k = 0; k < naxes; k++) {
+    const int a = axes_in[k];
+    if (a < 0 || a >= A.rank || !A.fus[a] || isun[a]) { err = "leg is not a fused leg"; return YTN_E_INVALID; }
+    isun[a] = 1;
+  }
+  const int nsym = A.nsym;
+  Tensor &C = p->out;
+  C = Tensor();
+  C.nsym = nsym;
+  std::memcpy(C.mod, A.mod, sizeof(C.mod));
+  std::memcpy(C.n, A.n, sizeof(C.n));
+  int r = 0;
+  for (int a = 0; a < A.rank; a++) {
+    if (isun[a]) {
+      for (int j = 0; j < A.fus[a]->nlegs; j++) {
+        if (r >= YTN_MAX_RANK) { err = "output rank too large"; return YTN_E_UNSUPPORTED; }
+        C.sig[r++] = A.fus[a]->sig[j];
+      }
+    } else {
+      if (r >= YTN_MAX_RANK) { err = "output rank too large"; return YTN_E_UNSUPPORTED; }
+      copy_fusion(A.fus[a].get(), C.fus[r]);
+      C.sig[r++] = A.sig[a];
+    }
+  }
+  C.rank = r;
+  // per unfused leg: nu -> list of (charges, dims, offset)
+  struct Ent { Key ch; std::vector<int64_t> d; int64_t off; };
+  std::vector<std::map<Key, std::vector<Ent>>> ents(A.rank);
+  for (int a = 0; a < A.rank; a++) {
+    if (!isun[a]) continue;
+    const Fusion &F = *A.fus[a];
+    std::map<Key, int64_t> acc;
+    for (int64_t e = 0; e < F.nentries; e++) {
+      Key nu(&F.nu[e * nsym], &F.nu[e * nsym] + nsym);
+      Ent en;
+      en.ch.assign(&F.t[e * F.nlegs * nsym], &F.t[(e + 1) * F.nlegs * nsym]);
+      en.d.assign(&F.D[e * F.nlegs], &F.D[(e + 1) * F.nlegs]);
+      en.off = acc[nu];
+      int64_t sz = 1;
+      for (auto d : en.d) sz *= d;
+      acc[nu] += sz;
+      ents[a][nu].push_back(en);
+    }
+  }
+  std::vector<OutBlock> outb;
+  struct Src { int64_t blk; std::vector<const Ent *> pick; };
+  std::vector<Src> srcs;
+  for (int64_t b = 0; b < A.nblocks; b++) {
+    std::vector<const std::vector<Ent> *> lists(A.rank, nullptr);
+    int64_t combos = 1;
+    for (int a = 0; a < A.rank; a++) {
+      if (!isun[a]) continue;
+      const int32_t *q = A.charge(b, a);
+      auto it = ents[a].find(Key(q, q + nsym));
+      if (it == ents[a].end()) { err = "fused block charge missing from its record"; return YTN_E_INVALID; }
+      lists[a] = &it->second;
+      combos *= (int64_t)it->second.size();
+    }
+    for (int64_t cidx = 0; cidx < combos; cidx++) {
+      int64_t rem = cidx;
+      std::vector<const Ent *> pick(A.rank, nullptr);
+      for (int a = A.rank - 1; a >= 0; a--) {
+        if (!isun[a]) continue;
+        const int64_t n = (int64_t)lists[a]->size();
+        pick[a] = &(*lists[a])[rem % n];
+        rem /= n;
+      }
+      OutBlock ob;
+      for (int a = 0; a < A.rank; a++) {
+        if (isun[a]) {
+          ob.key.insert(ob.key.end(), pick[a]->ch.begin(), pick[a]->ch.end());
+          ob.D.insert(ob.D.end(), pick[a]->d.begin(), pick[a]->d.end());
+        } else {
+          const int32_t *q = A.charge(b, a);
+          ob.key.insert(ob.key.end(), q, q + nsym);
+          ob.D.push_back(A.dim(b, a));
+        }
+      }
+      ob.id = (int64_t)srcs.size();
+      outb.push_back(ob);
+      srcs.push_back({b, pick});
+    }
+  }
+  std::vector<OutBlock> sorted = outb;
+  std::vector<int64_t> off_of_id;
+  finalize_out(C, sorted, off_of_id);
+  for (size_t i = 1; i < sorted.size(); i++)
+    if (!(sorted[i - 1].key < sorted[i].key)) { err = "unfused blocks collide"; return YTN_E_INVALID; }
+  p->jobs.clear();
+  p->items.clear();
+  p->moved = 0;
+  for (size_t id = 0; id < srcs.size(); id++) {
+    const Src &sr = srcs[id];
+    const OutBlock &ob = outb[id];
+    auto st = block_strides(A, sr.blk);
+    std::vector<int64_t> dstr(ob.D.size());
+    int64_t acc = 1;
+    for (int i = (int)ob.D.size() - 1; i >= 0; i--) { dstr[i] = acc; acc *= ob.D[i]; }
+    std::vector<Dim> dims;
+    int64_t src_off = A.off[sr.blk];
+    int r2 = 0;
+    for (int a = 0; a < A.rank; a++) {
+      if (isun[a]) {
+        const Ent *e = sr.pick[a];
+        src_off += e->off * st[a];
+        int64_t in = 1;
+        std::vector<int64_t> gs(e->d.size());
+        for (int i = (int)e->d.size() - 1; i >= 0; i--) { gs[i] = in; in *= e->d[i]; }
+        for (size_t i = 0; i < e->d.size(); i++, r2++) dims.push_back({e->d[i], gs[i] * st[a], dstr[r2]});
+      } else {
+        dims.push_back({A.dim(sr.blk, a), st[a], dstr[r2]});
+        r2++;
+      }
+    }
+    CopyJob J;
+    ytn_status s = make_job(dims, src_off, off_of_id[ob.id], J, err);
+    if (s != YTN_OK) return s;
+    p->jobs.push_back(J);
+    p->moved += acc;
+  }
+  make_items(p, 0, p->jobs.size());
+  p->items_a_begin = 0;
+  p->items_a_end = (int64_t)p->items.size();
+  p->zero_out = false;
+  p->kind = Kind::Unfuse;
+  p->a_size = A.size;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Trace
+// ---------------------------------------------------------------------------
+
+ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1_in, const int *ax2_in,
+                      std::string &err) {
+  if (naxes < 1 || 2 * naxes > A.rank) { err = "bad number of traced pairs"; return YTN_E_INVALID; }
+  std::vector<int> ax1(ax1_in, ax1_in + naxes), ax2(ax2_in, ax2_in + naxes);
+  std::vector<int> used(A.rank, 0);
+  for (int k = 0; k < naxes; k++) {
+    for (int a : {ax1[k], ax2[k]}) {
+      if (a < 0 || a >= A.rank || used[a]) { err = "trace axes must be distinct legs"; return YTN_E_INVALID; }
+      used[a] = 1;
+    }
+  }
+  for (int k = 0; k < naxes; k++) {
+    ytn_status st = check_pair(A, ax1[k], A, ax2[k], err);
+    if (st != YTN_OK) return st;
+  }
+  std::vector<int> rest;
+  for (int i = 0; i < A.rank; i++)
+    if (!used[i]) rest.push_back(i);
+  if ((int)rest.size() > kMaxCopyDims || naxes > kMaxCopyDims) { err = "trace needs more than 8 dims"; return YTN_E_UNSUPPORTED; }
+  const int nsym = A.nsym;
+  Tensor &C = p->out;
+  C = Tensor();
+  C.nsym = nsym;
+  std::memcpy(C.mod, A.mod, sizeof(C.mod));
+  std::memcpy(C.n, A.n, sizeof(C.n));
+  C.rank = (int)rest.size();
+  for (size_t i = 0; i < rest.size(); i++) {
+    C.sig[i] = A.sig[rest[i]];
+    copy_fusion(A.fus[rest[i]].get(), C.fus[i]);
+  }
+  std::map<Key, std::vector<int64_t>> contrib;   // out key -> contributing blocks (canonical order)
+  std::map<Key, std::vector<int64_t>> outdims;
+  for (int64_t b = 0; b < A.nblocks; b++) {
+    bool ok = true;
+    for (int k = 0; k < naxes && ok; k++) {
+      const int32_t *q1 = A.charge(b, ax1[k]), *q2 = A.charge(b, ax2[k]);
+      ok = std::equal(q1, q1 + nsym, q2);
+      if (ok && A.dim(b, ax1[k]) != A.dim(b, ax2[k])) {
+        err = "traced legs have different dimensions for one charge";
+        return YTN_E_DIM_MISMATCH;
+      }
+    }
+    if (!ok) continue;
+    Key k = sub_charges(A, b, rest);
+    contrib[k].push_back(b);
+    std::vector<int64_t> d;
+    for (int l : rest) d.push_back(A.dim(b, l));
+    outdims[k] = d;
+  }
+  std::vector<OutBlock> outb;
+  for (auto &kv : contrib) outb.push_back({kv.first, outdims[kv.first], (int64_t)outb.size()});
+  std::vector<OutBlock> sorted = outb;
+  std::vector<int64_t> off_of_id;
+  finalize_out(C, sorted, off_of_id);
+  p->tr_out.clear();
+  p->tr_contrib.clear();
+  int64_t id = 0;
+  for (auto &kv : contrib) {
+    TraceOut to{};
+    to.dst_off = off_of_id[id];
+    const auto &d = outdims[kv.first];
+    int64_t nrest = 1;
+    for (auto x : d) nrest *= x;
+    if (nrest > INT32_MAX) { err = "trace output block too large"; return YTN_E_UNSUPPORTED; }
+    to.nrest = (int32_t)nrest;
+    to.nrd = (int32_t)d.size();
+    for (size_t i = 0; i < d.size(); i++) to.rext[i] = (int32_t)d[i];
+    to.first = (int32_t)p->tr_contrib.size();
+    to.ncontrib = (int32_t)kv.second.size();
+    for (int64_t b : kv.second) {
+      TraceContrib tc{};
+      tc.src_off = A.off[b];
+      auto st = block_strides(A, b);
+      for (size_t i = 0; i < rest.size(); i++) tc.rstr[i] = (int32_t)st[rest[i]];
+      tc.ndiag = naxes;
+      for (int k = 0; k < naxes; k++) {
+        tc.dext[k] = (int32_t)A.dim(b, ax1[k]);
+        tc.dstr[k] = (int32_t)(st[ax1[k]] + st[ax2[k]]);
+      }
+      p->tr_contrib.push_back(tc);
+    }
+    p->tr_out.push_back(to);
+    id++;
+  }
+  p->kind = Kind::Trace;
+  p->a_size = A.size;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cache key and output view
+// ---------------------------------------------------------------------------
+
+static void put(std::string &s, const void *p, size_t n) { s.append((const char *)p, n); }
+
+static void key_struct(std::string &s, const ytn_struct *t) {
+  if (!t) { s += "N"; return; }
+  put(s, &t->sym, sizeof(t->sym));
+  put(s, &t->rank, sizeof(t->rank));
+  put(s, t->sig, sizeof(t->sig));
+  put(s, t->n, sizeof(t->n));
+  put(s, &t->nblocks, sizeof(t->nblocks));
+  put(s, &t->size, sizeof(t->size));
+  const int nsym = t->sym.nsym > 0 && t->sym.nsym <= YTN_MAX_SYM ? t->sym.nsym : 0;
+  const int rank = t->rank > 0 && t->rank <= YTN_MAX_RANK ? t->rank : 0;
+  if (t->t) put(s, t->t, (size_t)t->nblocks * rank * nsym * sizeof(int32_t));
+  if (t->D) put(s, t->D, (size_t)t->nblocks * rank * sizeof(int64_t));
+  s += t->off ? "O" : "P";
+  if (t->off) put(s, t->off, (size_t)t->nblocks * sizeof(int64_t));
+  for (int i = 0; i < rank; i++) {
+    const ytn_fusion *f = t->fus[i];
+    if (!f) { s += "-"; continue; }
+    s += "F";
+    put(s, &f->nlegs, sizeof(f->nlegs));
+    put(s, f->sig, sizeof(f->sig));
+    put(s, &f->nentries, sizeof(f->nentries));
+    const int m = f->nlegs > 0 && f->nlegs <= YTN_MAX_RANK ? f->nlegs : 0;
+    if (f->nu) put(s, f->nu, (size_t)f->nentries * nsym * sizeof(int32_t));
+    if (f->t) put(s, f->t, (size_t)f->nentries * m * nsym * sizeof(int32_t));
+    if (f->D) put(s, f->D, (size_t)f->nentries * m * sizeof(int64_t));
+  }
+}
+
+std::string plan_key(const ytn_op *op) {
+  std::string s;
+  put(s, &op->kind, sizeof(op->kind));
+  put(s, &op->naxes, sizeof(op->naxes));
+  put(s, op->axa, sizeof(op->axa));
+  put(s, op->axb, sizeof(op->axb));
+  put(s, &op->ngroups, sizeof(op->ngroups));
+  put(s, op->group_size, sizeof(op->group_size));
+  put(s, op->order, sizeof(op->order));
+  key_struct(s, op->a);
+  key_struct(s, op->b);
+  return s;
+}
+
+void finish_output_view(ytn_plan_t *p) {
+  Tensor &C = p->out;
+  ytn_struct &v = p->out_view;
+  std::memset(&v, 0, sizeof(v));
+  v.sym.nsym = C.nsym;
+  for (int c = 0; c < YTN_MAX_SYM; c++) v.sym.mod[c] = C.mod[c];
+  v.rank = C.rank;
+  for (int i = 0; i < C.rank; i++) v.sig[i] = (int8_t)C.sig[i];
+  for (int c = 0; c < YTN_MAX_SYM; c++) v.n[c] = C.n[c];
+  v.nblocks = C.nblocks;
+  v.t = C.t.data();
+  v.D = C.D.data();
+  v.off = C.off.data();
+  v.size = C.size;
+  p->out_fus_view.assign(C.rank, ytn_fusion{});
+  for (int i = 0; i < C.rank; i++) {
+    if (!C.fus[i]) continue;
+    ytn_fusion &f = p->out_fus_view[i];
+    const Fusion &F = *C.fus[i];
+    f.nlegs = F.nlegs;
+    for (int j = 0; j < F.nlegs; j++) f.sig[j] = (int8_t)F.sig[j];
+    f.nentries = F.nentries;
+    f.nu = F.nu.data();
+    f.t = F.t.data();
+    f.D = F.D.data();
+    v.fus[i] = &f;
+  }
+}
+
+}  // namespace ytn

@@ -1,0 +1,219 @@
+// Internal types shared by the host planner (planner.cpp) and the device code
+// (api.cu, copy_kernels.cu, gemm_fp64.cu, gemm_split.cu). Not part of the ABI.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ytn.h"
+
+namespace ytn {
+
+// ----------------------------------------------------------------------------
+// Device job tables
+// ----------------------------------------------------------------------------
+
+constexpr int kMaxCopyDims = 8;
+
+// One block moved between two layouts (gather into a sector matrix, scatter out
+// of one, or fuse / unfuse). Dimensions are listed outer -> inner in
+// destination order; the innermost has destination stride 1.
+//   mode 0 ("rows"): rows of ext[nd-1] elements, source stride sst[nd-1]
+//                    (1 for a contiguous copy);
+//   mode 1 ("tile"): 32x32 shared-memory transpose between the destination-
+//                    contiguous dim nd-1 and the source-contiguous dim p.
+struct CopyJob {
+  int64_t src_off;
+  int64_t dst_off;
+  int32_t nd;
+  int32_t mode;
+  int32_t p;
+  int32_t nchunk;   // mode 0: column chunks per row (rows longer than kRowChunk)
+  int32_t ext[kMaxCopyDims];
+  int32_t sst[kMaxCopyDims];
+  int32_t dst[kMaxCopyDims];
+};
+static_assert(sizeof(CopyJob) == 128, "CopyJob layout");
+
+constexpr int kRowChunk = 2048;   // mode-0 column chunk
+constexpr int kTile = 32;         // mode-1 tile edge
+
+// A contiguous range of work units of one job, processed by one CTA.
+// Units: mode 0 = (row, column chunk) pairs; mode 1 = 32x32 tiles.
+struct CopyItem {
+  int32_t job;
+  int32_t count;
+  int64_t begin;
+};
+static_assert(sizeof(CopyItem) == 16, "CopyItem layout");
+
+// One charge sector of a contraction: C_q (M x N, row-major, ldc = N) =
+// A_q (M x K) B_q (K x N). A_q is stored K-major (M rows of K, lda = K) when
+// a_kmajor, else M-major (K rows of M, lda = M); B_q is stored K-major
+// (N rows of K, ldb = K) when b_kmajor, else N-major (K rows of N, ldb = N).
+struct SectorDev {
+  int64_t a_off, b_off, c_off;     // element offsets in the FP64 workspaces
+  int32_t M, N, K;
+  int32_t a_kmajor, b_kmajor;
+  int32_t pad;
+};
+static_assert(sizeof(SectorDev) == 48, "SectorDev layout");
+
+// One output tile of the grouped FP64 GEMM.
+struct GemmTile {
+  int32_t sector;
+  int32_t mt, nt;
+  int32_t pad;
+};
+
+// Trace: one output block, fed by ncontrib contributing input blocks.
+struct TraceOut {
+  int64_t dst_off;
+  int32_t nrest;          // elements of the output block
+  int32_t nrd;            // rest dims
+  int32_t first, ncontrib;
+  int32_t rext[kMaxCopyDims];
+};
+struct TraceContrib {
+  int64_t src_off;
+  int32_t ndiag;          // paired dims
+  int32_t pad;
+  int32_t rstr[kMaxCopyDims];   // input strides of the rest dims
+  int32_t dext[kMaxCopyDims];   // extents of the paired dims
+  int32_t dstr[kMaxCopyDims];   // sum of the two strides of each pair
+};
+
+// ----------------------------------------------------------------------------
+// Host-side structures
+// ----------------------------------------------------------------------------
+
+struct Fusion {
+  int nlegs = 0;
+  int sig[YTN_MAX_RANK] = {0};
+  int64_t nentries = 0;
+  std::vector<int32_t> nu;   // [nentries][nsym]
+  std::vector<int32_t> t;    // [nentries][nlegs][nsym]
+  std::vector<int64_t> D;    // [nentries][nlegs]
+};
+
+struct Tensor {
+  int nsym = 0;
+  int mod[YTN_MAX_SYM] = {0};
+  int rank = 0;
+  int sig[YTN_MAX_RANK] = {0};
+  int n[YTN_MAX_SYM] = {0};
+  int64_t nblocks = 0;
+  std::vector<int32_t> t;    // [nblocks][rank][nsym]
+  std::vector<int64_t> D;    // [nblocks][rank]
+  std::vector<int64_t> off;  // [nblocks]
+  int64_t size = 0;
+  std::shared_ptr<Fusion> fus[YTN_MAX_RANK];
+
+  const int32_t *charge(int64_t b, int leg) const { return &t[((size_t)b * rank + leg) * nsym]; }
+  int64_t dim(int64_t b, int leg) const { return D[(size_t)b * rank + leg]; }
+  int64_t elems(int64_t b) const {
+    int64_t e = 1;
+    for (int i = 0; i < rank; i++) e *= dim(b, i);
+    return e;
+  }
+};
+
+struct HostSector {
+  int64_t M = 0, N = 0, K = 0;
+  int64_t a_off = 0, b_off = 0, c_off = 0;
+};
+
+enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4 };
+
+struct Plan;
+
+}  // namespace ytn
+
+struct ytn_ctx {
+  int device = 0;
+  int *status_dev = nullptr;   // device status word (bounded waits report here)
+  std::mutex mu;
+  std::unordered_map<std::string, ytn_plan_t *> cache;
+  // phase timing: a pool of CUDA events (cudaEvent_t stored as void*) and the
+  // (phase, start-event index) pairs recorded since the last read
+  bool prof = false;
+  std::vector<void *> ev_pool;
+  size_t ev_next = 0;
+  std::vector<std::pair<int, int>> pending;
+  int64_t dropped = 0;
+  std::mutex prof_mu;
+};
+
+struct ytn_plan_s {
+  std::atomic<int> refs{1};
+  ytn_ctx *ctx = nullptr;
+  ytn::Kind kind = ytn::Kind::Tensordot;
+  std::string key;
+
+  // input sizes and output structure (owned storage + ABI view)
+  int64_t a_size = 0, b_size = 0;
+  ytn::Tensor out;
+  ytn_struct out_view{};
+  std::vector<ytn_fusion> out_fus_view;
+
+  // tensordot
+  std::vector<ytn::HostSector> sectors;
+  std::vector<ytn::SectorDev> sectors_dev;
+  std::vector<ytn::GemmTile> tiles;
+  bool zero_a = false, zero_b = false;
+  bool a_kmajor = true, b_kmajor = false;
+  int64_t a_elems = 0, b_elems = 0, c_elems = 0;
+  int64_t max_m = 0, max_n = 0, max_k = 0;
+  double flops = 0;
+
+  // data movers: all copy jobs, and item ranges per phase
+  std::vector<ytn::CopyJob> jobs;
+  std::vector<ytn::CopyItem> items;
+  int64_t items_a_begin = 0, items_a_end = 0;   // gather A (tensordot) or the single phase
+  int64_t items_b_begin = 0, items_b_end = 0;   // gather B
+  int64_t items_c_begin = 0, items_c_end = 0;   // scatter C
+  bool zero_out = false;                        // fuse: output needs zero fill
+  int64_t moved = 0;
+
+  // trace
+  std::vector<ytn::TraceOut> tr_out;
+  std::vector<ytn::TraceContrib> tr_contrib;
+
+  // device copies of the tables (one allocation)
+  void *dev = nullptr;
+  size_t dev_bytes = 0;
+  const ytn::CopyJob *d_jobs = nullptr;
+  const ytn::CopyItem *d_items = nullptr;
+  const ytn::SectorDev *d_sectors = nullptr;
+  const ytn::GemmTile *d_tiles = nullptr;
+  const ytn::TraceOut *d_tr_out = nullptr;
+  const ytn::TraceContrib *d_tr_contrib = nullptr;
+
+  // split-precision tables (built on first use, see gemm_split.cu)
+  std::shared_ptr<void> split;
+};
+
+namespace ytn {
+
+// planner.cpp
+ytn_status load_struct(const ytn_struct *s, Tensor &T, std::string &err);
+ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int naxes,
+                          const int *axa, const int *axb, std::string &err);
+ytn_status plan_fuse(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size,
+                     const int *order, std::string &err);
+ytn_status plan_unfuse(ytn_plan_t *p, const Tensor &A, int naxes, const int *axes,
+                       std::string &err);
+ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1,
+                      const int *ax2, std::string &err);
+std::string plan_key(const ytn_op *op);
+void finish_output_view(ytn_plan_t *p);
+
+// error reporting (api.cu)
+ytn_status fail(ytn_status st, const std::string &msg);
+
+}  // namespace ytn

@@ -1,0 +1,356 @@
+"""Python binding of the C ABI in ``include/ytn.h`` (ctypes; argument marshalling only).
+
+Every entry point keeps the C name and forwards to ``libytn.so``; all structure work
+happens in the library's planner and all data work in its CUDA kernels. Device
+buffers are passed as torch CUDA tensors (or raw integer device pointers); host
+block structures as the plain-array tensor records of the ``workloads`` module:
+``{"mods", "sig", "n", "t": int32[nb, rank, nsym], "D": int64[nb, rank],
+"fus": optional per-leg fusion records}``.
+
+If the shared library has not been built, importing this module raises: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libytn.so")
+
+MAX_RANK = 16
+MAX_SYM = 4
+
+YTN_OK = 0
+STATUS = {
+    0: "YTN_OK", 1: "YTN_E_INVALID", 2: "YTN_E_SIGNATURE", 3: "YTN_E_DIM_MISMATCH",
+    4: "YTN_E_FUSION_MISMATCH", 5: "YTN_E_NOMEM", 6: "YTN_E_CUDA", 7: "YTN_E_TIMEOUT",
+    8: "YTN_E_UNSUPPORTED", 9: "YTN_E_TOLERANCE", 10: "YTN_E_CHARGE", 11: "YTN_E_WORKSPACE",
+}
+YTN_FP64 = 0
+YTN_SPLIT_BF16 = 1
+YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE = 1, 2, 3, 4
+
+
+class YtnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class ytn_sym(C.Structure):
+    _fields_ = [("nsym", C.c_int32), ("mod", C.c_int32 * MAX_SYM)]
+
+
+class ytn_fusion(C.Structure):
+    _fields_ = [("nlegs", C.c_int32), ("sig", C.c_int8 * MAX_RANK), ("nentries", C.c_int64),
+                ("nu", C.POINTER(C.c_int32)), ("t", C.POINTER(C.c_int32)),
+                ("D", C.POINTER(C.c_int64))]
+
+
+class ytn_struct(C.Structure):
+    _fields_ = [("sym", ytn_sym), ("rank", C.c_int32), ("sig", C.c_int8 * MAX_RANK),
+                ("n", C.c_int32 * MAX_SYM), ("nblocks", C.c_int64),
+                ("t", C.POINTER(C.c_int32)), ("D", C.POINTER(C.c_int64)),
+                ("off", C.POINTER(C.c_int64)), ("size", C.c_int64),
+                ("fus", C.POINTER(ytn_fusion) * MAX_RANK)]
+
+
+class ytn_op(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.POINTER(ytn_struct)), ("b", C.POINTER(ytn_struct)),
+                ("naxes", C.c_int32), ("axa", C.c_int32 * MAX_RANK), ("axb", C.c_int32 * MAX_RANK),
+                ("ngroups", C.c_int32), ("group_size", C.c_int32 * MAX_RANK),
+                ("order", C.c_int32 * MAX_RANK)]
+
+
+class ytn_plan_info(C.Structure):
+    _fields_ = [("useful_flops", C.c_double), ("nsectors", C.c_int64), ("max_m", C.c_int64),
+                ("max_n", C.c_int64), ("max_k", C.c_int64), ("a_elems", C.c_int64),
+                ("b_elems", C.c_int64), ("c_elems", C.c_int64), ("moved_elems", C.c_int64),
+                ("out_size", C.c_int64), ("njobs", C.c_int64)]
+
+
+NPHASES = 8
+PHASES = {0: "gather_a", 1: "gather_b", 2: "gemm", 3: "scatter", 4: "split", 5: "move"}
+
+
+class ytn_profile(C.Structure):
+    _fields_ = [("calls", C.c_int64 * NPHASES), ("ms", C.c_double * NPHASES), ("dropped", C.c_int64)]
+
+
+class ytn_result(C.Structure):
+    _fields_ = [("useful_flops", C.c_double), ("precision", C.c_int32), ("slices", C.c_int32),
+                ("err_bound", C.c_double)]
+
+
+# entry points declared in include/ytn.h
+SYMBOLS = {
+    "ytn_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "ytn_ctx_destroy": (None, [C.c_void_p]),
+    "ytn_plan": (C.c_int, [C.c_void_p, C.POINTER(ytn_op), C.POINTER(C.c_void_p)]),
+    "ytn_plan_output": (C.POINTER(ytn_struct), [C.c_void_p]),
+    "ytn_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(ytn_plan_info)]),
+    "ytn_plan_release": (None, [C.c_void_p]),
+    "ytn_workspace_size": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
+    "ytn_tensordot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                C.c_void_p, C.c_size_t, C.POINTER(ytn_result), C.c_void_p]),
+    "ytn_fuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ytn_unfuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ytn_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ytn_sync": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "ytn_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "ytn_profile_read": (C.c_int, [C.c_void_p, C.POINTER(ytn_profile)]),
+    "ytn_last_error": (C.c_char_p, []),
+    "ytn_version": (C.c_char_p, []),
+}
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libytn.so is not built ({path}); run paper_2405_12196_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SYMBOLS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(status):
+    if status != YTN_OK:
+        raise YtnError(status, _lib.ytn_last_error().decode())
+
+
+def _ptr(x):
+    """Device (or host) address of a torch tensor, a numpy array or an integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------ structures
+
+class Struct:
+    """A ytn_struct built from a tensor record; owns the arrays it points to."""
+
+    def __init__(self, rec):
+        mods = tuple(rec["mods"])
+        t = np.ascontiguousarray(rec["t"], dtype=np.int32)
+        D = np.ascontiguousarray(rec["D"], dtype=np.int64)
+        nb = t.shape[0]
+        rank = len(rec["sig"])
+        self._keep = [t, D]
+        s = ytn_struct()
+        s.sym.nsym = len(mods)
+        for c, m in enumerate(mods):
+            s.sym.mod[c] = m
+        s.rank = rank
+        for i, sg in enumerate(rec["sig"]):
+            s.sig[i] = sg
+        for c, q in enumerate(rec["n"]):
+            s.n[c] = q
+        s.nblocks = nb
+        s.t = t.ctypes.data_as(C.POINTER(C.c_int32))
+        s.D = D.ctypes.data_as(C.POINTER(C.c_int64))
+        if rec.get("off") is not None:
+            off = np.ascontiguousarray(rec["off"], dtype=np.int64)
+            self._keep.append(off)
+            s.off = off.ctypes.data_as(C.POINTER(C.c_int64))
+        sizes = np.prod(D, axis=1) if nb else np.zeros(0, np.int64)
+        s.size = int(rec.get("size", int(sizes.sum()) if nb else 0))
+        fus = rec.get("fus")
+        self._fus = []
+        if fus is not None:
+            for i, f in enumerate(fus):
+                if f is None:
+                    continue
+                nu = np.ascontiguousarray(f["nu"], dtype=np.int32)
+                ft = np.ascontiguousarray(f["t"], dtype=np.int32)
+                fD = np.ascontiguousarray(f["D"], dtype=np.int64)
+                fz = ytn_fusion()
+                fz.nlegs = len(f["sig"])
+                for j, sg in enumerate(f["sig"]):
+                    fz.sig[j] = sg
+                fz.nentries = nu.shape[0]
+                fz.nu = nu.ctypes.data_as(C.POINTER(C.c_int32))
+                fz.t = ft.ctypes.data_as(C.POINTER(C.c_int32))
+                fz.D = fD.ctypes.data_as(C.POINTER(C.c_int64))
+                self._keep += [nu, ft, fD]
+                self._fus.append(fz)
+                s.fus[i] = C.pointer(fz)
+        self.c = s
+
+    @property
+    def size(self):
+        return self.c.size
+
+
+def struct_to_record(p):
+    """Copy a library-owned ytn_struct into a tensor record (numpy arrays)."""
+    s = p.contents
+    nsym, rank, nb = s.sym.nsym, s.rank, s.nblocks
+    t = np.ctypeslib.as_array(s.t, shape=(nb * rank * nsym,)).copy().reshape(nb, rank, nsym) \
+        if nb and rank else np.zeros((nb, rank, nsym), np.int32)
+    D = np.ctypeslib.as_array(s.D, shape=(nb * rank,)).copy().reshape(nb, rank) \
+        if nb and rank else np.zeros((nb, rank), np.int64)
+    off = np.ctypeslib.as_array(s.off, shape=(nb,)).copy() if nb else np.zeros(0, np.int64)
+    fus = []
+    for i in range(rank):
+        if not s.fus[i]:
+            fus.append(None)
+            continue
+        f = s.fus[i].contents
+        m, ne = f.nlegs, f.nentries
+        fus.append({
+            "sig": tuple(int(f.sig[j]) for j in range(m)),
+            "nu": np.ctypeslib.as_array(f.nu, shape=(ne * nsym,)).copy().reshape(ne, nsym),
+            "t": np.ctypeslib.as_array(f.t, shape=(ne * m * nsym,)).copy().reshape(ne, m, nsym),
+            "D": np.ctypeslib.as_array(f.D, shape=(ne * m,)).copy().reshape(ne, m),
+        })
+    return {"mods": tuple(int(s.sym.mod[c]) for c in range(nsym)),
+            "sig": tuple(int(s.sig[i]) for i in range(rank)),
+            "n": tuple(int(s.n[c]) for c in range(nsym)), "t": t, "D": D, "off": off,
+            "size": int(s.size), "fus": fus if any(f is not None for f in fus) else None}
+
+
+# ------------------------------------------------------------------ entry points
+
+class Ctx:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        h, self.handle = self.handle, None
+        if h:
+            _lib.ytn_ctx_destroy(h)
+
+
+class Plan:
+    def __init__(self, ctx, handle, keep):
+        self.ctx = ctx
+        self.handle = handle
+        self._keep = keep
+        self.out = struct_to_record(_lib.ytn_plan_output(handle))
+        info = ytn_plan_info()
+        _check(_lib.ytn_plan_get_info(handle, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in ytn_plan_info._fields_}
+
+    def release(self):
+        h, self.handle = self.handle, None
+        if h and self.ctx.handle:
+            _lib.ytn_plan_release(h)
+
+    def __del__(self):
+        self.release()
+
+
+def ytn_version():
+    return _lib.ytn_version().decode()
+
+
+def ytn_ctx_create(device=0):
+    h = C.c_void_p()
+    _check(_lib.ytn_ctx_create(C.byref(h), int(device)))
+    return Ctx(h.value)
+
+
+def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None):
+    """Plan an operation. ``a``/``b``: tensor records. ``kind``: one of YTN_OP_*.
+    TENSORDOT: pairs (axa[k], axb[k]); FUSE: ``groups`` (list of leg tuples);
+    UNFUSE: legs ``axa``; TRACE: pairs (axa[k], axb[k]) of ``a``."""
+    sa = Struct(a)
+    sb = Struct(b) if b is not None else None
+    op = ytn_op()
+    op.kind = kind
+    op.a = C.pointer(sa.c)
+    op.b = C.pointer(sb.c) if sb is not None else None
+    op.naxes = len(axa)
+    for k, x in enumerate(axa):
+        op.axa[k] = x
+    for k, x in enumerate(axb):
+        op.axb[k] = x
+    if groups is not None:
+        gs = [tuple(g) if isinstance(g, (tuple, list)) else (g,) for g in groups]
+        op.ngroups = len(gs)
+        flat = [x for g in gs for x in g]
+        for k, g in enumerate(gs):
+            op.group_size[k] = len(g)
+        for k, x in enumerate(flat):
+            op.order[k] = x
+    h = C.c_void_p()
+    _check(_lib.ytn_plan(ctx.handle, C.byref(op), C.byref(h)))
+    return Plan(ctx, h.value, (sa, sb))
+
+
+def ytn_workspace_size(plan, prec=YTN_FP64, rtol=0.0):
+    n = C.c_size_t()
+    _check(_lib.ytn_workspace_size(plan.handle, prec, float(rtol), C.byref(n)))
+    return n.value
+
+
+def ytn_tensordot(plan, a, b, c, prec=YTN_FP64, rtol=0.0, workspace=None, workspace_bytes=None,
+                  stream=None):
+    res = ytn_result()
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.ytn_tensordot(plan.handle, _ptr(a), _ptr(b), _ptr(c), prec, float(rtol),
+                              _ptr(workspace), int(workspace_bytes), C.byref(res), _stream(stream)))
+    return {"useful_flops": res.useful_flops, "precision": res.precision, "slices": res.slices,
+            "err_bound": res.err_bound}
+
+
+def ytn_fuse(plan, a, out, stream=None):
+    _check(_lib.ytn_fuse(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ytn_unfuse(plan, a, out, stream=None):
+    _check(_lib.ytn_unfuse(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ytn_trace(plan, a, out, stream=None):
+    _check(_lib.ytn_trace(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ytn_sync(ctx, stream=None, timeout_ms=-1):
+    _check(_lib.ytn_sync(ctx.handle, _stream(stream), int(timeout_ms)))
+
+
+def ytn_profile_enable(ctx, enable=True):
+    _check(_lib.ytn_profile_enable(ctx.handle, 1 if enable else 0))
+
+
+def ytn_profile_read(ctx):
+    """Per-phase {name: (calls, total ms)} recorded since the last read, plus 'dropped'."""
+    p = ytn_profile()
+    _check(_lib.ytn_profile_read(ctx.handle, C.byref(p)))
+    out = {PHASES.get(i, str(i)): (int(p.calls[i]), float(p.ms[i])) for i in range(NPHASES) if p.calls[i]}
+    out["dropped"] = int(p.dropped)
+    return out
+
+
+def available_precisions():
+    """Precisions this build of the library executes."""
+    out = [YTN_FP64]
+    if hasattr(_lib, "ytn_split_available") and _lib.ytn_split_available():
+        out.append(YTN_SPLIT_BF16)
+    return out

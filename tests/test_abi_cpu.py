@@ -1,0 +1,172 @@
+"""CPU checks of the C ABI: the library loads and exports every entry point declared
+in include/ytn.h, and the host planner's structures (output blocks, offsets, fusion
+records, sizes) equal the oracle's bit for bit. No device work: a host-only context
+(device < 0) plans without uploading."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import random_legs, random_pair
+from paper_2405_12196_gb300 import ytn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "ytn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ytn_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_header_function():
+    names = header_functions()
+    assert "ytn_tensordot" in names and "ytn_plan" in names
+    lib = ytn.load_library()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(ytn.SYMBOLS), "binding and header declare different entry points"
+    assert "sm_103a" in ytn.ytn_version()
+
+
+@pytest.fixture(scope="module")
+def hctx():
+    return ytn.ytn_ctx_create(-1)
+
+
+def same_structure(rec, ref):
+    """Compare a library output record with an oracle record, bit for bit."""
+    assert tuple(rec["mods"]) == tuple(ref["mods"])
+    assert tuple(rec["sig"]) == tuple(ref["sig"])
+    assert tuple(rec["n"]) == tuple(ref["n"])
+    np.testing.assert_array_equal(rec["t"], ref["t"].reshape(rec["t"].shape))
+    np.testing.assert_array_equal(rec["D"], ref["D"].reshape(rec["D"].shape))
+    np.testing.assert_array_equal(rec["off"], W.block_offsets(ref["D"]))
+    assert rec["size"] == ref["data"].size
+    rf, ff = ref.get("fus"), rec.get("fus")
+    if rf is None:
+        assert ff is None
+    else:
+        for a, b in zip(ff, rf):
+            assert (a is None) == (b is None)
+            if a is not None:
+                assert tuple(a["sig"]) == tuple(b["sig"])
+                for k in ("nu", "t", "D"):
+                    np.testing.assert_array_equal(a[k], b[k])
+
+
+SYMS = {"U1": (0,), "Z2": (2,), "Z3": (3,), "U1xU1": (0, 0)}
+
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(10))
+def test_tensordot_structure_matches_oracle(hctx, sym, case):
+    mods = SYMS[sym]
+    rng = np.random.default_rng(7000 + 31 * case + len(sym))
+    rankA, rankB = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+    ncon = int(rng.integers(0, min(rankA, rankB) + 1))
+    A, B, axa, axb, _, _ = random_pair(rng, mods, rankA, rankB, ncon)
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    oA, oB = O.from_record(A), O.from_record(B)
+    ref = O.to_record(O.tensordot(oA, oB, axa, axb))
+    same_structure(plan.out, ref)
+    assert plan.info["useful_flops"] == O.useful_flops(oA, oB, axa, axb)
+
+
+def test_config1_plan_counts(hctx):
+    cfg = W.config1()
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    assert plan.info["nsectors"] == 5
+    assert plan.out["t"].shape[0] == 14 and plan.out["size"] == 458
+    assert plan.info["useful_flops"] == 5640
+    assert (plan.info["max_m"], plan.info["max_n"], plan.info["max_k"]) == (12, 12, 8)
+
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(6))
+def test_fuse_unfuse_structure_matches_oracle(hctx, sym, case):
+    mods = SYMS[sym]
+    rng = np.random.default_rng(8100 + case)
+    rank = int(rng.integers(2, 6))
+    legs = random_legs(rng, mods, rank)
+    rec = W.random_tensor(mods, legs, tuple([0] * len(mods)), 300 + case)
+    if rec["t"].shape[0] == 0:
+        return
+    perm = [int(a) for a in rng.permutation(rank)]
+    cut = int(rng.integers(1, rank))
+    groups = (tuple(perm[:cut]), tuple(perm[cut:]))
+    T = O.from_record(rec)
+    F = O.fuse(T, groups)
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_FUSE, rec, groups=groups)
+    same_structure(plan.out, O.to_record(F))
+    fused_legs = [i for i, g in enumerate(groups) if len(g) > 1]
+    U = O.unfuse(F, fused_legs)
+    uplan = ytn.ytn_plan(hctx, ytn.YTN_OP_UNFUSE, plan.out, axa=fused_legs)
+    same_structure(uplan.out, O.to_record(U))
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_trace_structure_matches_oracle(hctx, case):
+    rng = np.random.default_rng(9100 + case)
+    mods = [(0,), (2,), (0, 0), (3,)][case % 4]
+    base = random_legs(rng, mods, 2)
+    other = random_legs(rng, mods, int(rng.integers(0, 3)))
+    legs = [base[0], base[1], base[0].conj(), base[1].conj()] + other
+    npair = int(rng.integers(1, 3))
+    ax1, ax2 = (0, 1)[:npair], (2, 3)[:npair]
+    rec = W.random_tensor(mods, legs, tuple([0] * len(mods)), 60 + case)
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TRACE, rec, axa=ax1, axb=ax2)
+    same_structure(plan.out, O.to_record(O.trace(O.from_record(rec), ax1, ax2)))
+
+
+def test_errors_are_status_codes(hctx):
+    l = W.Leg(1, [(0,), (1,)], [2, 3])
+    A = W.random_tensor((0,), [l, l.conj()], (0,), 1)
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, A, A, (0,), (0,))
+    assert e.value.name == "YTN_E_SIGNATURE"
+    lb = W.Leg(-1, [(0,), (1,)], [2, 4])
+    B = W.random_tensor((0,), [lb, W.Leg(1, [(0,), (1,)], [2, 4])], (0,), 2)
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, A, B, (1,), (1,))
+    assert e.value.name == "YTN_E_DIM_MISMATCH"
+    bad = dict(A)
+    bad["t"] = A["t"].copy()
+    bad["t"][0, 0, 0] = 5
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, bad, A, (1,), (0,))
+    assert e.value.name in ("YTN_E_CHARGE", "YTN_E_INVALID")
+    unsorted = dict(A)
+    unsorted["t"] = A["t"][::-1].copy()
+    unsorted["D"] = A["D"][::-1].copy()
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, unsorted, A, (1,), (0,))
+    assert e.value.name == "YTN_E_INVALID"
+    fused = ytn.ytn_plan(hctx, ytn.YTN_OP_FUSE, A, groups=((0, 1),)).out
+    plain = W.random_tensor((0,), [W.Leg(-1, [(0,)], [13])], (0,), 3)
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, fused, plain, (0,), (0,))
+    assert e.value.name == "YTN_E_FUSION_MISMATCH"
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, A, A, (0, 0), (1, 1))
+    assert e.value.name == "YTN_E_INVALID"
+
+
+def test_plan_cache_returns_same_plan(hctx):
+    cfg = W.config1()
+    p1 = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    p2 = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    assert p1.handle == p2.handle
+    p3 = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], (0,), (2,))
+    assert p3.handle != p1.handle
+
+
+def test_execution_needs_a_device_context(hctx):
+    cfg = W.config1()
+    p = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_tensordot(p, 1 << 20, 1 << 20, 1 << 20, workspace=1 << 20, workspace_bytes=1 << 30)
+    assert e.value.name == "YTN_E_INVALID"

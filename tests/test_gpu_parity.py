@@ -1,0 +1,253 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Structure (blocks, charges, dimensions, offsets) must be bit-exact; pure data
+movement (fuse, unfuse) must be bit-exact; FP64 contractions must agree within a
+relative Frobenius error of 1e-12 (the bound the FP64 path is held to).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import (FP64_RTOL, check_against_oracle, oracle_tensordot, rel_frobenius,
+                         run_move, run_tensordot, same_structure)
+from helpers import random_legs, random_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device")
+    from paper_2405_12196_gb300 import ytn
+    return ytn.ytn_ctx_create(0)
+
+
+SYMS = {"U1": (0,), "Z2": (2,), "Z3": (3,), "U1xU1": (0, 0)}
+
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(10))
+def test_random_tensordot_fp64(ctx, sym, case):
+    mods = SYMS[sym]
+    rng = np.random.default_rng(12000 + 17 * case + len(sym))
+    rankA, rankB = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+    ncon = int(rng.integers(0, min(rankA, rankB) + 1))
+    A, B, axa, axb, _, _ = random_pair(rng, mods, rankA, rankB, ncon, max_sectors=4, max_dim=5)
+    _, rec, res = run_tensordot(ctx, A, B, axa, axb)
+    check_against_oracle(rec, oracle_tensordot(A, B, axa, axb))
+
+
+def test_config1(ctx):
+    cfg = W.config1()
+    plan, rec, res = run_tensordot(ctx, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    check_against_oracle(rec, oracle_tensordot(cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]))
+    assert res["useful_flops"] == 5640
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (64, 64, 16), (65, 63, 17), (200, 130, 77), (3, 300, 5),
+                                  (257, 1, 129)])
+def test_single_sector_tiles_and_ragged_tails(ctx, dims):
+    """One dense sector spanning several 64x64 tiles with ragged M, N and K tails."""
+    M, N, K = dims
+    l_m = W.Leg(1, [(0,)], [M])
+    l_k = W.Leg(1, [(0,)], [K])
+    l_n = W.Leg(1, [(0,)], [N])
+    A = W.random_tensor((0,), [l_m, l_k], (0,), M * 7 + K)
+    B = W.random_tensor((0,), [l_k.conj(), l_n], (0,), N * 3 + K)
+    _, rec, _ = run_tensordot(ctx, A, B, (1,), (0,))
+    want = A["data"].reshape(M, K) @ B["data"].reshape(K, N)
+    assert rel_frobenius(rec["data"], want.ravel()) <= FP64_RTOL
+
+
+def test_multi_leg_permutations(ctx):
+    """Contract middle legs in a permuted order: gathers need transposes."""
+    rng = np.random.default_rng(5)
+    legs = random_legs(rng, (0,), 5, max_sectors=3, max_dim=9)
+    A = W.random_tensor((0,), legs, (0,), 1)
+    legsB = [legs[3].conj(), W.Leg(1, [(0,), (1,)], [7, 11]), legs[1].conj()]
+    B = W.random_tensor((0,), legsB, (1,), 2)
+    _, rec, _ = run_tensordot(ctx, A, B, (3, 1), (0, 2))
+    check_against_oracle(rec, oracle_tensordot(A, B, (3, 1), (0, 2)))
+
+
+def test_large_blocks_transpose_paths(ctx):
+    """Blocks big enough for the shared-memory transpose path of the data movers."""
+    l0 = W.Leg(1, [(0,), (1,)], [40, 33])
+    l1 = W.Leg(1, [(0,), (1,)], [48, 37])
+    l2 = W.Leg(-1, [(0,), (1,), (2,)], [35, 41, 20])
+    A = W.random_tensor((0,), [l0, l1, l2], (0,), 3)
+    B = W.random_tensor((0,), [l0.conj(), W.Leg(1, [(0,), (1,)], [50, 45])], (0,), 4)
+    for axa, axb in (((0,), (0,)),):
+        _, rec, _ = run_tensordot(ctx, A, B, axa, axb)
+        check_against_oracle(rec, oracle_tensordot(A, B, axa, axb))
+    C = W.random_tensor((0,), [l2.conj(), l1.conj()], (-1,), 5)
+    _, rec, _ = run_tensordot(ctx, A, C, (2, 1), (0, 1))
+    check_against_oracle(rec, oracle_tensordot(A, C, (2, 1), (0, 1)))
+
+
+def test_edge_cases(ctx):
+    # outer product (no contracted leg)
+    l = W.Leg(1, [(0,), (1,)], [2, 3])
+    A = W.random_tensor((0,), [l, l.conj()], (0,), 1)
+    _, rec, _ = run_tensordot(ctx, A, A, (), ())
+    check_against_oracle(rec, oracle_tensordot(A, A, (), ()))
+    # full contraction to rank 0
+    B = W.random_tensor((0,), [l.conj(), l], (0,), 2)
+    _, rec, _ = run_tensordot(ctx, A, B, (0, 1), (0, 1))
+    check_against_oracle(rec, oracle_tensordot(A, B, (0, 1), (0, 1)))
+    # no matching charges: empty output
+    E = W.random_tensor((0,), [W.Leg(-1, [(7,)], [2]), W.Leg(1, [(7,)], [2])], (0,), 3)
+    _, rec, _ = run_tensordot(ctx, A, E, (1,), (0,))
+    assert rec["t"].shape[0] == 0 and rec["size"] == 0
+    # empty input tensor
+    Z = W.random_tensor((0,), [l, W.Leg(1, [(5,)], [1])], (0,), 4)
+    assert Z["t"].shape[0] == 0
+    _, rec, _ = run_tensordot(ctx, A, Z, (1,), (0,))
+    assert rec["t"].shape[0] == 0 and rec["size"] == 0
+    # 1x1x1 blocks only
+    one = W.Leg(1, [(q,) for q in range(-3, 4)], [1] * 7)
+    S = W.random_tensor((0,), [one, one, one.conj()], (0,), 9)
+    _, rec, _ = run_tensordot(ctx, S, S, (2,), (0,))
+    check_against_oracle(rec, oracle_tensordot(S, S, (2,), (0,)))
+
+
+def test_partially_populated_needs_zero_fill(ctx):
+    """Blocks missing from an allowed set: sector matrices get zero-filled gaps."""
+    rng = np.random.default_rng(11)
+    legs = random_legs(rng, (0,), 4, max_sectors=3, max_dim=4)
+    A = W.random_tensor((0,), legs, (0,), 5)
+    keep = np.arange(A["t"].shape[0]) % 3 != 1
+    sizes = np.prod(A["D"], axis=1)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    A2 = dict(A)
+    A2["t"], A2["D"] = A["t"][keep], A["D"][keep]
+    A2["data"] = np.concatenate([A["data"][offs[i]:offs[i + 1]] for i in np.nonzero(keep)[0]])
+    B = W.random_tensor((0,), [legs[2].conj(), legs[3].conj()], (0,), 6)
+    _, rec, _ = run_tensordot(ctx, A2, B, (2, 3), (0, 1))
+    check_against_oracle(rec, oracle_tensordot(A2, B, (2, 3), (0, 1)))
+
+
+def test_heisenberg_example_closed_form(ctx):
+    """The two-spin example of Sec. II: tensordot(H, H) = 3/16 - H/2 on the GPU."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "heisenberg_two_site.json")))
+    l = W.Leg(1, [(-1,), (1,)], [1, 1])
+    H = W.random_tensor((0,), [l, l, l.conj(), l.conj()], (0,), 0)
+    vals = {tuple(tuple(c) for c in k): v for k, v in g["blocks"]}
+    H["data"] = np.array([vals[tuple(tuple(int(c) for c in H["t"][b, a]) for a in range(4))]
+                          for b in range(H["t"].shape[0])], dtype=np.float64)
+    _, rec, _ = run_tensordot(ctx, H, H, (2, 3), (0, 1))
+    want = {tuple(tuple(c) for c in k): v for k, v in g["H2_blocks"]}
+    got = {tuple(tuple(int(c) for c in rec["t"][b, a]) for a in range(4)): rec["data"][b]
+           for b in range(rec["t"].shape[0])}
+    assert got.keys() == want.keys()
+    for k in want:
+        assert abs(got[k] - want[k]) <= 1e-15
+
+
+# ------------------------------------------------------------------ fuse / unfuse / trace
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(5))
+def test_fuse_unfuse_bit_exact(ctx, sym, case):
+    from paper_2405_12196_gb300 import ytn
+    mods = SYMS[sym]
+    rng = np.random.default_rng(33000 + case)
+    rank = int(rng.integers(2, 6))
+    legs = random_legs(rng, mods, rank, max_sectors=3, max_dim=6)
+    rec = W.random_tensor(mods, legs, tuple([0] * len(mods)), 700 + case)
+    if rec["t"].shape[0] == 0:
+        return
+    perm = [int(a) for a in rng.permutation(rank)]
+    cut = int(rng.integers(1, rank))
+    groups = (tuple(perm[:cut]), tuple(perm[cut:]))
+    F = O.fuse(O.from_record(rec), groups)
+    fplan, frec = run_move(ctx, ytn.YTN_OP_FUSE, rec, groups=groups)
+    check_against_oracle(frec, O.to_record(F), exact=True)
+    fused = [i for i, g in enumerate(groups) if len(g) > 1]
+    uplan, urec = run_move(ctx, ytn.YTN_OP_UNFUSE, frec, axa=fused)
+    check_against_oracle(urec, O.to_record(O.unfuse(F, fused)), exact=True)
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_trace(ctx, case):
+    from paper_2405_12196_gb300 import ytn
+    rng = np.random.default_rng(44000 + case)
+    mods = [(0,), (2,), (0, 0)][case % 3]
+    base = random_legs(rng, mods, 2, max_sectors=3, max_dim=5)
+    other = random_legs(rng, mods, int(rng.integers(0, 3)))
+    legs = [base[0], base[1], base[0].conj(), base[1].conj()] + other
+    npair = int(rng.integers(1, 3))
+    ax1, ax2 = (0, 1)[:npair], (2, 3)[:npair]
+    rec = W.random_tensor(mods, legs, tuple([0] * len(mods)), 80 + case)
+    _, trec = run_move(ctx, ytn.YTN_OP_TRACE, rec, axa=ax1, axb=ax2)
+    check_against_oracle(trec, O.to_record(O.trace(O.from_record(rec), ax1, ax2)))
+
+
+# ------------------------------------------------------------------ workload chains
+
+def test_config2_double_layer_chain(ctx):
+    """Z2 double layer: A . A* over the physical leg, fuse ket/bra pairs into D^2 legs,
+    then T . a over a D^2 leg; every step against the oracle."""
+    from paper_2405_12196_gb300 import ytn
+    cfg = W.config2()
+    A = cfg["A"]
+    Ac = dict(A)
+    Ac["sig"] = tuple(-s for s in A["sig"])
+    _, AA, _ = run_tensordot(ctx, A, Ac, (4,), (4,))
+    oAA = O.tensordot(O.from_record(A), O.conj(O.from_record(A)), (4,), (4,))
+    check_against_oracle(AA, O.to_record(oAA))
+    groups = ((0, 4), (1, 5), (2, 6), (3, 7))
+    _, a = run_move(ctx, ytn.YTN_OP_FUSE, AA, groups=groups)
+    oa = O.fuse(oAA, groups)
+    check_against_oracle(a, O.to_record(oa), rtol=FP64_RTOL)
+    # the edge tensor's D^2 leg is plain, the double layer's is fused: contract against
+    # an edge tensor carrying the conjugate fusion record of a's t leg
+    T = dict(cfg["T"])
+    T["fus"] = [None, dict(a["fus"][0], sig=tuple(-s for s in a["fus"][0]["sig"])), None]
+    _, Ta, _ = run_tensordot(ctx, T, a, (1,), (0,))
+    oTa = O.tensordot(O.from_record(T), O.from_record(a), (1,), (0,))
+    check_against_oracle(Ta, O.to_record(oTa))
+
+
+def test_config3_environment_contraction(ctx):
+    """U(1)xU(1) CTM step, dominant contraction X2 . a over two D^2 legs (7225 + 7225
+    blocks, 81 sectors)."""
+    cfg = W.config3()
+    X2 = cfg["X2"]
+    dl = cfg["dleg"]
+    a = W.random_tensor((0, 0), [W.Leg(-1, dl.t, dl.D), W.Leg(1, dl.t, dl.D), W.Leg(1, dl.t, dl.D),
+                                 W.Leg(-1, dl.t, dl.D)], (0, 0), 3999)
+    plan, rec, _ = run_tensordot(ctx, X2, a, (1, 2), (0, 1))
+    assert plan.info["nsectors"] == 81
+    check_against_oracle(rec, oracle_tensordot(X2, a, (1, 2), (0, 1)))
+
+
+@pytest.mark.slow
+def test_config5_full_size_sampled(ctx):
+    """Full-size U(1)xU(1) X2 . a (D=20, chi=400: 103,725 + 103,725 blocks, 225 sectors)
+    in the benchmark's configuration; sampled output blocks against the oracle."""
+    cfg = W.config5()
+    A, B = cfg["A"], cfg["B"]
+    plan, rec, res = run_tensordot(ctx, A, B, cfg["axa"], cfg["axb"])
+    assert plan.info["nsectors"] == 225
+    assert A["t"].shape[0] == 103725 and rec["t"].shape[0] == 103725
+    oA, oB = O.from_record(A), O.from_record(B)
+    rng = np.random.default_rng(0)
+    nb = rec["t"].shape[0]
+    sizes = np.prod(rec["D"], axis=1)
+    pick = list(rng.choice(nb, 24, replace=False)) + [int(np.argmax(sizes)), 0, nb - 1]
+    for b in pick:
+        key = tuple(tuple(int(c) for c in rec["t"][b, a]) for a in range(rec["t"].shape[1]))
+        want = O.tensordot_block(oA, oB, cfg["axa"], cfg["axb"], key)
+        got = rec["data"][rec["off"][b]:rec["off"][b] + sizes[b]].reshape(want.shape)
+        assert rel_frobenius(got, want) <= FP64_RTOL
+    # charge conservation of every output block (any size)
+    t = rec["t"].astype(np.int64)
+    tot = np.einsum("bac,a->bc", t, np.array(rec["sig"]))
+    assert np.all(tot == 0)
+    assert np.all(np.isfinite(rec["data"]))

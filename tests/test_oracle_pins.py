@@ -357,3 +357,16 @@ def test_conj_flips_signatures_and_charge(mods, n, want):
     Tc.validate()
     assert Tc.sig == tuple(-s for s in T.sig)
     assert Tc.n == want
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_tensordot_block_matches_tensordot(case):
+    """The single-block evaluation used for sampled checks of large contractions gives
+    the same blocks as the full contraction."""
+    rng = np.random.default_rng(4242 + case)
+    mods = [(0,), (2,), (0, 0), (3,)][case]
+    A, B, axa, axb, _, _ = random_pair(rng, mods, 3, 3, 2)
+    oA, oB = O.from_record(A), O.from_record(B)
+    C = O.tensordot(oA, oB, axa, axb)
+    for k, v in C.blocks.items():
+        np.testing.assert_allclose(O.tensordot_block(oA, oB, axa, axb, k), v, rtol=1e-14, atol=1e-14)
