@@ -8,7 +8,11 @@ stored. A step is one full contraction through the C ABI (gather the blocks into
 matrices, grouped GEMM over all sectors, scatter into the output blocks), plan cached.
 Inputs (2.7 GB each) are larger than L2, so no flush is needed between steps.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|split]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--precision split|fp64]
+
+The headline precision (default: split, at rtol 1e-10) is timed over K steps after W
+warm-up steps; the FP64 tensor-core path is timed beside it (--fp64-steps) and the
+relative Frobenius difference of the two results is reported.
 python bench.py --impl reference ...   (the CPU oracle, timed on host cores)
 
 Multi-GPU (torchrun, one rank per GPU): every rank contracts its own independent
@@ -226,7 +230,8 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}[args.precision]
+    PREC = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}
+    prec = PREC[args.precision]
 
     t_gen = time.perf_counter()
     cfg = make_workload(args.workload, rank)
@@ -246,44 +251,88 @@ def run_ours(args):
         da = torch.from_numpy(A["data"]).to(dev)
         db = torch.from_numpy(B["data"]).to(dev)
         dc = torch.empty(plan.out["size"], dtype=torch.float64, device=dev)
-        ws_bytes = ytn.ytn_workspace_size(plan, prec, args.rtol)
+        ws_bytes = max(ytn.ytn_workspace_size(plan, p, args.rtol) for p in PREC.values())
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     stream.synchronize()
 
-    def step():
-        return ytn.ytn_tensordot(plan, da, db, dc, prec=prec, rtol=args.rtol, workspace=ws, stream=stream)
+    def step(p):
+        return ytn.ytn_tensordot(plan, da, db, dc, prec=p, rtol=args.rtol, workspace=ws, stream=stream)
 
-    for _ in range(args.warmup):
-        res = step()
-    stream.synchronize()
+    def measure(p, steps, warmup, clocks=False):
+        res = None
+        for _ in range(warmup):
+            res = step(p)
+        stream.synchronize()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        ytn.ytn_profile_enable(ctx, True)
+        ytn.ytn_profile_read(ctx)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for k in range(steps):
+            res = step(p)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        clk = sampler.stop() if sampler else None
+        prof = ytn.ytn_profile_read(ctx)
+        ytn.ytn_profile_enable(ctx, False)
+        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        t = torch.tensor([ev[0].elapsed_time(ev[-1])], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        return {"total_ms": total_ms, "step_ms": step_ms, "prof": prof, "res": res, "clocks": clk,
+                "value": world * flops * steps / (total_ms * 1e-3) / 1e12}
 
-    # ---- timed region: K device-resident steps
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    ytn.ytn_profile_enable(ctx, True)
-    ytn.ytn_profile_read(ctx)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ev[0].record(stream)
-    for k in range(args.steps):
-        res = step()
-        ev[k + 1].record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    prof = ytn.ytn_profile_read(ctx)
-    ytn.ytn_profile_enable(ctx, False)
-    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * flops * args.steps / (total_ms * 1e-3) / 1e12
+    peaks, peak_src = load_peaks()
+
+    def roofline(p, m):
+        gemm_calls, gemm_ms = m["prof"].get("gemm", (0, 0.0))
+        kernel_ms = gemm_ms / max(1, gemm_calls)
+        if p == ytn.YTN_FP64:
+            kernel, kflops = "gemm_fp64_kernel", flops
+            peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+            note = (f"{peak_src} dense BF16 burst ({peaks['bf16_tflops']} TFLOP/s) x nominal FP64/BF16 ratio "
+                    f"{NOMINAL['fp64']}/{NOMINAL['bf16']}")
+        else:
+            s = m["res"]["slices"]
+            kernel, kflops = "gemm_split_kernel", flops * s * (s + 1) / 2
+            peak = peaks["bf16_tflops"]
+            note = (f"{peak_src} dense BF16 burst; achieved counts the BF16 slice-product FLOPs "
+                    f"(s(s+1)/2 = {s * (s + 1) // 2} per useful FLOP, s = {s} slices)")
+        achieved = kflops / (kernel_ms * 1e-3) / 1e12 if kernel_ms > 0 else None
+        return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": read_traffic(kernel, args.workload),
+                "kernel_ms": kernel_ms, "effective_fp64_tflops": flops / (kernel_ms * 1e-3) / 1e12 if kernel_ms else None,
+                "peak_source": note}
+
+    def phases(m):
+        return {k: {"calls": v[0], "ms_per_call": v[1] / max(1, v[0])} for k, v in m["prof"].items() if k != "dropped"}
+
+    # ---- headline precision: device-resident steps
+    head = measure(prec, args.steps, args.warmup, clocks=True)
+    value = head["value"]
+    ph = phases(head)
+    moved_bytes = 16.0 * plan.info["moved_elems"]
+    mover_ms = sum(ph[k]["ms_per_call"] for k in ("gather_a", "gather_b", "scatter") if k in ph)
+    out_head = dc.clone() if prec != ytn.YTN_FP64 else None
+
+    # ---- the other precision, for the FP64 vs split comparison
+    other = None
+    if prec != ytn.YTN_FP64 and args.fp64_steps > 0:
+        m64 = measure(ytn.YTN_FP64, args.fp64_steps, 1)
+        diff = float(torch.linalg.vector_norm(out_head - dc) / torch.linalg.vector_norm(dc))
+        other = {"precision": "fp64", "value": m64["value"], "unit": "TFLOP/s", "steps": args.fp64_steps,
+                 "ms_per_step": m64["total_ms"] / args.fp64_steps, "roofline": roofline(ytn.YTN_FP64, m64),
+                 "split_speedup": value / m64["value"], "split_vs_fp64_rel_frobenius": diff}
+        del out_head
 
     # ---- end to end through the C ABI: pinned host inputs in, result out, every step
     ha = torch.from_numpy(A["data"]).pin_memory()
@@ -299,69 +348,46 @@ def run_ours(args):
         for _ in range(e2e_steps):
             da.copy_(ha, non_blocking=True)
             db.copy_(hb, non_blocking=True)
-            step()
+            step(prec)
             hc.copy_(dc, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * flops * e2e_steps / (float(te.item()) * 1e-3) / 1e12
 
-    # ---- roofline of the dominant kernel (the grouped GEMM), timed live on its stream
-    peaks, peak_src = load_peaks()
-    gemm_calls, gemm_ms = prof.get("gemm", (0, 0.0))
-    kernel_ms = gemm_ms / max(1, gemm_calls)
-    if prec == ytn.YTN_FP64:
-        kernel = "gemm_fp64_kernel"
-        peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
-        peak_note = (f"{peak_src} dense BF16 burst ({peaks['bf16_tflops']} TFLOP/s) x nominal FP64/BF16 "
-                     f"ratio {NOMINAL['fp64']}/{NOMINAL['bf16']}")
-        dtype = "f64"
-    else:
-        kernel = "gemm_split_kernel"
-        peak = peaks["bf16_tflops"]
-        peak_note = f"{peak_src} dense BF16 burst"
-        dtype = "bf16-slices/f32-acc/f64-recombine"
-    slices = res.get("slices", 0) if isinstance(res, dict) else 0
-    # algorithmic work of the dominant kernel per launch: useful FLOPs (FP64 path) or
-    # the BF16 slice-product FLOPs (split path: s(s+1)/2 slice products per useful FLOP)
-    kernel_flops = flops if prec == ytn.YTN_FP64 else flops * slices * (slices + 1) / 2
-    achieved = kernel_flops / (kernel_ms * 1e-3) / 1e12 if kernel_ms > 0 else None
-    traffic = read_traffic(kernel, args.workload)
-    roofline = {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_source": peak_note}
-    phases = {k: {"calls": v[0], "ms_per_call": v[1] / max(1, v[0])} for k, v in prof.items() if k != "dropped"}
-    moved_bytes = 16.0 * plan.info["moved_elems"]
-    mover_ms = sum(phases[k]["ms_per_call"] for k in ("gather_a", "gather_b", "scatter") if k in phases)
-
+    res = head["res"]
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "precision": args.precision,
+        "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == ytn.YTN_FP64 else "bf16 slices, f32 accumulate, f64 recombine",
+        "data": "synthetic", "precision": args.precision,
         "config": {"workload": WORKLOAD_DESC[args.workload], "useful_flops_per_step": flops,
                    "blocks": [int(A["t"].shape[0]), int(B["t"].shape[0]), int(plan.out["t"].shape[0])],
-                   "sectors": plan.info["nsectors"], "max_mnk": [plan.info["max_m"], plan.info["max_n"],
-                                                                 plan.info["max_k"]],
-                   "l2": "inputs larger than L2 (no flush)", "rtol": args.rtol if prec != ytn.YTN_FP64 else None},
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-        "clocks": clocks,
+                   "sectors": plan.info["nsectors"],
+                   "max_mnk": [plan.info["max_m"], plan.info["max_n"], plan.info["max_k"]],
+                   "l2": "inputs larger than L2 (no flush)",
+                   "rtol": args.rtol if prec != ytn.YTN_FP64 else None},
+        "latency_ms": {"p50": float(np.percentile(head["step_ms"], 50)),
+                       "p99": float(np.percentile(head["step_ms"], 99))},
+        "clocks": head["clocks"],
         "e2e": {"value": e2e_value, "unit": "TFLOP/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": int(8 * (A["data"].size + B["data"].size)),
                 "d2h_bytes_per_step": int(8 * plan.out["size"])},
-        "gpu_launches": int(sum(v[0] for k, v in prof.items() if k != "dropped")),
-        "roofline": roofline,
-        "phases_ms": phases,
+        "gpu_launches": int(sum(v["calls"] for v in ph.values())),
+        "roofline": roofline(prec, head),
+        "phases_ms": ph,
         "data_movers": {"bytes_per_step": moved_bytes, "ms_per_step": mover_ms,
                         "GB_per_s": moved_bytes / (mover_ms * 1e-3) / 1e9 if mover_ms else None,
                         "peak_GB_per_s": peaks["hbm_gbs"]},
         "host": {"generate_s": t_gen, "plan_s": t_plan, "plan_cached_s": t_plan_cached},
     }
     if prec != ytn.YTN_FP64:
-        line["split"] = {"slices": slices, "err_bound": res.get("err_bound")}
-
+        line["split"] = {"slices": res["slices"], "err_est": res["err_est"]}
+    if other is not None:
+        line["fp64"] = other
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f, s, desc = oracle_sample(cfg, args.cpu_budget)
         line["cpu_baseline"] = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
@@ -380,7 +406,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--workload", default="cfg5", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--e2e-steps", type=int, default=3)

@@ -163,8 +163,9 @@ typedef struct {
   double useful_flops;
   int32_t precision;         /* ytn_precision used                              */
   int32_t slices;            /* split path: BF16 slices per operand, else 0     */
-  double err_bound;          /* split path: a-priori bound on the relative
-                                Frobenius error of the result; 0 for FP64     */
+  double err_est;            /* split path: a-priori estimate of the relative
+                                Frobenius error of the result (the model that
+                                picks the slice count); 0 for FP64            */
 } ytn_result;
 
 /* Context bound to one CUDA device; allocates a device status word.

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -59,6 +61,12 @@ static ytn_status upload(ytn_plan_t *p) {
   put_table(buf, p->tiles, o_tiles);
   put_table(buf, p->tr_out, o_tro);
   put_table(buf, p->tr_contrib, o_trc);
+  size_t o_spo, o_spe, o_sps, o_spsec, o_spt;
+  put_table(buf, p->sp_ops, o_spo);
+  put_table(buf, p->sp_exp_items, o_spe);
+  put_table(buf, p->sp_slice_items, o_sps);
+  put_table(buf, p->sp_sectors, o_spsec);
+  put_table(buf, p->sp_tiles, o_spt);
   p->dev_bytes = align256(buf.size()) + 256;
   cudaError_t e = cudaMalloc(&p->dev, p->dev_bytes);
   if (e != cudaSuccess) {
@@ -77,6 +85,11 @@ static ytn_status upload(ytn_plan_t *p) {
   p->d_tiles = reinterpret_cast<const GemmTile *>(d + o_tiles);
   p->d_tr_out = reinterpret_cast<const TraceOut *>(d + o_tro);
   p->d_tr_contrib = reinterpret_cast<const TraceContrib *>(d + o_trc);
+  p->d_sp_ops = reinterpret_cast<const SplitOperand *>(d + o_spo);
+  p->d_sp_exp_items = reinterpret_cast<const SplitItem *>(d + o_spe);
+  p->d_sp_slice_items = reinterpret_cast<const SplitItem *>(d + o_sps);
+  p->d_sp_sectors = reinterpret_cast<const SplitSector *>(d + o_spsec);
+  p->d_sp_tiles = reinterpret_cast<const SplitTile *>(d + o_spt);
   return YTN_OK;
 }
 
@@ -114,11 +127,53 @@ class PhaseTimer {
   int idx_ = -1;
 };
 
-// FP64 workspace: WA | WB | WC, each 256-byte aligned.
-static size_t fp64_workspace(const ytn_plan_t *p, size_t &ob, size_t &oc) {
-  ob = align256((size_t)p->a_elems * 8);
-  oc = ob + align256((size_t)p->b_elems * 8);
-  return oc + align256((size_t)p->c_elems * 8);
+// Workspace: WA | WB | WC (FP64 sector matrices), then for the split path
+// SA | SB (BF16 slice blocks) | EA | EB (row / column exponents); 256-byte aligned.
+struct WsLayout {
+  size_t wa = 0, wb = 0, wc = 0, sa = 0, sb = 0, ea = 0, eb = 0;
+};
+
+static size_t workspace_layout(const ytn_plan_t *p, bool split, WsLayout &w) {
+  size_t o = 0;
+  w.wa = o;
+  o += align256((size_t)p->a_elems * 8);
+  w.wb = o;
+  o += align256((size_t)p->b_elems * 8);
+  w.wc = o;
+  o += align256((size_t)p->c_elems * 8);
+  if (!split) return o;
+  w.sa = o;
+  o += align256((size_t)p->sp_sa_bytes);
+  w.sb = o;
+  o += align256((size_t)p->sp_sb_bytes);
+  w.ea = o;
+  o += align256((size_t)p->sp_ea * 4);
+  w.eb = o;
+  o += align256((size_t)p->sp_eb * 4);
+  return o;
+}
+
+// Error model of the split path (relative Frobenius error of the result):
+// rounding both operands to s digits of 8 bits relative to their row / column
+// scale (|error| <= 2^(-8s-1) of the scale per element) and the dropped products
+// contribute 2^(10-8s): room for a factor of about 2^10 between the scales and the
+// result (cancellation in small sectors); rounding of the FP32 accumulator of the
+// products of order >= 3 (at most 2^-24 of the result) over the whole K is kept
+// below 2^-44 sqrt(K). The slice count is the smallest s >= 4 whose estimate is at
+// most rtol (s = 6 for rtol = 1e-10).
+static double split_error_estimate(int s, int64_t kmax) {
+  return std::ldexp(1.0, 10 - 8 * s) + std::ldexp(1.0, -44) * std::sqrt((double)std::max<int64_t>(kmax, 1));
+}
+
+static ytn_status choose_slices(const ytn_plan_t *p, double rtol, int &s, double &est) {
+  if (p->max_k > 16384) return fail(YTN_E_UNSUPPORTED, "split path supports K up to 16384 per sector");
+  if (!(rtol > 0.0)) return fail(YTN_E_TOLERANCE, "split path needs rtol > 0");
+  for (s = 4; s <= kSlices; s++) {   // orders 0..2 are exact, so at least 4 slices
+    est = split_error_estimate(s, p->max_k);
+    if (est <= rtol) return YTN_OK;
+  }
+  est = split_error_estimate(kSlices, p->max_k);
+  return fail(YTN_E_TOLERANCE, "rtol below what the split path can reach for this plan");
 }
 
 }  // namespace ytn
@@ -152,6 +207,11 @@ ytn_status ytn_ctx_create(ytn_ctx **ctx, int device) {
   if (!g.ok()) {
     delete c;
     return fail(YTN_E_CUDA, "cannot select device");
+  }
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
   }
   e = cudaMalloc(&c->status_dev, sizeof(int) * 4);
   if (e != cudaSuccess) {
@@ -308,13 +368,20 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
   if (!p || !bytes) return fail(YTN_E_INVALID, "null argument");
   *bytes = 0;
   if (p->kind != Kind::Tensordot) return YTN_OK;
-  size_t ob, oc;
+  WsLayout w;
   if (prec == YTN_FP64) {
-    *bytes = fp64_workspace(p, ob, oc);
+    *bytes = workspace_layout(p, false, w);
     return YTN_OK;
   }
-  (void)rtol;
-  return fail(YTN_E_UNSUPPORTED, "precision not available in this build");
+  if (prec == YTN_SPLIT_BF16) {
+    int s;
+    double est;
+    ytn_status st = choose_slices(p, rtol, s, est);
+    if (st != YTN_OK) return st;
+    *bytes = workspace_layout(p, true, w);
+    return YTN_OK;
+  }
+  return fail(YTN_E_INVALID, "unknown precision");
 }
 
 ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, ytn_precision prec,
@@ -325,18 +392,24 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
   if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
   if ((p->a_size && !a) || (p->b_size && !b) || (p->out.size && !c))
     return fail(YTN_E_INVALID, "null data buffer");
-  if (prec != YTN_FP64) return fail(YTN_E_UNSUPPORTED, "precision not available in this build");
-  (void)rtol;
-  size_t ob, oc;
-  const size_t need = fp64_workspace(p, ob, oc);
+  if (prec != YTN_FP64 && prec != YTN_SPLIT_BF16) return fail(YTN_E_INVALID, "unknown precision");
+  const bool split = prec == YTN_SPLIT_BF16;
+  int slices = 0;
+  double est = 0.0;
+  if (split) {
+    ytn_status st = choose_slices(p, rtol, slices, est);
+    if (st != YTN_OK) return st;
+  }
+  WsLayout w;
+  const size_t need = workspace_layout(p, split, w);
   if (need && (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)))
     return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
   DeviceGuard g(p->ctx->device);
   if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char *ws = static_cast<char *>(workspace);
-  double *wa = reinterpret_cast<double *>(ws), *wb = reinterpret_cast<double *>(ws + ob),
-         *wc = reinterpret_cast<double *>(ws + oc);
+  double *wa = reinterpret_cast<double *>(ws + w.wa), *wb = reinterpret_cast<double *>(ws + w.wb),
+         *wc = reinterpret_cast<double *>(ws + w.wc);
   cudaError_t e;
   if (p->zero_a && (e = cudaMemsetAsync(wa, 0, (size_t)p->a_elems * 8, st)) != cudaSuccess)
     return cuda_fail(e, "memset A workspace");
@@ -352,11 +425,26 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, b, wb, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "gather B");
-  {
+  if (!split) {
     PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
     e = launch_gemm_fp64(p->d_sectors, p->d_tiles, (int64_t)p->tiles.size(), wa, wb, wc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped FP64 GEMM");
+  } else {
+    int32_t *ea = reinterpret_cast<int32_t *>(ws + w.ea), *eb = reinterpret_cast<int32_t *>(ws + w.eb);
+    uint8_t *sa = reinterpret_cast<uint8_t *>(ws + w.sa), *sb = reinterpret_cast<uint8_t *>(ws + w.sb);
+    {
+      PhaseTimer t(p->ctx, YTN_PHASE_SPLIT, st);
+      e = launch_split_prep(p->d_sp_ops, p->d_sp_exp_items, (int64_t)p->sp_exp_items.size(), p->d_sp_slice_items,
+                            (int64_t)p->sp_slice_items.size(), wa, wb, ea, eb, sa, sb, slices, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "split into slices");
+    {
+      PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
+      e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles, (int64_t)p->sp_tiles.size(), sa, sb, ea, eb, wc, slices,
+                            p->ctx->status_dev, p->ctx->num_sms, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "grouped split-precision GEMM");
   }
-  if (e != cudaSuccess) return cuda_fail(e, "grouped FP64 GEMM");
   {
     PhaseTimer t(p->ctx, YTN_PHASE_SCATTER, st);
     e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, wc, c, st);
@@ -364,9 +452,9 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
   if (e != cudaSuccess) return cuda_fail(e, "scatter C");
   if (res) {
     res->useful_flops = p->flops;
-    res->precision = YTN_FP64;
-    res->slices = 0;
-    res->err_bound = 0.0;
+    res->precision = prec;
+    res->slices = slices;
+    res->err_est = est;
   }
   return YTN_OK;
 }

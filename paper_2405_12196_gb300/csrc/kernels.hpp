@@ -19,4 +19,15 @@ cudaError_t launch_trace(const TraceOut *outs, int64_t nout, const TraceContrib 
 cudaError_t launch_gemm_fp64(const SectorDev *sectors, const GemmTile *tiles, int64_t ntiles,
                              const double *wa, const double *wb, double *wc, cudaStream_t stream);
 
+// Split-precision path: row exponents and BF16 slices of every sector operand.
+cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_items, int64_t nexp,
+                              const SplitItem *slice_items, int64_t nslice, const double *wa, const double *wb,
+                              int32_t *ea, int32_t *eb, uint8_t *sa, uint8_t *sb, int slices,
+                              cudaStream_t stream);
+
+// Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output C_q.
+cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
+                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc, int slices,
+                              int *status, int num_sms, cudaStream_t stream);
+
 }  // namespace ytn

@@ -688,10 +688,75 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   std::stable_sort(p->tiles.begin(), p->tiles.end(), [&](const GemmTile &x, const GemmTile &y) {
     return geo[x.sector].K > geo[y.sector].K;
   });
+  plan_split_tables(p);
   p->kind = Kind::Tensordot;
   p->a_size = A.size;
   p->b_size = B.size;
   return YTN_OK;
+}
+
+// Tables of the split-precision path: per sector, the slice blocks and
+// exponents of A (rows M) and B (rows N), the exponent / slicing work items and
+// the 128 x 128 output tiles (sectors by decreasing K; inside a sector, groups
+// of 8 row tiles with the column tiles innermost, so that CTAs running at the
+// same time share operand slices in L2).
+void plan_split_tables(ytn_plan_t *p) {
+  p->sp_ops.clear();
+  p->sp_exp_items.clear();
+  p->sp_slice_items.clear();
+  p->sp_sectors.clear();
+  p->sp_tiles.clear();
+  int64_t sa = 0, sb = 0, ea = 0, eb = 0;
+  const int64_t nsec = (int64_t)p->sectors.size();
+  for (int64_t q = 0; q < nsec; q++) {
+    const HostSector &h = p->sectors[q];
+    const int64_t tm = (h.M + kSplitBM - 1) / kSplitBM, tn = (h.N + kSplitBM - 1) / kSplitBM;
+    const int64_t ks = (h.K + kSplitBK - 1) / kSplitBK;
+    SplitSector s{};
+    s.sa_off = sa;
+    s.sb_off = sb;
+    s.ea_off = ea;
+    s.eb_off = eb;
+    s.c_off = h.c_off;
+    s.M = (int32_t)h.M;
+    s.N = (int32_t)h.N;
+    s.K = (int32_t)h.K;
+    s.ks = (int32_t)ks;
+    p->sp_sectors.push_back(s);
+    SplitOperand oa{h.a_off, ea, sa, (int32_t)h.M, (int32_t)h.K, (int32_t)ks, p->a_kmajor ? 1 : 0};
+    SplitOperand ob{h.b_off, eb, sb, (int32_t)h.N, (int32_t)h.K, (int32_t)ks, p->b_kmajor ? 1 : 0};
+    const int32_t ia = (int32_t)p->sp_ops.size();
+    p->sp_ops.push_back(oa);
+    p->sp_ops.push_back(ob);
+    for (int which = 0; which < 2; which++) {
+      const int64_t tiles = which == 0 ? tm : tn;
+      for (int64_t rt = 0; rt < tiles; rt++) {
+        p->sp_exp_items.push_back({ia + which, (int32_t)rt, 0, (int32_t)ks});
+        for (int64_t k0 = 0; k0 < ks; k0 += 8)
+          p->sp_slice_items.push_back({ia + which, (int32_t)rt, (int32_t)k0, (int32_t)std::min<int64_t>(8, ks - k0)});
+      }
+    }
+    sa += tm * ks * kBlockBytes;
+    sb += tn * ks * kBlockBytes;
+    ea += tm * kSplitBM;
+    eb += tn * kSplitBM;
+  }
+  p->sp_sa_bytes = sa;
+  p->sp_sb_bytes = sb;
+  p->sp_ea = ea;
+  p->sp_eb = eb;
+  std::vector<int64_t> order(nsec);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t x, int64_t y) { return p->sectors[x].K > p->sectors[y].K; });
+  for (int64_t q : order) {
+    const HostSector &h = p->sectors[q];
+    const int64_t tm = (h.M + kSplitBM - 1) / kSplitBM, tn = (h.N + kSplitBM - 1) / kSplitBM;
+    for (int64_t g0 = 0; g0 < tm; g0 += 8)
+      for (int64_t n = 0; n < tn; n++)
+        for (int64_t m = g0; m < std::min<int64_t>(g0 + 8, tm); m++)
+          p->sp_tiles.push_back({(int32_t)q, (int32_t)m, (int32_t)n, 0});
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,176 @@
+// Split of FP64 sector matrices into BF16 slices for the split-precision grouped
+// GEMM (an error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump,
+// Numer. Algorithms 2012, with power-of-two scales per row).
+//
+// For a row x_r of an operand (a row of A_q, or a column of B_q), with
+// e_r = 1 + floor(log2 max_k |x_rk|), every element is written in fixed point
+// relative to 2^e_r with s digits of 8 bits (s = slices in use, <= 6):
+//     x_rk = sign * 2^e_r * (sum_{p=1..s} d_p 2^{-8p} + t),   0 <= d_p < 256,
+// the last digit rounded to nearest, so |t| <= 2^(-8s-1). Slices beyond s are
+// zero. Slice p holds sign * d_p * 2^{-8(p-1)}, an
+// integer times a power of two with at most 8 significant bits, so it is exact
+// in BF16 and products of two slices are exact in FP32. The digits are taken
+// from the FP64 bit pattern with integer shifts only (no FP64 arithmetic, which
+// is slow on this GPU). Zero and subnormal inputs give zero digits.
+//
+// Output layout: for operand block (row tile rt, K stage kt) six consecutive
+// 128 x 32 BF16 slices, each K-major with the 64-byte swizzle (16-byte chunk c of
+// row r stored at chunk position c ^ ((r >> 1) & 3)), the layout the tensor
+// cores read from shared memory; rows and K beyond the operand are zero.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "kernels.hpp"
+
+namespace ytn {
+
+namespace {
+
+__device__ __forceinline__ int biased_exp(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// Row exponents: e_r = maxE - 1022 over the row (maxE = largest biased exponent).
+__global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__restrict__ ops,
+                                                        const SplitItem *__restrict__ items,
+                                                        const double *__restrict__ wa,
+                                                        const double *__restrict__ wb,
+                                                        int32_t *__restrict__ ea, int32_t *__restrict__ eb) {
+  const SplitItem it = items[blockIdx.x];
+  const SplitOperand o = ops[it.op];
+  const bool isA = (it.op & 1) == 0;
+  const double *X = (isA ? wa : wb) + o.src_off;
+  int32_t *E = (isA ? ea : eb) + o.exp_off;
+  const int r0 = it.rt * kSplitBM;
+  __shared__ int red[2][kSplitBM];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (o.kmajor) {
+    // rows of K contiguous elements: one warp per row
+    for (int rr = warp; rr < kSplitBM; rr += 8) {
+      const int r = r0 + rr;
+      int m = 0;
+      if (r < o.rows) {
+        const double *row = X + (int64_t)r * o.K;
+        for (int k = lane; k < o.K; k += 32) m = max(m, biased_exp(__ldg(row + k)));
+      }
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
+      if (lane == 0) red[0][rr] = m;
+    }
+    __syncthreads();
+    if (tid < kSplitBM) E[r0 + tid] = (r0 + tid < o.rows && red[0][tid] > 0) ? red[0][tid] - 1022 : -1022;
+  } else {
+    // K rows of `rows` contiguous elements: thread per row, two halves of K
+    const int rr = tid & (kSplitBM - 1), half = tid >> 7;
+    const int r = r0 + rr;
+    int m = 0;
+    if (r < o.rows)
+      for (int k = half; k < o.K; k += 2) m = max(m, biased_exp(__ldg(X + (int64_t)k * o.rows + r)));
+    red[half][rr] = m;
+    __syncthreads();
+    if (tid < kSplitBM) {
+      const int mm = max(red[0][tid], red[1][tid]);
+      E[r0 + tid] = (r0 + tid < o.rows && mm > 0) ? mm - 1022 : -1022;
+    }
+  }
+}
+
+// Slices: one 128 x 32 stage at a time through shared memory (raw FP64 bits).
+__global__ void __launch_bounds__(256) split_slice_kernel(const SplitOperand *__restrict__ ops,
+                                                          const SplitItem *__restrict__ items,
+                                                          const double *__restrict__ wa,
+                                                          const double *__restrict__ wb,
+                                                          const int32_t *__restrict__ ea,
+                                                          const int32_t *__restrict__ eb,
+                                                          uint8_t *__restrict__ sa, uint8_t *__restrict__ sb,
+                                                          int s) {
+  __shared__ unsigned long long tile[kSplitBM][kSplitBK + 1];
+  __shared__ int rexp[kSplitBM];
+  const SplitItem it = items[blockIdx.x];
+  const SplitOperand o = ops[it.op];
+  const bool isA = (it.op & 1) == 0;
+  const double *X = (isA ? wa : wb) + o.src_off;
+  const int32_t *E = (isA ? ea : eb) + o.exp_off;
+  uint8_t *S = (isA ? sa : sb) + o.slice_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = it.rt * kSplitBM;
+  if (tid < kSplitBM) rexp[tid] = E[r0 + tid];
+  for (int kt = it.kt0; kt < it.kt0 + it.nkt; kt++) {
+    const int k0 = kt * kSplitBK;
+    __syncthreads();
+    if (o.kmajor) {
+      for (int rr = warp; rr < kSplitBM; rr += 8) {
+        const int r = r0 + rr, k = k0 + lane;
+        double v = 0.0;
+        if (r < o.rows && k < o.K) v = __ldg(X + (int64_t)r * o.K + k);
+        tile[rr][lane] = (unsigned long long)__double_as_longlong(v);
+      }
+    } else {
+      for (int kk = warp; kk < kSplitBK; kk += 8) {
+        const int k = k0 + kk;
+#pragma unroll
+        for (int q = 0; q < kSplitBM / 32; q++) {
+          const int rr = q * 32 + lane, r = r0 + rr;
+          double v = 0.0;
+          if (r < o.rows && k < o.K) v = __ldg(X + (int64_t)k * o.rows + r);
+          tile[rr][kk] = (unsigned long long)__double_as_longlong(v);
+        }
+      }
+    }
+    __syncthreads();
+    uint8_t *blk = S + ((int64_t)it.rt * o.ks + kt) * kBlockBytes;
+    // 128 rows x 4 chunks of 8 elements; two chunks per thread
+    for (int task = tid; task < kSplitBM * 4; task += 256) {
+      const int rr = task >> 2, c = task & 3;
+      const int e = rexp[rr];
+      uint32_t packed[kSlices][4];
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const unsigned long long bits = tile[rr][c * 8 + j];
+        const int Eb = (int)((bits >> 52) & 0x7FF);
+        // u = round(|x| 2^-e 2^(8s)): the s kept digits, the last one rounded to nearest
+        unsigned long long u = 0;
+        if (Eb != 0) {
+          const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          const int shift = 1075 + e - Eb - 8 * s;   // >= 53 - 8s >= 5
+          if (shift < 64) {
+            u = (mant + (1ull << (shift - 1))) >> shift;
+            u = min(u, (1ull << (8 * s)) - 1ull);
+          }
+        }
+        const bool neg = (bits >> 63) != 0;
+#pragma unroll
+        for (int p = 0; p < kSlices; p++) {
+          const int d = p < s ? (int)((u >> (8 * (s - 1 - p))) & 0xFF) : 0;
+          float f = (float)d * __int_as_float((127 - 8 * p) << 23);   // d * 2^{-8p}
+          if (neg) f = -f;
+          const uint16_t h = __bfloat16_as_ushort(__float2bfloat16_rn(f));
+          if (j & 1) packed[p][j >> 1] |= (uint32_t)h << 16;
+          else packed[p][j >> 1] = h;
+        }
+      }
+      const int pos = rr * 64 + ((c ^ ((rr >> 1) & 3)) << 4);
+#pragma unroll
+      for (int p = 0; p < kSlices; p++)
+        if (p < s)   // slices beyond s are never read
+          *reinterpret_cast<uint4 *>(blk + p * kSliceBytes + pos) =
+              make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_items, int64_t nexp,
+                              const SplitItem *slice_items, int64_t nslice, const double *wa, const double *wb,
+                              int32_t *ea, int32_t *eb, uint8_t *sa, uint8_t *sb, int slices,
+                              cudaStream_t stream) {
+  if (nexp > INT32_MAX || nslice > INT32_MAX || slices < 1 || slices > kSlices) return cudaErrorInvalidValue;
+  if (nexp > 0) split_exp_kernel<<<(unsigned)nexp, 256, 0, stream>>>(ops, exp_items, wa, wb, ea, eb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (nslice > 0) split_slice_kernel<<<(unsigned)nslice, 256, 0, stream>>>(ops, slice_items, wa, wb, ea, eb, sa, sb, slices);
+  return cudaGetLastError();
+}
+
+}  // namespace ytn

@@ -89,6 +89,47 @@ struct TraceContrib {
 };
 
 // ----------------------------------------------------------------------------
+// Split-precision path tables
+// ----------------------------------------------------------------------------
+
+// Slices of one operand of one sector are stored pre-tiled and pre-swizzled:
+// block (row tile rt of 128 rows, K stage kt of 32) holds kSlices slices of
+// 128 x 32 BF16 each (8 KB per slice, the 64-byte-swizzled K-major layout the
+// tensor cores read), so that one bulk copy moves a whole stage.
+constexpr int kSplitBM = 128;              // rows per tile (M, and N)
+constexpr int kSplitBK = 32;               // K per stage
+constexpr int kSlices = 6;                 // slices stored per operand
+constexpr int kSliceBytes = kSplitBM * kSplitBK * 2;         // 8192
+constexpr int kBlockBytes = kSlices * kSliceBytes;           // 49152
+constexpr int kChunkStages = 4;            // exact-accumulation chunk: 4 stages = K 128
+
+// One operand (A rows = M, or B rows = N) of one sector, for the split kernels.
+struct SplitOperand {
+  int64_t src_off;     // element offset of the FP64 sector matrix in its workspace
+  int64_t exp_off;     // int offset of its row exponents
+  int64_t slice_off;   // byte offset of its slice blocks
+  int32_t rows, K, ks, kmajor;   // kmajor: stored rows x K (ld = K), else K x rows
+};
+static_assert(sizeof(SplitOperand) == 40, "SplitOperand layout");
+
+// Work item of the exponent / slicing kernels: operand, row tile, stage range.
+struct SplitItem {
+  int32_t op, rt, kt0, nkt;
+};
+
+struct SplitSector {
+  int64_t sa_off, sb_off;    // byte offsets of the slice blocks of A and B
+  int64_t ea_off, eb_off;    // int offsets of the row exponents of A and the column exponents of B
+  int64_t c_off;             // element offset of C_q in the FP64 workspace
+  int32_t M, N, K, ks;
+};
+static_assert(sizeof(SplitSector) == 56, "SplitSector layout");
+
+struct SplitTile {
+  int32_t sector, mt, nt, pad;
+};
+
+// ----------------------------------------------------------------------------
 // Host-side structures
 // ----------------------------------------------------------------------------
 
@@ -137,6 +178,7 @@ struct Plan;
 struct ytn_ctx {
   int device = 0;
   int *status_dev = nullptr;   // device status word (bounded waits report here)
+  int num_sms = 0;
   std::mutex mu;
   std::unordered_map<std::string, ytn_plan_t *> cache;
   // phase timing: a pool of CUDA events (cudaEvent_t stored as void*) and the
@@ -194,8 +236,16 @@ struct ytn_plan_s {
   const ytn::TraceOut *d_tr_out = nullptr;
   const ytn::TraceContrib *d_tr_contrib = nullptr;
 
-  // split-precision tables (built on first use, see gemm_split.cu)
-  std::shared_ptr<void> split;
+  // split-precision tables
+  std::vector<ytn::SplitOperand> sp_ops;
+  std::vector<ytn::SplitItem> sp_exp_items, sp_slice_items;
+  std::vector<ytn::SplitSector> sp_sectors;
+  std::vector<ytn::SplitTile> sp_tiles;
+  int64_t sp_sa_bytes = 0, sp_sb_bytes = 0, sp_ea = 0, sp_eb = 0;
+  const ytn::SplitOperand *d_sp_ops = nullptr;
+  const ytn::SplitItem *d_sp_exp_items = nullptr, *d_sp_slice_items = nullptr;
+  const ytn::SplitSector *d_sp_sectors = nullptr;
+  const ytn::SplitTile *d_sp_tiles = nullptr;
 };
 
 namespace ytn {
@@ -212,6 +262,7 @@ ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1,
                       const int *ax2, std::string &err);
 std::string plan_key(const ytn_op *op);
 void finish_output_view(ytn_plan_t *p);
+void plan_split_tables(ytn_plan_t *p);
 
 // error reporting (api.cu)
 ytn_status fail(ytn_status st, const std::string &msg);

@@ -83,7 +83,7 @@ class ytn_profile(C.Structure):
 
 class ytn_result(C.Structure):
     _fields_ = [("useful_flops", C.c_double), ("precision", C.c_int32), ("slices", C.c_int32),
-                ("err_bound", C.c_double)]
+                ("err_est", C.c_double)]
 
 
 # entry points declared in include/ytn.h
@@ -316,7 +316,7 @@ def ytn_tensordot(plan, a, b, c, prec=YTN_FP64, rtol=0.0, workspace=None, worksp
     _check(_lib.ytn_tensordot(plan.handle, _ptr(a), _ptr(b), _ptr(c), prec, float(rtol),
                               _ptr(workspace), int(workspace_bytes), C.byref(res), _stream(stream)))
     return {"useful_flops": res.useful_flops, "precision": res.precision, "slices": res.slices,
-            "err_bound": res.err_bound}
+            "err_est": res.err_est}
 
 
 def ytn_fuse(plan, a, out, stream=None):
@@ -350,7 +350,4 @@ def ytn_profile_read(ctx):
 
 def available_precisions():
     """Precisions this build of the library executes."""
-    out = [YTN_FP64]
-    if hasattr(_lib, "ytn_split_available") and _lib.ytn_split_available():
-        out.append(YTN_SPLIT_BF16)
-    return out
+    return [YTN_FP64, YTN_SPLIT_BF16]

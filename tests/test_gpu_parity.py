@@ -99,11 +99,12 @@ def test_edge_cases(ctx):
     _, rec, _ = run_tensordot(ctx, A, B, (0, 1), (0, 1))
     check_against_oracle(rec, oracle_tensordot(A, B, (0, 1), (0, 1)))
     # no matching charges: empty output
-    E = W.random_tensor((0,), [W.Leg(-1, [(7,)], [2]), W.Leg(1, [(7,)], [2])], (0,), 3)
+    E = W.random_tensor((0,), [W.Leg(1, [(7,)], [2]), W.Leg(-1, [(7,)], [2])], (0,), 3)
+    assert E["t"].shape[0] == 1
     _, rec, _ = run_tensordot(ctx, A, E, (1,), (0,))
     assert rec["t"].shape[0] == 0 and rec["size"] == 0
     # empty input tensor
-    Z = W.random_tensor((0,), [l, W.Leg(1, [(5,)], [1])], (0,), 4)
+    Z = W.random_tensor((0,), [l, W.Leg(-1, [(5,)], [1])], (0,), 4)
     assert Z["t"].shape[0] == 0
     _, rec, _ = run_tensordot(ctx, A, Z, (1,), (0,))
     assert rec["t"].shape[0] == 0 and rec["size"] == 0
@@ -169,6 +170,8 @@ def test_fuse_unfuse_bit_exact(ctx, sym, case):
     fplan, frec = run_move(ctx, ytn.YTN_OP_FUSE, rec, groups=groups)
     check_against_oracle(frec, O.to_record(F), exact=True)
     fused = [i for i, g in enumerate(groups) if len(g) > 1]
+    if not fused:
+        return
     uplan, urec = run_move(ctx, ytn.YTN_OP_UNFUSE, frec, axa=fused)
     check_against_oracle(urec, O.to_record(O.unfuse(F, fused)), exact=True)
 
@@ -251,3 +254,126 @@ def test_config5_full_size_sampled(ctx):
     tot = np.einsum("bac,a->bc", t, np.array(rec["sig"]))
     assert np.all(tot == 0)
     assert np.all(np.isfinite(rec["data"]))
+
+
+# ------------------------------------------------------------------ split precision (BF16 slices on tcgen05)
+
+SPLIT_RTOL = 1e-10
+
+
+def _split(ctx, A, B, axa, axb, rtol=SPLIT_RTOL):
+    from paper_2405_12196_gb300 import ytn
+    return run_tensordot(ctx, A, B, axa, axb, prec=ytn.YTN_SPLIT_BF16, rtol=rtol)
+
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(6))
+def test_random_tensordot_split(ctx, sym, case):
+    mods = SYMS[sym]
+    rng = np.random.default_rng(52000 + 13 * case + len(sym))
+    rankA, rankB = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+    ncon = int(rng.integers(0, min(rankA, rankB) + 1))
+    A, B, axa, axb, _, _ = random_pair(rng, mods, rankA, rankB, ncon, max_sectors=4, max_dim=7)
+    _, rec, res = _split(ctx, A, B, axa, axb)
+    err = check_against_oracle(rec, oracle_tensordot(A, B, axa, axb), rtol=SPLIT_RTOL)
+    assert res["slices"] >= 3 and err <= max(res["err_est"], 1e-15)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (128, 128, 32), (129, 127, 33), (300, 260, 500), (40, 700, 129),
+                                  (257, 3, 1000)])
+def test_split_tiles_chunks_and_ragged_tails(ctx, dims):
+    """Tiles of 128 x 128, K stages of 32 and exact-accumulation chunks of 128, all
+    with ragged tails."""
+    M, N, K = dims
+    l_m, l_k, l_n = W.Leg(1, [(0,)], [M]), W.Leg(1, [(0,)], [K]), W.Leg(1, [(0,)], [N])
+    A = W.random_tensor((0,), [l_m, l_k], (0,), M + 3 * K)
+    B = W.random_tensor((0,), [l_k.conj(), l_n], (0,), N + 5 * K)
+    _, rec, res = _split(ctx, A, B, (1,), (0,))
+    want = A["data"].reshape(M, K) @ B["data"].reshape(K, N)
+    err = rel_frobenius(rec["data"], want.ravel())
+    assert err <= SPLIT_RTOL, err
+
+
+def test_split_is_exact_on_small_integers(ctx):
+    """Integer operands with few significant bits are represented exactly by the
+    slices and every product sum is exact: the split path must reproduce the exact
+    result bit for bit."""
+    l_m, l_k, l_n = W.Leg(1, [(0,), (1,)], [150, 70]), W.Leg(1, [(0,), (1,)], [400, 333]), W.Leg(1, [(0,), (1,)], [90, 140])
+    A = W.random_tensor((0,), [l_m, l_k.conj()], (0,), 1, fill="integer")
+    B = W.random_tensor((0,), [l_k, l_n.conj()], (0,), 2, fill="integer")
+    _, rec, _ = _split(ctx, A, B, (1,), (0,))
+    ref = oracle_tensordot(A, B, (1,), (0,))
+    check_against_oracle(rec, ref, exact=True)
+
+
+def test_split_wide_dynamic_range(ctx):
+    """Rows and columns scaled over many orders of magnitude (per-row exponents)."""
+    rng = np.random.default_rng(77)
+    l_m, l_k, l_n = W.Leg(1, [(0,)], [96]), W.Leg(1, [(0,)], [300]), W.Leg(1, [(0,)], [80])
+    A = W.random_tensor((0,), [l_m, l_k], (0,), 3)
+    B = W.random_tensor((0,), [l_k.conj(), l_n], (0,), 4)
+    A["data"] = (A["data"].reshape(96, 300) * (10.0 ** rng.uniform(-30, 30, size=(96, 1)))).ravel()
+    B["data"] = (B["data"].reshape(300, 80) * (10.0 ** rng.uniform(-30, 30, size=(1, 80)))).ravel()
+    _, rec, _ = _split(ctx, A, B, (1,), (0,))
+    want = A["data"].reshape(96, 300) @ B["data"].reshape(300, 80)
+    # relative error per output element (each row/column has its own scale)
+    got = rec["data"].reshape(96, 80)
+    rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    assert np.median(rel) <= 1e-12
+    assert rel_frobenius(got / np.abs(want).max(axis=1, keepdims=True), want / np.abs(want).max(axis=1, keepdims=True)) <= SPLIT_RTOL
+
+
+def test_split_slice_count_follows_tolerance(ctx):
+    from paper_2405_12196_gb300 import ytn
+    cfg = W.config1()
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    counts = {}
+    for rtol in (1e-4, 1e-7, 1e-10):
+        _, rec, res = _split(ctx, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"], rtol=rtol)
+        counts[rtol] = res["slices"]
+        err = check_against_oracle(rec, oracle_tensordot(cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]), rtol=rtol)
+        assert err <= res["err_est"]
+    assert counts[1e-4] <= counts[1e-7] <= counts[1e-10]
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_workspace_size(plan, ytn.YTN_SPLIT_BF16, 1e-16)
+    assert e.value.name == "YTN_E_TOLERANCE"
+
+
+def test_split_config3(ctx):
+    cfg = W.config3()
+    dl = cfg["dleg"]
+    a = W.random_tensor((0, 0), [W.Leg(-1, dl.t, dl.D), W.Leg(1, dl.t, dl.D), W.Leg(1, dl.t, dl.D),
+                                 W.Leg(-1, dl.t, dl.D)], (0, 0), 3999)
+    _, rec, res = _split(ctx, cfg["X2"], a, (1, 2), (0, 1))
+    check_against_oracle(rec, oracle_tensordot(cfg["X2"], a, (1, 2), (0, 1)), rtol=SPLIT_RTOL)
+
+
+def test_split_reports_no_device_timeout(ctx):
+    from paper_2405_12196_gb300 import ytn
+    cfg = W.config1()
+    _split(ctx, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    ytn.ytn_sync(ctx, timeout_ms=10000)
+
+
+@pytest.mark.slow
+def test_config5_full_size_split_vs_fp64(ctx):
+    """Full-size U(1)xU(1) X2 . a in the benchmark's configuration: the split path
+    against the FP64 path on every element, and sampled blocks against the oracle."""
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    cfg = W.config5()
+    A, B = cfg["A"], cfg["B"]
+    _, r64, _ = run_tensordot(ctx, A, B, cfg["axa"], cfg["axb"])
+    plan, rsp, res = _split(ctx, A, B, cfg["axa"], cfg["axb"])
+    assert res["slices"] >= 3
+    err = rel_frobenius(rsp["data"], r64["data"])
+    assert err <= SPLIT_RTOL, err
+    oA, oB = O.from_record(A), O.from_record(B)
+    rng = np.random.default_rng(1)
+    sizes = np.prod(rsp["D"], axis=1)
+    for b in list(rng.choice(rsp["t"].shape[0], 8, replace=False)) + [int(np.argmax(sizes))]:
+        key = tuple(tuple(int(c) for c in rsp["t"][b, x]) for x in range(rsp["t"].shape[1]))
+        want = O.tensordot_block(oA, oB, cfg["axa"], cfg["axb"], key)
+        got = rsp["data"][rsp["off"][b]:rsp["off"][b] + sizes[b]].reshape(want.shape)
+        assert rel_frobenius(got, want) <= SPLIT_RTOL
+    del torch
