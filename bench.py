@@ -123,6 +123,8 @@ def make_workload(name, rank):
         return W.config5(seed=5001 + seed_shift)
     if name == "cfg5b":
         return W.config5b(seed=5101 + seed_shift)
+    if name == "d14":
+        return W.config5(seed=5201 + seed_shift, D=14)
     if name == "cfg3":
         c = W.config3(seed=3001 + seed_shift)
         dl = c["dleg"]
@@ -136,6 +138,7 @@ WORKLOAD_DESC = {
     "cfg5": "U(1)xU(1) iPEPS environment contraction X2.a, D=20 (13 sectors), chi=400 (61 sectors)",
     "cfg5b": "U(1)xU(1) iPEPS environment contraction X2.a, D=20 (9 sectors, 25-sector D^2 legs), chi=400",
     "cfg3": "U(1)xU(1) CTMRG X2.a, D=12, chi=144",
+    "d14": "U(1)xU(1) iPEPS environment contraction X2.a, D=14, chi=D^2 (profiling size)",
 }
 
 

@@ -12,12 +12,14 @@
 //   E2 = A_0 B_0                     order 0, exact in FP32 per K chunk of 64
 //   E3 = A_0 B_1 + A_1 B_0           order 1, exact (an integer times 2^-8)
 //   E4 = A_0 B_2 + A_1 B_1 + A_2 B_0 order 2, exact (an integer times 2^-16)
-//   R  = every kept product of order >= 3, FP32 over the whole tile
+//   R  = every kept product of order >= 3, FP32 per K chunk of 64
 // Chunk sums stay below 2^24 units of their lowest bit (3 * 64 * 255^2 < 2^24), so
 // the three exact accumulators are exact; after each chunk the epilogue warps
-// read them from tensor memory and add them into a 64-bit fixed-point accumulator
-// (units of 2^-24 of the order-0 product). R, at most 2^-24 of the result, is
-// rounded in FP32 and read once per tile. The result is converted to FP64 and
+// read all four from tensor memory and add them into a 64-bit fixed-point
+// accumulator (units of 2^-24 of the order-0 product). Only R, at most 2^-22 of
+// the result, is rounded in FP32, and only over 64 of K at a time (the tensor
+// cores' FP32 accumulation of mixed-magnitude products is not round-to-nearest,
+// so its error grows with the number of additions). The result is converted to FP64 and
 // scaled by 2^(e_i + f_j - 40). Tensor memory: E2 [0,128), E3 [128,256),
 // E4 [256,384), R [384,512).
 //
@@ -26,8 +28,8 @@
 //              one of the B block (s slices each, 8 KB per slice) into a
 //              double-buffered shared-memory ring;
 //   warp 1     MMA issuer (one thread): tcgen05.mma kind::f16, M = N = 128, K = 16;
-//              inside a chunk the R products are issued first, so that the drain
-//              of the previous chunk's exact accumulators overlaps tensor work;
+//              the drain of the exact accumulators overlaps a chunk's last R
+//              products, the drain of R the next chunk's first exact products;
 //   warps 2-3  idle;
 //   warps 4-15 epilogue: chunk drains and the FP64 output (three warps per
 //              32-lane quarter of tensor memory, 40, 40 and 48 columns), which
@@ -135,10 +137,77 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// acc * 2^e as an FP64 value, rounded to nearest even. The bit pattern is built
+// with integer operations (FP64 arithmetic is slow on this GPU); results outside
+// the normal range take the FP64 path.
+__device__ __forceinline__ double scaled_double(long long acc, int e) {
+  if (acc == 0) return 0.0;
+  const unsigned long long sign = acc < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long m = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;
+  const int lz = __clzll((long long)m);
+  const unsigned long long mn = m << lz;           // leading one at bit 63
+  unsigned long long mant = mn >> 11;               // 53 bits with the leading one
+  const unsigned long long rem = mn & 0x7FFull;
+  int be = 63 - lz + e + 1023;                      // biased exponent of the result
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+    mant += 1ull;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      be += 1;
+    }
+  }
+  if (be >= 1 && be <= 2046)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+  const int ec = min(max(e, -2044), 2046), e1 = ec >> 1, e2 = ec - e1;
+  return __ll2double_rn(acc) * __longlong_as_double((long long)(e1 + 1023) << 52) *
+         __longlong_as_double((long long)(e2 + 1023) << 52);
+}
+
+// Descriptor offsets in the 16-byte units of the start-address field: one slice
+// (8 KB) and one K step of 16 (32 bytes). The shared-memory footprint stays below
+// 256 KB, so additions never carry out of the 14-bit field.
+constexpr uint64_t kSliceU = kSliceBytes >> 4, kStepU = 2;
+
+// Orders 0, 1, 2 of one 32-wide K stage into the exact accumulators; `fresh`
+// starts a new chunk. a0 / b0: descriptors of slice 0 of the stage.
+__device__ __forceinline__ void issue_exact(uint32_t tmem, uint64_t a0, uint64_t b0, bool fresh) {
+#pragma unroll
+  for (int ks = 0; ks < 2; ks++) {
+    const uint64_t a = a0 + ks * kStepU, b = b0 + ks * kStepU;
+    const uint32_t acc = (fresh && ks == 0) ? 0u : 1u;
+    umma(tmem + kColE2, a, b, acc);
+    umma(tmem + kColE3, a, b + kSliceU, acc);
+    umma(tmem + kColE3, a + kSliceU, b, 1u);
+    umma(tmem + kColE4, a, b + 2 * kSliceU, acc);
+    umma(tmem + kColE4, a + kSliceU, b + kSliceU, 1u);
+    umma(tmem + kColE4, a + 2 * kSliceU, b, 1u);
+  }
+}
+
+// Orders 3 .. S-1 of one stage into R; `fresh` starts a new chunk.
+template <int S>
+__device__ __forceinline__ void issue_rest(uint32_t tmem, uint64_t a0, uint64_t b0, bool fresh) {
+#pragma unroll
+  for (int ks = 0; ks < 2; ks++) {
+    const uint64_t a = a0 + ks * kStepU, b = b0 + ks * kStepU;
+#pragma unroll
+    for (int L = 3; L <= S - 1; L++) {
+#pragma unroll
+      for (int p = 0; p <= L; p++) {
+        if (p > S - 1 || L - p > S - 1) continue;
+        const uint32_t acc = (fresh && ks == 0 && L == 3 && p == 0) ? 0u : 1u;
+        umma(tmem + kColR, a + p * kSliceU, b + (L - p) * kSliceU, acc);
+      }
+    }
+  }
+}
+
+template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_split_kernel(const SplitSector *__restrict__ sectors, const SplitTile *__restrict__ tiles, int ntiles,
                       const uint8_t *__restrict__ sa, const uint8_t *__restrict__ sb, const int32_t *__restrict__ ea,
-                      const int32_t *__restrict__ eb, double *__restrict__ wc, int s, int *status) {
+                      const int32_t *__restrict__ eb, double *__restrict__ wc, int *status) {
+  constexpr int s = S;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStagesRing * kSlotBytes);
@@ -214,60 +283,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t aS = slot_base + slot * kSlotBytes, bS = aS + kBlockBytes;
             const bool first = st == st0, last = st == st1 - 1;
-            auto mma = [&](uint32_t col, int p, int q, int ks, uint32_t acc) {
-              umma(tmem + col, sdesc(aS + p * kSliceBytes + ks * 32), sdesc(bS + q * kSliceBytes + ks * 32), acc);
-            };
-            // orders 0, 1, 2 into the exact accumulators; `fresh` starts a new chunk
-            auto issue_E = [&](bool fresh) {
-              for (int ks = 0; ks < 2; ks++) {
-                const uint32_t acc = (fresh && ks == 0) ? 0u : 1u;
-                mma(kColE2, 0, 0, ks, acc);
-                mma(kColE3, 0, 1, ks, acc);
-                mma(kColE3, 1, 0, ks, 1u);
-                mma(kColE4, 0, 2, ks, acc);
-                mma(kColE4, 1, 1, ks, 1u);
-                mma(kColE4, 2, 0, ks, 1u);
-              }
-            };
-            // orders 3 .. s-1 into R; `fresh` starts a new tile
-            auto issue_R = [&](bool fresh) {
-              for (int ks = 0; ks < 2; ks++)
-                for (int L = 3; L <= s - 1; L++)
-                  for (int p = (L > s - 1 ? L - (s - 1) : 0); p <= L && p <= s - 1; p++)
-                    mma(kColR, p, L - p, ks, (fresh && ks == 0 && L == 3 && p == 0) ? 0u : 1u);
-            };
+            const uint64_t a0 = sdesc(aS), b0 = sdesc(bS);
             auto wait_e_empty = [&]() {
               if (cc >= 1) {
                 ok = mbar_wait(bar(kEEmpty), (cc - 1) & 1, abort_flag, status, 5);
                 tc_fence_after();
               }
             };
-            if (first && c == 0) {
-              // new tile: exact accumulators after the previous chunk's drain, R after
-              // the previous tile's R was read
+            // Every chunk starts all four accumulators afresh: the exact ones once the
+            // previous chunk's exact drain is done, R once its R drain is done. The
+            // drain of the exact accumulators overlaps the chunk's last R products,
+            // the drain of R the next chunk's first exact products.
+            if (first) {
               wait_e_empty();
               if (!ok) break;
-              issue_E(true);
-              if (tcount >= 1) {
-                ok = mbar_wait(bar(kREmpty), (tcount - 1) & 1, abort_flag, status, 4);
+              issue_exact(tmem, a0, b0, true);
+              if (last) umma_commit(bar(kEFull));
+              if (cc >= 1) {
+                ok = mbar_wait(bar(kREmpty), (cc - 1) & 1, abort_flag, status, 4);
                 if (!ok) break;
                 tc_fence_after();
               }
-              issue_R(true);
-              if (last) umma_commit(bar(kEFull));
-            } else if (first) {
-              issue_R(false);
-              wait_e_empty();
-              if (!ok) break;
-              issue_E(true);
-              if (last) umma_commit(bar(kEFull));
+              issue_rest<S>(tmem, a0, b0, true);
             } else {
-              issue_E(false);
+              issue_exact(tmem, a0, b0, false);
               umma_commit(bar(kEFull));
-              issue_R(false);
+              issue_rest<S>(tmem, a0, b0, false);
             }
             umma_commit(bar(kEmpty0 + slot));
-            if (last && c == nchunks - 1) umma_commit(bar(kRFull));
+            if (last) umma_commit(bar(kRFull));
           }
         }
       }
@@ -307,7 +351,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-              const long long x2 = __float2int_rn(__uint_as_float(v2[i]));
+              // order 0: |E2| < 2^22, converted through the FP32 bit pattern
+              const long long x2 = __float_as_int(__uint_as_float(v2[i]) + 12582912.0f) - 0x4B400000;
               const long long x3 = __float2int_rn(__uint_as_float(v3[i]) * 256.0f);
               const long long x4 = __float2int_rn(__uint_as_float(v4[i]) * 65536.0f);
               acc[g * 4 + i] += (x2 << 24) + (x3 << 16) + (x4 << 8);
@@ -317,24 +362,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(kEEmpty));
-      }
-      if (!ok) break;
-      ok = mbar_wait(bar(kRFull), tcount & 1, abort_flag, status, 8);
-      if (!ok) break;
-      tc_fence_after();
+        ok = mbar_wait(bar(kRFull), cc & 1, abort_flag, status, 8);
+        if (!ok) break;
+        tc_fence_after();
 #pragma unroll
-      for (int g = 0; g < 6; g++) {
-        if (g < ngroups / 2) {
-          uint32_t vr[8];
-          tmem_ld8(lane_addr + kColR + c0 + g * 8, vr);
-          tmem_wait_ld();
+        for (int g = 0; g < 6; g++) {
+          if (g < ngroups / 2) {
+            uint32_t vr[8];
+            tmem_ld8(lane_addr + kColR + c0 + g * 8, vr);
+            tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 8; i++) acc[g * 8 + i] += __float2ll_rn(__uint_as_float(vr[i]) * 16777216.0f);
+            // |R| over one chunk < 64 * 4 * 255^2 * 2^-24 < 1, so R * 2^24 fits 32 bits
+            for (int i = 0; i < 8; i++)
+              acc[g * 8 + i] += (long long)__float2int_rn(__uint_as_float(vr[i]) * 16777216.0f);
+          }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(kREmpty));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(kREmpty));
+      if (!ok) break;
       // C = acc * 2^(e_i + f_j - 40)
       const int row = tl.mt * kSplitBM + rl;
       if (row < sc.M) {
@@ -345,11 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 48; j++) {
           if (j < ngroups * 4 && n0 + j < sc.N) {
-            // acc * 2^e as two exact power-of-two factors (covers |e| <= 2044)
-            const int e = min(max(ei + __ldg(fcol + j) - 40, -2044), 2046);
-            const int e1 = e >> 1, e2 = e - e1;
-            crow[n0 + j] = __ll2double_rn(acc[j]) * __longlong_as_double((long long)(e1 + 1023) << 52) *
-                           __longlong_as_double((long long)(e2 + 1023) << 52);
+            crow[n0 + j] = scaled_double(acc[j], ei + __ldg(fcol + j) - 40);
           }
         }
       }
@@ -368,11 +411,11 @@ cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles
                               int *status, int num_sms, cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles > INT32_MAX || slices < 4 || slices > kSlices) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(gemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  auto kernel = slices == 4 ? gemm_split_kernel<4> : slices == 5 ? gemm_split_kernel<5> : gemm_split_kernel<6>;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<int64_t>(ntiles, num_sms);
-  gemm_split_kernel<<<grid, kThreads, kSmemBytes, stream>>>(sectors, tiles, (int)ntiles, sa, sb, ea, eb, wc, slices,
-                                                            status);
+  kernel<<<grid, kThreads, kSmemBytes, stream>>>(sectors, tiles, (int)ntiles, sa, sb, ea, eb, wc, status);
   return cudaGetLastError();
 }
 
