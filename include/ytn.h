@@ -210,6 +210,23 @@ ytn_status ytn_tensordot(ytn_plan_t *plan, const double *a, const double *b, dou
                          ytn_precision prec, double rtol, void *workspace,
                          size_t workspace_bytes, ytn_result *res, ytn_stream stream);
 
+/* C = tensordot(A, B) on the FP64 path without a caller workspace and without
+ * allocating anything. The paper has no counterpart: this is for callers that
+ * cannot allocate device memory, for instance code inside a host application
+ * that reserves all device memory for its own pool, or code that must not call
+ * cudaMalloc for its latency and implicit synchronisation. The plan must exist
+ * already (ytn_plan uploads its tables once). The workspace is a static 64 MiB
+ * array inside the library, present on every GPU that loads the library until
+ * the process exits; plans whose FP64 workspace (ytn_workspace_size) exceeds
+ * 64 MiB are rejected with YTN_E_WORKSPACE. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture. Every call uses the same
+ * array: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller. Results are those of ytn_tensordot with
+ * YTN_FP64. Errors: as ytn_tensordot, plus YTN_E_WORKSPACE (too large). */
+ytn_status ytn_tensordot_noalloc(ytn_plan_t *plan, const double *a, const double *b, double *c,
+                                 ytn_stream stream);
+
 /* out = fuse(a) / unfuse(a) (Sec. II.B). a: device buffer of the planned
  * input's size; out: device buffer of ytn_plan_output(plan)->size elements,
  * every element written (fused entries with no stored block are zero).

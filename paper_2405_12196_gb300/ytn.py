@@ -97,6 +97,7 @@ SYMBOLS = {
     "ytn_workspace_size": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
     "ytn_tensordot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                 C.c_void_p, C.c_size_t, C.POINTER(ytn_result), C.c_void_p]),
+    "ytn_tensordot_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_fuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_unfuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -317,6 +318,12 @@ def ytn_tensordot(plan, a, b, c, prec=YTN_FP64, rtol=0.0, workspace=None, worksp
                               _ptr(workspace), int(workspace_bytes), C.byref(res), _stream(stream)))
     return {"useful_flops": res.useful_flops, "precision": res.precision, "slices": res.slices,
             "err_est": res.err_est}
+
+
+def ytn_tensordot_noalloc(plan, a, b, c, stream=None):
+    """FP64 contraction with the library's static scratch instead of a caller
+    workspace (for callers that cannot allocate device memory)."""
+    _check(_lib.ytn_tensordot_noalloc(plan.handle, _ptr(a), _ptr(b), _ptr(c), _stream(stream)))
 
 
 def ytn_fuse(plan, a, out, stream=None):
