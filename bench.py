@@ -403,6 +403,91 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ serving (continuous batching)
+
+def run_serving(args):
+    """Poisson stream of tensordot requests from independent U(1) iPEPS runs (D uniform
+    in {4,6,8,10,12}, chi in [4D, 8D], random sector splits per run), tensors resident on
+    the device, admission by an HBM budget, served by the library's continuous-batching
+    server. First the saturation rate is measured (all requests at once), then the
+    requests arrive as a Poisson stream at 0.8x that rate; latency = completion time -
+    arrival time."""
+    import torch
+
+    from paper_2405_12196_gb300 import ytn
+    dev = torch.device("cuda:0")
+    prec = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}[args.precision]
+    ctx = ytn.ytn_ctx_create(0)
+    runs = W.serving_runs(nruns=args.serve_runs)
+    res = []
+    resident = 0
+    for r in runs:
+        X2, a = W.serving_request(r)
+        plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, X2, a, (1, 2), (0, 1))
+        da = torch.from_numpy(X2["data"]).to(dev)
+        db = torch.from_numpy(a["data"]).to(dev)
+        dc = torch.empty(max(plan.out["size"], 1), dtype=torch.float64, device=dev)
+        resident += 8 * (da.numel() + db.numel() + dc.numel())
+        res.append({"plan": plan, "a": da, "b": db, "c": dc, "flops": plan.info["useful_flops"],
+                    "D": r["D"], "chi": r["chi"]})
+    budget = int(args.serve_budget_gb * 1e9)
+    arena_bytes = (budget - resident) // 256 * 256
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(4242)
+    pick = rng.integers(0, len(res), size=args.serve_requests)
+    total_flops = float(sum(res[i]["flops"] for i in pick))
+
+    def serve(arrivals):
+        srv = ytn.Server(ctx, args.serve_slots, arena)
+        t0 = srv.now_ms()
+        for k, i in enumerate(pick):
+            ta = t0 + arrivals[k]
+            while True:
+                now = srv.now_ms()
+                if now >= ta:
+                    break
+                if ta - now > 0.2:
+                    time.sleep((ta - now - 0.1) * 1e-3)
+            r = res[i]
+            srv.submit(k, r["plan"], r["a"], r["b"], r["c"], prec=prec, rtol=args.rtol, t_arrive=ta)
+        srv.drain(timeout_ms=600000)
+        infos = srv.poll(len(pick) + 16)
+        srv.close()
+        assert len(infos) == len(pick) and all(x["status"] == 0 for x in infos), "request failed"
+        lat = np.array([x["t_done"] - x["t_arrive"] for x in infos])
+        span = max(x["t_done"] for x in infos) - min(x["t_arrive"] for x in infos)
+        return lat, span
+
+    for i in range(len(res)):   # warm every plan once
+        r = res[i]
+        ws = torch.empty(ytn.ytn_workspace_size(r["plan"], prec, args.rtol), dtype=torch.uint8, device=dev)
+        ytn.ytn_tensordot(r["plan"], r["a"], r["b"], r["c"], prec=prec, rtol=args.rtol, workspace=ws)
+        del ws
+    torch.cuda.synchronize()
+    lat_sat, span_sat = serve(np.zeros(len(pick)))
+    rate = len(pick) / span_sat            # requests per ms at saturation
+    lam = 0.8 * rate
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(pick)))
+    lat, span = serve(arrivals)
+    line = {
+        "metric": "serving: block-sparse tensordot requests, p50/p99 latency and useful TFLOP/s",
+        "value": total_flops / (span * 1e-3) / 1e12, "unit": "TFLOP/s", "impl": "ours", "n_gpus": 1,
+        "higher_is_better": True, "precision": args.precision, "data": "synthetic",
+        "config": {"workload": f"{len(pick)} requests from {len(res)} independent U(1) iPEPS runs, D in "
+                               f"{{4,6,8,10,12}}, chi in [4D,8D]; X2 . a over two legs",
+                   "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
+                   "resident_gb": resident / 1e9, "arena_gb": arena_bytes / 1e9,
+                   "requests_flops": total_flops},
+        "saturation": {"requests_per_s": rate * 1e3, "tflops": total_flops / (span_sat * 1e-3) / 1e12,
+                       "p50_ms": float(np.percentile(lat_sat, 50)), "p99_ms": float(np.percentile(lat_sat, 99))},
+        "poisson": {"rate_per_s": lam * 1e3, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                    "span_ms": span},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,11 +502,18 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="run the continuous-batching serving benchmark")
+    ap.add_argument("--serve-runs", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -243,6 +243,78 @@ ytn_status ytn_trace(ytn_plan_t *plan, const double *a, double *out, ytn_stream 
  * stream reported an error. */
 ytn_status ytn_sync(ytn_ctx *ctx, ytn_stream stream, int64_t timeout_ms);
 
+/* ---------------------------------------------------------------------------
+ * Graphs: batching a sequence of calls (for instance the contractions and
+ * fusions of one corner-transfer-matrix step, Sec. III Fig. 3) into one CUDA
+ * graph that the host launches with a single call. No counterpart in the paper.
+ * Between ytn_graph_begin and ytn_graph_end, execution calls on `stream` (a
+ * created stream, not the default stream) are recorded instead of run; the
+ * data and workspace buffers they name stay owned by the caller, must stay
+ * valid while the graph exists, and are reused by every launch. The graph
+ * holds a reference to each plan that a recorded call used (released by
+ * ytn_graph_destroy), so the caller may release its own. One capture per
+ * context at a time (YTN_E_INVALID otherwise); a CUDA failure in capture or
+ * instantiation returns YTN_E_CUDA and leaves no graph. Phase timing is not
+ * recorded while a stream is being captured.
+ * ------------------------------------------------------------------------- */
+typedef struct ytn_graph_s ytn_graph_t;
+ytn_status ytn_graph_begin(ytn_ctx *ctx, ytn_stream stream);
+ytn_status ytn_graph_end(ytn_ctx *ctx, ytn_stream stream, ytn_graph_t **graph);
+ytn_status ytn_graph_launch(ytn_graph_t *graph, ytn_stream stream);
+void ytn_graph_destroy(ytn_graph_t *graph);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of contraction requests (no counterpart in the
+ * paper, whose CTM drivers run one contraction at a time).
+ *
+ * A server owns `nslots` CUDA streams and an admission thread. Submitted
+ * requests wait in FIFO order; a request is admitted as soon as a slot is free
+ * and its workspace (ytn_workspace_size for its precision) fits in the device
+ * arena the caller handed over (the HBM budget for workspaces; inputs and
+ * outputs stay wherever the caller keeps them). Admitted requests run
+ * concurrently on their slots' streams, overlapping on the device; a finished
+ * request releases its slot and its arena range. Each request computes exactly
+ * what ytn_tensordot computes alone (no cross-request state), so its result does
+ * not depend on what else runs. Times are milliseconds on the server's steady
+ * clock (ytn_server_now_ms).
+ * ------------------------------------------------------------------------- */
+typedef struct ytn_server_s ytn_server_t;
+
+typedef struct {
+  int64_t id;          /* the caller's request id                               */
+  int32_t status;      /* ytn_status of the request                             */
+  int32_t slot;        /* stream slot it ran on                                 */
+  double t_arrive;     /* arrival time given at submission                      */
+  double t_admit;      /* admitted (slot and arena range granted, launched)     */
+  double t_done;       /* completion observed by the server                     */
+  size_t workspace;    /* arena bytes it held                                   */
+} ytn_request_info;
+
+/* arena: device buffer of arena_bytes (256-byte aligned) owned by the caller for
+ * the server's lifetime. Errors: YTN_E_INVALID, YTN_E_CUDA. */
+ytn_status ytn_server_create(ytn_ctx *ctx, int nslots, void *arena, size_t arena_bytes,
+                             ytn_server_t **server);
+
+/* Queue C = tensordot(A, B) for `plan` (a, b, c: device buffers as for
+ * ytn_tensordot). t_arrive < 0 means now. Requests larger than the whole arena
+ * fail at once with YTN_E_WORKSPACE (reported through ytn_server_poll). */
+ytn_status ytn_server_submit(ytn_server_t *server, int64_t id, ytn_plan_t *plan, const double *a,
+                             const double *b, double *c, ytn_precision prec, double rtol,
+                             double t_arrive);
+
+/* Move up to `max` finished requests into out[]; *n receives the count. */
+ytn_status ytn_server_poll(ytn_server_t *server, ytn_request_info *out, int64_t max, int64_t *n);
+
+/* Wait until every submitted request has finished (at most timeout_ms; < 0
+ * without limit). YTN_E_TIMEOUT if some are still running. */
+ytn_status ytn_server_drain(ytn_server_t *server, int64_t timeout_ms);
+
+/* Current time on the server's clock, in milliseconds. */
+double ytn_server_now_ms(const ytn_server_t *server);
+
+/* Drains, stops the admission thread and destroys the streams. */
+void ytn_server_destroy(ytn_server_t *server);
+
 /* Phase timing. While enabled on a context, every execution call on its plans
  * records a CUDA event pair on the call's stream around each kernel phase
  * (events come from a pool created by ytn_profile_enable; when the pool is

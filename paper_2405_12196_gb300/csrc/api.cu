@@ -107,6 +107,8 @@ class PhaseTimer {
  public:
   PhaseTimer(ytn_ctx *ctx, int phase, cudaStream_t st) : ctx_(ctx), st_(st) {
     if (!ctx_->prof) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st_, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(ctx_->prof_mu);
     if (ctx_->ev_next + 2 > ctx_->ev_pool.size()) {
       ctx_->dropped++;
@@ -126,6 +128,17 @@ class PhaseTimer {
   cudaStream_t st_;
   int idx_ = -1;
 };
+
+// A plan used by a launch that is being recorded into a graph stays alive
+// until the graph is destroyed.
+static void note_capture(ytn_plan_t *p, cudaStream_t st) {
+  ytn_ctx *c = p->ctx;
+  if (!c->capturing.load()) return;
+  std::lock_guard<std::mutex> lk(c->cap_mu);
+  if (c->cap_stream != static_cast<void *>(st)) return;
+  p->refs++;
+  c->cap_plans.push_back(p);
+}
 
 // Workspace: WA | WB | WC (FP64 sector matrices), then for the split path
 // SA | SB (BF16 slice blocks) | EA | EB (row / column exponents); 256-byte aligned.
@@ -212,6 +225,11 @@ ytn_status ytn_ctx_create(ytn_ctx **ctx, int device) {
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  e = configure_split_gemm();
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "configure split-precision GEMM");
   }
   e = cudaMalloc(&c->status_dev, sizeof(int) * 4);
   if (e != cudaSuccess) {
@@ -407,6 +425,7 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
   DeviceGuard g(p->ctx->device);
   if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  note_capture(p, st);
   char *ws = static_cast<char *>(workspace);
   double *wa = reinterpret_cast<double *>(ws + w.wa), *wb = reinterpret_cast<double *>(ws + w.wb),
          *wc = reinterpret_cast<double *>(ws + w.wc);
@@ -468,6 +487,7 @@ static ytn_status run_move(ytn_plan_t *p, Kind k, const double *a, double *out, 
   DeviceGuard g(p->ctx->device);
   if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  note_capture(p, st);
   cudaError_t e;
   if (p->zero_out && (e = cudaMemsetAsync(out, 0, (size_t)p->out.size * 8, st)) != cudaSuccess)
     return cuda_fail(e, "memset output");

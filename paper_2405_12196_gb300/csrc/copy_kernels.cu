@@ -10,6 +10,10 @@
 //   tile mode: the two layouts have different contiguous dimensions; a 32x32
 //     tile is staged through shared memory so that both the global loads and
 //     the global stores are coalesced.
+//   staged modes: blocks of at most a few thousand elements, up to 32 of them
+//     per CTA, pass whole through shared memory: the contiguous side is moved
+//     linearly, the strided side in its own coalescing order, so that one CTA
+//     moves about 32 KB whatever the block shapes.
 #include <cuda_runtime.h>
 
 #include "kernels.hpp"
@@ -33,13 +37,86 @@ __device__ __forceinline__ void row_offsets(const CopyJob &J, uint32_t row, int6
   }
 }
 
+// Element l (in the order of the job's dims) of a staged job: its offsets
+// along the two sides, relative to the job's origins.
+__device__ __forceinline__ void staged_offsets(const CopyJob &J, uint32_t l, int64_t &so, int64_t &dof) {
+  so = 0;
+  dof = 0;
+  for (int i = J.nd - 1; i > 0; i--) {
+    const uint32_t e = (uint32_t)J.ext[i];
+    const uint32_t idx = l % e;
+    l /= e;
+    so += (int64_t)idx * J.sst[i];
+    dof += (int64_t)idx * J.dst[i];
+  }
+  so += (int64_t)l * J.sst[0];
+  dof += (int64_t)l * J.dst[0];
+}
+
+union CopySmem {
+  double tile[kTile][kTile + 1];
+  double stage[kStageElems];
+};
+
+__device__ __forceinline__ void copy_staged(const CopyJob *__restrict__ jobs, const CopyItem &it,
+                                            const double *__restrict__ src, double *__restrict__ dst,
+                                            CopyJob *Js, double *stage) {
+  const int nj = -it.count;
+  const int total = (int)it.begin;
+  if (nj > kStageJobs || total > kStageElems) return;   // the planner never makes such items
+  {
+    const int32_t *s = reinterpret_cast<const int32_t *>(jobs + it.job);
+    int32_t *d = reinterpret_cast<int32_t *>(Js);
+    for (int w = threadIdx.x; w < nj * 32; w += kThreads) d[w] = s[w];
+  }
+  __syncthreads();
+  const bool src_linear = Js[0].mode == 2;
+  // load: contiguous source ranges (mode 2) or the strided source in its own order (mode 3)
+  int j = 0;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    while (j + 1 < nj && Js[j + 1].p <= e) j++;
+    const CopyJob &J = Js[j];
+    const int l = e - J.p;
+    if (src_linear) {
+      stage[e] = __ldg(src + J.src_off + l);
+    } else {
+      int64_t so, dof;
+      staged_offsets(J, (uint32_t)l, so, dof);
+      const int64_t at = J.p + dof;
+      if (at < total) stage[at] = __ldg(src + J.src_off + so);
+    }
+  }
+  __syncthreads();
+  // store: the strided destination in its own order (mode 2) or contiguous ranges (mode 3)
+  j = 0;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    while (j + 1 < nj && Js[j + 1].p <= e) j++;
+    const CopyJob &J = Js[j];
+    const int l = e - J.p;
+    if (src_linear) {
+      int64_t so, dof;
+      staged_offsets(J, (uint32_t)l, so, dof);
+      const int64_t at = J.p + so;
+      if (at < total) dst[J.dst_off + dof] = stage[at];
+    } else {
+      dst[J.dst_off + l] = stage[e];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) copy_kernel(const CopyJob *__restrict__ jobs,
                                                         const CopyItem *__restrict__ items,
                                                         const double *__restrict__ src,
                                                         double *__restrict__ dst) {
-  __shared__ CopyJob J;
-  __shared__ double tile[kTile][kTile + 1];
+  __shared__ CopyJob Js[kStageJobs];
+  __shared__ CopySmem sm;
+  CopyJob &J = Js[0];
+  auto &tile = sm.tile;
   const CopyItem it = items[blockIdx.x];
+  if (it.count < 0) {
+    copy_staged(jobs, it, src, dst, Js, sm.stage);
+    return;
+  }
   if (threadIdx.x < 32) {
     const int32_t *s = reinterpret_cast<const int32_t *>(&jobs[it.job]);
     reinterpret_cast<int32_t *>(&J)[threadIdx.x] = s[threadIdx.x];

@@ -406,14 +406,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
+// Opt the kernels in to their shared-memory size; once per device (a context
+// does it at creation), so that launches stay free of non-stream calls.
+cudaError_t configure_split_gemm() {
+  for (auto kernel : {gemm_split_kernel<4>, gemm_split_kernel<5>, gemm_split_kernel<6>}) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
                               const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc, int slices,
                               int *status, int num_sms, cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles > INT32_MAX || slices < 4 || slices > kSlices) return cudaErrorInvalidValue;
   auto kernel = slices == 4 ? gemm_split_kernel<4> : slices == 5 ? gemm_split_kernel<5> : gemm_split_kernel<6>;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  if (e != cudaSuccess) return e;
   const int grid = (int)std::min<int64_t>(ntiles, num_sms);
   kernel<<<grid, kThreads, kSmemBytes, stream>>>(sectors, tiles, (int)ntiles, sa, sb, ea, eb, wc, status);
   return cudaGetLastError();

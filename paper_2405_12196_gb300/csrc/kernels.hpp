@@ -25,6 +25,9 @@ cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_item
                               int32_t *ea, int32_t *eb, uint8_t *sa, uint8_t *sb, int slices,
                               cudaStream_t stream);
 
+// Shared-memory opt-in of the split-precision GEMM kernels (once per device).
+cudaError_t configure_split_gemm();
+
 // Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output C_q.
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
                               const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc, int slices,

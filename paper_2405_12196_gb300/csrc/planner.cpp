@@ -321,10 +321,76 @@ static int64_t job_units(const CopyJob &J) {
   return u;
 }
 
-// Split jobs [j0, j1) into CTA work items of about 8K elements.
+static int64_t job_elems(const CopyJob &J) {
+  int64_t n = 1;
+  for (int i = 0; i < J.nd; i++) n *= J.ext[i];
+  return n;
+}
+
+// True if the job's elements fill one dense range on the source (or the
+// destination) side.
+static bool side_dense(const CopyJob &J, bool src) {
+  std::vector<std::pair<int64_t, int64_t>> v;   // (stride, extent)
+  for (int i = 0; i < J.nd; i++)
+    if (J.ext[i] > 1) v.push_back({src ? J.sst[i] : J.dst[i], J.ext[i]});
+  std::sort(v.begin(), v.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+  int64_t expect = 1;
+  for (size_t i = v.size(); i-- > 0;) {
+    if (v[i].first != expect) return false;
+    expect *= v[i].second;
+  }
+  return true;
+}
+
+// Staged mode for a small job with a dense side (2: source, 3: destination),
+// else the job keeps its mode. Mode 3 lists the dims in source order.
+static void stage_job(CopyJob &J) {
+  if (job_elems(J) > kStageElems) return;
+  if (side_dense(J, true)) {
+    J.mode = 2;
+    return;
+  }
+  if (!side_dense(J, false)) return;
+  int idx[kMaxCopyDims];
+  for (int i = 0; i < J.nd; i++) idx[i] = i;
+  std::stable_sort(idx, idx + J.nd, [&](int a, int b) { return J.sst[a] > J.sst[b]; });
+  CopyJob K = J;
+  for (int i = 0; i < J.nd; i++) {
+    K.ext[i] = J.ext[idx[i]];
+    K.sst[i] = J.sst[idx[i]];
+    K.dst[i] = J.dst[idx[i]];
+  }
+  K.mode = 3;
+  J = K;
+}
+
+// Split jobs [j0, j1) into CTA work items of about 8K elements; runs of small
+// staged jobs of one mode are packed into items of at most kStageElems
+// elements and kStageJobs jobs.
 static void make_items(ytn_plan_t *p, size_t j0, size_t j1) {
+  for (size_t j = j0; j < j1; j++) stage_job(p->jobs[j]);
   for (size_t j = j0; j < j1; j++) {
-    const CopyJob &J = p->jobs[j];
+    CopyJob &J = p->jobs[j];
+    if (J.mode >= 2) {
+      const int mode = J.mode;
+      size_t k = j;
+      int64_t tot = 0;
+      while (k < j1 && p->jobs[k].mode == mode && k - j < (size_t)kStageJobs &&
+             tot + job_elems(p->jobs[k]) <= kStageElems) {
+        CopyJob &K = p->jobs[k];
+        K.p = (int32_t)tot;
+        K.nchunk = (int32_t)job_elems(K);
+        tot += K.nchunk;
+        k++;
+      }
+      CopyItem it;
+      it.job = (int32_t)j;
+      it.count = -(int32_t)(k - j);
+      it.begin = tot;
+      p->items.push_back(it);
+      j = k - 1;
+      continue;
+    }
     const int64_t units = job_units(J);
     int64_t per_unit;
     if (J.mode == 0) per_unit = std::min<int64_t>(J.ext[J.nd - 1], kRowChunk);

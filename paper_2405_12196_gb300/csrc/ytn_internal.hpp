@@ -27,6 +27,13 @@ constexpr int kMaxCopyDims = 8;
 //                    (1 for a contiguous copy);
 //   mode 1 ("tile"): 32x32 shared-memory transpose between the destination-
 //                    contiguous dim nd-1 and the source-contiguous dim p.
+//   modes 2 and 3 ("staged"): small blocks, several to a CTA, staged whole in
+//                    shared memory. Mode 2: the source range is contiguous; it
+//                    is read linearly and written out in destination order.
+//                    Mode 3: the destination range is contiguous; dims are
+//                    listed in source order (source stride 1 innermost), read
+//                    in that order and written out linearly. p is the job's
+//                    offset in its item's staging buffer, nchunk its size.
 struct CopyJob {
   int64_t src_off;
   int64_t dst_off;
@@ -42,9 +49,13 @@ static_assert(sizeof(CopyJob) == 128, "CopyJob layout");
 
 constexpr int kRowChunk = 2048;   // mode-0 column chunk
 constexpr int kTile = 32;         // mode-1 tile edge
+constexpr int kStageElems = 4096; // staged modes: elements per CTA item
+constexpr int kStageJobs = 32;    // staged modes: jobs per CTA item
 
 // A contiguous range of work units of one job, processed by one CTA.
 // Units: mode 0 = (row, column chunk) pairs; mode 1 = 32x32 tiles.
+// Staged items: jobs [job, job - count) (count < 0) of one staged mode, with
+// begin = their total size (at most kStageElems).
 struct CopyItem {
   int32_t job;
   int32_t count;
@@ -189,6 +200,12 @@ struct ytn_ctx {
   std::vector<std::pair<int, int>> pending;
   int64_t dropped = 0;
   std::mutex prof_mu;
+  // graph capture: the stream being captured (cudaStream_t as void*) and the
+  // plans whose device tables the recorded launches use (one reference each)
+  std::atomic<bool> capturing{false};
+  void *cap_stream = nullptr;
+  std::vector<ytn_plan_s *> cap_plans;
+  std::mutex cap_mu;
 };
 
 struct ytn_plan_s {

@@ -86,6 +86,11 @@ class ytn_result(C.Structure):
                 ("err_est", C.c_double)]
 
 
+class ytn_request_info(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("slot", C.c_int32), ("t_arrive", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("workspace", C.c_size_t)]
+
+
 # entry points declared in include/ytn.h
 SYMBOLS = {
     "ytn_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
@@ -104,6 +109,17 @@ SYMBOLS = {
     "ytn_sync": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "ytn_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ytn_profile_read": (C.c_int, [C.c_void_p, C.POINTER(ytn_profile)]),
+    "ytn_graph_begin": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ytn_graph_end": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "ytn_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ytn_graph_destroy": (None, [C.c_void_p]),
+    "ytn_server_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]),
+    "ytn_server_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_int, C.c_double, C.c_double]),
+    "ytn_server_poll": (C.c_int, [C.c_void_p, C.POINTER(ytn_request_info), C.c_int64, C.POINTER(C.c_int64)]),
+    "ytn_server_drain": (C.c_int, [C.c_void_p, C.c_int64]),
+    "ytn_server_now_ms": (C.c_double, [C.c_void_p]),
+    "ytn_server_destroy": (None, [C.c_void_p]),
     "ytn_last_error": (C.c_char_p, []),
     "ytn_version": (C.c_char_p, []),
 }
@@ -358,3 +374,76 @@ def ytn_profile_read(ctx):
 def available_precisions():
     """Precisions this build of the library executes."""
     return [YTN_FP64, YTN_SPLIT_BF16]
+
+
+# ------------------------------------------------------------------ graphs
+
+class Graph:
+    """A recorded sequence of library calls (ytn_graph_*), replayed by launch()."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def launch(self, stream):
+        _check(_lib.ytn_graph_launch(self.handle, _stream(stream)))
+
+    def close(self):
+        h, self.handle = self.handle, None
+        if h:
+            _lib.ytn_graph_destroy(h)
+
+    def __del__(self):
+        self.close()
+
+
+def ytn_graph_begin(ctx, stream):
+    _check(_lib.ytn_graph_begin(ctx.handle, _stream(stream)))
+
+
+def ytn_graph_end(ctx, stream):
+    h = C.c_void_p()
+    _check(_lib.ytn_graph_end(ctx.handle, _stream(stream), C.byref(h)))
+    return Graph(h.value)
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """Continuous-batching server (ytn_server_*): `arena` is a device buffer (torch
+    uint8 tensor) that bounds the workspace of admitted requests."""
+
+    def __init__(self, ctx, nslots, arena):
+        self.ctx = ctx
+        self.arena = arena
+        h = C.c_void_p()
+        _check(_lib.ytn_server_create(ctx.handle, int(nslots), _ptr(arena),
+                                      arena.numel() * arena.element_size(), C.byref(h)))
+        self.handle = h.value
+
+    def submit(self, rid, plan, a, b, c, prec=YTN_FP64, rtol=0.0, t_arrive=-1.0):
+        _check(_lib.ytn_server_submit(self.handle, int(rid), plan.handle, _ptr(a), _ptr(b), _ptr(c), prec,
+                                      float(rtol), float(t_arrive)))
+
+    def poll(self, max_n=4096):
+        buf = (ytn_request_info * max_n)()
+        n = C.c_int64()
+        _check(_lib.ytn_server_poll(self.handle, buf, max_n, C.byref(n)))
+        return [{k: getattr(buf[i], k) for k, _ in ytn_request_info._fields_} for i in range(n.value)]
+
+    def drain(self, timeout_ms=-1):
+        _check(_lib.ytn_server_drain(self.handle, int(timeout_ms)))
+
+    def now_ms(self):
+        return _lib.ytn_server_now_ms(self.handle)
+
+    def close(self):
+        h, self.handle = self.handle, None
+        if h:
+            _lib.ytn_server_destroy(h)
+
+    def __del__(self):
+        self.close()
+
+
+def ytn_server_create(ctx, nslots, arena):
+    return Server(ctx, nslots, arena)
