@@ -70,8 +70,11 @@ typedef enum {
 
 typedef enum {
   YTN_FP64 = 0,        /* FP64 operands, FP64 tensor-core (DMMA) products        */
-  YTN_SPLIT_BF16 = 1   /* FP64 operands split into BF16 slices, tcgen05 products  *
+  YTN_SPLIT_BF16 = 1,  /* FP64 operands split into BF16 slices, tcgen05 products  *
                         * with exact FP32 accumulation, recombined to FP64        */
+  YTN_AUTO = 2         /* the faster of the two for this plan among those that   *
+                        * meet rtol (FP64 always does): autotuned, see            *
+                        * ytn_tensordot                                           */
 } ytn_precision;
 
 /* Same type as cudaStream_t; NULL is the legacy default stream. */
@@ -198,12 +201,23 @@ ytn_status ytn_workspace_size(const ytn_plan_t *plan, ytn_precision prec, double
 
 /* C = tensordot(A, B) (Sec. II.B contraction equation): gather the blocks of A
  * and B into one matrix per charge sector, multiply the sectors in one grouped
- * launch, scatter the products into the blocks of C. a, b, c: device buffers
- * of sizes a->size, b->size and ytn_plan_output(plan)->size; every element of
- * c is written. prec/rtol select the product precision (rtol is the target
+ * launch, scatter the products into the blocks of C. a, b, c: buffers of
+ * sizes a->size, b->size and ytn_plan_output(plan)->size, each either device
+ * memory of the context's device or page-locked host memory (cudaHostAlloc or
+ * cudaHostRegister, mapped into the device's address space). Host-resident
+ * data is read (and C written) by the data-mover kernels directly over the
+ * host link, with no staging copy. Pageable host memory is rejected
+ * (YTN_E_INVALID). Every element of c is written. prec/rtol select the product precision (rtol is the target
  * relative Frobenius error of the split path, ignored for FP64).
  * workspace: device buffer of at least ytn_workspace_size bytes, 256-byte
  * aligned. res (optional, host): filled before return. Asynchronous on stream.
+ * YTN_AUTO (no counterpart in the paper) picks, per plan and slice count, the
+ * faster of the FP64 path and the split path when the split path meets rtol:
+ * the first such call times both paths on the caller's stream (it runs both,
+ * leaves the split result in c and synchronises the stream); later calls reuse
+ * the cached choice. While the stream is being captured into a graph, a cost
+ * model of the two kernels' tile-padded work decides instead. res->precision
+ * reports the path that wrote c; the workspace is ytn_workspace_size(YTN_AUTO).
  * Errors: YTN_E_INVALID (wrong plan kind), YTN_E_WORKSPACE, YTN_E_TOLERANCE
  * (rtol below what the split path can guarantee), YTN_E_CUDA (launch). */
 ytn_status ytn_tensordot(ytn_plan_t *plan, const double *a, const double *b, double *c,
@@ -227,9 +241,10 @@ ytn_status ytn_tensordot(ytn_plan_t *plan, const double *a, const double *b, dou
 ytn_status ytn_tensordot_noalloc(ytn_plan_t *plan, const double *a, const double *b, double *c,
                                  ytn_stream stream);
 
-/* out = fuse(a) / unfuse(a) (Sec. II.B). a: device buffer of the planned
- * input's size; out: device buffer of ytn_plan_output(plan)->size elements,
- * every element written (fused entries with no stored block are zero).
+/* out = fuse(a) / unfuse(a) (Sec. II.B). a: buffer of the planned input's
+ * size; out: buffer of ytn_plan_output(plan)->size elements, every element
+ * written (fused entries with no stored block are zero). Buffers may be device
+ * memory or page-locked host memory, as for ytn_tensordot.
  * Asynchronous on stream. Errors: YTN_E_INVALID (wrong plan kind), YTN_E_CUDA. */
 ytn_status ytn_fuse(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
 ytn_status ytn_unfuse(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);

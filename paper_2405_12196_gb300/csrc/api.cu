@@ -129,6 +129,41 @@ class PhaseTimer {
   int idx_ = -1;
 };
 
+// The address the kernels use for a caller's data buffer: device memory of the
+// context's device as is; page-locked host memory (cudaHostAlloc, or registered
+// with cudaHostRegister) through its device mapping, so that the data movers
+// read or write it over the host link with no separate copy. Pageable host
+// memory and other devices' memory are rejected before anything is launched.
+static ytn_status device_view(const ytn_ctx *ctx, const void *ptr, const void **out, const char *what) {
+  *out = ptr;
+  if (!ptr) return YTN_OK;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(YTN_E_INVALID, std::string(what) + ": not a CUDA-visible pointer");
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    if (at.type == cudaMemoryTypeDevice && at.device != ctx->device)
+      return fail(YTN_E_INVALID, std::string(what) + ": device memory of another GPU");
+    return YTN_OK;
+  }
+  if (at.type == cudaMemoryTypeHost) {
+    if (!at.devicePointer) return fail(YTN_E_INVALID, std::string(what) + ": page-locked host memory without a device mapping");
+    *out = at.devicePointer;
+    return YTN_OK;
+  }
+  return fail(YTN_E_INVALID, std::string(what) + ": pageable host memory (page-lock it with cudaHostRegister first)");
+}
+
+template <class T>
+static ytn_status device_view(const ytn_ctx *ctx, T *ptr, T **out, const char *what) {
+  const void *v = nullptr;
+  ytn_status st = device_view(ctx, static_cast<const void *>(ptr), &v, what);
+  *out = static_cast<T *>(const_cast<void *>(v));
+  return st;
+}
+
 // A plan used by a launch that is being recorded into a graph stays alive
 // until the graph is destroyed.
 static void note_capture(ytn_plan_t *p, cudaStream_t st) {
@@ -399,33 +434,21 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
     *bytes = workspace_layout(p, true, w);
     return YTN_OK;
   }
+  if (prec == YTN_AUTO) {
+    int s;
+    double est;
+    const bool split_ok = choose_slices(p, rtol, s, est) == YTN_OK;
+    *bytes = workspace_layout(p, split_ok, w);   // the split layout extends the FP64 one
+    return YTN_OK;
+  }
   return fail(YTN_E_INVALID, "unknown precision");
 }
 
-ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, ytn_precision prec,
-                         double rtol, void *workspace, size_t workspace_bytes, ytn_result *res,
-                         ytn_stream stream) {
-  if (!p) return fail(YTN_E_INVALID, "null plan");
-  if (p->kind != Kind::Tensordot) return fail(YTN_E_INVALID, "plan is not a tensordot plan");
-  if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
-  if ((p->a_size && !a) || (p->b_size && !b) || (p->out.size && !c))
-    return fail(YTN_E_INVALID, "null data buffer");
-  if (prec != YTN_FP64 && prec != YTN_SPLIT_BF16) return fail(YTN_E_INVALID, "unknown precision");
-  const bool split = prec == YTN_SPLIT_BF16;
-  int slices = 0;
-  double est = 0.0;
-  if (split) {
-    ytn_status st = choose_slices(p, rtol, slices, est);
-    if (st != YTN_OK) return st;
-  }
+// One contraction on the chosen path; arguments already checked and mapped.
+static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, bool split, int slices,
+                                 void *workspace, cudaStream_t st) {
   WsLayout w;
-  const size_t need = workspace_layout(p, split, w);
-  if (need && (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)))
-    return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
-  DeviceGuard g(p->ctx->device);
-  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  note_capture(p, st);
+  workspace_layout(p, split, w);
   char *ws = static_cast<char *>(workspace);
   double *wa = reinterpret_cast<double *>(ws + w.wa), *wb = reinterpret_cast<double *>(ws + w.wb),
          *wc = reinterpret_cast<double *>(ws + w.wc);
@@ -469,11 +492,114 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, wc, c, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "scatter C");
+  return YTN_OK;
+}
+
+// Cost model of the two paths (ms): tile-padded tensor-core work at the rates
+// the kernels reach on this GPU, plus the HBM traffic of the split operands.
+// Used by YTN_AUTO while a stream is being captured (no timing possible).
+static bool model_prefers_split(const ytn_plan_t *p, int s) {
+  double f64 = 0.0, f16 = 0.0;
+  for (const HostSector &h : p->sectors) {
+    const double m64 = std::ceil(h.M / 64.0) * 64, n64 = std::ceil(h.N / 64.0) * 64;
+    const double m128 = std::ceil(h.M / 128.0) * 128, n128 = std::ceil(h.N / 128.0) * 128;
+    const double k32 = std::ceil(h.K / 32.0) * 32;
+    f64 += 2.0 * m64 * n64 * (double)h.K;
+    f16 += 2.0 * m128 * n128 * k32 * (s * (s + 1) / 2);
+  }
+  const double t64 = f64 / 1.0e12;
+  const double t16 = f16 / 1.3e15 + (double)(p->a_elems + p->b_elems) * (16.0 + 2.0 * s) / 6.0e12 + 5e-6;
+  return t16 < t64;
+}
+
+ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, ytn_precision prec,
+                         double rtol, void *workspace, size_t workspace_bytes, ytn_result *res,
+                         ytn_stream stream) {
+  if (!p) return fail(YTN_E_INVALID, "null plan");
+  if (p->kind != Kind::Tensordot) return fail(YTN_E_INVALID, "plan is not a tensordot plan");
+  if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
+  if ((p->a_size && !a) || (p->b_size && !b) || (p->out.size && !c))
+    return fail(YTN_E_INVALID, "null data buffer");
+  if (prec != YTN_FP64 && prec != YTN_SPLIT_BF16 && prec != YTN_AUTO)
+    return fail(YTN_E_INVALID, "unknown precision");
+  int slices = 0;
+  double est = 0.0;
+  bool split_ok = false;
+  if (prec == YTN_SPLIT_BF16) {
+    ytn_status st = choose_slices(p, rtol, slices, est);
+    if (st != YTN_OK) return st;
+    split_ok = true;
+  } else if (prec == YTN_AUTO) {
+    split_ok = choose_slices(p, rtol, slices, est) == YTN_OK;
+  }
+  WsLayout w;
+  const size_t need = workspace_layout(p, split_ok, w);
+  if (need && (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)))
+    return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
+  DeviceGuard g(p->ctx->device);
+  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  {
+    ytn_status vs;
+    if ((vs = device_view(p->ctx, a, &a, "A")) != YTN_OK || (vs = device_view(p->ctx, b, &b, "B")) != YTN_OK ||
+        (vs = device_view(p->ctx, c, &c, "C")) != YTN_OK)
+      return vs;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  note_capture(p, st);
+  bool split = prec == YTN_SPLIT_BF16;
+  if (prec == YTN_AUTO && split_ok) {
+    // the choice is made once per plan and slice count and cached on the plan
+    int choice;
+    {
+      std::lock_guard<std::mutex> lk(p->auto_mu);
+      choice = p->auto_choice[slices];
+    }
+    if (choice < 0) {
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        choice = model_prefers_split(p, slices) ? 1 : 0;
+      } else {
+        // time both paths once on the caller's stream (this call synchronises it)
+        cudaEvent_t ev[3];
+        for (auto &x : ev) cudaEventCreate(&x);
+        cudaEventRecord(ev[0], st);
+        ytn_status r = exec_tensordot(p, a, b, c, false, 0, workspace, st);
+        cudaEventRecord(ev[1], st);
+        if (r == YTN_OK) r = exec_tensordot(p, a, b, c, true, slices, workspace, st);
+        cudaEventRecord(ev[2], st);
+        cudaError_t e = cudaEventSynchronize(ev[2]);
+        float t64 = 0.f, t16 = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t64, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t16, ev[1], ev[2]);
+        for (auto &x : ev) cudaEventDestroy(x);
+        if (r != YTN_OK) return r;
+        if (e != cudaSuccess) return cuda_fail(e, "timing the two paths");
+        {
+          std::lock_guard<std::mutex> lk(p->auto_mu);
+          p->auto_choice[slices] = t16 < t64 ? 1 : 0;
+          p->auto_ms[slices][0] = t64;
+          p->auto_ms[slices][1] = t16;
+        }
+        if (res) {   // C holds the split result (the last run)
+          res->useful_flops = p->flops;
+          res->precision = YTN_SPLIT_BF16;
+          res->slices = slices;
+          res->err_est = est;
+        }
+        return YTN_OK;
+      }
+      std::lock_guard<std::mutex> lk(p->auto_mu);
+      if (p->auto_choice[slices] < 0) p->auto_choice[slices] = choice;
+    }
+    split = choice == 1;
+  }
+  ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, workspace, st);
+  if (r != YTN_OK) return r;
   if (res) {
     res->useful_flops = p->flops;
-    res->precision = prec;
-    res->slices = slices;
-    res->err_est = est;
+    res->precision = split ? YTN_SPLIT_BF16 : YTN_FP64;
+    res->slices = split ? slices : 0;
+    res->err_est = split ? est : 0.0;
   }
   return YTN_OK;
 }
@@ -486,6 +612,11 @@ static ytn_status run_move(ytn_plan_t *p, Kind k, const double *a, double *out, 
   if ((p->a_size && !a) || (p->out.size && !out)) return fail(YTN_E_INVALID, "null data buffer");
   DeviceGuard g(p->ctx->device);
   if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  {
+    ytn_status vs;
+    if ((vs = device_view(p->ctx, a, &a, "input")) != YTN_OK || (vs = device_view(p->ctx, out, &out, "output")) != YTN_OK)
+      return vs;
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   note_capture(p, st);
   cudaError_t e;

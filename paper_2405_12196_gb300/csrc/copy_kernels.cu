@@ -1,19 +1,14 @@
 // Data movers of the contraction path and of fuse / unfuse (Sec. II.B: the
 // "permutes, reshapes, and copies" that fill the fused storage), plus the trace.
 //
-// One launch runs every job of a phase: each CTA takes one work item (a range
-// of rows or tiles of one block). HBM-bound: every element is read once and
-// written once.
-//   rows mode: the destination-contiguous dimension is also the source's
-//     innermost one; warps copy whole rows with coalesced loads and stores.
-//     Rows shorter than 16 elements are packed several to a warp.
-//   tile mode: the two layouts have different contiguous dimensions; a 32x32
-//     tile is staged through shared memory so that both the global loads and
-//     the global stores are coalesced.
-//   staged modes: blocks of at most a few thousand elements, up to 32 of them
-//     per CTA, pass whole through shared memory: the contiguous side is moved
-//     linearly, the strided side in its own coalescing order, so that one CTA
-//     moves about 32 KB whatever the block shapes.
+// One launch runs every piece of a phase. A CTA takes one work item: up to 32
+// pieces (see CopyJob) with at most 4096 elements in all, staged whole in
+// shared memory. The dense side of each piece (a contiguous range of its
+// block) is moved linearly; the strided side is visited in its own order, so
+// that consecutive threads touch consecutive addresses along its innermost
+// dim. Index arithmetic per element is one multiply-high division per dim; the
+// reads are asynchronous copies into shared memory, a whole item in flight.
+// HBM-bound: every element is read once and written once.
 #include <cuda_runtime.h>
 
 #include "kernels.hpp"
@@ -23,177 +18,143 @@ namespace ytn {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kJobWords = (int)(sizeof(CopyJob) / 4);
 
-__device__ __forceinline__ void row_offsets(const CopyJob &J, uint32_t row, int64_t &so, int64_t &dof) {
-  so = J.src_off;
-  dof = J.dst_off;
-  for (int i = J.nd - 2; i >= 0; i--) {
-    const uint32_t e = (uint32_t)J.ext[i];
-    const uint32_t idx = row % e;
-    row /= e;
-    so += (int64_t)idx * J.sst[i];
-    dof += (int64_t)idx * J.dst[i];
-  }
+__device__ __forceinline__ void cp_async8(double *smem_dst, const double *gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
 }
 
-// Element l (in the order of the job's dims) of a staged job: its offsets
-// along the two sides, relative to the job's origins.
-__device__ __forceinline__ void staged_offsets(const CopyJob &J, uint32_t l, int64_t &so, int64_t &dof) {
-  so = 0;
-  dof = 0;
-  for (int i = J.nd - 1; i > 0; i--) {
-    const uint32_t e = (uint32_t)J.ext[i];
-    const uint32_t idx = l % e;
-    l /= e;
-    so += (int64_t)idx * J.sst[i];
-    dof += (int64_t)idx * J.dst[i];
-  }
-  so += (int64_t)l * J.sst[0];
-  dof += (int64_t)l * J.dst[0];
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-union CopySmem {
-  double tile[kTile][kTile + 1];
-  double stage[kStageElems];
+// The parameters of one piece, in registers: the last ND of its dim slots.
+template <int ND>
+struct Piece {
+  int64_t g_off, d_off;
+  int p, end;   // [p, end): the piece's range in the staging buffer
+  int ext[ND], gstr[ND], lstr[ND], shf[ND];
+  uint32_t mag[ND];
+
+  __device__ __forceinline__ void load(const CopyJob &J, int end_) {
+    g_off = J.g_off;
+    d_off = J.d_off;
+    p = J.p;
+    end = end_;
+#pragma unroll
+    for (int i = 0; i < ND; i++) {
+      const int k = kMaxCopyDims - ND + i;
+      ext[i] = J.ext[k];
+      gstr[i] = J.gstr[k];
+      lstr[i] = J.lstr[k];
+      mag[i] = J.mag[k];
+      shf[i] = J.shf[k];
+    }
+  }
+
+  // Element l of the piece (in strided-side order): its offsets on the strided
+  // side (global, from g_off) and on the dense side (from the piece's start).
+  __device__ __forceinline__ void offsets(uint32_t l, int64_t &go, int &lo) const {
+    go = 0;
+    lo = 0;
+#pragma unroll
+    for (int i = ND - 1; i > 0; i--) {
+      const uint32_t q = (l + __umulhi(l, mag[i])) >> shf[i];
+      const int r = (int)(l - q * (uint32_t)ext[i]);
+      go += (int64_t)r * gstr[i];
+      lo += r * lstr[i];
+      l = q;
+    }
+    go += (int64_t)l * gstr[0];
+    lo += (int)l * lstr[0];
+  }
 };
 
-__device__ __forceinline__ void copy_staged(const CopyJob *__restrict__ jobs, const CopyItem &it,
-                                            const double *__restrict__ src, double *__restrict__ dst,
-                                            CopyJob *Js, double *stage) {
-  const int nj = -it.count;
-  const int total = (int)it.begin;
-  if (nj > kStageJobs || total > kStageElems) return;   // the planner never makes such items
+template <int ND>
+__device__ __forceinline__ void next_piece(Piece<ND> &P, int &j, int e, const CopyJob *Js, int nj, int total) {
+  while (e >= P.end && j + 1 < nj) {
+    j++;
+    P.load(Js[j], j + 1 < nj ? Js[j + 1].p : total);
+  }
+}
+
+// DENSE_SRC (mode 2): read linearly, write in destination order; else
+// (mode 3) read in source order, write linearly. The reads are asynchronous
+// copies straight into shared memory, all of an item's in flight at once.
+template <int ND, bool DENSE_SRC>
+__device__ __forceinline__ void stage_item(const CopyJob *Js, int nj, int total, const double *__restrict__ src,
+                                           double *__restrict__ dst, double *stage) {
+  {
+    int j = 0;
+    Piece<ND> P;
+    P.load(Js[0], nj > 1 ? Js[1].p : total);
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      next_piece(P, j, e, Js, nj, total);
+      if (DENSE_SRC) {
+        cp_async8(stage + e, src + P.d_off + (e - P.p));
+      } else {
+        int64_t go;
+        int lo;
+        P.offsets((uint32_t)(e - P.p), go, lo);
+        const int at = P.p + lo;
+        if ((unsigned)at < (unsigned)total) cp_async8(stage + at, src + P.g_off + go);
+      }
+    }
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  int j = 0;
+  Piece<ND> P;
+  P.load(Js[0], nj > 1 ? Js[1].p : total);
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    next_piece(P, j, e, Js, nj, total);
+    if (DENSE_SRC) {
+      int64_t go;
+      int lo;
+      P.offsets((uint32_t)(e - P.p), go, lo);
+      const int at = P.p + lo;
+      if ((unsigned)at < (unsigned)total) dst[P.g_off + go] = stage[at];
+    } else {
+      dst[P.d_off + (e - P.p)] = stage[e];
+    }
+  }
+}
+
+template <int ND>
+__device__ __forceinline__ void stage_dispatch(bool dense_src, const CopyJob *Js, int nj, int total,
+                                               const double *src, double *dst, double *stage) {
+  if (dense_src) stage_item<ND, true>(Js, nj, total, src, dst, stage);
+  else stage_item<ND, false>(Js, nj, total, src, dst, stage);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) copy_kernel(const CopyJob *__restrict__ jobs,
+                                                           const CopyItem *__restrict__ items,
+                                                           const double *__restrict__ src,
+                                                           double *__restrict__ dst) {
+  __shared__ CopyJob Js[kStageJobs];
+  __shared__ double stage[kStageElems];
+  const CopyItem it = items[blockIdx.x];
+  const int nj = it.njobs, total = it.total, nd = it.kind & 255, mode = it.kind >> 8;
+  // the planner never makes other items
+  if (nj < 1 || nj > kStageJobs || total < 1 || total > kStageElems || nd < 1 || nd > kMaxCopyDims) return;
   {
     const int32_t *s = reinterpret_cast<const int32_t *>(jobs + it.job);
     int32_t *d = reinterpret_cast<int32_t *>(Js);
-    for (int w = threadIdx.x; w < nj * 32; w += kThreads) d[w] = s[w];
+    for (int w = threadIdx.x; w < nj * kJobWords; w += kThreads) d[w] = s[w];
   }
   __syncthreads();
-  const bool src_linear = Js[0].mode == 2;
-  // load: contiguous source ranges (mode 2) or the strided source in its own order (mode 3)
-  int j = 0;
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    while (j + 1 < nj && Js[j + 1].p <= e) j++;
-    const CopyJob &J = Js[j];
-    const int l = e - J.p;
-    if (src_linear) {
-      stage[e] = __ldg(src + J.src_off + l);
-    } else {
-      int64_t so, dof;
-      staged_offsets(J, (uint32_t)l, so, dof);
-      const int64_t at = J.p + dof;
-      if (at < total) stage[at] = __ldg(src + J.src_off + so);
-    }
-  }
-  __syncthreads();
-  // store: the strided destination in its own order (mode 2) or contiguous ranges (mode 3)
-  j = 0;
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    while (j + 1 < nj && Js[j + 1].p <= e) j++;
-    const CopyJob &J = Js[j];
-    const int l = e - J.p;
-    if (src_linear) {
-      int64_t so, dof;
-      staged_offsets(J, (uint32_t)l, so, dof);
-      const int64_t at = J.p + so;
-      if (at < total) dst[J.dst_off + dof] = stage[at];
-    } else {
-      dst[J.dst_off + l] = stage[e];
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) copy_kernel(const CopyJob *__restrict__ jobs,
-                                                        const CopyItem *__restrict__ items,
-                                                        const double *__restrict__ src,
-                                                        double *__restrict__ dst) {
-  __shared__ CopyJob Js[kStageJobs];
-  __shared__ CopySmem sm;
-  CopyJob &J = Js[0];
-  auto &tile = sm.tile;
-  const CopyItem it = items[blockIdx.x];
-  if (it.count < 0) {
-    copy_staged(jobs, it, src, dst, Js, sm.stage);
-    return;
-  }
-  if (threadIdx.x < 32) {
-    const int32_t *s = reinterpret_cast<const int32_t *>(&jobs[it.job]);
-    reinterpret_cast<int32_t *>(&J)[threadIdx.x] = s[threadIdx.x];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nd = J.nd;
-  if (J.mode == 0) {
-    const int L = J.ext[nd - 1];
-    const int64_t sin = J.sst[nd - 1];
-    const int64_t din = J.dst[nd - 1];
-    if (J.nchunk == 1 && L <= 16) {
-      // several short rows per warp
-      const int P = 32 / L;
-      const int sub = lane / L, col = lane - sub * L;
-      if (sub >= P) return;
-      const int64_t end = it.begin + it.count;
-      for (int64_t u = it.begin + (int64_t)warp * P + sub; u < end; u += (int64_t)kWarps * P) {
-        int64_t so, dof;
-        row_offsets(J, (uint32_t)u, so, dof);
-        dst[dof + col * din] = src[so + col * sin];
-      }
-      return;
-    }
-    const int64_t end = it.begin + it.count;
-    const uint32_t nchunk = (uint32_t)J.nchunk;
-    for (int64_t u = it.begin + warp; u < end; u += kWarps) {
-      const uint32_t row = (uint32_t)u / nchunk, chunk = (uint32_t)u - row * nchunk;
-      int64_t so, dof;
-      row_offsets(J, row, so, dof);
-      const int c0 = (int)chunk * kRowChunk;
-      const int n = min(kRowChunk, L - c0);
-      so += c0 * sin;
-      dof += c0 * din;
-      if (sin == 1 && din == 1) {
-        const double *s = src + so;
-        double *d = dst + dof;
-#pragma unroll 4
-        for (int c = lane; c < n; c += 32) d[c] = __ldg(s + c);
-      } else {
-        for (int c = lane; c < n; c += 32) dst[dof + c * din] = src[so + c * sin];
-      }
-    }
-    return;
-  }
-  // tile mode: q = nd-1 is destination-contiguous, p is source-contiguous
-  const int q = nd - 1, p = J.p;
-  const uint32_t ntq = (uint32_t)((J.ext[q] + kTile - 1) / kTile);
-  const uint32_t ntp = (uint32_t)((J.ext[p] + kTile - 1) / kTile);
-  const int64_t end = it.begin + it.count;
-  for (int64_t u64 = it.begin; u64 < end; u64++) {
-    uint32_t u = (uint32_t)u64;
-    const uint32_t tq = u % ntq;
-    u /= ntq;
-    const uint32_t tp = u % ntp;
-    u /= ntp;
-    int64_t so = J.src_off, dof = J.dst_off;
-    for (int i = nd - 1; i >= 0; i--) {
-      if (i == p || i == q) continue;
-      const uint32_t e = (uint32_t)J.ext[i];
-      const uint32_t idx = u % e;
-      u /= e;
-      so += (int64_t)idx * J.sst[i];
-      dof += (int64_t)idx * J.dst[i];
-    }
-    const int ep = J.ext[p], eq = J.ext[q];
-    const int p0 = (int)tp * kTile, q0 = (int)tq * kTile;
-    for (int i = warp; i < kTile; i += kWarps) {
-      const int qq = q0 + i, pp = p0 + lane;
-      if (qq < eq && pp < ep) tile[i][lane] = __ldg(src + so + pp + (int64_t)qq * J.sst[q]);
-    }
-    __syncthreads();
-    for (int i = warp; i < kTile; i += kWarps) {
-      const int pp = p0 + i, qq = q0 + lane;
-      if (pp < ep && qq < eq) dst[dof + (int64_t)pp * J.dst[p] + qq] = tile[lane][i];
-    }
-    __syncthreads();
+  const bool dense_src = mode == 2;
+  switch (nd) {
+    case 1: stage_dispatch<1>(dense_src, Js, nj, total, src, dst, stage); break;
+    case 2: stage_dispatch<2>(dense_src, Js, nj, total, src, dst, stage); break;
+    case 3: stage_dispatch<3>(dense_src, Js, nj, total, src, dst, stage); break;
+    case 4: stage_dispatch<4>(dense_src, Js, nj, total, src, dst, stage); break;
+    case 5: stage_dispatch<5>(dense_src, Js, nj, total, src, dst, stage); break;
+    case 6: stage_dispatch<6>(dense_src, Js, nj, total, src, dst, stage); break;
+    case 7: stage_dispatch<7>(dense_src, Js, nj, total, src, dst, stage); break;
+    default: stage_dispatch<8>(dense_src, Js, nj, total, src, dst, stage); break;
   }
 }
 

@@ -351,11 +351,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-              // order 0: |E2| < 2^22, converted through the FP32 bit pattern
-              const long long x2 = __float_as_int(__uint_as_float(v2[i]) + 12582912.0f) - 0x4B400000;
-              const long long x3 = __float2int_rn(__uint_as_float(v3[i]) * 256.0f);
-              const long long x4 = __float2int_rn(__uint_as_float(v4[i]) * 65536.0f);
-              acc[g * 4 + i] += (x2 << 24) + (x3 << 16) + (x4 << 8);
+              // order 0: |E2| < 2^22, read from the bit pattern of E2 + 1.5 * 2^23
+              const int x2 = __float_as_int(__uint_as_float(v2[i]) + 12582912.0f) - 0x4B400000;
+              // order 1: |E3 * 2^8| <= 64 * 2 * 255^2 < 2^23
+              const int x3 = __float2int_rn(__uint_as_float(v3[i]) * 256.0f);
+              // order 2: |E4 * 2^16| <= 64 * 3 * 255^2 < 2^24
+              const int x4 = __float2int_rn(__uint_as_float(v4[i]) * 65536.0f);
+              // x3 * 2^8 + x4 <= 2,143,224,000 < 2^31
+              const int t = x3 * 256 + x4;
+              acc[g * 4 + i] += (long long)x2 * 16777216 + (long long)t * 256;
             }
           }
         }
@@ -371,8 +375,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t vr[8];
             tmem_ld8(lane_addr + kColR + c0 + g * 8, vr);
             tmem_wait_ld();
+            // |R| over one chunk < 64 (4 * 255^2 * 2^-24 + 5 * 255^2 * 2^-32 + 6 * 256 * 255 * 2^-40)
+            // < 1, so R * 2^24 fits 32 bits
 #pragma unroll
-            // |R| over one chunk < 64 * 4 * 255^2 * 2^-24 < 1, so R * 2^24 fits 32 bits
             for (int i = 0; i < 8; i++)
               acc[g * 8 + i] += (long long)__float2int_rn(__uint_as_float(vr[i]) * 16777216.0f);
           }

@@ -249,15 +249,26 @@ struct Dim {
   int64_t ext, sst, dst;
 };
 
-// Normalise a copy (dims outer -> inner in destination order): drop unit dims,
-// merge dims contiguous in both layouts, pick rows or tile mode.
-static ytn_status make_job(std::vector<Dim> dims, int64_t src_off, int64_t dst_off, CopyJob &J,
-                           std::string &err) {
-  std::vector<Dim> v;
-  for (auto &d : dims)
-    if (d.ext != 1) v.push_back(d);
+// Division by d >= 1 of any n < 2^31 as (n + umulhi(n, m)) >> sh: with
+// l = ceil(log2 d), M = ceil(2^(32 + l) / d) in [2^32, 2^33), m = M - 2^32 and
+// sh = l, the sum is floor(n M / 2^32) and the quotient is exact, because
+// M d - 2^(32 + l) < d makes the excess of n M / 2^(32 + l) over n / d smaller
+// than n / 2^(32 + l) < 2^-(l + 1) < 1 / d. d = 1 gives m = 0, sh = 0.
+static void division_magic(int64_t d, uint32_t &m, uint8_t &sh) {
+  int l = 0;
+  while ((int64_t(1) << l) < d) l++;
+  const uint64_t num = uint64_t(1) << (32 + l);   // l <= 31: no overflow below
+  const uint64_t M = (num + (uint64_t)d - 1) / (uint64_t)d;
+  m = (uint32_t)(M - (uint64_t(1) << 32));
+  sh = (uint8_t)l;
+}
+
+// Drop unit dims and merge neighbours that are contiguous in both layouts
+// (dims listed outer -> inner in the order that is kept).
+static std::vector<Dim> merge_dims(const std::vector<Dim> &dims) {
   std::vector<Dim> m;
-  for (auto &d : v) {
+  for (auto &d : dims) {
+    if (d.ext == 1) continue;
     if (!m.empty() && m.back().sst == d.sst * d.ext && m.back().dst == d.dst * d.ext) {
       m.back().ext *= d.ext;
       m.back().sst = d.sst;
@@ -266,73 +277,14 @@ static ytn_status make_job(std::vector<Dim> dims, int64_t src_off, int64_t dst_o
       m.push_back(d);
     }
   }
-  if (m.empty()) m.push_back({1, 1, 1});
-  // put the destination-contiguous dim innermost when it is not already
-  if (m.back().dst != 1) {
-    for (size_t i = 0; i + 1 < m.size(); i++)
-      if (m[i].dst == 1) {
-        Dim d = m[i];
-        m.erase(m.begin() + i);
-        m.push_back(d);
-        break;
-      }
-  }
-  if ((int)m.size() > kMaxCopyDims) { err = "copy job needs more than 8 dimensions"; return YTN_E_UNSUPPORTED; }
-  std::memset(&J, 0, sizeof(J));
-  J.src_off = src_off;
-  J.dst_off = dst_off;
-  J.nd = (int)m.size();
-  for (int i = 0; i < J.nd; i++) {
-    if (m[i].ext > INT32_MAX || m[i].sst > INT32_MAX || m[i].dst > INT32_MAX) {
-      err = "copy job stride exceeds 32 bits";
-      return YTN_E_UNSUPPORTED;
-    }
-    J.ext[i] = (int32_t)m[i].ext;
-    J.sst[i] = (int32_t)m[i].sst;
-    J.dst[i] = (int32_t)m[i].dst;
-  }
-  const int q = J.nd - 1;
-  int64_t tot = 1;
-  for (int i = 0; i < J.nd; i++) tot *= J.ext[i];
-  if (tot > INT32_MAX) { err = "copy job larger than 2^31 elements"; return YTN_E_UNSUPPORTED; }
-  J.mode = 0;
-  J.p = q;
-  if (J.sst[q] != 1 && J.dst[q] == 1) {
-    for (int i = 0; i < q; i++)
-      if (J.sst[i] == 1 && J.ext[i] >= 8 && J.ext[q] >= 8) {
-        J.mode = 1;
-        J.p = i;
-      }
-  }
-  J.nchunk = J.mode == 0 ? (J.ext[q] + kRowChunk - 1) / kRowChunk : 0;
-  return YTN_OK;
+  return m;
 }
 
-static int64_t job_units(const CopyJob &J) {
-  int64_t u = 1;
-  if (J.mode == 0) {
-    for (int i = 0; i + 1 < J.nd; i++) u *= J.ext[i];
-    return u * J.nchunk;
-  }
-  for (int i = 0; i < J.nd; i++) {
-    if (i == J.p || i == J.nd - 1) u *= (J.ext[i] + kTile - 1) / kTile;
-    else u *= J.ext[i];
-  }
-  return u;
-}
-
-static int64_t job_elems(const CopyJob &J) {
-  int64_t n = 1;
-  for (int i = 0; i < J.nd; i++) n *= J.ext[i];
-  return n;
-}
-
-// True if the job's elements fill one dense range on the source (or the
-// destination) side.
-static bool side_dense(const CopyJob &J, bool src) {
+// True if the dims fill a dense row-major range on the source (or destination)
+// side, starting at its origin.
+static bool side_dense(const std::vector<Dim> &dims, bool src) {
   std::vector<std::pair<int64_t, int64_t>> v;   // (stride, extent)
-  for (int i = 0; i < J.nd; i++)
-    if (J.ext[i] > 1) v.push_back({src ? J.sst[i] : J.dst[i], J.ext[i]});
+  for (auto &d : dims) v.push_back({src ? d.sst : d.dst, d.ext});
   std::sort(v.begin(), v.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
   int64_t expect = 1;
   for (size_t i = v.size(); i-- > 0;) {
@@ -342,68 +294,135 @@ static bool side_dense(const CopyJob &J, bool src) {
   return true;
 }
 
-// Staged mode for a small job with a dense side (2: source, 3: destination),
-// else the job keeps its mode. Mode 3 lists the dims in source order.
-static void stage_job(CopyJob &J) {
-  if (job_elems(J) > kStageElems) return;
-  if (side_dense(J, true)) {
-    J.mode = 2;
-    return;
+// One staged job: `dims` (ext, local stride, global stride) of a piece whose
+// dense side starts at d_off and strided side at g_off.
+static ytn_status push_piece(ytn_plan_t *p, std::vector<Dim> dims, int mode, int64_t g_off, int64_t d_off,
+                             std::string &err) {
+  // enumeration order: strided (global) side outer -> inner
+  std::stable_sort(dims.begin(), dims.end(), [](const Dim &a, const Dim &b) { return a.dst > b.dst; });
+  std::vector<Dim> m = merge_dims(dims);
+  if (m.empty()) m.push_back({1, 1, 1});
+  if ((int)m.size() > kMaxCopyDims) {
+    err = "copy job needs more than 8 dimensions";
+    return YTN_E_UNSUPPORTED;
   }
-  if (!side_dense(J, false)) return;
-  int idx[kMaxCopyDims];
-  for (int i = 0; i < J.nd; i++) idx[i] = i;
-  std::stable_sort(idx, idx + J.nd, [&](int a, int b) { return J.sst[a] > J.sst[b]; });
-  CopyJob K = J;
+  CopyJob J;
+  std::memset(&J, 0, sizeof(J));
+  J.g_off = g_off;
+  J.d_off = d_off;
+  J.nd = (int32_t)m.size();
+  J.mode = mode;
+  int64_t size = 1;
+  // dims right-aligned in the kMaxCopyDims slots; the outer slots are unit dims
+  const int o = kMaxCopyDims - J.nd;
+  for (int i = 0; i < kMaxCopyDims; i++) {
+    J.ext[i] = 1;
+    division_magic(1, J.mag[i], J.shf[i]);
+  }
   for (int i = 0; i < J.nd; i++) {
-    K.ext[i] = J.ext[idx[i]];
-    K.sst[i] = J.sst[idx[i]];
-    K.dst[i] = J.dst[idx[i]];
+    if (m[i].dst > INT32_MAX) {
+      err = "copy job stride exceeds 32 bits";
+      return YTN_E_UNSUPPORTED;
+    }
+    J.ext[o + i] = (int32_t)m[i].ext;
+    J.lstr[o + i] = (int32_t)m[i].sst;
+    J.gstr[o + i] = (int32_t)m[i].dst;
+    division_magic(m[i].ext, J.mag[o + i], J.shf[o + i]);
+    size *= m[i].ext;
   }
-  K.mode = 3;
-  J = K;
+  J.size = (int32_t)size;
+  p->jobs.push_back(J);
+  return YTN_OK;
 }
 
-// Split jobs [j0, j1) into CTA work items of about 8K elements; runs of small
-// staged jobs of one mode are packed into items of at most kStageElems
-// elements and kStageJobs jobs.
+// A block copy (dims outer -> inner in destination order, strides of both
+// sides) becomes staged jobs of at most kStageElems elements. One side is a
+// dense range (the whole block on the tensor side); it is cut into contiguous
+// pieces by fixing its outer indices and splitting the next one.
+static ytn_status add_copy(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t src_off, int64_t dst_off,
+                           std::string &err) {
+  std::vector<Dim> v;
+  for (auto &d : dims)
+    if (d.ext != 1) v.push_back(d);
+  int mode;
+  int64_t g0, d0;
+  // local form: ext, dense-side stride (sst field), strided-side stride (dst field)
+  std::vector<Dim> loc;
+  if (side_dense(v, true)) {
+    mode = 2;   // dense source: read linearly, written in destination order
+    for (auto &d : v) loc.push_back({d.ext, d.sst, d.dst});
+    d0 = src_off;
+    g0 = dst_off;
+  } else if (side_dense(v, false)) {
+    mode = 3;   // dense destination: read in source order, written linearly
+    for (auto &d : v) loc.push_back({d.ext, d.dst, d.sst});
+    d0 = dst_off;
+    g0 = src_off;
+  } else {
+    err = "copy job without a dense side";
+    return YTN_E_UNSUPPORTED;
+  }
+  // dense-side order, outer -> inner
+  std::sort(loc.begin(), loc.end(), [](const Dim &a, const Dim &b) { return a.sst > b.sst; });
+  const int n = (int)loc.size();
+  // k: outermost dim whose inner product fits a piece
+  int64_t inner = 1;
+  int k = n;
+  while (k > 0 && inner * loc[k - 1].ext <= kStageElems) {
+    inner *= loc[k - 1].ext;
+    k--;
+  }
+  if (k == 0) return push_piece(p, loc, mode, g0, d0, err);
+  // dims [0, k-1) are fixed per piece, dim k-1 is split into runs of `c`
+  const int ks = k - 1;
+  const int64_t c = std::max<int64_t>(1, kStageElems / inner);
+  std::vector<int64_t> idx(ks, 0);
+  for (;;) {
+    int64_t go = g0, dof = d0;
+    for (int i = 0; i < ks; i++) {
+      go += idx[i] * loc[i].dst;
+      dof += idx[i] * loc[i].sst;
+    }
+    for (int64_t a = 0; a < loc[ks].ext; a += c) {
+      std::vector<Dim> piece(loc.begin() + ks, loc.end());
+      piece[0].ext = std::min(c, loc[ks].ext - a);
+      ytn_status s = push_piece(p, piece, mode, go + a * loc[ks].dst, dof + a * loc[ks].sst, err);
+      if (s != YTN_OK) return s;
+    }
+    int i = ks - 1;
+    for (; i >= 0; i--) {
+      if (++idx[i] < loc[i].ext) break;
+      idx[i] = 0;
+    }
+    if (i < 0) break;
+  }
+  return YTN_OK;
+}
+
+// Pack jobs [j0, j1) into CTA work items: runs of consecutive jobs of one
+// mode, at most kStageElems elements and kStageJobs jobs each; the item's
+// dimension count is the largest of its jobs' (the others have unit dims in
+// the outer slots).
 static void make_items(ytn_plan_t *p, size_t j0, size_t j1) {
-  for (size_t j = j0; j < j1; j++) stage_job(p->jobs[j]);
-  for (size_t j = j0; j < j1; j++) {
-    CopyJob &J = p->jobs[j];
-    if (J.mode >= 2) {
-      const int mode = J.mode;
-      size_t k = j;
-      int64_t tot = 0;
-      while (k < j1 && p->jobs[k].mode == mode && k - j < (size_t)kStageJobs &&
-             tot + job_elems(p->jobs[k]) <= kStageElems) {
-        CopyJob &K = p->jobs[k];
-        K.p = (int32_t)tot;
-        K.nchunk = (int32_t)job_elems(K);
-        tot += K.nchunk;
-        k++;
-      }
-      CopyItem it;
-      it.job = (int32_t)j;
-      it.count = -(int32_t)(k - j);
-      it.begin = tot;
-      p->items.push_back(it);
-      j = k - 1;
-      continue;
+  size_t j = j0;
+  while (j < j1) {
+    const CopyJob &F = p->jobs[j];
+    size_t k = j;
+    int32_t tot = 0, nd = 1;
+    while (k < j1 && k - j < (size_t)kStageJobs && p->jobs[k].mode == F.mode &&
+           tot + p->jobs[k].size <= kStageElems) {
+      p->jobs[k].p = tot;
+      tot += p->jobs[k].size;
+      nd = std::max(nd, p->jobs[k].nd);
+      k++;
     }
-    const int64_t units = job_units(J);
-    int64_t per_unit;
-    if (J.mode == 0) per_unit = std::min<int64_t>(J.ext[J.nd - 1], kRowChunk);
-    else per_unit = kTile * kTile;
-    int64_t per_item = std::max<int64_t>(1, 8192 / std::max<int64_t>(1, per_unit));
-    per_item = std::min<int64_t>(per_item, 1 << 20);
-    for (int64_t u = 0; u < units; u += per_item) {
-      CopyItem it;
-      it.job = (int32_t)j;
-      it.begin = u;
-      it.count = (int32_t)std::min<int64_t>(per_item, units - u);
-      p->items.push_back(it);
-    }
+    CopyItem it;
+    it.job = (int32_t)j;
+    it.njobs = (int32_t)(k - j);
+    it.total = tot;
+    it.kind = nd | (F.mode << 8);
+    p->items.push_back(it);
+    j = k;
   }
 }
 
@@ -639,10 +658,8 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
             for (size_t i = 0; i < freeL.size(); i++) dims.push_back({T.dim(b, freeL[i]), st[freeL[i]], fstr[i]});
             dst_off = base + xoff * ldk + foff;
           }
-          CopyJob J;
-          ytn_status s = make_job(dims, T.off[b], dst_off, J, err);
+          ytn_status s = add_copy(p, dims, T.off[b], dst_off, err);
           if (s != YTN_OK) return s;
-          p->jobs.push_back(J);
           covered += T.elems(b);
           p->moved += T.elems(b);
         }
@@ -733,10 +750,8 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
     acc = 1;
     for (int i = C.rank - 1; i >= (int)freeA.size(); i--) { ss[i] = acc; acc *= cd[i]; }
     for (int i = 0; i < C.rank; i++) dims.push_back({cd[i], ss[i], ds[i]});
-    CopyJob J;
-    s = make_job(dims, h.c_off + sr.roff * h.N + sr.coff, off_of_id[id], J, err);
+    s = add_copy(p, dims, h.c_off + sr.roff * h.N + sr.coff, off_of_id[id], err);
     if (s != YTN_OK) return s;
-    p->jobs.push_back(J);
     p->moved += acc;
   }
   size_t j3 = p->jobs.size();
@@ -966,10 +981,8 @@ ytn_status plan_fuse(ytn_plan_t *p, const Tensor &A, int ngroups, const int *gro
         dst_off += suboff[g][nu][sub_charges(A, b, grp)] * nst[g];
       }
     }
-    CopyJob J;
-    ytn_status s = make_job(dims, A.off[b], dst_off, J, err);
+    ytn_status s = add_copy(p, dims, A.off[b], dst_off, err);
     if (s != YTN_OK) return s;
-    p->jobs.push_back(J);
     p->moved += A.elems(b);
   }
   make_items(p, 0, p->jobs.size());
@@ -1102,10 +1115,8 @@ ytn_status plan_unfuse(ytn_plan_t *p, const Tensor &A, int naxes, const int *axe
         r2++;
       }
     }
-    CopyJob J;
-    ytn_status s = make_job(dims, src_off, off_of_id[ob.id], J, err);
+    ytn_status s = add_copy(p, dims, src_off, off_of_id[ob.id], err);
     if (s != YTN_OK) return s;
-    p->jobs.push_back(J);
     p->moved += acc;
   }
   make_items(p, 0, p->jobs.size());

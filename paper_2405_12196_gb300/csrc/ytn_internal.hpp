@@ -20,46 +20,47 @@ namespace ytn {
 
 constexpr int kMaxCopyDims = 8;
 
-// One block moved between two layouts (gather into a sector matrix, scatter out
-// of one, or fuse / unfuse). Dimensions are listed outer -> inner in
-// destination order; the innermost has destination stride 1.
-//   mode 0 ("rows"): rows of ext[nd-1] elements, source stride sst[nd-1]
-//                    (1 for a contiguous copy);
-//   mode 1 ("tile"): 32x32 shared-memory transpose between the destination-
-//                    contiguous dim nd-1 and the source-contiguous dim p.
-//   modes 2 and 3 ("staged"): small blocks, several to a CTA, staged whole in
-//                    shared memory. Mode 2: the source range is contiguous; it
-//                    is read linearly and written out in destination order.
-//                    Mode 3: the destination range is contiguous; dims are
-//                    listed in source order (source stride 1 innermost), read
-//                    in that order and written out linearly. p is the job's
-//                    offset in its item's staging buffer, nchunk its size.
+// One piece of a block moved between two layouts (gather into a sector
+// matrix, scatter out of one, fuse, unfuse). Every block copy has one dense
+// side: the block itself, a contiguous range in its tensor. The planner cuts
+// a block into pieces of at most kStageElems elements that are contiguous on
+// that side; a CTA stages the pieces of one work item whole in shared memory.
+//   mode 2: the dense side is the source. The piece is read linearly and
+//           written in destination order.
+//   mode 3: the dense side is the destination. The piece is read in source
+//           order and written linearly.
+// Dims are listed outer -> inner in the order of the strided (global) side,
+// which has stride 1 innermost when the layouts allow, right-aligned in the
+// kMaxCopyDims slots (the nd used ones last, unit dims before them): gstr are
+// the strided side's strides from g_off, lstr the dense side's strides from
+// the piece's start (d_off in global memory, p in the item's staging buffer).
+// mag / shf divide by ext: n / ext = (n + umulhi(n, mag)) >> shf for n < 2^31.
 struct CopyJob {
-  int64_t src_off;
-  int64_t dst_off;
+  int64_t g_off;
+  int64_t d_off;
   int32_t nd;
   int32_t mode;
   int32_t p;
-  int32_t nchunk;   // mode 0: column chunks per row (rows longer than kRowChunk)
+  int32_t size;
   int32_t ext[kMaxCopyDims];
-  int32_t sst[kMaxCopyDims];
-  int32_t dst[kMaxCopyDims];
+  int32_t gstr[kMaxCopyDims];
+  int32_t lstr[kMaxCopyDims];
+  uint32_t mag[kMaxCopyDims];
+  uint8_t shf[kMaxCopyDims];
+  int32_t reserved[6];
 };
-static_assert(sizeof(CopyJob) == 128, "CopyJob layout");
+static_assert(sizeof(CopyJob) == 192, "CopyJob layout");
 
-constexpr int kRowChunk = 2048;   // mode-0 column chunk
-constexpr int kTile = 32;         // mode-1 tile edge
-constexpr int kStageElems = 4096; // staged modes: elements per CTA item
-constexpr int kStageJobs = 32;    // staged modes: jobs per CTA item
+constexpr int kStageElems = 4096; // elements per CTA work item
+constexpr int kStageJobs = 32;    // pieces per CTA work item
 
-// A contiguous range of work units of one job, processed by one CTA.
-// Units: mode 0 = (row, column chunk) pairs; mode 1 = 32x32 tiles.
-// Staged items: jobs [job, job - count) (count < 0) of one staged mode, with
-// begin = their total size (at most kStageElems).
+// A run of consecutive jobs [job, job + njobs) of one mode, processed by one
+// CTA; kind = nd | mode << 8 with nd the largest dimension count of its jobs.
 struct CopyItem {
   int32_t job;
-  int32_t count;
-  int64_t begin;
+  int32_t njobs;
+  int32_t total;
+  int32_t kind;
 };
 static_assert(sizeof(CopyItem) == 16, "CopyItem layout");
 
@@ -259,6 +260,10 @@ struct ytn_plan_s {
   std::vector<ytn::SplitSector> sp_sectors;
   std::vector<ytn::SplitTile> sp_tiles;
   int64_t sp_sa_bytes = 0, sp_sb_bytes = 0, sp_ea = 0, sp_eb = 0;
+  // YTN_AUTO: per slice count, -1 undecided, 0 FP64, 1 split; the timings (ms)
+  std::mutex auto_mu;
+  int auto_choice[ytn::kSlices + 1] = {-1, -1, -1, -1, -1, -1, -1};
+  float auto_ms[ytn::kSlices + 1][2] = {};
   const ytn::SplitOperand *d_sp_ops = nullptr;
   const ytn::SplitItem *d_sp_exp_items = nullptr, *d_sp_slice_items = nullptr;
   const ytn::SplitSector *d_sp_sectors = nullptr;

@@ -31,6 +31,7 @@ STATUS = {
 }
 YTN_FP64 = 0
 YTN_SPLIT_BF16 = 1
+YTN_AUTO = 2
 YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE = 1, 2, 3, 4
 
 
@@ -373,7 +374,7 @@ def ytn_profile_read(ctx):
 
 def available_precisions():
     """Precisions this build of the library executes."""
-    return [YTN_FP64, YTN_SPLIT_BF16]
+    return [YTN_FP64, YTN_SPLIT_BF16, YTN_AUTO]
 
 
 # ------------------------------------------------------------------ graphs

@@ -172,3 +172,17 @@ def test_execution_needs_a_device_context(hctx):
     with pytest.raises(ytn.YtnError) as e:
         ytn.ytn_tensordot(p, 1 << 20, 1 << 20, 1 << 20, workspace=1 << 20, workspace_bytes=1 << 30)
     assert e.value.name == "YTN_E_INVALID"
+
+
+def test_auto_workspace_covers_the_admissible_paths(hctx):
+    """YTN_AUTO needs the split layout when the split path meets rtol (it may run
+    both paths), else the FP64 layout."""
+    cfg = W.config1()
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    f64 = ytn.ytn_workspace_size(plan, ytn.YTN_FP64)
+    split = ytn.ytn_workspace_size(plan, ytn.YTN_SPLIT_BF16, 1e-10)
+    assert split > f64 > 0
+    assert ytn.ytn_workspace_size(plan, ytn.YTN_AUTO, 1e-10) == split
+    assert ytn.ytn_workspace_size(plan, ytn.YTN_AUTO, 1e-16) == f64
+    with pytest.raises(ytn.YtnError):
+        ytn.ytn_workspace_size(plan, ytn.YTN_SPLIT_BF16, 1e-16)
