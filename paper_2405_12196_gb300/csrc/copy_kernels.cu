@@ -34,15 +34,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
 template <int ND>
 struct Piece {
   int64_t g_off, d_off;
-  int p, end;   // [p, end): the piece's range in the staging buffer
+  int p;   // the piece's start in the staging buffer
   int ext[ND], gstr[ND], lstr[ND], shf[ND];
   uint32_t mag[ND];
 
-  __device__ __forceinline__ void load(const CopyJob &J, int end_) {
+  __device__ __forceinline__ void load(const CopyJob &J) {
     g_off = J.g_off;
     d_off = J.d_off;
     p = J.p;
-    end = end_;
 #pragma unroll
     for (int i = 0; i < ND; i++) {
       const int k = kMaxCopyDims - ND + i;
@@ -72,53 +71,64 @@ struct Piece {
   }
 };
 
-template <int ND>
-__device__ __forceinline__ void next_piece(Piece<ND> &P, int &j, int e, const CopyJob *Js, int nj, int total) {
-  while (e >= P.end && j + 1 < nj) {
-    j++;
-    P.load(Js[j], j + 1 < nj ? Js[j + 1].p : total);
+// Calls body(P, l, e) for every element e of the item's flat range
+// [w0, w1) of this warp: lanes take consecutive elements of one piece at a time
+// (l: the element's index in its piece), so that a warp's accesses to the
+// strided side follow that side's innermost dim. A piece's parameters are read
+// from shared memory once per warp and piece.
+template <int ND, class Body>
+__device__ __forceinline__ void for_warp_range(const CopyJob *Js, int nj, int w0, int w1, Body body) {
+  if (w0 >= w1) return;
+  const int lane = threadIdx.x & 31;
+  // first piece: the last one starting at or before w0
+  int j = 31 - __clz(__ballot_sync(0xffffffffu, lane < nj && Js[lane].p <= w0));
+  for (int e0 = w0; e0 < w1; j++) {
+    Piece<ND> P;
+    P.load(Js[j]);
+    const int seg_end = min(w1, P.p + Js[j].size);
+#pragma unroll 4
+    for (int e = e0 + lane; e < seg_end; e += 32) body(P, e - P.p, e);
+    e0 = seg_end;
   }
 }
 
 // DENSE_SRC (mode 2): read linearly, write in destination order; else
 // (mode 3) read in source order, write linearly. The reads are asynchronous
 // copies straight into shared memory, all of an item's in flight at once.
+// Each warp takes one eighth of the item's elements in both phases.
 template <int ND, bool DENSE_SRC>
 __device__ __forceinline__ void stage_item(const CopyJob *Js, int nj, int total, const double *__restrict__ src,
                                            double *__restrict__ dst, double *stage) {
-  {
-    int j = 0;
-    Piece<ND> P;
-    P.load(Js[0], nj > 1 ? Js[1].p : total);
-    for (int e = threadIdx.x; e < total; e += kThreads) {
-      next_piece(P, j, e, Js, nj, total);
-      if (DENSE_SRC) {
-        cp_async8(stage + e, src + P.d_off + (e - P.p));
-      } else {
-        int64_t go;
-        int lo;
-        P.offsets((uint32_t)(e - P.p), go, lo);
-        const int at = P.p + lo;
-        if ((unsigned)at < (unsigned)total) cp_async8(stage + at, src + P.g_off + go);
-      }
-    }
-    cp_async_wait_all();
-  }
-  __syncthreads();
-  int j = 0;
-  Piece<ND> P;
-  P.load(Js[0], nj > 1 ? Js[1].p : total);
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    next_piece(P, j, e, Js, nj, total);
-    if (DENSE_SRC) {
+  constexpr int kWarps = kThreads / 32;
+  const int per_warp = (total + kWarps - 1) / kWarps;
+  const int w0 = min(total, (int)(threadIdx.x >> 5) * per_warp), w1 = min(total, w0 + per_warp);
+  if (DENSE_SRC) {
+    for_warp_range<ND>(Js, nj, w0, w1, [&](const Piece<ND> &P, int l, int e) {
+      cp_async8(stage + e, src + P.d_off + l);
+    });
+  } else {
+    for_warp_range<ND>(Js, nj, w0, w1, [&](const Piece<ND> &P, int l, int e) {
       int64_t go;
       int lo;
-      P.offsets((uint32_t)(e - P.p), go, lo);
+      P.offsets((uint32_t)l, go, lo);
+      const int at = P.p + lo;
+      if ((unsigned)at < (unsigned)total) cp_async8(stage + at, src + P.g_off + go);
+    });
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (DENSE_SRC) {
+    for_warp_range<ND>(Js, nj, w0, w1, [&](const Piece<ND> &P, int l, int e) {
+      int64_t go;
+      int lo;
+      P.offsets((uint32_t)l, go, lo);
       const int at = P.p + lo;
       if ((unsigned)at < (unsigned)total) dst[P.g_off + go] = stage[at];
-    } else {
-      dst[P.d_off + (e - P.p)] = stage[e];
-    }
+    });
+  } else {
+    for_warp_range<ND>(Js, nj, w0, w1, [&](const Piece<ND> &P, int l, int e) {
+      dst[P.d_off + l] = stage[e];
+    });
   }
 }
 

@@ -113,7 +113,6 @@ constexpr int kSplitBK = 32;               // K per stage
 constexpr int kSlices = 6;                 // slices stored per operand
 constexpr int kSliceBytes = kSplitBM * kSplitBK * 2;         // 8192
 constexpr int kBlockBytes = kSlices * kSliceBytes;           // 49152
-constexpr int kChunkStages = 4;            // exact-accumulation chunk: 4 stages = K 128
 
 // One operand (A rows = M, or B rows = N) of one sector, for the split kernels.
 struct SplitOperand {

@@ -280,9 +280,9 @@ def test_random_tensordot_split(ctx, sym, case):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (128, 128, 32), (129, 127, 33), (300, 260, 500), (40, 700, 129),
-                                  (257, 3, 1000)])
+                                  (257, 3, 1000), (65, 64, 64), (64, 130, 65), (3, 5, 63)])
 def test_split_tiles_chunks_and_ragged_tails(ctx, dims):
-    """Tiles of 128 x 128, K stages of 32 and exact-accumulation chunks of 128, all
+    """Tiles of 128 x 128, K stages of 32 and exact-accumulation chunks of 64, all
     with ragged tails."""
     M, N, K = dims
     l_m, l_k, l_n = W.Leg(1, [(0,)], [M]), W.Leg(1, [(0,)], [K]), W.Leg(1, [(0,)], [N])
