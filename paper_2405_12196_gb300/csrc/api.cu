@@ -202,15 +202,16 @@ static size_t workspace_layout(const ytn_plan_t *p, bool split, WsLayout &w) {
 }
 
 // Error model of the split path (relative Frobenius error of the result):
-// rounding both operands to s digits of 8 bits relative to their row / column
-// scale (|error| <= 2^(-8s-1) of the scale per element) and the dropped products
-// contribute 2^(10-8s): room for a factor of about 2^10 between the scales and the
-// result (cancellation in small sectors); rounding of the FP32 accumulator of the
-// products of order >= 3 (at most 2^-24 of the result) over the whole K is kept
-// below 2^-44 sqrt(K). The slice count is the smallest s >= 4 whose estimate is at
-// most rtol (s = 6 for rtol = 1e-10).
+// rounding both operands to 8s - 1 significant bits relative to their row /
+// column scale (|error| <= 2^(-8s-1) of the scale 2^e per element, with
+// |x| < 2^(e-1)) and the dropped products contribute 2^(11-8s): room for a
+// factor of about 2^10 between the scales and the result (cancellation in small
+// sectors); rounding of the FP32 accumulator of the products of order >= 3 (at
+// most 2^-23 of the result) over the whole K is kept below 2^-43 sqrt(K). The
+// slice count is the smallest s >= 4 whose estimate is at most rtol (s = 6 for
+// rtol = 1e-10).
 static double split_error_estimate(int s, int64_t kmax) {
-  return std::ldexp(1.0, 10 - 8 * s) + std::ldexp(1.0, -44) * std::sqrt((double)std::max<int64_t>(kmax, 1));
+  return std::ldexp(1.0, 11 - 8 * s) + std::ldexp(1.0, -43) * std::sqrt((double)std::max<int64_t>(kmax, 1));
 }
 
 static ytn_status choose_slices(const ytn_plan_t *p, double rtol, int &s, double &est) {

@@ -2,24 +2,25 @@
 // 5th-generation tensor cores (tcgen05, accumulators in tensor memory, operands
 // fed by bulk TMA copies), with FP64 results.
 //
-// Operands are the BF16 slices written by split_kernels.cu: A_q ~ 2^(e_i - 8)
-// sum_p A_p and B_q ~ 2^(f_j - 8) sum_q B_q, with slice p (0-based) an integer
-// digit times 2^{-8p}. C_q = 2^(e_i + f_j - 16) sum_{p + q <= s - 1} A_p B_q^T,
-// where s is the number of slices used (products of order p + q >= s are
-// dropped, as in the Ozaki scheme).
+// Operands are the BF16 slices written by split_kernels.cu: A_q = 2^(e_i - 8)
+// sum_p A_p and B_q = 2^(f_j - 8) sum_q B_q (up to the rounding of the last digit),
+// with slice p a signed digit of magnitude <= 2^7 times 2^{-8p}.
+// C_q = 2^(e_i + f_j - 16) sum_{p + q <= s - 1} A_p B_q^T, where s is the number of
+// slices used (products of order p + q >= s are dropped, as in the Ozaki scheme).
 //
 // Accumulation, per 128 x 128 output tile:
-//   E2 = A_0 B_0                     order 0, exact in FP32 per K chunk of 64
+//   E2 = A_0 B_0                     order 0, exact in FP32 per K chunk of 256
 //   E3 = A_0 B_1 + A_1 B_0           order 1, exact (an integer times 2^-8)
 //   E4 = A_0 B_2 + A_1 B_1 + A_2 B_0 order 2, exact (an integer times 2^-16)
-//   R  = every kept product of order >= 3, FP32 per K chunk of 64
-// Chunk sums stay below 2^24 units of their lowest bit (3 * 64 * 255^2 < 2^24), so
-// the three exact accumulators are exact; after each chunk the epilogue warps
-// read all four from tensor memory and add them into a 64-bit fixed-point
-// accumulator (units of 2^-24 of the order-0 product). Only R, at most 2^-22 of
-// the result, is rounded in FP32, and only over 64 of K at a time (the tensor
-// cores' FP32 accumulation of mixed-magnitude products is not round-to-nearest,
-// so its error grows with the number of additions). The result is converted to FP64 and
+//   R  = every kept product of order >= 3, FP32 per K chunk of 256
+// A digit product is at most 2^14 in magnitude, so over a chunk of 256 the three
+// exact accumulators stay within 3 * 256 * 2^14 < 2^24 units of their lowest bit
+// and FP32 holds them exactly; after each chunk the epilogue warps read all four
+// from tensor memory and add them into a 64-bit fixed-point accumulator (units
+// of 2^-24 of the order-0 product). Only R, about 2^-24 of the result per K, is
+// rounded in FP32, and only over 256 of K at a time (the tensor cores' FP32
+// accumulation of mixed-magnitude products is not round-to-nearest, so its error
+// grows with the number of additions). The result is converted to FP64 and
 // scaled by 2^(e_i + f_j - 40). Tensor memory: E2 [0,128), E3 [128,256),
 // E4 [256,384), R [384,512).
 //
@@ -51,7 +52,7 @@ constexpr int kFirstEpiWarp = 4;  // warps 4..15: epilogue
 constexpr int kEpiWarps = 12;
 constexpr int kStagesRing = 2;
 constexpr int kSlotBytes = 2 * kBlockBytes;
-constexpr int kChunk = 2;         // K stages per exact-accumulation chunk (K 64)
+constexpr int kChunk = 8;         // K stages per exact-accumulation chunk (K 256)
 constexpr uint32_t kColE2 = 0, kColE3 = 128, kColE4 = 256, kColR = 384;
 constexpr uint32_t kMaxPolls = 1u << 26;
 constexpr int kSmemBytes = kStagesRing * kSlotBytes + 1024 + 256;
@@ -292,8 +293,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             };
             // Every chunk starts all four accumulators afresh: the exact ones once the
             // previous chunk's exact drain is done, R once its R drain is done. The
-            // drain of the exact accumulators overlaps the chunk's last R products,
-            // the drain of R the next chunk's first exact products.
+            // exact accumulators are complete after the last stage's exact products,
+            // so their drain overlaps that stage's R products; the drain of R
+            // overlaps the next chunk's first exact products.
             if (first) {
               wait_e_empty();
               if (!ok) break;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               issue_rest<S>(tmem, a0, b0, true);
             } else {
               issue_exact(tmem, a0, b0, false);
-              umma_commit(bar(kEFull));
+              if (last) umma_commit(bar(kEFull));
               issue_rest<S>(tmem, a0, b0, false);
             }
             umma_commit(bar(kEmpty0 + slot));
@@ -351,15 +353,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-              // order 0: |E2| < 2^22, read from the bit pattern of E2 + 1.5 * 2^23
+              // order 0: |E2| <= 256 * 2^14 = 2^22, read from the bit pattern of
+              // E2 + 1.5 * 2^23 (exact on the closed range: the pattern is linear in
+              // the integer up to and including 2^24)
               const int x2 = __float_as_int(__uint_as_float(v2[i]) + 12582912.0f) - 0x4B400000;
-              // order 1: |E3 * 2^8| <= 64 * 2 * 255^2 < 2^23
+              // order 1: |E3 * 2^8| <= 2 * 256 * 2^14 = 2^23
               const int x3 = __float2int_rn(__uint_as_float(v3[i]) * 256.0f);
-              // order 2: |E4 * 2^16| <= 64 * 3 * 255^2 < 2^24
+              // order 2: |E4 * 2^16| <= 3 * 256 * 2^14 < 2^24
               const int x4 = __float2int_rn(__uint_as_float(v4[i]) * 65536.0f);
-              // x3 * 2^8 + x4 <= 2,143,224,000 < 2^31
-              const int t = x3 * 256 + x4;
-              acc[g * 4 + i] += (long long)x2 * 16777216 + (long long)t * 256;
+              // |x2 * 2^8 + x3| <= 2^30 + 2^23 < 2^31
+              acc[g * 4 + i] += (long long)(x2 * 256 + x3) * 65536 + (long long)x4 * 256;
             }
           }
         }
@@ -375,8 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t vr[8];
             tmem_ld8(lane_addr + kColR + c0 + g * 8, vr);
             tmem_wait_ld();
-            // |R| over one chunk < 64 (4 * 255^2 * 2^-24 + 5 * 255^2 * 2^-32 + 6 * 256 * 255 * 2^-40)
-            // < 1, so R * 2^24 fits 32 bits
+            // |R| over one chunk <= 256 (4 * 2^14 * 2^-24 + 5 * 2^14 * 2^-32 + 6 * 2^14 * 2^-40)
+            // < 1.02, so R * 2^24 fits 32 bits
 #pragma unroll
             for (int i = 0; i < 8; i++)
               acc[g * 8 + i] += (long long)__float2int_rn(__uint_as_float(vr[i]) * 16777216.0f);

@@ -3,15 +3,18 @@
 // Numer. Algorithms 2012, with power-of-two scales per row).
 //
 // For a row x_r of an operand (a row of A_q, or a column of B_q), with
-// e_r = 1 + floor(log2 max_k |x_rk|), every element is written in fixed point
-// relative to 2^e_r with s digits of 8 bits (s = slices in use, <= 6):
-//     x_rk = sign * 2^e_r * (sum_{p=1..s} d_p 2^{-8p} + t),   0 <= d_p < 256,
-// the last digit rounded to nearest, so |t| <= 2^(-8s-1). Slices beyond s are
-// zero. Slice p holds sign * d_p * 2^{-8(p-1)}, an
-// integer times a power of two with at most 8 significant bits, so it is exact
-// in BF16 and products of two slices are exact in FP32. The digits are taken
-// from the FP64 bit pattern with integer shifts only (no FP64 arithmetic, which
-// is slow on this GPU). Zero and subnormal inputs give zero digits.
+// e_r = 2 + floor(log2 max_k |x_rk|) (one bit of headroom: |x_rk| < 2^(e_r - 1)),
+// every element is rounded to the integer u = round(x_rk 2^(8s - e_r)),
+// |u| <= 2^(8s-1), and u is written in balanced base 256 (s = slices in use, <= 6):
+//     u = sum_{p=0..s-1} d_p 256^(s-1-p),  d_p in [-128, 127] for p >= 1,
+//     d_0 in [-128, 128],
+// so x_rk = 2^e_r (sum_p d_p 2^{-8(p+1)} + t) with |t| <= 2^(-8s-1). Slices beyond
+// s are zero. Slice p holds d_p 2^{-8p}: a signed integer of magnitude at most 2^7
+// times a power of two, exact in BF16; products of two slices are exact in FP32
+// and at most 2^14 times their power of two, which lets the GEMM sum 256 of K
+// exactly per accumulator. The digits are taken from the FP64 bit pattern with
+// integer operations only (no FP64 arithmetic, which is slow on this GPU). Zero
+// and subnormal inputs give zero digits.
 //
 // Output layout: for operand block (row tile rt, K stage kt) six consecutive
 // 128 x 32 BF16 slices, each K-major with the 64-byte swizzle (16-byte chunk c of
@@ -30,7 +33,7 @@ __device__ __forceinline__ int biased_exp(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// Row exponents: e_r = maxE - 1022 over the row (maxE = largest biased exponent).
+// Row exponents: e_r = maxE - 1021 over the row (maxE = largest biased exponent).
 __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__restrict__ ops,
                                                         const SplitItem *__restrict__ items,
                                                         const double *__restrict__ wa,
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__re
       if (lane == 0) red[0][rr] = m;
     }
     __syncthreads();
-    if (tid < kSplitBM) E[r0 + tid] = (r0 + tid < o.rows && red[0][tid] > 0) ? red[0][tid] - 1022 : -1022;
+    if (tid < kSplitBM) E[r0 + tid] = (r0 + tid < o.rows && red[0][tid] > 0) ? red[0][tid] - 1021 : -1021;
   } else {
     // K rows of `rows` contiguous elements: thread per row, two halves of K
     const int rr = tid & (kSplitBM - 1), half = tid >> 7;
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__re
     __syncthreads();
     if (tid < kSplitBM) {
       const int mm = max(red[0][tid], red[1][tid]);
-      E[r0 + tid] = (r0 + tid < o.rows && mm > 0) ? mm - 1022 : -1022;
+      E[r0 + tid] = (r0 + tid < o.rows && mm > 0) ? mm - 1021 : -1021;
     }
   }
 }
@@ -128,22 +131,30 @@ __global__ void __launch_bounds__(256) split_slice_kernel(const SplitOperand *__
       for (int j = 0; j < 8; j++) {
         const unsigned long long bits = tile[rr][c * 8 + j];
         const int Eb = (int)((bits >> 52) & 0x7FF);
-        // u = round(|x| 2^-e 2^(8s)): the s kept digits, the last one rounded to nearest
-        unsigned long long u = 0;
+        // |u| = round(|x| 2^-e 2^(8s)) <= 2^(8s-1): the s kept digits, rounded to nearest
+        long long u = 0;
         if (Eb != 0) {
           const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-          const int shift = 1075 + e - Eb - 8 * s;   // >= 53 - 8s >= 5
-          if (shift < 64) {
-            u = (mant + (1ull << (shift - 1))) >> shift;
-            u = min(u, (1ull << (8 * s)) - 1ull);
+          const int shift = 1075 + e - Eb - 8 * s;   // >= 54 - 8s >= 6
+          if (shift < 64) u = (long long)((mant + (1ull << (shift - 1))) >> shift);
+          if (bits >> 63) u = -u;
+        }
+        // balanced digits, least significant first: d = u mod 256 in [-128, 127]
+        int dg[kSlices];
+#pragma unroll
+        for (int p = kSlices - 1; p >= 1; p--) {
+          if (p < s) {
+            const int d = (int)(((u + 128) & 255) - 128);
+            dg[p] = d;
+            u = (u - d) >> 8;   // exact: u - d is a multiple of 256
+          } else {
+            dg[p] = 0;
           }
         }
-        const bool neg = (bits >> 63) != 0;
+        dg[0] = (int)u;       // in [-128, 128]
 #pragma unroll
         for (int p = 0; p < kSlices; p++) {
-          const int d = p < s ? (int)((u >> (8 * (s - 1 - p))) & 0xFF) : 0;
-          float f = (float)d * __int_as_float((127 - 8 * p) << 23);   // d * 2^{-8p}
-          if (neg) f = -f;
+          const float f = (float)dg[p] * __int_as_float((127 - 8 * p) << 23);   // d * 2^{-8p}
           const uint16_t h = __bfloat16_as_ushort(__float2bfloat16_rn(f));
           if (j & 1) packed[p][j >> 1] |= (uint32_t)h << 16;
           else packed[p][j >> 1] = h;
