@@ -252,6 +252,14 @@ ytn_status ytn_unfuse(ytn_plan_t *plan, const double *a, double *out, ytn_stream
 /* out = trace of a over the planned leg pairs. Same buffer rules as ytn_fuse. */
 ytn_status ytn_trace(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
 
+/* Number of CTAs (one per SM) of the persistent split-precision GEMM of this
+ * context; 0 (the default) uses every SM. Leaving some SMs free lets the data
+ * movers of another call, for instance one that reads its operands from host
+ * memory over the host link, run beside a contraction's GEMM instead of after
+ * it. No counterpart in the paper. Errors: YTN_E_INVALID (host-only context, or
+ * nsms outside [0, number of SMs]). */
+ytn_status ytn_ctx_set_gemm_sms(ytn_ctx *ctx, int nsms);
+
 /* Wait for the stream (at most timeout_ms; < 0 waits without limit) and report
  * the context's device status word: YTN_E_TIMEOUT if a bounded device wait
  * ran out since the last call (the word is then cleared), YTN_E_CUDA if the

@@ -484,7 +484,8 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
     {
       PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
       e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles, (int64_t)p->sp_tiles.size(), sa, sb, ea, eb, wc, slices,
-                            p->ctx->status_dev, p->ctx->num_sms, st);
+                            p->ctx->status_dev, p->ctx->gemm_sms.load() > 0 ? p->ctx->gemm_sms.load() : p->ctx->num_sms,
+                            st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grouped split-precision GEMM");
   }
@@ -645,6 +646,14 @@ ytn_status ytn_unfuse(ytn_plan_t *p, const double *a, double *out, ytn_stream st
 
 ytn_status ytn_trace(ytn_plan_t *p, const double *a, double *out, ytn_stream stream) {
   return run_move(p, Kind::Trace, a, out, stream, "trace");
+}
+
+ytn_status ytn_ctx_set_gemm_sms(ytn_ctx *ctx, int nsms) {
+  if (!ctx) return fail(YTN_E_INVALID, "null ctx");
+  if (ctx->device < 0) return fail(YTN_E_INVALID, "host-only context");
+  if (nsms < 0 || nsms > ctx->num_sms) return fail(YTN_E_INVALID, "SM count out of range");
+  ctx->gemm_sms.store(nsms);
+  return YTN_OK;
 }
 
 ytn_status ytn_profile_enable(ytn_ctx *ctx, int enable) {

@@ -190,6 +190,7 @@ struct ytn_ctx {
   int device = 0;
   int *status_dev = nullptr;   // device status word (bounded waits report here)
   int num_sms = 0;
+  std::atomic<int> gemm_sms{0};   // CTAs of the persistent split GEMM (0: one per SM)
   std::mutex mu;
   std::unordered_map<std::string, ytn_plan_t *> cache;
   // phase timing: a pool of CUDA events (cudaEvent_t stored as void*) and the

@@ -108,6 +108,7 @@ SYMBOLS = {
     "ytn_unfuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_sync": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "ytn_ctx_set_gemm_sms": (C.c_int, [C.c_void_p, C.c_int]),
     "ytn_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ytn_profile_read": (C.c_int, [C.c_void_p, C.POINTER(ytn_profile)]),
     "ytn_graph_begin": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -357,6 +358,10 @@ def ytn_trace(plan, a, out, stream=None):
 
 def ytn_sync(ctx, stream=None, timeout_ms=-1):
     _check(_lib.ytn_sync(ctx.handle, _stream(stream), int(timeout_ms)))
+
+
+def ytn_ctx_set_gemm_sms(ctx, nsms):
+    _check(_lib.ytn_ctx_set_gemm_sms(ctx.handle, int(nsms)))
 
 
 def ytn_profile_enable(ctx, enable=True):

@@ -186,3 +186,8 @@ def test_auto_workspace_covers_the_admissible_paths(hctx):
     assert ytn.ytn_workspace_size(plan, ytn.YTN_AUTO, 1e-16) == f64
     with pytest.raises(ytn.YtnError):
         ytn.ytn_workspace_size(plan, ytn.YTN_SPLIT_BF16, 1e-16)
+
+
+def test_gemm_sms_needs_a_device_context(hctx):
+    with pytest.raises(ytn.YtnError):
+        ytn.ytn_ctx_set_gemm_sms(hctx, 8)

@@ -114,3 +114,22 @@ def test_pageable_host_memory_is_rejected(ctx):
     with pytest.raises(ytn.YtnError) as ei:
         ytn.ytn_tensordot(plan, A["data"], torch.from_numpy(B["data"]).to(device()), c, workspace=ws)
     assert ei.value.name == "YTN_E_INVALID"
+
+
+def test_split_gemm_on_a_subset_of_the_sms(ctx):
+    """The persistent split GEMM on fewer CTAs than SMs gives the same bits."""
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    rng = np.random.default_rng(77)
+    A, B, axa, axb, _, _ = random_pair(rng, (0, 0), 3, 3, 2, max_sectors=4, max_dim=9)
+    plan, ref, _ = run_tensordot(ctx, A, B, axa, axb, prec=ytn.YTN_SPLIT_BF16, rtol=1e-10)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    with pytest.raises(ytn.YtnError):
+        ytn.ytn_ctx_set_gemm_sms(ctx, nsm + 1)
+    try:
+        for n in (1, 16, nsm - 8):
+            ytn.ytn_ctx_set_gemm_sms(ctx, n)
+            _, rec, _ = run_tensordot(ctx, A, B, axa, axb, prec=ytn.YTN_SPLIT_BF16, rtol=1e-10)
+            np.testing.assert_array_equal(rec["data"], ref["data"])
+    finally:
+        ytn.ytn_ctx_set_gemm_sms(ctx, 0)

@@ -280,9 +280,10 @@ def test_random_tensordot_split(ctx, sym, case):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (128, 128, 32), (129, 127, 33), (300, 260, 500), (40, 700, 129),
-                                  (257, 3, 1000), (65, 64, 64), (64, 130, 65), (3, 5, 63)])
+                                  (257, 3, 1000), (65, 64, 64), (64, 130, 65), (3, 5, 63), (130, 128, 256),
+                                  (128, 129, 257), (64, 64, 512), (5, 7, 255)])
 def test_split_tiles_chunks_and_ragged_tails(ctx, dims):
-    """Tiles of 128 x 128, K stages of 32 and exact-accumulation chunks of 64, all
+    """Tiles of 128 x 128, K stages of 32 and exact-accumulation chunks of 256, all
     with ragged tails."""
     M, N, K = dims
     l_m, l_k, l_n = W.Leg(1, [(0,)], [M]), W.Leg(1, [(0,)], [K]), W.Leg(1, [(0,)], [N])
@@ -292,6 +293,23 @@ def test_split_tiles_chunks_and_ragged_tails(ctx, dims):
     want = A["data"].reshape(M, K) @ B["data"].reshape(K, N)
     err = rel_frobenius(rec["data"], want.ravel())
     assert err <= SPLIT_RTOL, err
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_split_extreme_digits_fill_the_exact_accumulators(ctx, sign):
+    """Every element just below a power of two has leading digit +-128, so over a
+    full chunk of 256 the order-0 accumulator reaches exactly +-2^22, the end of its
+    exact range; the result must still be right."""
+    x = 2.0 - 2.0 ** -40
+    K = 512
+    l_m, l_k, l_n = W.Leg(1, [(0,)], [130]), W.Leg(1, [(0,)], [K]), W.Leg(1, [(0,)], [129])
+    A = W.random_tensor((0,), [l_m, l_k], (0,), 1)
+    B = W.random_tensor((0,), [l_k.conj(), l_n], (0,), 2)
+    A["data"] = np.full_like(A["data"], sign * x)
+    B["data"] = np.full_like(B["data"], x)
+    _, rec, _ = _split(ctx, A, B, (1,), (0,))
+    want = np.full(130 * 129, sign * K * x * x)
+    assert rel_frobenius(rec["data"], want) <= 1e-15
 
 
 def test_split_is_exact_on_small_integers(ctx):
