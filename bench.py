@@ -195,7 +195,7 @@ def oracle_sample(cfg, budget_s, seed=0):
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return 0
     cfg = make_workload(args.workload, 0)
@@ -218,6 +218,30 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ ranks
+
+def rank_env():
+    """(world size, rank, local rank) from the torchrun environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, device):
+    """The largest value over all ranks (a timing reduction, not a data-path one)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(flops_per_rank, steps, world, seconds):
+    """Whole-job useful TFLOP/s: every rank contracts its own problem of the same
+    size, the slowest rank's time counts."""
+    return world * flops_per_rank * steps / seconds / 1e12
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
@@ -226,9 +250,7 @@ def run_ours(args):
 
     from paper_2405_12196_gb300 import ytn
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -287,12 +309,9 @@ def run_ours(args):
         prof = ytn.ytn_profile_read(ctx)
         ytn.ytn_profile_enable(ctx, False)
         step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
-        t = torch.tensor([ev[0].elapsed_time(ev[-1])], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dev)
         return {"total_ms": total_ms, "step_ms": step_ms, "prof": prof, "res": res, "clocks": clk,
-                "value": world * flops * steps / (total_ms * 1e-3) / 1e12}
+                "value": weak_value(flops, steps, world, total_ms * 1e-3)}
 
     peaks, peak_src = load_peaks()
 
@@ -354,10 +373,7 @@ def run_ours(args):
             body()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        return world * flops * e2e_steps / (float(te.item()) * 1e-3) / 1e12
+        return weak_value(flops, e2e_steps, world, max_over_ranks(e0.elapsed_time(e1), dev) * 1e-3)
 
     def host_call():
         ytn.ytn_tensordot(plan, ha, hb, hc, prec=prec, rtol=args.rtol, workspace=ws, stream=stream)
@@ -398,11 +414,9 @@ def run_ours(args):
         for _ in range(e2e_steps):
             pipelined_call()
         torch.cuda.synchronize(dev)
-        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        elapsed = time.perf_counter() - t0
         ytn.ytn_ctx_set_gemm_sms(ctx, 0)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        return world * flops * e2e_steps / float(te.item()) / 1e12
+        return weak_value(flops, e2e_steps, world, max_over_ranks(elapsed, dev))
 
     pipelined_call()
     pipelined_call()
