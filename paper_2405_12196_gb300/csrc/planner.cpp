@@ -759,12 +759,17 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   make_items(p, j2, j3);
   p->items_c_end = (int64_t)p->items.size();
 
-  // Grouped-GEMM tiles (64 x 64), largest K first.
+  // Grouped-GEMM tiles, largest K first. The tile edge is chosen per sector from
+  // its size: 32 when 32 x 32 tiles cover the sector with at most 60% of the
+  // padded area of 64 x 64 tiles (small or thin M, N), else 64.
   p->tiles.clear();
   for (size_t si = 0; si < geo.size(); si++) {
-    const int64_t mt = (geo[si].M + 63) / 64, nt = (geo[si].N + 63) / 64;
+    const int64_t M = geo[si].M, N = geo[si].N;
+    const int64_t a64 = ((M + 63) / 64) * ((N + 63) / 64) * 4096, a32 = ((M + 31) / 32) * ((N + 31) / 32) * 1024;
+    const int T = 10 * a32 <= 6 * a64 ? 32 : 64;
+    const int64_t mt = (M + T - 1) / T, nt = (N + T - 1) / T;
     for (int64_t i = 0; i < mt; i++)
-      for (int64_t j = 0; j < nt; j++) p->tiles.push_back({(int32_t)si, (int32_t)i, (int32_t)j, 0});
+      for (int64_t j = 0; j < nt; j++) p->tiles.push_back({(int32_t)si, (int32_t)i, (int32_t)j, T});
   }
   std::stable_sort(p->tiles.begin(), p->tiles.end(), [&](const GemmTile &x, const GemmTile &y) {
     return geo[x.sector].K > geo[y.sector].K;

@@ -79,8 +79,8 @@ static_assert(sizeof(SectorDev) == 48, "SectorDev layout");
 // One output tile of the grouped FP64 GEMM.
 struct GemmTile {
   int32_t sector;
-  int32_t mt, nt;
-  int32_t pad;
+  int32_t mt, nt;   // tile coordinates in units of `size`
+  int32_t size;     // tile edge: 64, or 32 for small sectors
 };
 
 // Trace: one output block, fed by ncontrib contributing input blocks.

@@ -48,9 +48,11 @@ def test_config1(ctx):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (64, 64, 16), (65, 63, 17), (200, 130, 77), (3, 300, 5),
-                                  (257, 1, 129)])
+                                  (257, 1, 129), (32, 32, 16), (33, 31, 17), (20, 100, 40), (31, 65, 3)])
 def test_single_sector_tiles_and_ragged_tails(ctx, dims):
-    """One dense sector spanning several 64x64 tiles with ragged M, N and K tails."""
+    """One dense sector spanning several tiles with ragged M, N and K tails; the
+    planner picks 64x64 tiles for the larger sectors here and 32x32 tiles for the
+    small or thin ones ((1,1), (3,300), (257,1), (32,32), (33,31), (20,100), (31,65))."""
     M, N, K = dims
     l_m = W.Leg(1, [(0,)], [M])
     l_k = W.Leg(1, [(0,)], [K])
