@@ -44,7 +44,7 @@ __all__ = [
     "OTensor", "OracleError", "SignatureError", "DimMismatchError", "FusionMismatchError",
     "ChargeError", "InvalidError", "UnsupportedError",
     "from_record", "to_record", "conj", "tensordot", "fuse", "unfuse", "trace",
-    "to_dense", "leg_sectors", "useful_flops", "tensordot_block",
+    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot",
 ]
 
 
@@ -490,6 +490,38 @@ def trace(A, ax1, ax2):
         kc = tuple(key[i] for i in rest)
         out.blocks[kc] = out.blocks[kc] + val if kc in out.blocks else np.array(val, dtype=np.float64)
     return out
+
+
+# ------------------------------------------------------------------ reductions
+
+def vdot(A, B):
+    """Scalar product <A, B> = sum over every element of A times the same element of B
+    (the Frobenius product of the dense embeddings; elements are real).
+
+    The paper leaves the scalar reductions of a tensor network (norms, overlaps,
+    expectation values) to the backend; they are kept in FP64 here. Two tensors are
+    comparable when they have the same symmetry, rank and leg signatures, one
+    dimension per charge on each leg and identical fusion records; blocks present in
+    only one of them contribute nothing. The sum runs over the common blocks in
+    canonical order, each block's products summed with numpy. The norm is
+    sqrt(vdot(A, A))."""
+    if A.mods != B.mods or A.rank != B.rank:
+        raise InvalidError("tensors of different symmetry or rank")
+    if A.sig != B.sig:
+        raise SignatureError("tensors with different leg signatures")
+    for a in range(A.rank):
+        da, db = leg_sectors(A, a), leg_sectors(B, a)
+        for q in set(da) & set(db):
+            if da[q] != db[q]:
+                raise DimMismatchError(f"leg {a} charge {q}: dimension {da[q]} vs {db[q]}")
+        fa, fb = A.fus[a], B.fus[a]
+        if (fa is None) != (fb is None) or (fa is not None and fa.key() != fb.key()):
+            raise FusionMismatchError(f"leg {a}: fusion records differ")
+    total = 0.0
+    for key in A.keys():
+        if key in B.blocks:
+            total += float(np.sum(A.blocks[key] * B.blocks[key]))
+    return total
 
 
 # ------------------------------------------------------------------ dense embedding

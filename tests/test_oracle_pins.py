@@ -370,3 +370,67 @@ def test_tensordot_block_matches_tensordot(case):
     C = O.tensordot(oA, oB, axa, axb)
     for k, v in C.blocks.items():
         np.testing.assert_allclose(O.tensordot_block(oA, oB, axa, axb, k), v, rtol=1e-14, atol=1e-14)
+
+
+# ---------------------------------------------------------------- scalar products
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(8))
+def test_vdot_equals_dense_scalar_product(sym, case):
+    """<A, B> of two tensors on the same legs == numpy.vdot of their dense embeddings,
+    also when B lacks some of A's blocks; <A, A> is the squared Frobenius norm."""
+    mods = SYMS[sym]
+    rng = np.random.default_rng(7000 + 31 * case + len(sym))
+    legs = random_legs(rng, mods, int(rng.integers(1, 5)))
+    n = tuple(int(rng.integers(0, m)) if m else int(rng.integers(-1, 2)) for m in mods)
+    A = O.from_record(W.random_tensor(mods, legs, n, 2 * case + 1))
+    B = O.from_record(W.random_tensor(mods, legs, n, 2 * case + 2))
+    for k in list(B.blocks)[::3]:
+        del B.blocks[k]
+    lm = [leg_map(l) for l in legs]
+    dA, dB = O.to_dense(A, lm), O.to_dense(B, lm)
+    assert O.vdot(A, B) == pytest.approx(float(np.vdot(dA, dB)), rel=1e-12, abs=1e-12)
+    assert O.vdot(A, A) == pytest.approx(float(np.sum(dA * dA)), rel=1e-12, abs=1e-300)
+    assert O.vdot(A, A) >= 0.0
+
+
+def test_vdot_is_the_full_contraction_with_the_dual_tensor():
+    """<A, B> == tensordot over every leg of A with B on dual legs (flipped signatures
+    and total charge), a different route through the oracle."""
+    rng = np.random.default_rng(11)
+    legs = random_legs(rng, (0, 0), 3)
+    A = O.from_record(W.random_tensor((0, 0), legs, (0, 0), 5))
+    B = O.from_record(W.random_tensor((0, 0), legs, (0, 0), 6))
+    Bd = O.OTensor(B.mods, tuple(-s for s in B.sig), tuple(-q for q in B.n), dict(B.blocks))
+    C = O.tensordot(A, Bd, (0, 1, 2), (0, 1, 2))
+    want = float(C.blocks[()]) if C.blocks else 0.0
+    assert O.vdot(A, B) == pytest.approx(want, rel=1e-13, abs=1e-13)
+
+
+def test_vdot_is_invariant_under_fusion():
+    """Fusion only relabels and regroups elements (Sec. II.B): <fuse A, fuse B> == <A, B>."""
+    rng = np.random.default_rng(13)
+    legs = random_legs(rng, (0,), 4)
+    A = O.from_record(W.random_tensor((0,), legs, (0,), 7))
+    B = O.from_record(W.random_tensor((0,), legs, (0,), 8))
+    g = ((0, 2), (1, 3))
+    assert O.vdot(O.fuse(A, g), O.fuse(B, g)) == pytest.approx(O.vdot(A, B), rel=1e-12, abs=1e-12)
+
+
+def test_heisenberg_norm():
+    """The paper's two-spin example: ||H||^2 = Tr H^2 = 3/4 (H is symmetric)."""
+    g = _golden("heisenberg_two_site.json")
+    H = _tensor_from_golden(g)
+    assert O.vdot(H, H) == pytest.approx(g["trace_H2"], abs=1e-15)
+
+
+def test_vdot_rejects_incomparable_tensors():
+    l = W.Leg(1, [(-1,), (1,)], [2, 3])
+    A = O.from_record(W.random_tensor((0,), [l, l.conj()], (0,), 1))
+    with pytest.raises(O.SignatureError):
+        O.vdot(A, O.from_record(W.random_tensor((0,), [l.conj(), l], (0,), 2)))
+    l2 = W.Leg(1, [(-1,), (1,)], [2, 4])
+    with pytest.raises(O.DimMismatchError):
+        O.vdot(A, O.from_record(W.random_tensor((0,), [l2, l2.conj()], (0,), 3)))
+    with pytest.raises(O.InvalidError):
+        O.vdot(A, O.from_record(W.random_tensor((2,), [W.Leg(1, [(0,), (1,)], [2, 3])] * 2, (0,), 4)))
