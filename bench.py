@@ -557,6 +557,141 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ CTM chain as one graph
+
+def ctm_chain(ytn, ctx, dev, prec, rtol, seed=3001):
+    """The contractions of one CTMRG step of the U(1)xU(1) D=12, chi=144 workload
+    as one chain of library calls: A.A* over the physical leg, fuse of the ket/bra
+    pairs into the double layer a, C.T, CT.T, and X2.a over two legs (X2 carries
+    the conjugate fusion records of a's legs). Returns (run(stream), plans, output
+    buffer of X2.a, its size, useful FLOPs per chain)."""
+    import torch
+    cfg = W.config3(seed=seed)
+    A, C, T, X2 = cfg["A"], cfg["C"], cfg["T"], dict(cfg["X2"])
+    Ac = dict(A)
+    Ac["sig"] = tuple(-s for s in A["sig"])
+    p_aa = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, Ac, (4,), (4,))
+    groups = ((0, 4), (1, 5), (2, 6), (3, 7))
+    p_fuse = ytn.ytn_plan(ctx, ytn.YTN_OP_FUSE, dict(p_aa.out), groups=groups)
+    a = dict(p_fuse.out)
+    conj = lambda f: dict(f, sig=tuple(-x for x in f["sig"]))   # noqa: E731
+    X2["fus"] = [None, conj(a["fus"][0]), conj(a["fus"][1]), None]
+    p_ct = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, C, T, (1,), (0,))
+    p_ctt = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, dict(p_ct.out, data=None), T, (2,), (0,))
+    p_x2a = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, X2, a, (1, 2), (0, 1))
+
+    def dbuf(n):
+        return torch.empty(max(int(n), 1), dtype=torch.float64, device=dev)
+
+    buf = {k: torch.from_numpy(v["data"]).to(dev) for k, v in (("A", A), ("C", C), ("T", T), ("X2", X2))}
+    buf["AA"], buf["a"] = dbuf(p_aa.out["size"]), dbuf(a["size"])
+    buf["CT"], buf["CTT"], buf["X2a"] = dbuf(p_ct.out["size"]), dbuf(p_ctt.out["size"]), dbuf(p_x2a.out["size"])
+    tds = [(p_aa, "A", "A", "AA"), (p_ct, "C", "T", "CT"), (p_ctt, "CT", "T", "CTT"), (p_x2a, "X2", "a", "X2a")]
+    ws = {id(p): torch.empty(max(ytn.ytn_workspace_size(p, prec, rtol), 1), dtype=torch.uint8, device=dev)
+          for p, *_ in tds}
+
+    def run(stream):
+        p, x, y, z = tds[0]
+        ytn.ytn_tensordot(p, buf[x], buf[y], buf[z], prec=prec, rtol=rtol, workspace=ws[id(p)], stream=stream)
+        ytn.ytn_fuse(p_fuse, buf["AA"], buf["a"], stream=stream)
+        for p, x, y, z in tds[1:]:
+            ytn.ytn_tensordot(p, buf[x], buf[y], buf[z], prec=prec, rtol=rtol, workspace=ws[id(p)],
+                              stream=stream)
+
+    flops = sum(p.info["useful_flops"] for p, *_ in tds)
+    return run, [p_aa, p_fuse, p_ct, p_ctt, p_x2a], buf["X2a"], p_x2a.out["size"], flops
+
+
+def run_chain(args):
+    """Eager calls vs one CUDA-graph launch per chain (YTN_AUTO picks each
+    contraction's path on the eager warm-up, before the capture)."""
+    import torch
+
+    from paper_2405_12196_gb300 import ytn
+    dev = torch.device("cuda:0")
+    ctx = ytn.ytn_ctx_create(0)
+    stream = torch.cuda.Stream(device=dev)
+    run, plans, out, n, flops = ctm_chain(ytn, ctx, dev, ytn.YTN_AUTO, args.rtol)
+    for _ in range(args.warmup):
+        run(stream)
+    stream.synchronize()
+    eager = out[:n].clone()
+
+    def timed(body):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            body()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_eager = timed(lambda: run(stream))
+    ytn.ytn_graph_begin(ctx, stream)
+    run(stream)
+    graph = ytn.ytn_graph_end(ctx, stream)
+    graph.launch(stream)
+    stream.synchronize()
+    same = bool(torch.equal(out[:n], eager))
+    ms_graph = timed(lambda: graph.launch(stream))
+    graph.close()
+    line = {
+        "metric": "CTMRG step chain (A.A*, fuse, C.T, CT.T, X2.a): useful TFLOP/s, eager vs one graph",
+        "value": flops / (ms_graph * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "precision": "auto", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC["cfg3"] + ", chain of 4 contractions and 1 fuse",
+                   "useful_flops_per_chain": flops, "rtol": args.rtol},
+        "eager": {"ms_per_chain": ms_eager, "tflops": flops / (ms_eager * 1e-3) / 1e12},
+        "graph": {"ms_per_chain": ms_graph, "tflops": flops / (ms_graph * 1e-3) / 1e12},
+        "graph_equals_eager": same,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
+def run_reduce(args):
+    """Scalar product <X2, X2'> of two D=20 environment tensors on the same legs
+    (3.36e8 common elements, 5.4 GB read per call): HBM-bound."""
+    import torch
+
+    from paper_2405_12196_gb300 import ytn
+    dev = torch.device("cuda:0")
+    ctx = ytn.ytn_ctx_create(0)
+    A = W.config5(seed=5001)["A"]
+    B = W.config5(seed=6001)["A"]
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_VDOT, A, B)
+    da, db = torch.from_numpy(A["data"]).to(dev), torch.from_numpy(B["data"]).to(dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = torch.empty(max(ytn.ytn_workspace_size(plan), 1), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    for _ in range(args.warmup):
+        ytn.ytn_vdot(plan, da, db, out, workspace=ws, stream=stream)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ytn.ytn_vdot(plan, da, db, out, workspace=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    nbytes = 16.0 * plan.info["moved_elems"]
+    peaks, src = load_peaks()
+    line = {
+        "metric": "FP64 scalar product of two block-sparse tensors: GB/s", "value": nbytes / (ms * 1e-3) / 1e9,
+        "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "data": "synthetic", "dtype": "f64",
+        "config": {"workload": WORKLOAD_DESC["cfg5"] + "; <X2, X2'> on the same legs",
+                   "common_elements": plan.info["moved_elems"], "l2": "inputs larger than L2 (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": src},
+        "result": float(out.cpu()[0]),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -572,6 +707,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the continuous-batching serving benchmark")
+    ap.add_argument("--chain", action="store_true", help="time the CTMRG-step chain eager and as one CUDA graph")
+    ap.add_argument("--reduce", action="store_true", help="time the FP64 scalar product of two D=20 tensors")
     ap.add_argument("--serve-runs", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-slots", type=int, default=8)
@@ -583,6 +720,10 @@ def main():
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.chain:
+        return run_chain(args)
+    if args.reduce:
+        return run_reduce(args)
     return run_ours(args)
 
 

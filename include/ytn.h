@@ -123,7 +123,8 @@ typedef enum {
   YTN_OP_TENSORDOT = 1,  /* C = sum_x A B over pairs (axa[k], axb[k]), Sec. II.B */
   YTN_OP_FUSE = 2,       /* fuse groups of legs, Sec. II.B                        */
   YTN_OP_UNFUSE = 3,     /* undo the fusion of legs axa[0..naxes), Sec. II.B      */
-  YTN_OP_TRACE = 4       /* sum the diagonals of leg pairs (axa[k], axb[k]) of a  */
+  YTN_OP_TRACE = 4,      /* sum the diagonals of leg pairs (axa[k], axb[k]) of a  */
+  YTN_OP_VDOT = 5        /* scalar product <a, b> of two tensors on the same legs */
 } ytn_op_kind;
 
 /* A planned operation.
@@ -137,7 +138,10 @@ typedef enum {
  *  UNFUSE:    a, naxes fused legs axa[]; each is replaced by its constituents.
  *  TRACE:     a, naxes pairs (axa[k], axb[k]) of legs of a, with opposite
  *             signatures (the paper has no trace; this is the block-diagonal
- *             sum that the block structure implies). */
+ *             sum that the block structure implies).
+ *  VDOT:      a, b on the same legs: same symmetry, rank and signatures, one
+ *             dimension per charge on each leg, identical fusion records. The
+ *             output is one element (a rank-0 tensor). */
 typedef struct {
   ytn_op_kind kind;
   const ytn_struct *a;
@@ -195,7 +199,8 @@ ytn_status ytn_plan_get_info(const ytn_plan_t *plan, ytn_plan_info *info);
 void ytn_plan_release(ytn_plan_t *plan);
 
 /* Device workspace (bytes) a ytn_tensordot call needs for this precision and
- * tolerance; 0 for the other operations. */
+ * tolerance, or a ytn_vdot call (prec and rtol ignored); 0 for the other
+ * operations. */
 ytn_status ytn_workspace_size(const ytn_plan_t *plan, ytn_precision prec, double rtol,
                               size_t *bytes);
 
@@ -252,6 +257,19 @@ ytn_status ytn_unfuse(ytn_plan_t *plan, const double *a, double *out, ytn_stream
 /* out = trace of a over the planned leg pairs. Same buffer rules as ytn_fuse. */
 ytn_status ytn_trace(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
 
+/* out[0] = <A, B>, the sum over the elements of the blocks present in both
+ * tensors of A's element times B's, in FP64 (a VDOT plan; ||A||^2 = <A, A>).
+ * The paper leaves norms, overlaps and expectation values to its backend; they
+ * are FP64 reductions here. a, b: buffers of the planned sizes; out: one double;
+ * each device memory or page-locked host memory, as for ytn_tensordot.
+ * workspace: device buffer of ytn_workspace_size bytes (8 bytes per 8192 common
+ * elements), 256-byte aligned. Deterministic: the same call gives the same bits.
+ * Asynchronous on stream. Errors: YTN_E_INVALID (wrong plan kind, null buffer),
+ * YTN_E_WORKSPACE, YTN_E_CUDA. Planning errors (YTN_E_SIGNATURE,
+ * YTN_E_DIM_MISMATCH, YTN_E_FUSION_MISMATCH, YTN_E_INVALID) come from ytn_plan. */
+ytn_status ytn_vdot(ytn_plan_t *plan, const double *a, const double *b, double *out, void *workspace,
+                    size_t workspace_bytes, ytn_stream stream);
+
 /* Number of CTAs (one per SM) of the persistent split-precision GEMM of this
  * context; 0 (the default) uses every SM. Leaving some SMs free lets the data
  * movers of another call, for instance one that reads its operands from host
@@ -259,6 +277,14 @@ ytn_status ytn_trace(ytn_plan_t *plan, const double *a, double *out, ytn_stream 
  * it. No counterpart in the paper. Errors: YTN_E_INVALID (host-only context, or
  * nsms outside [0, number of SMs]). */
 ytn_status ytn_ctx_set_gemm_sms(ytn_ctx *ctx, int nsms);
+
+/* Self-test of the failure path (no counterpart in the paper): enqueue on stream
+ * a kernel that waits, bounded to about 2 ms, for a flag that nothing sets, then
+ * records a code in the context's status word, as every bounded device wait of
+ * the library does when it runs out. The next ytn_sync returns YTN_E_TIMEOUT
+ * (and clears the word); the context stays usable. Nothing faults or hangs.
+ * Errors: YTN_E_INVALID (host-only context), YTN_E_CUDA (launch). */
+ytn_status ytn_selftest_timeout(ytn_ctx *ctx, ytn_stream stream);
 
 /* Wait for the stream (at most timeout_ms; < 0 waits without limit) and report
  * the context's device status word: YTN_E_TIMEOUT if a bounded device wait
@@ -351,6 +377,7 @@ enum {
   YTN_PHASE_SCATTER = 3,    /* sector matrices -> blocks of C                 */
   YTN_PHASE_SPLIT = 4,      /* FP64 -> BF16 slices (split path)               */
   YTN_PHASE_MOVE = 5,       /* fuse / unfuse / trace                          */
+  YTN_PHASE_REDUCE = 6,     /* scalar products                                */
   YTN_NPHASES = 8
 };
 typedef struct {

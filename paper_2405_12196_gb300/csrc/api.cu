@@ -61,6 +61,9 @@ static ytn_status upload(ytn_plan_t *p) {
   put_table(buf, p->tiles, o_tiles);
   put_table(buf, p->tr_out, o_tro);
   put_table(buf, p->tr_contrib, o_trc);
+  size_t o_vdp, o_vdc;
+  put_table(buf, p->vd_pieces, o_vdp);
+  put_table(buf, p->vd_chunks, o_vdc);
   size_t o_spo, o_spe, o_sps, o_spsec, o_spt;
   put_table(buf, p->sp_ops, o_spo);
   put_table(buf, p->sp_exp_items, o_spe);
@@ -85,6 +88,8 @@ static ytn_status upload(ytn_plan_t *p) {
   p->d_tiles = reinterpret_cast<const GemmTile *>(d + o_tiles);
   p->d_tr_out = reinterpret_cast<const TraceOut *>(d + o_tro);
   p->d_tr_contrib = reinterpret_cast<const TraceContrib *>(d + o_trc);
+  p->d_vd_pieces = reinterpret_cast<const VdotPiece *>(d + o_vdp);
+  p->d_vd_chunks = reinterpret_cast<const VdotChunk *>(d + o_vdc);
   p->d_sp_ops = reinterpret_cast<const SplitOperand *>(d + o_spo);
   p->d_sp_exp_items = reinterpret_cast<const SplitItem *>(d + o_spe);
   p->d_sp_slice_items = reinterpret_cast<const SplitItem *>(d + o_sps);
@@ -344,6 +349,10 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
             st = plan_unfuse(p, A, op->naxes, op->axa, err);
           }
           break;
+        case YTN_OP_VDOT:
+          st = load_struct(op->b, B, err);
+          if (st == YTN_OK) st = plan_vdot(p, A, B, err);
+          break;
         case YTN_OP_TRACE:
           if (op->naxes < 1 || op->naxes > YTN_MAX_RANK) {
             st = YTN_E_INVALID;
@@ -421,6 +430,10 @@ void ytn_plan_release(ytn_plan_t *plan) {
 ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rtol, size_t *bytes) {
   if (!p || !bytes) return fail(YTN_E_INVALID, "null argument");
   *bytes = 0;
+  if (p->kind == Kind::Vdot) {
+    *bytes = align256(p->vd_chunks.size() * sizeof(double));
+    return YTN_OK;
+  }
   if (p->kind != Kind::Tensordot) return YTN_OK;
   WsLayout w;
   if (prec == YTN_FP64) {
@@ -646,6 +659,35 @@ ytn_status ytn_unfuse(ytn_plan_t *p, const double *a, double *out, ytn_stream st
 
 ytn_status ytn_trace(ytn_plan_t *p, const double *a, double *out, ytn_stream stream) {
   return run_move(p, Kind::Trace, a, out, stream, "trace");
+}
+
+ytn_status ytn_vdot(ytn_plan_t *p, const double *a, const double *b, double *out, void *workspace,
+                    size_t workspace_bytes, ytn_stream stream) {
+  if (!p) return fail(YTN_E_INVALID, "null plan");
+  if (p->kind != Kind::Vdot) return fail(YTN_E_INVALID, "plan is not a scalar-product plan");
+  if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
+  if ((p->a_size && !a) || (p->b_size && !b) || !out) return fail(YTN_E_INVALID, "null data buffer");
+  const size_t need = align256(p->vd_chunks.size() * sizeof(double));
+  if (need && (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)))
+    return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
+  DeviceGuard g(p->ctx->device);
+  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  {
+    ytn_status vs;
+    if ((vs = device_view(p->ctx, a, &a, "A")) != YTN_OK || (vs = device_view(p->ctx, b, &b, "B")) != YTN_OK ||
+        (vs = device_view(p->ctx, out, &out, "output")) != YTN_OK)
+      return vs;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  note_capture(p, st);
+  cudaError_t e;
+  {
+    PhaseTimer t(p->ctx, YTN_PHASE_REDUCE, st);
+    e = launch_vdot(p->d_vd_chunks, (int64_t)p->vd_chunks.size(), p->d_vd_pieces, a, b,
+                    static_cast<double *>(workspace), out, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "scalar product");
+  return YTN_OK;
 }
 
 ytn_status ytn_ctx_set_gemm_sms(ytn_ctx *ctx, int nsms) {

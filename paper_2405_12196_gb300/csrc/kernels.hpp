@@ -15,6 +15,11 @@ cudaError_t launch_copy(const CopyJob *jobs, const CopyItem *items, int64_t nite
 cudaError_t launch_trace(const TraceOut *outs, int64_t nout, const TraceContrib *contribs,
                          const double *src, double *dst, cudaStream_t stream);
 
+// Scalar product <A, B> over the planned common elements (FP64, deterministic):
+// one partial per chunk into `partials`, then their fixed-order sum into out[0].
+cudaError_t launch_vdot(const VdotChunk *chunks, int64_t nchunks, const VdotPiece *pieces, const double *a,
+                        const double *b, double *partials, double *out, cudaStream_t stream);
+
 // Grouped FP64 GEMM (DMMA) over 64x64 tiles: C_q = A_q B_q.
 cudaError_t launch_gemm_fp64(const SectorDev *sectors, const GemmTile *tiles, int64_t ntiles,
                              const double *wa, const double *wb, double *wc, cudaStream_t stream);

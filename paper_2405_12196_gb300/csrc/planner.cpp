@@ -743,6 +743,7 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
     for (int l : freeB) cd.push_back(B.dim(sr.b_blk, l));
     int64_t acc = 1;
     for (int i = C.rank - 1; i >= 0; i--) { ds[i] = acc; acc *= cd[i]; }
+    const int64_t nblk = acc;
     // source: inside I the legs are row-major, times ldc = N; inside J row-major
     std::vector<int64_t> ss(C.rank);
     acc = 1;
@@ -752,7 +753,7 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
     for (int i = 0; i < C.rank; i++) dims.push_back({cd[i], ss[i], ds[i]});
     s = add_copy(p, dims, h.c_off + sr.roff * h.N + sr.coff, off_of_id[id], err);
     if (s != YTN_OK) return s;
-    p->moved += acc;
+    p->moved += nblk;
   }
   size_t j3 = p->jobs.size();
   p->items_c_begin = (int64_t)p->items.size();
@@ -1223,6 +1224,86 @@ ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1_
   }
   p->kind = Kind::Trace;
   p->a_size = A.size;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Scalar product
+// ---------------------------------------------------------------------------
+
+static bool fusion_equal(const Fusion &a, const Fusion &b) {
+  if (a.nlegs != b.nlegs || a.nentries != b.nentries) return false;
+  for (int j = 0; j < a.nlegs; j++)
+    if (a.sig[j] != b.sig[j]) return false;
+  return a.nu == b.nu && a.t == b.t && a.D == b.D;
+}
+
+// <A, B>: the sum over the elements of the blocks present in both tensors of A's
+// element times B's. The tensors must lie on the same legs: same symmetry, rank
+// and signatures, one dimension per charge on each leg, identical fusion records.
+ytn_status plan_vdot(ytn_plan_t *p, const Tensor &A, const Tensor &B, std::string &err) {
+  if (A.nsym != B.nsym || std::memcmp(A.mod, B.mod, sizeof(A.mod)) != 0 || A.rank != B.rank) {
+    err = "tensors of different symmetry or rank";
+    return YTN_E_INVALID;
+  }
+  for (int i = 0; i < A.rank; i++)
+    if (A.sig[i] != B.sig[i]) { err = "tensors with different leg signatures"; return YTN_E_SIGNATURE; }
+  for (int i = 0; i < A.rank; i++) {
+    auto da = leg_dims(A, i), db = leg_dims(B, i);
+    for (auto &kv : da) {
+      auto it = db.find(kv.first);
+      if (it != db.end() && it->second != kv.second) {
+        err = "leg " + std::to_string(i) + " charge " + keystr(kv.first) + ": dimension " +
+              std::to_string(kv.second) + " vs " + std::to_string(it->second);
+        return YTN_E_DIM_MISMATCH;
+      }
+    }
+    const bool fa = (bool)A.fus[i], fb = (bool)B.fus[i];
+    if (fa != fb || (fa && !fusion_equal(*A.fus[i], *B.fus[i]))) {
+      err = "leg " + std::to_string(i) + ": fusion records differ";
+      return YTN_E_FUSION_MISMATCH;
+    }
+  }
+  // common blocks: both block lists are in canonical (ascending) order
+  const size_t w = (size_t)A.rank * A.nsym;
+  auto key_of = [w](const Tensor &T, int64_t b) { return Key(T.t.begin() + b * w, T.t.begin() + (b + 1) * w); };
+  p->vd_pieces.clear();
+  p->vd_chunks.clear();
+  int64_t common = 0;
+  for (int64_t i = 0, j = 0; i < A.nblocks && j < B.nblocks;) {
+    const Key ka = key_of(A, i), kb = key_of(B, j);
+    if (ka < kb) { i++; continue; }
+    if (kb < ka) { j++; continue; }
+    const int64_t n = A.elems(i);
+    for (int64_t e = 0; e < n; e += kVdotPiece)
+      p->vd_pieces.push_back({A.off[i] + e, B.off[j] + e, (int32_t)std::min<int64_t>(kVdotPiece, n - e), 0});
+    common += n;
+    i++;
+    j++;
+  }
+  // CTA shares: consecutive pieces, at most kVdotChunk elements and 64 pieces
+  for (size_t k = 0; k < p->vd_pieces.size();) {
+    size_t m = k;
+    int64_t tot = 0;
+    while (m < p->vd_pieces.size() && m - k < 64 && tot + p->vd_pieces[m].len <= kVdotChunk) tot += p->vd_pieces[m++].len;
+    p->vd_chunks.push_back({(int32_t)k, (int32_t)(m - k)});
+    k = m;
+  }
+  if (p->vd_chunks.size() > (size_t)INT32_MAX) { err = "scalar product too large"; return YTN_E_UNSUPPORTED; }
+  // output: a rank-0 tensor with one element
+  Tensor &C = p->out;
+  C = Tensor();
+  C.nsym = A.nsym;
+  for (int c = 0; c < A.nsym; c++) C.mod[c] = A.mod[c];
+  C.rank = 0;
+  C.nblocks = 1;
+  C.off.push_back(0);
+  C.size = 1;
+  p->flops = 2.0 * (double)common;
+  p->moved = common;
+  p->kind = Kind::Vdot;
+  p->a_size = A.size;
+  p->b_size = B.size;
   return YTN_OK;
 }
 

@@ -100,6 +100,20 @@ struct TraceContrib {
   int32_t dstr[kMaxCopyDims];   // sum of the two strides of each pair
 };
 
+// Scalar product: a contiguous run of elements common to A and B (part of one
+// block, at most kVdotPiece elements), and a CTA's share: pieces
+// [first, first + count) of the piece table.
+constexpr int kVdotPiece = 4096;
+constexpr int kVdotChunk = 8192;   // elements per CTA
+struct VdotPiece {
+  int64_t a_off, b_off;
+  int32_t len, pad;
+};
+static_assert(sizeof(VdotPiece) == 24, "VdotPiece layout");
+struct VdotChunk {
+  int32_t first, count;
+};
+
 // ----------------------------------------------------------------------------
 // Split-precision path tables
 // ----------------------------------------------------------------------------
@@ -180,7 +194,7 @@ struct HostSector {
   int64_t a_off = 0, b_off = 0, c_off = 0;
 };
 
-enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4 };
+enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5 };
 
 struct Plan;
 
@@ -243,6 +257,8 @@ struct ytn_plan_s {
   // trace
   std::vector<ytn::TraceOut> tr_out;
   std::vector<ytn::TraceContrib> tr_contrib;
+  std::vector<ytn::VdotPiece> vd_pieces;
+  std::vector<ytn::VdotChunk> vd_chunks;
 
   // device copies of the tables (one allocation)
   void *dev = nullptr;
@@ -253,6 +269,8 @@ struct ytn_plan_s {
   const ytn::GemmTile *d_tiles = nullptr;
   const ytn::TraceOut *d_tr_out = nullptr;
   const ytn::TraceContrib *d_tr_contrib = nullptr;
+  const ytn::VdotPiece *d_vd_pieces = nullptr;
+  const ytn::VdotChunk *d_vd_chunks = nullptr;
 
   // split-precision tables
   std::vector<ytn::SplitOperand> sp_ops;
@@ -280,6 +298,7 @@ ytn_status plan_fuse(ytn_plan_t *p, const Tensor &A, int ngroups, const int *gro
                      const int *order, std::string &err);
 ytn_status plan_unfuse(ytn_plan_t *p, const Tensor &A, int naxes, const int *axes,
                        std::string &err);
+ytn_status plan_vdot(ytn_plan_t *p, const Tensor &A, const Tensor &B, std::string &err);
 ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1,
                       const int *ax2, std::string &err);
 std::string plan_key(const ytn_op *op);

@@ -32,7 +32,7 @@ STATUS = {
 YTN_FP64 = 0
 YTN_SPLIT_BF16 = 1
 YTN_AUTO = 2
-YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE = 1, 2, 3, 4
+YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE, YTN_OP_VDOT = 1, 2, 3, 4, 5
 
 
 class YtnError(RuntimeError):
@@ -75,7 +75,7 @@ class ytn_plan_info(C.Structure):
 
 
 NPHASES = 8
-PHASES = {0: "gather_a", 1: "gather_b", 2: "gemm", 3: "scatter", 4: "split", 5: "move"}
+PHASES = {0: "gather_a", 1: "gather_b", 2: "gemm", 3: "scatter", 4: "split", 5: "move", 6: "reduce"}
 
 
 class ytn_profile(C.Structure):
@@ -107,8 +107,10 @@ SYMBOLS = {
     "ytn_fuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_unfuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ytn_vdot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "ytn_sync": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "ytn_ctx_set_gemm_sms": (C.c_int, [C.c_void_p, C.c_int]),
+    "ytn_selftest_timeout": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ytn_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ytn_profile_read": (C.c_int, [C.c_void_p, C.POINTER(ytn_profile)]),
     "ytn_graph_begin": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -356,8 +358,20 @@ def ytn_trace(plan, a, out, stream=None):
     _check(_lib.ytn_trace(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
 
 
+def ytn_vdot(plan, a, b, out, workspace=None, workspace_bytes=None, stream=None):
+    """out[0] = <A, B> (a VDOT plan); `out` holds one double."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.ytn_vdot(plan.handle, _ptr(a), _ptr(b), _ptr(out), _ptr(workspace), int(workspace_bytes),
+                         _stream(stream)))
+
+
 def ytn_sync(ctx, stream=None, timeout_ms=-1):
     _check(_lib.ytn_sync(ctx.handle, _stream(stream), int(timeout_ms)))
+
+
+def ytn_selftest_timeout(ctx, stream=None):
+    _check(_lib.ytn_selftest_timeout(ctx.handle, _stream(stream)))
 
 
 def ytn_ctx_set_gemm_sms(ctx, nsms):

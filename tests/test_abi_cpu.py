@@ -74,6 +74,12 @@ def test_tensordot_structure_matches_oracle(hctx, sym, case):
     ref = O.to_record(O.tensordot(oA, oB, axa, axb))
     same_structure(plan.out, ref)
     assert plan.info["useful_flops"] == O.useful_flops(oA, oB, axa, axb)
+    # moved elements: the A and B blocks with a partner on the contracted legs, and C
+    ka = [tuple(map(tuple, t[list(axa)])) for t in A["t"]]
+    kb = [tuple(map(tuple, t[list(axb)])) for t in B["t"]]
+    cov_a = sum(int(np.prod(d)) for k, d in zip(ka, A["D"]) if k in set(kb))
+    cov_b = sum(int(np.prod(d)) for k, d in zip(kb, B["D"]) if k in set(ka))
+    assert plan.info["moved_elems"] == cov_a + cov_b + ref["data"].size
 
 
 def test_config1_plan_counts(hctx):
@@ -191,3 +197,32 @@ def test_auto_workspace_covers_the_admissible_paths(hctx):
 def test_gemm_sms_needs_a_device_context(hctx):
     with pytest.raises(ytn.YtnError):
         ytn.ytn_ctx_set_gemm_sms(hctx, 8)
+
+
+def test_vdot_planning_matches_the_oracle_rules(hctx):
+    """VDOT plans: common elements counted as the oracle's common blocks; the same
+    errors as the oracle for tensors that do not lie on the same legs."""
+    rng = np.random.default_rng(21)
+    for mods in [(0,), (2,), (0, 0)]:
+        legs = random_legs(rng, mods, 3)
+        A = W.random_tensor(mods, legs, (0,) * len(mods), 1)
+        B = W.random_tensor(mods, legs, (0,) * len(mods), 2)
+        plan = ytn.ytn_plan(hctx, ytn.YTN_OP_VDOT, A, B)
+        oA, oB = O.from_record(A), O.from_record(B)
+        common = sum(oA.blocks[k].size for k in oA.blocks if k in oB.blocks)
+        assert plan.info["moved_elems"] == common
+        assert plan.info["useful_flops"] == 2 * common
+        assert plan.out["size"] == 1
+        assert ytn.ytn_workspace_size(plan) == (0 if common == 0 else 256 * (-(-8 * -(-common // 8192) // 256)))
+    l = W.Leg(1, [(-1,), (1,)], [2, 3])
+    A = W.random_tensor((0,), [l, l.conj()], (0,), 1)
+    bad = {
+        "YTN_E_SIGNATURE": W.random_tensor((0,), [l.conj(), l], (0,), 2),
+        "YTN_E_DIM_MISMATCH": W.random_tensor((0,), [W.Leg(1, [(-1,), (1,)], [2, 4]),
+                                                     W.Leg(-1, [(-1,), (1,)], [2, 4])], (0,), 3),
+        "YTN_E_INVALID": W.random_tensor((2,), [W.Leg(1, [(0,), (1,)], [2, 3])] * 2, (0,), 4),
+    }
+    for name, B in bad.items():
+        with pytest.raises(ytn.YtnError) as ei:
+            ytn.ytn_plan(hctx, ytn.YTN_OP_VDOT, A, B)
+        assert ei.value.name == name

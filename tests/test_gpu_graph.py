@@ -117,3 +117,42 @@ def test_graph_capture_errors(ctx):
     g.close()
     with pytest.raises(ytn.YtnError):
         ytn.ytn_graph_end(ctx, stream)          # not capturing any more
+
+
+def test_ctm_step_chain_as_one_graph(ctx):
+    """The contractions of one U(1)xU(1) CTMRG step (A.A*, fuse, C.T, CT.T, X2.a;
+    the bench's --chain workload) with YTN_AUTO: one graph launch gives the bits of
+    the eager calls, and X2.a matches the oracle within the split tolerance."""
+    import os
+    import sys
+
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    stream = torch.cuda.Stream(device=device())
+    run, plans, out, n, flops = bench.ctm_chain(ytn, ctx, device(), ytn.YTN_AUTO, 1e-10)
+    assert flops > 3e10
+    run(stream)                      # eager: YTN_AUTO decides (and caches) each path
+    run(stream)
+    ytn.ytn_sync(ctx, stream)
+    eager = out[:n].cpu().numpy().copy()
+    ytn.ytn_graph_begin(ctx, stream)
+    run(stream)
+    g = ytn.ytn_graph_end(ctx, stream)
+    out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    g.launch(stream)
+    ytn.ytn_sync(ctx, stream)
+    np.testing.assert_array_equal(out[:n].cpu().numpy(), eager)
+    g.close()
+    # X2.a against the oracle: a = fuse(A.A*), X2 with a's conjugate fusion records
+    cfg = W.config3()
+    A, X2 = cfg["A"], dict(cfg["X2"])
+    oA = O.from_record(A)
+    oa = O.fuse(O.tensordot(oA, O.conj(oA), (4,), (4,)), ((0, 4), (1, 5), (2, 6), (3, 7)))
+    ra = O.to_record(oa)
+    conj = lambda f: dict(f, sig=tuple(-x for x in f["sig"]))   # noqa: E731
+    X2["fus"] = [None, conj(ra["fus"][0]), conj(ra["fus"][1]), None]
+    want = O.to_record(O.tensordot(O.from_record(X2), oa, (1, 2), (0, 1)))["data"]
+    assert rel_frobenius(eager, want) <= 1e-10
