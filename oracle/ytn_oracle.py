@@ -44,7 +44,7 @@ __all__ = [
     "OTensor", "OracleError", "SignatureError", "DimMismatchError", "FusionMismatchError",
     "ChargeError", "InvalidError", "UnsupportedError",
     "from_record", "to_record", "conj", "tensordot", "fuse", "unfuse", "trace",
-    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot",
+    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity",
 ]
 
 
@@ -489,6 +489,50 @@ def trace(A, ax1, ax2):
         val = np.trace(m, axis1=1, axis2=2).reshape(R)
         kc = tuple(key[i] for i in rest)
         out.blocks[kc] = out.blocks[kc] + val if kc in out.blocks else np.array(val, dtype=np.float64)
+    return out
+
+
+# ------------------------------------------------------------------ fermionic swap gate
+
+def charge_parity(q, mods, fermionic=None):
+    """Fermionic parity (0 or 1) of one leg charge: the sum of its fermionic components
+    modulo 2. ``fermionic``: one flag per symmetry component (default: all). A fermionic
+    component must be U(1) (a particle number) or Z_m with m even (Z_2 parity), so
+    that the parity is well defined on its charges."""
+    fm = tuple(bool(x) for x in fermionic) if fermionic is not None else (True,) * len(mods)
+    if len(fm) != len(mods):
+        raise InvalidError("one fermionic flag per symmetry component")
+    p = 0
+    for c, m, f in zip(q, mods, fm):
+        if f:
+            if m % 2:
+                raise InvalidError("a fermionic component must be U(1) or Z_m with m even")
+            p += int(c)
+    return p % 2
+
+
+def swap_gate(A, axes1, axes2, fermionic=None):
+    """Fermionic swap gate between two groups of legs (Sec. IV, use case 3): the lattice
+    is projected onto a plane in a canonical fermionic order and a swap gate acts at
+    every crossing of two lines; it changes the sign of the blocks whose charges have
+    odd parity on both crossing lines.
+
+    A group's parity is the parity of the sum of its legs' charges (the sum of their
+    parities modulo 2; a leg signature does not change a parity). A block is multiplied
+    by -1 when both groups are odd, else kept; the structure and fusion records are
+    unchanged. Groups must be disjoint lists of distinct legs."""
+    axes1, axes2 = tuple(int(a) for a in axes1), tuple(int(b) for b in axes2)
+    allax = axes1 + axes2
+    if len(set(allax)) != len(allax):
+        raise InvalidError("swap-gate groups must be disjoint lists of distinct legs")
+    if any(a < 0 or a >= A.rank for a in allax):
+        raise InvalidError("axis out of range")
+    charge_parity((0,) * A.nsym, A.mods, fermionic)   # validates the flags, also with no blocks
+    out = OTensor(A.mods, A.sig, A.n, fus=list(A.fus))
+    for key in A.keys():
+        p1 = sum(charge_parity(key[a], A.mods, fermionic) for a in axes1) % 2
+        p2 = sum(charge_parity(key[b], A.mods, fermionic) for b in axes2) % 2
+        out.blocks[key] = -A.blocks[key] if (p1 and p2) else A.blocks[key].copy()
     return out
 
 

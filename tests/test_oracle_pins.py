@@ -434,3 +434,99 @@ def test_vdot_rejects_incomparable_tensors():
         O.vdot(A, O.from_record(W.random_tensor((0,), [l2, l2.conj()], (0,), 3)))
     with pytest.raises(O.InvalidError):
         O.vdot(A, O.from_record(W.random_tensor((2,), [W.Leg(1, [(0,), (1,)], [2, 3])] * 2, (0,), 4)))
+
+
+# ---------------------------------------------------------------- fermionic swap gates
+
+FERMI_SYMS = {"U1": (0,), "Z2": (2,), "U1xU1": (0, 0)}
+
+
+def _dense_parities(legs):
+    """Per leg, the parity of every dense index: the parity of its sector's charge
+    (sum of the components, all fermionic), sectors in ascending charge order."""
+    out = []
+    for lg in legs:
+        lm = leg_map(lg)
+        out.append(np.concatenate([np.full(lm[q], sum(q) % 2) for q in sorted(lm)]))
+    return out
+
+
+def _dense_sign(par, g1, g2):
+    """(-1)^(P1 P2) on the dense index grid, P_g = sum of the group's index parities."""
+    grids = np.meshgrid(*par, indexing="ij")
+    p1 = sum(grids[a] for a in g1) % 2 if g1 else 0
+    p2 = sum(grids[b] for b in g2) % 2 if g2 else 0
+    return np.where((p1 * p2) % 2 == 1, -1.0, 1.0)
+
+
+@pytest.mark.parametrize("sym", list(FERMI_SYMS))
+@pytest.mark.parametrize("case", range(8))
+def test_swap_gate_equals_dense_parity_sign(sym, case):
+    """Sec. IV: a swap gate changes the sign where both crossing lines are odd. On the
+    dense embedding this is the element-wise product with (-1)^(P1 P2), P the parity
+    of a group's indices -- checked element by element."""
+    mods = FERMI_SYMS[sym]
+    rng = np.random.default_rng(8100 + 13 * case + len(sym))
+    rank = int(rng.integers(2, 5))
+    legs = random_legs(rng, mods, rank)
+    n = tuple(int(rng.integers(0, m)) if m else int(rng.integers(-1, 2)) for m in mods)
+    A = O.from_record(W.random_tensor(mods, legs, n, case + 1))
+    perm = [int(x) for x in rng.permutation(rank)]
+    k1 = int(rng.integers(1, rank))
+    k2 = int(rng.integers(1, rank - k1 + 1))
+    g1, g2 = perm[:k1], perm[k1:k1 + k2]
+    lm = [leg_map(lg) for lg in legs]
+    got = O.to_dense(O.swap_gate(A, g1, g2), lm)
+    want = O.to_dense(A, lm) * _dense_sign(_dense_parities(legs), g1, g2)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_swap_gate_is_an_involution_and_bilinear():
+    """Applying a swap gate twice is the identity; a gate against a union of two groups
+    is the product of the two gates (the parity of a union is the sum of parities)."""
+    rng = np.random.default_rng(17)
+    legs = random_legs(rng, (0, 0), 4)
+    A = O.from_record(W.random_tensor((0, 0), legs, (1, 0), 3))
+    S = O.swap_gate(O.swap_gate(A, (0,), (2, 3)), (0,), (2, 3))
+    assert all(np.array_equal(S.blocks[k], A.blocks[k]) for k in A.blocks)
+    one = O.swap_gate(A, (0, 1), (2, 3))
+    two = O.swap_gate(O.swap_gate(A, (0, 1), (2,)), (0, 1), (3,))
+    assert all(np.array_equal(one.blocks[k], two.blocks[k]) for k in A.blocks)
+
+
+def test_swap_gate_fermionic_swap_of_two_modes():
+    """Closed form: the swap gate applied to the permutation P[o1, o2, i1, i2] =
+    delta(o1, i2) delta(o2, i1) of two spinless fermionic modes (Z2, |0>, |1>) gives
+    the fermionic SWAP, diag(1, 1, 1, -1) times the swap of the occupations."""
+    l = W.Leg(1, [(0,), (1,)], [1, 1])
+    blocks = {}
+    for a in (0, 1):
+        for b in (0, 1):
+            blocks[((a,), (b,), (b,), (a,))] = np.ones((1, 1, 1, 1))
+    P = O.OTensor((2,), (1, 1, -1, -1), (0,), blocks).validate()
+    F = O.swap_gate(P, (2,), (3,))
+    lm = [leg_map(l)] * 4
+    mat = O.to_dense(F, lm).reshape(4, 4)
+    want = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, -1]], dtype=np.float64)
+    np.testing.assert_array_equal(mat, want)
+
+
+def test_swap_gate_special_cases():
+    """Bosonic components (no fermionic flag) and even groups leave every block as it
+    is; a Z3 component cannot carry a parity."""
+    rng = np.random.default_rng(19)
+    legs = random_legs(rng, (2,), 3)
+    A = O.from_record(W.random_tensor((2,), legs, (0,), 5))
+    B = O.swap_gate(A, (0,), (1,), fermionic=(False,))
+    assert all(np.array_equal(B.blocks[k], A.blocks[k]) for k in A.blocks)
+    ev = W.Leg(1, [(0,), (2,)], [2, 3])
+    od = W.Leg(1, [(-1,), (1,)], [1, 2])
+    T = O.from_record(W.random_tensor((0,), [ev, od, od.conj()], (0,), 6))
+    S = O.swap_gate(T, (0,), (1, 2))
+    assert all(np.array_equal(S.blocks[k], T.blocks[k]) for k in T.blocks)
+    U = O.swap_gate(T, (1,), (2,))
+    assert any(not np.array_equal(U.blocks[k], T.blocks[k]) for k in T.blocks)
+    with pytest.raises(O.InvalidError):
+        O.swap_gate(O.from_record(W.random_tensor((3,), random_legs(rng, (3,), 2), (0,), 7)), (0,), (1,))
+    with pytest.raises(O.InvalidError):
+        O.swap_gate(A, (0, 1), (1,))
