@@ -279,16 +279,60 @@ def _check_compatible(A, a, B, b):
         raise FusionMismatchError("fusion records of contracted legs differ")
 
 
+def _mismatched(A, a, B, b):
+    fa, fb = A.fus[a], B.fus[b]
+    return fa is not None and fb is not None and fa.key() != fb.conj().key()
+
+
+def _check_resolvable(fa, fb):
+    """Two fused legs with different histories can be contracted when they were fused
+    from the same constituent legs (same count, opposite signatures) and agree on the
+    dimensions of every constituent charge tuple both records list."""
+    if len(fa.sig) != len(fb.sig) or any(x != -y for x, y in zip(fa.sig, fb.sig)):
+        raise FusionMismatchError("contracted fused legs come from different constituent legs")
+    da = {ch: d for lst in fa.entries.values() for ch, d in lst}
+    db = {ch: d for lst in fb.entries.values() for ch, d in lst}
+    for ch in set(da) & set(db):
+        if da[ch] != db[ch]:
+            raise DimMismatchError(f"constituent charges {ch}: dimensions {da[ch]} vs {db[ch]}")
+
+
+def _expand_axes(T, axes, unf):
+    """Positions of legs after unfusing the legs in ``unf``: each unfused leg becomes
+    its constituents, in order, at its place."""
+    pos, p = [], 0
+    for a in range(T.rank):
+        n = len(T.fus[a].sig) if a in unf else 1
+        pos.append(list(range(p, p + n)))
+        p += n
+    return [q for a in axes for q in pos[a]]
+
+
 def tensordot(A, B, axa, axb):
     """C = sum over the contracted indices of A * B (Sec. II.B, contraction equation).
 
     Every pair (alpha, beta) of stored blocks whose charges agree on all contracted legs
     contributes tensordot(A_alpha, B_beta) to the C block keyed by A's free charges
     followed by B's free charges. Blocks of C exist when at least one pair contributed
-    (lazy storage, Sec. II.A)."""
+    (lazy storage, Sec. II.A).
+
+    Contracted fused legs with different fusion histories (Sec. II.B footnote: a charge
+    of the history missing on one side but present on the other) are resolved: a
+    missing constituent charge tuple counts as a zero sub-block, so the contraction
+    over the fused index is the contraction over its constituent legs. The oracle
+    unfuses those legs on both sides and contracts over the constituents."""
     if A.mods != B.mods:
         raise InvalidError("tensors have different symmetries")
     axa, axb = _check_pairs(A.rank, B.rank, axa, axb)
+    mism = [k for k, (a, b) in enumerate(zip(axa, axb)) if _mismatched(A, a, B, b)]
+    if mism:
+        for k in mism:
+            if A.sig[axa[k]] != -B.sig[axb[k]]:
+                raise SignatureError(f"leg {axa[k]} of A and leg {axb[k]} of B have equal signatures")
+            _check_resolvable(A.fus[axa[k]], B.fus[axb[k]])
+        ua, ub = {axa[k] for k in mism}, {axb[k] for k in mism}
+        A2, B2 = unfuse(A, sorted(ua)), unfuse(B, sorted(ub))
+        return tensordot(A2, B2, _expand_axes(A, axa, ua), _expand_axes(B, axb, ub))
     for a, b in zip(axa, axb):
         _check_compatible(A, a, B, b)
     freeA = [i for i in range(A.rank) if i not in axa]
