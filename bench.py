@@ -342,7 +342,9 @@ def run_ours(args):
     head = measure(prec, args.steps, args.warmup, clocks=True)
     value = head["value"]
     ph = phases(head)
-    moved_bytes = 16.0 * plan.info["moved_elems"]
+    # the split GEMM writes device-resident C's blocks itself: then only A and B move
+    moved_elems = plan.info["moved_elems"] - (0 if "scatter" in ph else plan.info["out_size"])
+    moved_bytes = 16.0 * moved_elems
     mover_ms = sum(ph[k]["ms_per_call"] for k in ("gather_a", "gather_b", "scatter") if k in ph)
     out_head = dc.clone() if prec != ytn.YTN_FP64 else None
 
@@ -692,6 +694,46 @@ def run_reduce(args):
     return 0
 
 
+def run_swap(args):
+    """Fermionic swap gate on a D=20 environment tensor (3.36e8 elements, lines 0, 1
+    against 2, 3), out of place: 16 bytes moved per element, HBM-bound."""
+    import torch
+
+    from paper_2405_12196_gb300 import ytn
+    dev = torch.device("cuda:0")
+    ctx = ytn.ytn_ctx_create(0)
+    A = W.config5(seed=5001)["A"]
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_SWAP_GATE, A, groups=((0, 1), (2, 3)))
+    da = torch.from_numpy(A["data"]).to(dev)
+    out = torch.empty_like(da)
+    stream = torch.cuda.Stream(device=dev)
+    for _ in range(args.warmup):
+        ytn.ytn_swap_gate(plan, da, out, stream=stream)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ytn.ytn_swap_gate(plan, da, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    nbytes = 16.0 * plan.info["moved_elems"]
+    peaks, src = load_peaks()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "fermionic swap gate on a block-sparse tensor: GB/s", "value": gbs, "unit": "GB/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "data": "synthetic", "dtype": "f64",
+        "config": {"workload": WORKLOAD_DESC["cfg5"] + "; swap gate of legs (0, 1) against (2, 3) on X2",
+                   "elements": plan.info["moved_elems"], "blocks": int(A["t"].shape[0]),
+                   "l2": "inputs larger than L2 (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -709,6 +751,7 @@ def main():
     ap.add_argument("--serving", action="store_true", help="run the continuous-batching serving benchmark")
     ap.add_argument("--chain", action="store_true", help="time the CTMRG-step chain eager and as one CUDA graph")
     ap.add_argument("--reduce", action="store_true", help="time the FP64 scalar product of two D=20 tensors")
+    ap.add_argument("--swap", action="store_true", help="time the fermionic swap gate on a D=20 tensor")
     ap.add_argument("--serve-runs", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-slots", type=int, default=8)
@@ -724,6 +767,8 @@ def main():
         return run_chain(args)
     if args.reduce:
         return run_reduce(args)
+    if args.swap:
+        return run_swap(args)
     return run_ours(args)
 
 

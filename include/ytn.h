@@ -119,12 +119,15 @@ typedef struct {
   const ytn_fusion *fus[YTN_MAX_RANK]; /* per leg; NULL for a plain leg       */
 } ytn_struct;
 
+#define YTN_FERMIONIC_EXPLICIT 0x80000000u
+
 typedef enum {
   YTN_OP_TENSORDOT = 1,  /* C = sum_x A B over pairs (axa[k], axb[k]), Sec. II.B */
   YTN_OP_FUSE = 2,       /* fuse groups of legs, Sec. II.B                        */
   YTN_OP_UNFUSE = 3,     /* undo the fusion of legs axa[0..naxes), Sec. II.B      */
   YTN_OP_TRACE = 4,      /* sum the diagonals of leg pairs (axa[k], axb[k]) of a  */
-  YTN_OP_VDOT = 5        /* scalar product <a, b> of two tensors on the same legs */
+  YTN_OP_VDOT = 5,       /* scalar product <a, b> of two tensors on the same legs */
+  YTN_OP_SWAP_GATE = 6   /* fermionic swap gate between two groups of legs, Sec. IV */
 } ytn_op_kind;
 
 /* A planned operation.
@@ -141,7 +144,17 @@ typedef enum {
  *             sum that the block structure implies).
  *  VDOT:      a, b on the same legs: same symmetry, rank and signatures, one
  *             dimension per charge on each leg, identical fusion records. The
- *             output is one element (a rank-0 tensor). */
+ *             output is one element (a rank-0 tensor).
+ *  SWAP_GATE: a, ngroups = 2 groups of legs (group_size, order as for FUSE;
+ *             disjoint, each leg at most once). A block changes sign when the
+ *             parities of both groups' charges are odd (Sec. IV: the swap gate
+ *             at a crossing of two lines in the fermionic order). The parity
+ *             of a charge is the sum of its fermionic components modulo 2;
+ *             `fermionic` selects them: 0 = every component; otherwise
+ *             YTN_FERMIONIC_EXPLICIT | (bit c for component c), so that an
+ *             explicit empty set (all components bosonic) is expressible. Each
+ *             fermionic component must be U(1) or Z_m with m even. Output
+ *             structure = a's. */
 typedef struct {
   ytn_op_kind kind;
   const ytn_struct *a;
@@ -152,6 +165,8 @@ typedef struct {
   int32_t ngroups;
   int32_t group_size[YTN_MAX_RANK];
   int32_t order[YTN_MAX_RANK];
+  uint32_t fermionic;         /* SWAP_GATE only: 0 = all components fermionic, else
+                                 YTN_FERMIONIC_EXPLICIT | component bits      */
 } ytn_op;
 
 /* Sizes of a plan. */
@@ -206,7 +221,9 @@ ytn_status ytn_workspace_size(const ytn_plan_t *plan, ytn_precision prec, double
 
 /* C = tensordot(A, B) (Sec. II.B contraction equation): gather the blocks of A
  * and B into one matrix per charge sector, multiply the sectors in one grouped
- * launch, scatter the products into the blocks of C. a, b, c: buffers of
+ * launch, scatter the products into the blocks of C (on the split path with
+ * C in device memory the GEMM's epilogue writes C's blocks itself and there is
+ * no separate scatter; the workspace size does not depend on it). a, b, c: buffers of
  * sizes a->size, b->size and ytn_plan_output(plan)->size, each either device
  * memory of the context's device or page-locked host memory (cudaHostAlloc or
  * cudaHostRegister, mapped into the device's address space). Host-resident
@@ -269,6 +286,14 @@ ytn_status ytn_trace(ytn_plan_t *plan, const double *a, double *out, ytn_stream 
  * YTN_E_DIM_MISMATCH, YTN_E_FUSION_MISMATCH, YTN_E_INVALID) come from ytn_plan. */
 ytn_status ytn_vdot(ytn_plan_t *plan, const double *a, const double *b, double *out, void *workspace,
                     size_t workspace_bytes, ytn_stream stream);
+
+/* out = swap_gate(a) (a SWAP_GATE plan): every block of a copied to the same
+ * place in out, negated when both groups of legs have odd parity (Sec. IV).
+ * out may be a itself (in place). a, out: buffers of the plan's size, device
+ * memory or page-locked host memory as for ytn_tensordot. Bit-exact.
+ * Asynchronous on stream. Errors: YTN_E_INVALID (wrong plan kind, null
+ * buffer), YTN_E_CUDA. */
+ytn_status ytn_swap_gate(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
 
 /* Number of CTAs (one per SM) of the persistent split-precision GEMM of this
  * context; 0 (the default) uses every SM. Leaving some SMs free lets the data

@@ -30,11 +30,18 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// Negation by the sign bit (an integer operation: this GPU's FP64 pipe is far
+// slower than its memory system); exact, and it keeps NaN payloads.
+__device__ __forceinline__ double flip(double x, unsigned long long mask) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)mask);
+}
+
 // The parameters of one piece, in registers: the last ND of its dim slots.
 template <int ND>
 struct Piece {
   int64_t g_off, d_off;
-  int p;   // the piece's start in the staging buffer
+  int p;                  // the piece's start in the staging buffer
+  unsigned long long neg; // sign-bit mask: set for a negated piece (fermionic swap gate)
   int ext[ND], gstr[ND], lstr[ND], shf[ND];
   uint32_t mag[ND];
 
@@ -42,6 +49,7 @@ struct Piece {
     g_off = J.g_off;
     d_off = J.d_off;
     p = J.p;
+    neg = J.negate ? 0x8000000000000000ull : 0ull;
 #pragma unroll
     for (int i = 0; i < ND; i++) {
       const int k = kMaxCopyDims - ND + i;
@@ -123,11 +131,11 @@ __device__ __forceinline__ void stage_item(const CopyJob *Js, int nj, int total,
       int lo;
       P.offsets((uint32_t)l, go, lo);
       const int at = P.p + lo;
-      if ((unsigned)at < (unsigned)total) dst[P.g_off + go] = stage[at];
+      if ((unsigned)at < (unsigned)total) dst[P.g_off + go] = flip(stage[at], P.neg);
     });
   } else {
     for_warp_range<ND>(Js, nj, w0, w1, [&](const Piece<ND> &P, int l, int e) {
-      dst[P.d_off + l] = stage[e];
+      dst[P.d_off + l] = flip(stage[e], P.neg);
     });
   }
 }

@@ -111,7 +111,9 @@ ytn_status load_struct(const ytn_struct *s, Tensor &T, std::string &err) {
   for (int i = 0; i < T.rank; i++) {
     const ytn_fusion *f = s->fus[i];
     if (!f) continue;
-    if (f->nlegs < 2 || f->nlegs > YTN_MAX_RANK || f->nentries < 1 || !f->nu || !f->t || !f->D) {
+    // a record with no rows (the fusion of a tensor without blocks) may have null arrays
+    if (f->nlegs < 2 || f->nlegs > YTN_MAX_RANK || f->nentries < 0 ||
+        (f->nentries > 0 && (!f->nu || !f->t || !f->D))) {
       err = "malformed fusion record";
       return YTN_E_INVALID;
     }
@@ -122,9 +124,11 @@ ytn_status load_struct(const ytn_struct *s, Tensor &T, std::string &err) {
       F->sig[j] = f->sig[j];
     }
     F->nentries = f->nentries;
-    F->nu.assign(f->nu, f->nu + f->nentries * T.nsym);
-    F->t.assign(f->t, f->t + f->nentries * f->nlegs * T.nsym);
-    F->D.assign(f->D, f->D + f->nentries * f->nlegs);
+    if (f->nentries > 0) {
+      F->nu.assign(f->nu, f->nu + f->nentries * T.nsym);
+      F->t.assign(f->t, f->t + f->nentries * f->nlegs * T.nsym);
+      F->D.assign(f->D, f->D + f->nentries * f->nlegs);
+    }
     // entries sorted by (nu, constituent charges); each row consistent with F2
     std::map<Key, int64_t> dnu;
     for (int64_t e = 0; e < F->nentries; e++) {
@@ -236,6 +240,7 @@ static ytn_status check_pair(const Tensor &A, int a, const Tensor &B, int b, std
 
 // Row-major element strides of block b.
 static std::vector<int64_t> block_strides(const Tensor &T, int64_t b) {
+  if (!T.bstr.empty()) return std::vector<int64_t>(T.bstr.begin() + b * T.rank, T.bstr.begin() + (b + 1) * T.rank);
   std::vector<int64_t> st(T.rank);
   int64_t acc = 1;
   for (int i = T.rank - 1; i >= 0; i--) {
@@ -297,7 +302,7 @@ static bool side_dense(const std::vector<Dim> &dims, bool src) {
 // One staged job: `dims` (ext, local stride, global stride) of a piece whose
 // dense side starts at d_off and strided side at g_off.
 static ytn_status push_piece(ytn_plan_t *p, std::vector<Dim> dims, int mode, int64_t g_off, int64_t d_off,
-                             std::string &err) {
+                             std::string &err, bool negate = false) {
   // enumeration order: strided (global) side outer -> inner
   std::stable_sort(dims.begin(), dims.end(), [](const Dim &a, const Dim &b) { return a.dst > b.dst; });
   std::vector<Dim> m = merge_dims(dims);
@@ -312,6 +317,7 @@ static ytn_status push_piece(ytn_plan_t *p, std::vector<Dim> dims, int mode, int
   J.d_off = d_off;
   J.nd = (int32_t)m.size();
   J.mode = mode;
+  J.negate = negate ? 1 : 0;
   int64_t size = 1;
   // dims right-aligned in the kMaxCopyDims slots; the outer slots are unit dims
   const int o = kMaxCopyDims - J.nd;
@@ -340,7 +346,7 @@ static ytn_status push_piece(ytn_plan_t *p, std::vector<Dim> dims, int mode, int
 // dense range (the whole block on the tensor side); it is cut into contiguous
 // pieces by fixing its outer indices and splitting the next one.
 static ytn_status add_copy(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t src_off, int64_t dst_off,
-                           std::string &err) {
+                           std::string &err, bool negate = false) {
   std::vector<Dim> v;
   for (auto &d : dims)
     if (d.ext != 1) v.push_back(d);
@@ -359,8 +365,42 @@ static ytn_status add_copy(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t 
     d0 = dst_off;
     g0 = src_off;
   } else {
-    err = "copy job without a dense side";
-    return YTN_E_UNSUPPORTED;
+    // neither side is one contiguous range (a strided view of a block): on the
+    // side with the longer contiguous innermost run, fix the outer indices and
+    // copy each run (a single element when neither side has one)
+    auto suffix = [&](bool src, std::vector<Dim> &srt, int64_t &run) {
+      srt = v;
+      std::sort(srt.begin(), srt.end(),
+                [src](const Dim &a, const Dim &b) { return src ? a.sst > b.sst : a.dst > b.dst; });
+      size_t k = srt.size();
+      run = 1;
+      while (k > 0 && (src ? srt[k - 1].sst : srt[k - 1].dst) == run) {
+        run *= srt[k - 1].ext;
+        k--;
+      }
+      return k;
+    };
+    std::vector<Dim> ss, sd;
+    int64_t rs, rd;
+    const size_t ks_ = suffix(true, ss, rs), kd_ = suffix(false, sd, rd);
+    const bool use_src = rs >= rd;
+    const std::vector<Dim> &srt = use_src ? ss : sd;
+    const size_t k = use_src ? ks_ : kd_;
+    std::vector<Dim> inner(srt.begin() + k, srt.end());
+    std::vector<int64_t> idx(k, 0);
+    for (;;) {
+      int64_t so = src_off, dof = dst_off;
+      for (size_t i = 0; i < k; i++) {
+        so += idx[i] * srt[i].sst;
+        dof += idx[i] * srt[i].dst;
+      }
+      ytn_status s = add_copy(p, inner, so, dof, err, negate);
+      if (s != YTN_OK) return s;
+      size_t i = k;
+      while (i > 0 && ++idx[i - 1] == srt[i - 1].ext) idx[--i] = 0;
+      if (i == 0) break;
+    }
+    return YTN_OK;
   }
   // dense-side order, outer -> inner
   std::sort(loc.begin(), loc.end(), [](const Dim &a, const Dim &b) { return a.sst > b.sst; });
@@ -372,7 +412,7 @@ static ytn_status add_copy(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t 
     inner *= loc[k - 1].ext;
     k--;
   }
-  if (k == 0) return push_piece(p, loc, mode, g0, d0, err);
+  if (k == 0) return push_piece(p, loc, mode, g0, d0, err, negate);
   // dims [0, k-1) are fixed per piece, dim k-1 is split into runs of `c`
   const int ks = k - 1;
   const int64_t c = std::max<int64_t>(1, kStageElems / inner);
@@ -386,7 +426,7 @@ static ytn_status add_copy(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t 
     for (int64_t a = 0; a < loc[ks].ext; a += c) {
       std::vector<Dim> piece(loc.begin() + ks, loc.end());
       piece[0].ext = std::min(c, loc[ks].ext - a);
-      ytn_status s = push_piece(p, piece, mode, go + a * loc[ks].dst, dof + a * loc[ks].sst, err);
+      ytn_status s = push_piece(p, piece, mode, go + a * loc[ks].dst, dof + a * loc[ks].sst, err, negate);
       if (s != YTN_OK) return s;
     }
     int i = ks - 1;
@@ -461,6 +501,136 @@ static void finalize_out(Tensor &C, std::vector<OutBlock> &blocks, std::vector<i
 // Tensordot
 // ---------------------------------------------------------------------------
 
+// A view of T with the fused legs `legs` replaced by their constituents (the
+// unfusion of Sec. II.B without moving data): every recorded sub-block of every
+// stored fused block becomes a block of the view, addressed inside the fused
+// block through explicit strides. Blocks are put in canonical order.
+static ytn_status unfuse_view(const Tensor &T, const std::vector<int> &legs, Tensor &V, std::string &err) {
+  std::vector<char> isun(T.rank, 0);
+  int rank = T.rank;
+  for (int l : legs) {
+    isun[l] = 1;
+    rank += T.fus[l]->nlegs - 1;
+  }
+  if (rank > YTN_MAX_RANK) { err = "unfused view exceeds the maximum rank"; return YTN_E_UNSUPPORTED; }
+  const int nsym = T.nsym;
+  V = Tensor();
+  V.nsym = nsym;
+  std::memcpy(V.mod, T.mod, sizeof(V.mod));
+  std::memcpy(V.n, T.n, sizeof(V.n));
+  V.rank = rank;
+  V.size = T.size;
+  for (int l = 0, r = 0; l < T.rank; l++) {
+    if (isun[l]) {
+      for (int j = 0; j < T.fus[l]->nlegs; j++) V.sig[r++] = T.fus[l]->sig[j];
+    } else {
+      V.fus[r] = T.fus[l];
+      V.sig[r++] = T.sig[l];
+    }
+  }
+  // per fused leg and fused charge: the record's rows with their offsets
+  struct Row { int64_t e, off; };
+  std::vector<std::map<Key, std::vector<Row>>> rows(T.rank);
+  for (int l : legs) {
+    const Fusion &F = *T.fus[l];
+    for (int64_t e = 0; e < F.nentries; e++) {
+      Key nu(&F.nu[e * nsym], &F.nu[e * nsym] + nsym);
+      auto &lst = rows[l][nu];
+      int64_t off = 0;
+      if (!lst.empty()) {
+        const Row &pr = lst.back();
+        int64_t sz = 1;
+        for (int j = 0; j < F.nlegs; j++) sz *= F.D[pr.e * F.nlegs + j];
+        off = pr.off + sz;
+      }
+      lst.push_back({e, off});
+    }
+  }
+  struct Sub { Key key; std::vector<int64_t> D, st; int64_t off; };
+  std::vector<Sub> subs;
+  for (int64_t b = 0; b < T.nblocks; b++) {
+    const auto st = block_strides(T, b);
+    std::vector<const std::vector<Row> *> ch(T.rank, nullptr);
+    bool ok = true;
+    for (int l : legs) {
+      const int32_t *q = T.charge(b, l);
+      auto it = rows[l].find(Key(q, q + nsym));
+      if (it == rows[l].end()) { ok = false; break; }   // not in the record: checked at load
+      ch[l] = &it->second;
+    }
+    if (!ok) { err = "fused block without a record row"; return YTN_E_INVALID; }
+    std::vector<size_t> pick(T.rank, 0);
+    for (;;) {
+      Sub sb;
+      sb.off = T.off[b];
+      for (int l = 0; l < T.rank; l++) {
+        if (!isun[l]) {
+          const int32_t *q = T.charge(b, l);
+          sb.key.insert(sb.key.end(), q, q + nsym);
+          sb.D.push_back(T.dim(b, l));
+          sb.st.push_back(st[l]);
+          continue;
+        }
+        const Fusion &F = *T.fus[l];
+        const Row &rw = (*ch[l])[pick[l]];
+        sb.off += rw.off * st[l];
+        int64_t inner = st[l];
+        std::vector<int64_t> cst(F.nlegs);
+        for (int j = F.nlegs - 1; j >= 0; j--) {
+          cst[j] = inner;
+          inner *= F.D[rw.e * F.nlegs + j];
+        }
+        for (int j = 0; j < F.nlegs; j++) {
+          const int32_t *q = &F.t[(rw.e * F.nlegs + j) * nsym];
+          sb.key.insert(sb.key.end(), q, q + nsym);
+          sb.D.push_back(F.D[rw.e * F.nlegs + j]);
+          sb.st.push_back(cst[j]);
+        }
+      }
+      subs.push_back(std::move(sb));
+      int l = T.rank - 1;
+      for (; l >= 0; l--) {
+        if (!isun[l]) continue;
+        if (++pick[l] < ch[l]->size()) break;
+        pick[l] = 0;
+      }
+      if (l < 0) break;
+    }
+  }
+  std::sort(subs.begin(), subs.end(), [](const Sub &x, const Sub &y) { return x.key < y.key; });
+  V.nblocks = (int64_t)subs.size();
+  for (auto &sb : subs) {
+    V.t.insert(V.t.end(), sb.key.begin(), sb.key.end());
+    V.D.insert(V.D.end(), sb.D.begin(), sb.D.end());
+    V.bstr.insert(V.bstr.end(), sb.st.begin(), sb.st.end());
+    V.off.push_back(sb.off);
+  }
+  return YTN_OK;
+}
+
+// Contracted fused legs with different fusion histories (Sec. II.B footnote):
+// resolvable when both come from the same number of constituent legs with
+// opposite signatures and agree on the dimensions of every constituent charge
+// tuple both records list. A tuple missing on one side is a zero sub-block, so
+// the contraction runs over the constituents of unfused views of both tensors.
+static ytn_status check_resolvable(const Fusion &a, const Fusion &b, int nsym, std::string &err) {
+  if (a.nlegs != b.nlegs) { err = "contracted fused legs come from different constituent legs"; return YTN_E_FUSION_MISMATCH; }
+  for (int j = 0; j < a.nlegs; j++)
+    if (a.sig[j] != -b.sig[j]) { err = "contracted fused legs come from different constituent legs"; return YTN_E_FUSION_MISMATCH; }
+  std::map<Key, std::vector<int64_t>> da;
+  const int64_t w = (int64_t)a.nlegs * nsym;
+  for (int64_t e = 0; e < a.nentries; e++)
+    da[Key(&a.t[e * w], &a.t[e * w] + w)] = std::vector<int64_t>(&a.D[e * a.nlegs], &a.D[e * a.nlegs] + a.nlegs);
+  for (int64_t e = 0; e < b.nentries; e++) {
+    auto it = da.find(Key(&b.t[e * w], &b.t[e * w] + w));
+    if (it != da.end() && it->second != std::vector<int64_t>(&b.D[e * b.nlegs], &b.D[e * b.nlegs] + b.nlegs)) {
+      err = "a constituent charge tuple has different dimensions on the contracted fused legs";
+      return YTN_E_DIM_MISMATCH;
+    }
+  }
+  return YTN_OK;
+}
+
 ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int naxes,
                           const int *axa_in, const int *axb_in, std::string &err) {
   if (A.nsym != B.nsym || std::memcmp(A.mod, B.mod, sizeof(A.mod)) != 0) {
@@ -479,6 +649,40 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
       }
   }
   if (A.rank + B.rank - 2 * naxes > YTN_MAX_RANK) { err = "output rank too large"; return YTN_E_UNSUPPORTED; }
+  {
+    std::vector<int> ua, ub;
+    for (int k = 0; k < naxes; k++) {
+      const int a = axa[k], b = axb[k];
+      if (!A.fus[a] || !B.fus[b] || fusion_conj_equal(*A.fus[a], *B.fus[b])) continue;
+      if (A.sig[a] != -B.sig[b]) {
+        err = "paired legs " + std::to_string(a) + "/" + std::to_string(b) + " have equal signatures";
+        return YTN_E_SIGNATURE;
+      }
+      ytn_status st = check_resolvable(*A.fus[a], *B.fus[b], A.nsym, err);
+      if (st != YTN_OK) return st;
+      ua.push_back(a);
+      ub.push_back(b);
+    }
+    if (!ua.empty()) {
+      Tensor VA, VB;
+      ytn_status st = unfuse_view(A, ua, VA, err);
+      if (st == YTN_OK) st = unfuse_view(B, ub, VB, err);
+      if (st != YTN_OK) return st;
+      auto expand = [](const Tensor &T, const std::vector<int> &un, const std::vector<int> &ax) {
+        std::vector<std::vector<int>> pos(T.rank);
+        for (int l = 0, r = 0; l < T.rank; l++) {
+          const int n = std::find(un.begin(), un.end(), l) != un.end() ? T.fus[l]->nlegs : 1;
+          for (int j = 0; j < n; j++) pos[l].push_back(r++);
+        }
+        std::vector<int> out;
+        for (int a : ax) out.insert(out.end(), pos[a].begin(), pos[a].end());
+        return out;
+      };
+      const std::vector<int> xa = expand(A, ua, axa), xb = expand(B, ub, axb);
+      if ((int)xa.size() > YTN_MAX_RANK) { err = "unfused view exceeds the maximum rank"; return YTN_E_UNSUPPORTED; }
+      return plan_tensordot(p, VA, VB, (int)xa.size(), xa.data(), xb.data(), err);
+    }
+  }
   for (int k = 0; k < naxes; k++) {
     ytn_status st = check_pair(A, axa[k], B, axb[k], err);
     if (st != YTN_OK) return st;
@@ -759,6 +963,43 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   p->items_c_begin = (int64_t)p->items.size();
   make_items(p, j2, j3);
   p->items_c_end = (int64_t)p->items.size();
+
+  // Epilogue tables: the split GEMM writes C's blocks directly (see EpiTables).
+  p->ep_sec.clear();
+  p->ep_rows.clear();
+  p->ep_cols.clear();
+  p->ep_blk.clear();
+  {
+    std::vector<std::map<int64_t, int32_t>> rs_of(geo.size()), cs_of(geo.size());
+    for (size_t si = 0; si < geo.size(); si++) {
+      SplitEpi se{};
+      se.row_off = (int64_t)p->ep_rows.size();
+      se.col_off = (int64_t)p->ep_cols.size();
+      se.blk_off = (int64_t)p->ep_blk.size();
+      int32_t seg = 0;
+      for (auto &r : sbs[si]->rows) {
+        rs_of[si][geo[si].row_off.at(r.first)] = seg;
+        for (int64_t i = 0; i < r.second.first; i++) p->ep_rows.push_back({seg, (int32_t)i});
+        seg++;
+      }
+      const int32_t nrs = seg;
+      seg = 0;
+      for (auto &c : sbs[si]->cols) {
+        cs_of[si][geo[si].col_off.at(c.first)] = seg;
+        for (int64_t j = 0; j < c.second.first; j++) p->ep_cols.push_back({seg, (int32_t)j});
+        seg++;
+      }
+      se.ncs = seg;
+      p->ep_blk.resize(p->ep_blk.size() + (size_t)nrs * (size_t)seg, EpiBlock{-1, 0});
+      p->ep_sec.push_back(se);
+    }
+    for (size_t id = 0; id < srcs.size(); id++) {
+      const Src &sr = srcs[id];
+      const SplitEpi &se = p->ep_sec[sr.sector];
+      const int64_t k = se.blk_off + (int64_t)rs_of[sr.sector].at(sr.roff) * se.ncs + cs_of[sr.sector].at(sr.coff);
+      p->ep_blk[k] = {off_of_id[id], sr.nJ};
+    }
+  }
 
   // Grouped-GEMM tiles, largest K first. The tile edge is chosen per sector from
   // its size: 32 when 32 x 32 tiles cover the sector with at most 60% of the
@@ -1308,6 +1549,71 @@ ytn_status plan_vdot(ytn_plan_t *p, const Tensor &A, const Tensor &B, std::strin
 }
 
 // ---------------------------------------------------------------------------
+// Fermionic swap gate
+// ---------------------------------------------------------------------------
+
+// Sec. IV: at a crossing of two lines in the fermionic order, a swap gate
+// changes the sign of the blocks whose charges are odd on both lines. A
+// group's parity is the sum over its legs of the fermionic components of the
+// leg's charge, modulo 2 (a signature does not change a parity). The output
+// has a's structure and layout; each block is one copy, negated or not.
+ytn_status plan_swap_gate(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
+                          uint32_t fermionic, std::string &err) {
+  if (ngroups != 2) { err = "a swap gate takes two groups of legs"; return YTN_E_INVALID; }
+  std::vector<int> seen(A.rank, 0);
+  std::vector<int> g[2];
+  int pos = 0;
+  for (int k = 0; k < 2; k++) {
+    if (group_size[k] < 1 || pos + group_size[k] > A.rank) { err = "bad group sizes"; return YTN_E_INVALID; }
+    for (int i = 0; i < group_size[k]; i++) {
+      const int l = order[pos++];
+      if (l < 0 || l >= A.rank || seen[l]) { err = "swap-gate groups must be disjoint legs in range"; return YTN_E_INVALID; }
+      seen[l] = 1;
+      g[k].push_back(l);
+    }
+  }
+  const uint32_t mask = fermionic == 0 ? ((1u << A.nsym) - 1u) : (fermionic & ~YTN_FERMIONIC_EXPLICIT);
+  if (fermionic != 0 && !(fermionic & YTN_FERMIONIC_EXPLICIT)) {
+    err = "an explicit fermionic set needs YTN_FERMIONIC_EXPLICIT";
+    return YTN_E_INVALID;
+  }
+  if (mask >> A.nsym) { err = "fermionic flag of a component the symmetry does not have"; return YTN_E_INVALID; }
+  for (int c = 0; c < A.nsym; c++)
+    if (((mask >> c) & 1u) && (A.mod[c] % 2) != 0) {
+      err = "a fermionic component must be U(1) or Z_m with m even";
+      return YTN_E_INVALID;
+    }
+  auto parity = [&](int64_t b, const std::vector<int> &legs) {
+    int64_t s = 0;
+    for (int l : legs) {
+      const int32_t *q = A.charge(b, l);
+      for (int c = 0; c < A.nsym; c++)
+        if ((mask >> c) & 1u) s += q[c];
+    }
+    return (int)(((s % 2) + 2) % 2);
+  };
+  p->out = A;
+  p->jobs.clear();
+  p->items.clear();
+  p->moved = 0;
+  for (int64_t b = 0; b < A.nblocks; b++) {
+    const int64_t n = A.elems(b);
+    const bool neg = parity(b, g[0]) == 1 && parity(b, g[1]) == 1;
+    ytn_status s = add_copy(p, {{n, 1, 1}}, A.off[b], A.off[b], err, neg);
+    if (s != YTN_OK) return s;
+    p->moved += n;
+  }
+  p->items_a_begin = 0;
+  make_items(p, 0, p->jobs.size());
+  p->items_a_end = (int64_t)p->items.size();
+  p->zero_out = false;
+  p->flops = 0.0;
+  p->kind = Kind::Swap;
+  p->a_size = A.size;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Cache key and output view
 // ---------------------------------------------------------------------------
 
@@ -1350,6 +1656,7 @@ std::string plan_key(const ytn_op *op) {
   put(s, &op->ngroups, sizeof(op->ngroups));
   put(s, op->group_size, sizeof(op->group_size));
   put(s, op->order, sizeof(op->order));
+  if (op->kind == YTN_OP_SWAP_GATE) put(s, &op->fermionic, sizeof(op->fermionic));
   key_struct(s, op->a);
   key_struct(s, op->b);
   return s;

@@ -32,7 +32,8 @@ STATUS = {
 YTN_FP64 = 0
 YTN_SPLIT_BF16 = 1
 YTN_AUTO = 2
-YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE, YTN_OP_VDOT = 1, 2, 3, 4, 5
+YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE, YTN_OP_VDOT, YTN_OP_SWAP_GATE = 1, 2, 3, 4, 5, 6
+YTN_FERMIONIC_EXPLICIT = 1 << 31
 
 
 class YtnError(RuntimeError):
@@ -64,7 +65,7 @@ class ytn_op(C.Structure):
     _fields_ = [("kind", C.c_int), ("a", C.POINTER(ytn_struct)), ("b", C.POINTER(ytn_struct)),
                 ("naxes", C.c_int32), ("axa", C.c_int32 * MAX_RANK), ("axb", C.c_int32 * MAX_RANK),
                 ("ngroups", C.c_int32), ("group_size", C.c_int32 * MAX_RANK),
-                ("order", C.c_int32 * MAX_RANK)]
+                ("order", C.c_int32 * MAX_RANK), ("fermionic", C.c_uint32)]
 
 
 class ytn_plan_info(C.Structure):
@@ -107,6 +108,7 @@ SYMBOLS = {
     "ytn_fuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_unfuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ytn_swap_gate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_vdot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "ytn_sync": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "ytn_ctx_set_gemm_sms": (C.c_int, [C.c_void_p, C.c_int]),
@@ -242,6 +244,10 @@ def struct_to_record(p):
             continue
         f = s.fus[i].contents
         m, ne = f.nlegs, f.nentries
+        if ne == 0:   # the fusion of a tensor without blocks
+            fus.append({"sig": tuple(int(f.sig[j]) for j in range(m)), "nu": np.zeros((0, nsym), np.int32),
+                        "t": np.zeros((0, m, nsym), np.int32), "D": np.zeros((0, m), np.int64)})
+            continue
         fus.append({
             "sig": tuple(int(f.sig[j]) for j in range(m)),
             "nu": np.ctypeslib.as_array(f.nu, shape=(ne * nsym,)).copy().reshape(ne, nsym),
@@ -295,10 +301,11 @@ def ytn_ctx_create(device=0):
     return Ctx(h.value)
 
 
-def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None):
+def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None):
     """Plan an operation. ``a``/``b``: tensor records. ``kind``: one of YTN_OP_*.
     TENSORDOT: pairs (axa[k], axb[k]); FUSE: ``groups`` (list of leg tuples);
-    UNFUSE: legs ``axa``; TRACE: pairs (axa[k], axb[k]) of ``a``."""
+    UNFUSE: legs ``axa``; TRACE: pairs (axa[k], axb[k]) of ``a``; SWAP_GATE: two
+    ``groups`` and ``fermionic`` (one flag per symmetry component; None = all)."""
     sa = Struct(a)
     sb = Struct(b) if b is not None else None
     op = ytn_op()
@@ -318,6 +325,8 @@ def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None):
             op.group_size[k] = len(g)
         for k, x in enumerate(flat):
             op.order[k] = x
+    if fermionic is not None:
+        op.fermionic = YTN_FERMIONIC_EXPLICIT | sum(1 << c for c, f in enumerate(fermionic) if f)
     h = C.c_void_p()
     _check(_lib.ytn_plan(ctx.handle, C.byref(op), C.byref(h)))
     return Plan(ctx, h.value, (sa, sb))
@@ -356,6 +365,11 @@ def ytn_unfuse(plan, a, out, stream=None):
 
 def ytn_trace(plan, a, out, stream=None):
     _check(_lib.ytn_trace(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ytn_swap_gate(plan, a, out, stream=None):
+    """out = swap_gate(a) for a SWAP_GATE plan; ``out`` may be ``a`` (in place)."""
+    _check(_lib.ytn_swap_gate(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
 
 
 def ytn_vdot(plan, a, b, out, workspace=None, workspace_bytes=None, stream=None):

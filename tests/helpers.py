@@ -1,6 +1,8 @@
-"""Test helpers: random symmetric structures for brute-force pins. Builds inputs only."""
+"""Test helpers: random symmetric structures for brute-force pins, and inputs built
+with the oracle's fuse (fused tensors with chosen fusion histories). Builds inputs only."""
 import numpy as np
 
+import oracle as O
 import workloads as W
 
 
@@ -43,3 +45,26 @@ def random_pair(rng, mods, rankA, rankB, ncon, **kw):
 
 def leg_map(leg):
     return {q: d for q, d in zip(leg.t, leg.D)}
+
+
+def fusion_mismatch_pair(drop_a=1, drop_b=None, seed=0):
+    """A = fuse(T_A, (0, 1), (2,)) and B = fuse(T_B, (0, 1), (2,)) on dual constituent
+    legs, where T_A lacks every block with charge ``drop_a`` on its leg 0 (and T_B those
+    with ``drop_b``), so the two fusion records of the contracted fused leg differ.
+    Returns A, B and the zero-padded A_pad, B_pad whose records are the union."""
+    l0 = W.Leg(1, [(-1,), (0,), (1,)], [2, 3, 1])
+    l1 = W.Leg(1, [(0,), (1,)], [2, 2])
+    l2 = W.Leg(-1, [(-1,), (0,), (1,), (2,)], [1, 2, 2, 1])
+    l3 = W.Leg(1, [(-1,), (0,), (1,), (2,)], [2, 1, 3, 1])
+    TA = O.from_record(W.random_tensor((0,), [l0, l1, l2], (0,), 11 + seed))
+    TB = O.from_record(W.random_tensor((0,), [l0.conj(), l1.conj(), l3], (0,), 12 + seed))
+
+    def drop(T, q):
+        keep = {k: v for k, v in T.blocks.items() if q is None or k[0] != (q,)}
+        pad = {k: (v if q is None or k[0] != (q,) else np.zeros_like(v)) for k, v in T.blocks.items()}
+        return O.OTensor(T.mods, T.sig, T.n, keep), O.OTensor(T.mods, T.sig, T.n, pad)
+
+    a, a_pad = drop(TA, drop_a)
+    b, b_pad = drop(TB, drop_b)
+    g = ((0, 1), (2,))
+    return O.fuse(a, g), O.fuse(b, g), O.fuse(a_pad, g), O.fuse(b_pad, g), a, b

@@ -10,7 +10,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from helpers import random_legs, random_pair
+from helpers import fusion_mismatch_pair, random_legs, random_pair
 from paper_2405_12196_gb300 import ytn
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -225,4 +225,69 @@ def test_vdot_planning_matches_the_oracle_rules(hctx):
     for name, B in bad.items():
         with pytest.raises(ytn.YtnError) as ei:
             ytn.ytn_plan(hctx, ytn.YTN_OP_VDOT, A, B)
+        assert ei.value.name == name
+
+
+def test_swap_gate_planning(hctx):
+    """SWAP_GATE plans keep the structure of a, move every element once and reject
+    what the oracle rejects (overlapping groups, a Z3 component as fermionic)."""
+    rng = np.random.default_rng(23)
+    for mods in [(0,), (2,), (0, 0)]:
+        legs = random_legs(rng, mods, 4)
+        A = W.random_tensor(mods, legs, (0,) * len(mods), 1)
+        plan = ytn.ytn_plan(hctx, ytn.YTN_OP_SWAP_GATE, A, groups=((0, 2), (3,)))
+        same_structure(plan.out, O.to_record(O.swap_gate(O.from_record(A), (0, 2), (3,))))
+        assert plan.info["moved_elems"] == A["data"].size
+        ytn.ytn_plan(hctx, ytn.YTN_OP_SWAP_GATE, A, groups=((1,), (0,)), fermionic=(False,) * len(mods))
+    A = W.random_tensor((0,), random_legs(rng, (0,), 3), (0,), 2)
+    for groups in [((0, 1), (1,)), ((0,),), ((0,), (3,)), ((), (1,))]:
+        with pytest.raises(ytn.YtnError) as ei:
+            ytn.ytn_plan(hctx, ytn.YTN_OP_SWAP_GATE, A, groups=groups)
+        assert ei.value.name == "YTN_E_INVALID"
+    Z3 = W.random_tensor((3,), random_legs(rng, (3,), 2), (0,), 3)
+    with pytest.raises(ytn.YtnError):
+        ytn.ytn_plan(hctx, ytn.YTN_OP_SWAP_GATE, Z3, groups=((0,), (1,)))
+    U1Z3 = W.random_tensor((0, 3), random_legs(rng, (0, 3), 2), (0, 0), 4)
+    ytn.ytn_plan(hctx, ytn.YTN_OP_SWAP_GATE, U1Z3, groups=((0,), (1,)), fermionic=(True, False))
+
+
+def test_empty_fusion_record_round_trip(hctx):
+    """Fusing a tensor without blocks gives a fused leg with an empty record; that
+    record comes back through the ABI and plans like any other."""
+    rng = np.random.default_rng(31)
+    A = W.random_tensor((0, 2), random_legs(rng, (0, 2), 4, max_dim=6), (0, 0), 5)
+    assert A["data"].size == 0
+    pf = ytn.ytn_plan(hctx, ytn.YTN_OP_FUSE, A, groups=((0, 1), (2,), (3,)))
+    F = O.to_record(O.fuse(O.from_record(A), ((0, 1), (2,), (3,))))
+    same_structure(pf.out, F)
+    assert pf.out["fus"][0]["nu"].shape[0] == 0
+    for rec in (F, dict(pf.out)):
+        ytn.ytn_plan(hctx, ytn.YTN_OP_SWAP_GATE, rec, groups=((0,), (2,)))
+        pu = ytn.ytn_plan(hctx, ytn.YTN_OP_UNFUSE, rec, axa=(0,))
+        assert pu.out["size"] == 0
+
+
+@pytest.mark.parametrize("drops", [(1, None), (None, -1), (1, -1), (0, 1)])
+def test_fusion_mismatch_resolution_structure(hctx, drops):
+    """Contracted fused legs with different fusion histories plan (Sec. II.B footnote):
+    C's structure and useful FLOPs equal the oracle's resolved contraction."""
+    A, B, _, _, _, _ = fusion_mismatch_pair(*drops)
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, O.to_record(A), O.to_record(B), (0,), (0,))
+    ref = O.tensordot(A, B, (0,), (0,))
+    same_structure(plan.out, O.to_record(ref))
+    assert plan.info["useful_flops"] == O.useful_flops(O.unfuse(A, [0]), O.unfuse(B, [0]), (0, 1), (0, 1))
+
+
+def test_fusion_mismatch_errors_as_status_codes(hctx):
+    A, _, _, _, _, _ = fusion_mismatch_pair(1, None)
+    l0 = W.Leg(-1, [(-1,), (0,), (1,)], [2, 3, 1])
+    l1 = W.Leg(-1, [(0,), (1,)], [2, 2])
+    l1b = W.Leg(-1, [(0,), (1,)], [2, 5])
+    lx = W.Leg(-1, [(0,)], [1])
+    l3 = W.Leg(1, [(-1,), (0,), (1,)], [1, 1, 1])
+    three = O.fuse(O.from_record(W.random_tensor((0,), [l0, l1, lx, l3], (0,), 5)), ((0, 1, 2), (3,)))
+    wrong = O.fuse(O.from_record(W.random_tensor((0,), [l0, l1b, l3], (0,), 6)), ((0, 1), (2,)))
+    for other, name in ((three, "YTN_E_FUSION_MISMATCH"), (wrong, "YTN_E_DIM_MISMATCH")):
+        with pytest.raises(ytn.YtnError) as ei:
+            ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, O.to_record(A), O.to_record(other), (0,), (0,))
         assert ei.value.name == name

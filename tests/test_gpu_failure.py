@@ -4,7 +4,6 @@ A kernel waits (bounded) for a flag that nothing sets; it must record its code i
 the context's status word, ytn_sync must report YTN_E_TIMEOUT once and clear it,
 and the context must still run contractions correctly afterwards.
 """
-import numpy as np
 import pytest
 
 import workloads as W
@@ -34,7 +33,6 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         want = O.to_record(O.tensordot(O.from_record(cfg["A"]), O.from_record(cfg["B"]), cfg["axa"], cfg["axb"]))
         check_against_oracle(rec, want, rtol=FP64_RTOL if prec == ytn.YTN_FP64 else 1e-10)
     ytn.ytn_sync(ctx, timeout_ms=10000)
-    del np
 
 
 def test_selftest_needs_a_device_context():

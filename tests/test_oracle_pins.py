@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from helpers import leg_map, random_legs, random_pair
+from helpers import fusion_mismatch_pair, leg_map, random_legs, random_pair
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -534,35 +534,12 @@ def test_swap_gate_special_cases():
 
 # ---------------------------------------------------------------- fusion-history mismatch
 
-def _mismatch_pair(drop_a=1, drop_b=None, seed=0):
-    """A = fuse(T_A, (0, 1), (2,)) and B = fuse(T_B, (0, 1), (2,)) on dual constituent
-    legs, where T_A lacks every block with charge ``drop_a`` on its leg 0 (and T_B those
-    with ``drop_b``), so the two fusion records of the contracted fused leg differ.
-    Returns A, B and the zero-padded A_pad, B_pad whose records are the union."""
-    l0 = W.Leg(1, [(-1,), (0,), (1,)], [2, 3, 1])
-    l1 = W.Leg(1, [(0,), (1,)], [2, 2])
-    l2 = W.Leg(-1, [(-1,), (0,), (1,), (2,)], [1, 2, 2, 1])
-    l3 = W.Leg(1, [(-1,), (0,), (1,), (2,)], [2, 1, 3, 1])
-    TA = O.from_record(W.random_tensor((0,), [l0, l1, l2], (0,), 11 + seed))
-    TB = O.from_record(W.random_tensor((0,), [l0.conj(), l1.conj(), l3], (0,), 12 + seed))
-
-    def drop(T, q):
-        keep = {k: v for k, v in T.blocks.items() if q is None or k[0] != (q,)}
-        pad = {k: (v if q is None or k[0] != (q,) else np.zeros_like(v)) for k, v in T.blocks.items()}
-        return O.OTensor(T.mods, T.sig, T.n, keep), O.OTensor(T.mods, T.sig, T.n, pad)
-
-    a, a_pad = drop(TA, drop_a)
-    b, b_pad = drop(TB, drop_b)
-    g = ((0, 1), (2,))
-    return O.fuse(a, g), O.fuse(b, g), O.fuse(a_pad, g), O.fuse(b_pad, g), a, b
-
-
 @pytest.mark.parametrize("drops", [(1, None), (None, -1), (1, -1), (0, 1)])
 def test_fusion_mismatch_is_zero_padding(drops):
     """Sec. II.B footnote: a charge of the fusion history missing on one contracted
     fused leg but present on its partner is resolved. The result equals the ordinary
     contraction of the zero-padded tensors, whose records agree."""
-    A, B, A_pad, B_pad, _, _ = _mismatch_pair(*drops)
+    A, B, A_pad, B_pad, _, _ = fusion_mismatch_pair(*drops)
     assert A.fus[0].key() != B.fus[0].conj().key()
     assert A_pad.fus[0].key() == B_pad.fus[0].conj().key()
     got = O.tensordot(A, B, (0,), (0,))
@@ -576,7 +553,7 @@ def test_fusion_mismatch_is_zero_padding(drops):
 def test_fusion_mismatch_matches_the_dense_constituent_contraction():
     """The resolved contraction over the fused leg is the contraction over its
     constituent legs, checked on dense embeddings with numpy."""
-    A, B, _, _, a, b = _mismatch_pair(1, -1)
+    A, B, _, _, a, b = fusion_mismatch_pair(1, -1)
     C = O.tensordot(A, B, (0,), (0,))
     la = [O.leg_sectors(a, i) for i in range(3)]
     lb = [O.leg_sectors(b, i) for i in range(3)]
@@ -592,7 +569,7 @@ def test_fusion_mismatch_matches_the_dense_constituent_contraction():
 def test_fusion_mismatch_errors():
     """Fused legs from a different number of constituents, or disagreeing on the
     dimension of a common constituent charge, are not resolvable."""
-    A, B, _, _, a, _ = _mismatch_pair(1, None)
+    A, B, _, _, a, _ = fusion_mismatch_pair(1, None)
     l0 = W.Leg(-1, [(-1,), (0,), (1,)], [2, 3, 1])
     l1 = W.Leg(-1, [(0,), (1,)], [2, 2])
     l1b = W.Leg(-1, [(0,), (1,)], [2, 5])
