@@ -44,7 +44,7 @@ __all__ = [
     "OTensor", "OracleError", "SignatureError", "DimMismatchError", "FusionMismatchError",
     "ChargeError", "InvalidError", "UnsupportedError",
     "from_record", "to_record", "conj", "tensordot", "fuse", "unfuse", "trace",
-    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity",
+    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon",
 ]
 
 
@@ -534,6 +534,66 @@ def trace(A, ax1, ax2):
         kc = tuple(key[i] for i in rest)
         out.blocks[kc] = out.blocks[kc] + val if kc in out.blocks else np.array(val, dtype=np.float64)
     return out
+
+
+# ------------------------------------------------------------------ networks (ncon)
+
+def ncon(tensors, labels):
+    """Contraction of a network of tensors (Sec. II.B: general networks are contracted
+    through pairwise tensordot by the einsum/ncon convenience functions; the labelling
+    is the ncon convention of Pfeifer, Evenbly, Singh and Vidal, 2015).
+
+    ``labels[i][k]`` labels leg k of tensor i. A positive label is summed and appears
+    on exactly two legs; the negative labels -1, -2, ... name the output legs, in that
+    order. The order of evaluation: while positive labels remain, take the smallest;
+    if both its legs are on one tensor, trace every label that tensor carries twice;
+    else contract the two tensors that carry it over every label they share, as
+    tensordot(first in list order, second) with the shared labels in ascending order,
+    the result taking the first tensor's place. Tensors left with only negative labels
+    are then joined by outer products in list order. Last, the legs are permuted into
+    the order -1, -2, ...; a network of one tensor is copied."""
+    if len(tensors) != len(labels) or not tensors:
+        raise InvalidError("one label list per tensor, at least one tensor")
+    items = []
+    for T, lab in zip(tensors, labels):
+        lab = [int(x) for x in lab]
+        if len(lab) != T.rank or 0 in lab:
+            raise InvalidError("one nonzero label per leg")
+        items.append((T, lab))
+    flat = [x for _, lab in items for x in lab]
+    pos = sorted(x for x in set(flat) if x > 0)
+    neg = sorted((x for x in set(flat) if x < 0), reverse=True)
+    if any(flat.count(x) != 2 for x in pos) or any(flat.count(x) != 1 for x in neg):
+        raise InvalidError("a positive label must appear twice, a negative label once")
+    if neg and neg != list(range(-1, -len(neg) - 1, -1)):
+        raise InvalidError("negative labels must be -1, -2, ... without gaps")
+    while True:
+        rest = sorted({x for _, lab in items for x in lab if x > 0})
+        if not rest:
+            break
+        x = rest[0]
+        where = [i for i, (_, lab) in enumerate(items) if x in lab]
+        if len(where) == 1:
+            T, lab = items[where[0]]
+            twice = sorted({y for y in lab if y > 0 and lab.count(y) == 2})
+            ax1 = [lab.index(y) for y in twice]
+            ax2 = [len(lab) - 1 - lab[::-1].index(y) for y in twice]
+            out = trace(T, ax1, ax2)
+            items[where[0]] = (out, [y for k, y in enumerate(lab) if k not in ax1 + ax2])
+            continue
+        i, j = where
+        (A, la), (B, lb) = items[i], items[j]
+        shared = sorted(set(la) & set(lb))
+        C = tensordot(A, B, [la.index(y) for y in shared], [lb.index(y) for y in shared])
+        lc = [y for y in la if y not in shared] + [y for y in lb if y not in shared]
+        items[i] = (C, lc)
+        del items[j]
+    while len(items) > 1:
+        (A, la), (B, lb) = items[0], items[1]
+        items[0:2] = [(tensordot(A, B, (), ()), la + lb)]
+    T, lab = items[0]
+    order = [lab.index(-k) for k in range(1, len(lab) + 1)]
+    return fuse(T, [(a,) for a in order]) if T.rank else OTensor(T.mods, (), T.n, dict(T.blocks))
 
 
 # ------------------------------------------------------------------ fermionic swap gate

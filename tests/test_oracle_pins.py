@@ -581,3 +581,67 @@ def test_fusion_mismatch_errors():
     wrong = O.fuse(O.from_record(W.random_tensor((0,), [l0, l1b, l3], (0,), 6)), ((0, 1), (2,)))
     with pytest.raises(O.DimMismatchError):
         O.tensordot(A, wrong, (0,), (0,))
+
+
+# ---------------------------------------------------------------- networks (ncon)
+
+def _network(rng, mods, kind):
+    """A random network: legs, tensors and ncon labels. kind: 'chain' (three tensors
+    in a loop), 'trace' (a tensor with a traced pair), 'outer' (two disconnected
+    pieces)."""
+    L = random_legs(rng, mods, 7, max_sectors=3, max_dim=3)
+    n0 = (0,) * len(mods)
+    if kind == "chain":
+        legs = [[L[0], L[1], L[2]], [L[1].conj(), L[3], L[4]], [L[2].conj(), L[4].conj(), L[5]]]
+        labels = [[-1, 1, 2], [1, -2, 3], [2, 3, -3]]
+    elif kind == "trace":
+        legs = [[L[0], L[1], L[1].conj(), L[2]], [L[2].conj(), L[3]]]
+        labels = [[-2, 5, 5, 1], [1, -1]]
+    else:
+        legs = [[L[0], L[1]], [L[1].conj(), L[2]], [L[3], L[4]]]
+        labels = [[-3, 1], [1, -1], [-2, -4]]
+    ts = [W.random_tensor(mods, lg, n0, 100 + k) for k, lg in enumerate(legs)]
+    return legs, ts, labels
+
+
+@pytest.mark.parametrize("sym", ["U1", "Z2", "U1xU1"])
+@pytest.mark.parametrize("kind", ["chain", "trace", "outer"])
+@pytest.mark.parametrize("case", range(3))
+def test_ncon_equals_dense_einsum(sym, kind, case):
+    """ncon of a network == numpy.einsum of the dense embeddings with the same labels
+    (a library routine as the independent route; output legs -1, -2, ... in order)."""
+    mods = SYMS[sym]
+    rng = np.random.default_rng(8700 + 31 * case + len(sym) + len(kind))
+    legs, ts, labels = _network(rng, mods, kind)
+    C = O.ncon([O.from_record(t) for t in ts], labels)
+    letters = {}
+    def sub(lab):
+        return "".join(letters.setdefault(x, "abcdefghijklmnop"[len(letters)]) for x in lab)
+    dense = [O.to_dense(O.from_record(t), [leg_map(l) for l in lg]) for t, lg in zip(ts, legs)]
+    outl = sorted({x for lab in labels for x in lab if x < 0}, reverse=True)
+    spec = ",".join(sub(lab) for lab in labels) + "->" + sub(outl)
+    want = np.einsum(spec, *dense)
+    out_legs = {x: leg_map(l) for lg, lab in zip(legs, labels) for l, x in zip(lg, lab) if x < 0}
+    got = O.to_dense(C, [out_legs[x] for x in outl])
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_ncon_two_spin_example():
+    """The paper's example H2 = tensordot(H, H, axes=((2, 3), (0, 1))) as a network:
+    ncon([H, H], [[-1, -2, 1, 2], [1, 2, -3, -4]]) gives (S1.S2)^2 = 3/16 - H/2."""
+    g = _golden("heisenberg_two_site.json")
+    H = _tensor_from_golden(g)
+    H2 = O.ncon([H, H], [[-1, -2, 1, 2], [1, 2, -3, -4]])
+    ref = O.tensordot(H, H, (2, 3), (0, 1))
+    for k in set(H2.blocks) | set(ref.blocks):
+        np.testing.assert_allclose(H2.blocks[k], ref.blocks[k], atol=1e-15)
+        want = 3.0 / 16 * (1.0 if k[:2] == k[2:] else 0.0) - 0.5 * (H.blocks[k] if k in H.blocks else 0.0)
+        np.testing.assert_allclose(H2.blocks[k], np.full_like(H2.blocks[k], want), atol=1e-15)
+
+
+def test_ncon_label_errors():
+    l = W.Leg(1, [(0,), (1,)], [2, 3])
+    A = O.from_record(W.random_tensor((0,), [l, l.conj()], (0,), 1))
+    for labels in ([[1, 1, 2]], [[1, -1]], [[-1, -3]], [[0, -1]], [[1, 2]]):
+        with pytest.raises(O.InvalidError):
+            O.ncon([A], labels)
