@@ -734,6 +734,47 @@ def run_swap(args):
     return 0
 
 
+def run_ncon(args):
+    """The enlarged corner of a U(1)xU(1) CTMRG step (C.T.T.a, D=12, chi=144) as one
+    ncon network: four library calls planned once, timed per network."""
+    import torch
+
+    from paper_2405_12196_gb300 import ytn
+    dev = torch.device("cuda:0")
+    ctx = ytn.ytn_ctx_create(0)
+    ts, labels = W.ctm_corner_network(W.config3())
+    nc = ytn.ytn_ncon_plan(ctx, ts, labels)
+    data = [torch.from_numpy(t["data"]).to(dev) for t in ts]
+    out = torch.empty(max(nc.out["size"], 1), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    for name, prec, rtol in (("fp64", ytn.YTN_FP64, 0.0), ("split", ytn.YTN_SPLIT_BF16, args.rtol)):
+        ws = torch.empty(max(ytn.ytn_ncon_workspace_size(nc, prec, rtol), 1), dtype=torch.uint8, device=dev)
+        steps = args.steps if name == "split" else max(1, args.steps // 10)
+        for _ in range(args.warmup):
+            ytn.ytn_ncon(nc, data, out, prec=prec, rtol=rtol, workspace=ws, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ytn.ytn_ncon(nc, data, out, prec=prec, rtol=rtol, workspace=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"ms_per_network": ms, "tflops": nc.info["useful_flops"] / (ms * 1e-3) / 1e12, "steps": steps}
+    line = {
+        "metric": "CTMRG enlarged corner as one ncon network: useful TFLOP/s", "value": res["split"]["tflops"],
+        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["split"]["ms_per_network"], "higher_is_better": True, "data": "synthetic",
+        "dtype": "bf16 slices, f32 accumulate, f64 recombine",
+        "config": {"workload": WORKLOAD_DESC["cfg3"] + "; ncon([C, T, T, a]) -> 4 library calls",
+                   "useful_flops_per_network": nc.info["useful_flops"], "rtol": args.rtol},
+        "fp64": res["fp64"], "split": res["split"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -752,6 +793,7 @@ def main():
     ap.add_argument("--chain", action="store_true", help="time the CTMRG-step chain eager and as one CUDA graph")
     ap.add_argument("--reduce", action="store_true", help="time the FP64 scalar product of two D=20 tensors")
     ap.add_argument("--swap", action="store_true", help="time the fermionic swap gate on a D=20 tensor")
+    ap.add_argument("--ncon", action="store_true", help="time the CTMRG enlarged corner as one ncon network")
     ap.add_argument("--serve-runs", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-slots", type=int, default=8)
@@ -769,6 +811,8 @@ def main():
         return run_reduce(args)
     if args.swap:
         return run_swap(args)
+    if args.ncon:
+        return run_ncon(args)
     return run_ours(args)
 
 

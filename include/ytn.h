@@ -82,6 +82,7 @@ typedef struct CUstream_st *ytn_stream;
 
 typedef struct ytn_ctx ytn_ctx;
 typedef struct ytn_plan_s ytn_plan_t;
+typedef struct ytn_ncon_s ytn_ncon_t;
 
 /* Abelian group: nsym components; mod[c] == 0 is U(1), mod[c] == m > 1 is Z_m. */
 typedef struct {
@@ -302,6 +303,38 @@ ytn_status ytn_swap_gate(ytn_plan_t *plan, const double *a, double *out, ytn_str
  * it. No counterpart in the paper. Errors: YTN_E_INVALID (host-only context, or
  * nsms outside [0, number of SMs]). */
 ytn_status ytn_ctx_set_gemm_sms(ytn_ctx *ctx, int nsms);
+
+/* Networks (Sec. II.B: general networks are contracted through pairwise
+ * tensordot by the einsum / ncon convenience functions; labels in the ncon
+ * convention of Pfeifer, Evenbly, Singh and Vidal, 2015).
+ * tensors[i]: the structure of tensor i; labels: concatenated, tensors[i]->rank
+ * per tensor. A positive label is summed and appears on exactly two legs; the
+ * negative labels -1, -2, ... name the output legs in that order. Evaluation
+ * order: while positive labels remain, take the smallest; a label twice on one
+ * tensor traces every label that tensor carries twice; else the two tensors that
+ * carry it are contracted over every label they share (tensordot(first in list
+ * order, second), shared labels ascending), the result taking the first one's
+ * place; what is left is joined by outer products in list order; last, the
+ * legs are permuted into -1, -2, .... Each call has its own cached plan (made
+ * now); the network object holds them. Errors: YTN_E_INVALID (labels), the
+ * planning errors of the calls, YTN_E_UNSUPPORTED (a network of one rank-0
+ * tensor). Release with ytn_ncon_release. */
+ytn_status ytn_ncon_plan(ytn_ctx *ctx, int32_t ntensors, const ytn_struct *const *tensors,
+                         const int32_t *labels, ytn_ncon_t **out);
+/* Output structure (library-owned, valid until the network is released). */
+const ytn_struct *ytn_ncon_output(const ytn_ncon_t *nc);
+/* Useful FLOPs of all contractions and the number of library calls. */
+ytn_status ytn_ncon_info(const ytn_ncon_t *nc, double *useful_flops, int32_t *ncalls);
+/* Workspace bytes of ytn_ncon: every intermediate (256-byte aligned), then one
+ * contraction workspace shared by the calls (the largest ytn_workspace_size). */
+ytn_status ytn_ncon_workspace_size(const ytn_ncon_t *nc, ytn_precision prec, double rtol, size_t *bytes);
+/* Run the network: data[i] is tensor i's buffer, out the output's (device or
+ * page-locked host memory, as for ytn_tensordot; intermediates stay in the
+ * device workspace). Every contraction uses prec / rtol. Asynchronous on stream.
+ * Errors: YTN_E_WORKSPACE and those of the calls. */
+ytn_status ytn_ncon(ytn_ncon_t *nc, const double *const *data, double *out, ytn_precision prec, double rtol,
+                    void *workspace, size_t workspace_bytes, ytn_stream stream);
+void ytn_ncon_release(ytn_ncon_t *nc);
 
 /* Self-test of the failure path (no counterpart in the paper): enqueue on stream
  * a kernel that waits, bounded to about 2 ms, for a flag that nothing sets, then

@@ -109,6 +109,14 @@ SYMBOLS = {
     "ytn_unfuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_swap_gate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ytn_ncon_plan": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.POINTER(ytn_struct)), C.POINTER(C.c_int32),
+                                C.POINTER(C.c_void_p)]),
+    "ytn_ncon_output": (C.POINTER(ytn_struct), [C.c_void_p]),
+    "ytn_ncon_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "ytn_ncon_workspace_size": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
+    "ytn_ncon": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_double, C.c_void_p,
+                           C.c_size_t, C.c_void_p]),
+    "ytn_ncon_release": (None, [C.c_void_p]),
     "ytn_vdot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "ytn_sync": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "ytn_ctx_set_gemm_sms": (C.c_int, [C.c_void_p, C.c_int]),
@@ -291,6 +299,27 @@ class Plan:
         self.release()
 
 
+class Ncon:
+    """A planned network (ytn_ncon_plan): output record, useful FLOPs, call count."""
+
+    def __init__(self, ctx, handle, keep):
+        self.ctx = ctx
+        self.handle = handle
+        self._keep = keep
+        self.out = struct_to_record(_lib.ytn_ncon_output(handle))
+        fl, nc = C.c_double(), C.c_int32()
+        _check(_lib.ytn_ncon_info(handle, C.byref(fl), C.byref(nc)))
+        self.info = {"useful_flops": fl.value, "ncalls": nc.value}
+
+    def release(self):
+        h, self.handle = self.handle, None
+        if h and self.ctx.handle:
+            _lib.ytn_ncon_release(h)
+
+    def __del__(self):
+        self.release()
+
+
 def ytn_version():
     return _lib.ytn_version().decode()
 
@@ -347,6 +376,32 @@ def ytn_tensordot(plan, a, b, c, prec=YTN_FP64, rtol=0.0, workspace=None, worksp
                               _ptr(workspace), int(workspace_bytes), C.byref(res), _stream(stream)))
     return {"useful_flops": res.useful_flops, "precision": res.precision, "slices": res.slices,
             "err_est": res.err_est}
+
+
+def ytn_ncon_plan(ctx, records, labels):
+    """Plan the network of tensor ``records`` with ncon ``labels`` (one list per tensor)."""
+    structs = [Struct(r) for r in records]
+    arr = (C.POINTER(ytn_struct) * len(structs))(*[C.pointer(x.c) for x in structs])
+    flat = np.ascontiguousarray([int(x) for lab in labels for x in lab] or [0], dtype=np.int32)
+    h = C.c_void_p()
+    _check(_lib.ytn_ncon_plan(ctx.handle, len(structs), arr, flat.ctypes.data_as(C.POINTER(C.c_int32)),
+                              C.byref(h)))
+    return Ncon(ctx, h.value, (structs, arr, flat))
+
+
+def ytn_ncon_workspace_size(nc, prec=YTN_FP64, rtol=0.0):
+    n = C.c_size_t()
+    _check(_lib.ytn_ncon_workspace_size(nc.handle, prec, float(rtol), C.byref(n)))
+    return n.value
+
+
+def ytn_ncon(nc, data, out, prec=YTN_FP64, rtol=0.0, workspace=None, workspace_bytes=None, stream=None):
+    """Run a planned network: ``data`` one buffer per tensor, ``out`` the output buffer."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ptrs = (C.c_void_p * len(data))(*[_ptr(d) for d in data])
+    _check(_lib.ytn_ncon(nc.handle, ptrs, _ptr(out), prec, float(rtol), _ptr(workspace), int(workspace_bytes),
+                         _stream(stream)))
 
 
 def ytn_tensordot_noalloc(plan, a, b, c, stream=None):

@@ -68,3 +68,22 @@ def fusion_mismatch_pair(drop_a=1, drop_b=None, seed=0):
     b, b_pad = drop(TB, drop_b)
     g = ((0, 1), (2,))
     return O.fuse(a, g), O.fuse(b, g), O.fuse(a_pad, g), O.fuse(b_pad, g), a, b
+
+
+def random_network(rng, mods, kind):
+    """A random network: legs, tensors and ncon labels. kind: 'chain' (three tensors
+    in a loop), 'trace' (a tensor with a traced pair), 'outer' (two disconnected
+    pieces)."""
+    L = random_legs(rng, mods, 7, max_sectors=3, max_dim=3)
+    n0 = (0,) * len(mods)
+    if kind == "chain":
+        legs = [[L[0], L[1], L[2]], [L[1].conj(), L[3], L[4]], [L[2].conj(), L[4].conj(), L[5]]]
+        labels = [[-1, 1, 2], [1, -2, 3], [2, 3, -3]]
+    elif kind == "trace":
+        legs = [[L[0], L[1], L[1].conj(), L[2]], [L[2].conj(), L[3]]]
+        labels = [[-2, 5, 5, 1], [1, -1]]
+    else:
+        legs = [[L[0], L[1]], [L[1].conj(), L[2]], [L[3], L[4]]]
+        labels = [[-3, 1], [1, -1], [-2, -4]]
+    ts = [W.random_tensor(mods, lg, n0, 100 + k) for k, lg in enumerate(legs)]
+    return legs, ts, labels

@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from helpers import fusion_mismatch_pair, leg_map, random_legs, random_pair
+from helpers import fusion_mismatch_pair, leg_map, random_legs, random_network, random_pair
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -585,25 +585,6 @@ def test_fusion_mismatch_errors():
 
 # ---------------------------------------------------------------- networks (ncon)
 
-def _network(rng, mods, kind):
-    """A random network: legs, tensors and ncon labels. kind: 'chain' (three tensors
-    in a loop), 'trace' (a tensor with a traced pair), 'outer' (two disconnected
-    pieces)."""
-    L = random_legs(rng, mods, 7, max_sectors=3, max_dim=3)
-    n0 = (0,) * len(mods)
-    if kind == "chain":
-        legs = [[L[0], L[1], L[2]], [L[1].conj(), L[3], L[4]], [L[2].conj(), L[4].conj(), L[5]]]
-        labels = [[-1, 1, 2], [1, -2, 3], [2, 3, -3]]
-    elif kind == "trace":
-        legs = [[L[0], L[1], L[1].conj(), L[2]], [L[2].conj(), L[3]]]
-        labels = [[-2, 5, 5, 1], [1, -1]]
-    else:
-        legs = [[L[0], L[1]], [L[1].conj(), L[2]], [L[3], L[4]]]
-        labels = [[-3, 1], [1, -1], [-2, -4]]
-    ts = [W.random_tensor(mods, lg, n0, 100 + k) for k, lg in enumerate(legs)]
-    return legs, ts, labels
-
-
 @pytest.mark.parametrize("sym", ["U1", "Z2", "U1xU1"])
 @pytest.mark.parametrize("kind", ["chain", "trace", "outer"])
 @pytest.mark.parametrize("case", range(3))
@@ -612,7 +593,7 @@ def test_ncon_equals_dense_einsum(sym, kind, case):
     (a library routine as the independent route; output legs -1, -2, ... in order)."""
     mods = SYMS[sym]
     rng = np.random.default_rng(8700 + 31 * case + len(sym) + len(kind))
-    legs, ts, labels = _network(rng, mods, kind)
+    legs, ts, labels = random_network(rng, mods, kind)
     C = O.ncon([O.from_record(t) for t in ts], labels)
     letters = {}
     def sub(lab):

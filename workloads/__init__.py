@@ -271,6 +271,17 @@ def _x2_a(mods, dl, seed):
     return X2, a
 
 
+def ctm_corner_network(cfg):
+    """The enlarged corner of a CTMRG step as an ncon network: corner C, two edges T
+    and the double layer a (random, on the D^2 legs of the U(1)xU(1) D=12 workload).
+    Output legs: T1's chi, T2's chi, a's two outer D^2 legs."""
+    dl = cfg["dleg"]
+    _, a = _x2_a(cfg["mods"], dl, 3101)
+    tensors = [cfg["C"], cfg["T"], cfg["T"], a]
+    labels = [[1, 2], [2, 3, -1], [-2, 4, 1], [3, -3, -4, 4]]
+    return tensors, labels
+
+
 def config5(seed=5001, D=20):
     """Large U(1)xU(1) Hubbard-like environment contraction X2 . a over two legs:
     D=20 over the 25 candidate charges {-2..2}^2 with sizes multinomial(20,
