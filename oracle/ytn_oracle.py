@@ -123,12 +123,16 @@ class OTensor:
     """A block-sparse symmetric tensor: ``blocks`` maps a tuple of per-leg charge tuples
     to a dense FP64 array whose shape is the per-leg sector dimensions."""
 
-    def __init__(self, mods, sig, n, blocks=None, fus=None):
+    def __init__(self, mods, sig, n, blocks=None, fus=None, dtype=None):
         self.mods = tuple(int(m) for m in mods)
         self.sig = tuple(int(s) for s in sig)
         self.n = _red(n, self.mods)
         self.blocks = {} if blocks is None else blocks
         self.fus = list(fus) if fus is not None else [None] * len(self.sig)
+        # element type: float64, or complex128 (given, or found in the blocks)
+        if dtype is None:
+            dtype = np.complex128 if any(np.iscomplexobj(b) for b in self.blocks.values()) else np.float64
+        self.dtype = np.dtype(dtype)
 
     @property
     def rank(self):
@@ -183,7 +187,8 @@ def from_record(rec):
     mods = tuple(rec["mods"])
     t = np.asarray(rec["t"])
     D = np.asarray(rec["D"])
-    data = np.asarray(rec["data"], dtype=np.float64)
+    dtype = np.complex128 if rec.get("dtype") == "c128" else np.float64
+    data = np.asarray(rec["data"], dtype=dtype)
     blocks = {}
     off = 0
     for b in range(len(t)):
@@ -199,7 +204,7 @@ def from_record(rec):
     fus = None
     if rec.get("fus") is not None:
         fus = [None if f is None else _record_from_plain(f) for f in rec["fus"]]
-    return OTensor(mods, rec["sig"], rec["n"], blocks, fus).validate()
+    return OTensor(mods, rec["sig"], rec["n"], blocks, fus, dtype=dtype).validate()
 
 
 def _record_from_plain(f):
@@ -236,20 +241,23 @@ def to_record(T):
             t[b, a, :] = key[a]
         D[b, :] = T.blocks[key].shape
         parts.append(np.ascontiguousarray(T.blocks[key]).ravel())
-    data = np.concatenate(parts) if parts else np.zeros(0)
+    data = np.concatenate(parts).astype(T.dtype) if parts else np.zeros(0, dtype=T.dtype)
     fus = [None if f is None else _record_to_plain(f, T.nsym) for f in T.fus]
-    return {"mods": T.mods, "sig": T.sig, "n": T.n, "t": t, "D": D, "data": data,
-            "fus": fus if any(f is not None for f in fus) else None}
+    rec = {"mods": T.mods, "sig": T.sig, "n": T.n, "t": t, "D": D, "data": data,
+           "fus": fus if any(f is not None for f in fus) else None}
+    if T.dtype == np.complex128:
+        rec["dtype"] = "c128"
+    return rec
 
 
 # ------------------------------------------------------------------ basic operations
 
 def conj(T):
     """Conjugate: every leg's signature flips (Sec. II.A footnote), so the total charge
-    becomes -n; real data is unchanged."""
+    becomes -n, and every element is complex-conjugated (real data is unchanged)."""
     fus = [None if f is None else f.conj() for f in T.fus]
     return OTensor(T.mods, tuple(-s for s in T.sig), _scale(-1, T.n, T.mods),
-                   {k: v.copy() for k, v in T.blocks.items()}, fus)
+                   {k: np.conj(v) for k, v in T.blocks.items()}, fus, dtype=T.dtype)
 
 
 def _check_pairs(rankA, rankB, axa, axb):
@@ -339,7 +347,8 @@ def tensordot(A, B, axa, axb):
     freeB = [i for i in range(B.rank) if i not in axb]
     C = OTensor(A.mods, tuple(A.sig[i] for i in freeA) + tuple(B.sig[i] for i in freeB),
                 _add(A.n, B.n, A.mods),
-                fus=[A.fus[i] for i in freeA] + [B.fus[i] for i in freeB])
+                fus=[A.fus[i] for i in freeA] + [B.fus[i] for i in freeB],
+                dtype=np.result_type(A.dtype, B.dtype))
     byx = {}
     for kb in B.keys():
         byx.setdefault(tuple(kb[b] for b in axb), []).append(kb)
@@ -351,7 +360,7 @@ def tensordot(A, B, axa, axb):
             if kc in C.blocks:
                 C.blocks[kc] = C.blocks[kc] + prod
             else:
-                C.blocks[kc] = np.array(prod, dtype=np.float64)
+                C.blocks[kc] = np.array(prod, dtype=C.dtype)
     return C
 
 
@@ -440,7 +449,7 @@ def fuse(A, groups):
         rec.append(FusionRecord(tuple(A.sig[a] for a in g), entries))
     sig = tuple(A.sig[g[0]] for g in gs)
     fus = [A.fus[g[0]] if len(g) == 1 else rec[i] for i, g in enumerate(gs)]
-    out = OTensor(mods, sig, A.n, fus=fus)
+    out = OTensor(mods, sig, A.n, fus=fus, dtype=A.dtype)
     order = [a for g in gs for a in g]
     for key in A.keys():
         blk = A.blocks[key]
@@ -464,7 +473,7 @@ def fuse(A, groups):
                         break
         newkey = tuple(newkey)
         if newkey not in out.blocks:
-            out.blocks[newkey] = np.zeros(shape)
+            out.blocks[newkey] = np.zeros(shape, dtype=A.dtype)
         sub = np.transpose(blk, order).reshape([b[1] for b in box])
         out.blocks[newkey][tuple(slice(o, o + n) for o, n in box)] = sub
     return out
@@ -488,7 +497,7 @@ def unfuse(A, axes):
         else:
             sig.append(A.sig[a])
             fus.append(A.fus[a])
-    out = OTensor(A.mods, tuple(sig), A.n, fus=fus)
+    out = OTensor(A.mods, tuple(sig), A.n, fus=fus, dtype=A.dtype)
     for key in A.keys():
         blk = A.blocks[key]
         choices = []
@@ -522,7 +531,7 @@ def trace(A, ax1, ax2):
     for a, b in zip(ax1, ax2):
         _check_compatible(A, a, A, b)
     rest = [i for i in range(A.rank) if i not in ax1 + ax2]
-    out = OTensor(A.mods, tuple(A.sig[i] for i in rest), A.n, fus=[A.fus[i] for i in rest])
+    out = OTensor(A.mods, tuple(A.sig[i] for i in rest), A.n, fus=[A.fus[i] for i in rest], dtype=A.dtype)
     for key in A.keys():
         if any(key[a] != key[b] for a, b in zip(ax1, ax2)):
             continue
@@ -532,7 +541,7 @@ def trace(A, ax1, ax2):
         m = np.transpose(blk, rest + list(ax1) + list(ax2)).reshape(int(np.prod(R)) if R else 1, P, P)
         val = np.trace(m, axis1=1, axis2=2).reshape(R)
         kc = tuple(key[i] for i in rest)
-        out.blocks[kc] = out.blocks[kc] + val if kc in out.blocks else np.array(val, dtype=np.float64)
+        out.blocks[kc] = out.blocks[kc] + val if kc in out.blocks else np.array(val, dtype=A.dtype)
     return out
 
 
@@ -593,7 +602,7 @@ def ncon(tensors, labels):
         items[0:2] = [(tensordot(A, B, (), ()), la + lb)]
     T, lab = items[0]
     order = [lab.index(-k) for k in range(1, len(lab) + 1)]
-    return fuse(T, [(a,) for a in order]) if T.rank else OTensor(T.mods, (), T.n, dict(T.blocks))
+    return fuse(T, [(a,) for a in order]) if T.rank else OTensor(T.mods, (), T.n, dict(T.blocks), dtype=T.dtype)
 
 
 # ------------------------------------------------------------------ fermionic swap gate
@@ -632,7 +641,7 @@ def swap_gate(A, axes1, axes2, fermionic=None):
     if any(a < 0 or a >= A.rank for a in allax):
         raise InvalidError("axis out of range")
     charge_parity((0,) * A.nsym, A.mods, fermionic)   # validates the flags, also with no blocks
-    out = OTensor(A.mods, A.sig, A.n, fus=list(A.fus))
+    out = OTensor(A.mods, A.sig, A.n, fus=list(A.fus), dtype=A.dtype)
     for key in A.keys():
         p1 = sum(charge_parity(key[a], A.mods, fermionic) for a in axes1) % 2
         p2 = sum(charge_parity(key[b], A.mods, fermionic) for b in axes2) % 2
@@ -643,8 +652,9 @@ def swap_gate(A, axes1, axes2, fermionic=None):
 # ------------------------------------------------------------------ reductions
 
 def vdot(A, B):
-    """Scalar product <A, B> = sum over every element of A times the same element of B
-    (the Frobenius product of the dense embeddings; elements are real).
+    """Scalar product <A, B> = sum over every element of conj(A) times the same element
+    of B (the Frobenius product of the dense embeddings; for real data, A's element
+    times B's).
 
     The paper leaves the scalar reductions of a tensor network (norms, overlaps,
     expectation values) to the backend; they are kept in FP64 here. Two tensors are
@@ -665,10 +675,12 @@ def vdot(A, B):
         fa, fb = A.fus[a], B.fus[a]
         if (fa is None) != (fb is None) or (fa is not None and fa.key() != fb.key()):
             raise FusionMismatchError(f"leg {a}: fusion records differ")
-    total = 0.0
+    cplx = np.result_type(A.dtype, B.dtype) == np.complex128
+    total = 0.0 + 0.0j if cplx else 0.0
     for key in A.keys():
         if key in B.blocks:
-            total += float(np.sum(A.blocks[key] * B.blocks[key]))
+            v = np.sum(np.conj(A.blocks[key]) * B.blocks[key])
+            total += complex(v) if cplx else float(v)
     return total
 
 
@@ -690,7 +702,7 @@ def to_dense(T, legs=None):
             acc += lg[q]
         offs.append(o)
         dims.append(acc)
-    out = np.zeros(dims)
+    out = np.zeros(dims, dtype=T.dtype)
     for key, blk in T.blocks.items():
         sl = tuple(slice(offs[a][key[a]], offs[a][key[a]] + blk.shape[a]) for a in range(T.rank))
         out[sl] = blk

@@ -213,45 +213,6 @@ __device__ __forceinline__ void issue_rest(uint32_t tmem, uint64_t a0, uint64_t 
   }
 }
 
-// The final store of one tile straight into C's blocks (C in device memory). A
-// warp first stages its share of the column table, the column exponents and its
-// lanes' row entries in shared memory (one round of loads), then each lane writes
-// its row: the block changes with the column segment, and columns that C has no
-// block for (no K charge joins them) are dropped, being zero. Kept out of line so
-// that the accumulation loop's register allocation does not depend on it.
-__device__ __noinline__ void store_tile_direct(const long long *acc, EpiWarpStage *ws, const EpiTables &ep,
-                                               const SplitTile &tl, const SplitSector &sc,
-                                               const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
-                                               double *__restrict__ c, int c0, int rl, int ngroups) {
-  const int lane = threadIdx.x & 31;
-  const SplitEpi se = ep.sec[tl.sector];
-  const int n0 = tl.nt * kSplitBM + c0, row = tl.mt * kSplitBM + rl;
-  __syncwarp();
-  for (int j = lane; j < ngroups * 4; j += 32) {
-    const bool in = n0 + j < sc.N;
-    ws->col[j] = in ? __ldg(reinterpret_cast<const int2 *>(ep.cols + se.col_off + n0 + j)) : make_int2(-1, 0);
-    ws->fexp[j] = in ? __ldg(eb + sc.eb_off + n0 + j) : 0;
-  }
-  ws->row[lane] = row < sc.M ? __ldg(reinterpret_cast<const int2 *>(ep.rows + se.row_off + row)) : make_int2(-1, 0);
-  __syncwarp();
-  if (row >= sc.M) return;
-  const int ei = ea[sc.ea_off + row];
-  const int2 ri = ws->row[lane];
-  const EpiBlock *bt = ep.blk + se.blk_off + (int64_t)ri.x * se.ncs;
-  int seg = -1;
-  double *dst = nullptr;
-  for (int j = 0; j < ngroups * 4; j++) {
-    const int2 cj = ws->col[j];   // (segment, local column)
-    if (cj.x < 0) break;          // past N
-    if (cj.x != seg) {
-      seg = cj.x;
-      const EpiBlock b = bt[seg];
-      dst = b.off >= 0 ? c + b.off + (int64_t)ri.y * b.ld : nullptr;
-    }
-    if (dst) dst[cj.y] = scaled_double(acc[j], ei + ws->fexp[j] - 40);
-  }
-}
-
 template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_split_kernel(const SplitSector *__restrict__ sectors, const SplitTile *__restrict__ tiles, int ntiles,
@@ -441,12 +402,44 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       // C = acc * 2^(e_i + f_j - 40)
       if (ep.sec != nullptr) {
-        // the out-of-line store reads a copy, so that acc itself stays in registers
-        long long out[48];
-#pragma unroll
-        for (int j = 0; j < 48; j++) out[j] = acc[j];
+        // straight into C's blocks (C in device memory): the warp stages its share
+        // of the column table, the column exponents and its lanes' row entries in
+        // shared memory (one round of loads, while the next tile's first chunk
+        // runs), then each lane writes its row. The block changes with the column
+        // segment; columns that C has no block for (no K charge joins them) are
+        // dropped, being zero.
         EpiWarpStage *ws = reinterpret_cast<EpiWarpStage *>(smem + kStagesRing * kSlotBytes + 256) + (warp - kFirstEpiWarp);
-        store_tile_direct(out, ws, ep, tl, sc, ea, eb, wc, c0, rl, ngroups);
+        const SplitEpi se = ep.sec[tl.sector];
+        const int n0 = tl.nt * kSplitBM + c0, row = tl.mt * kSplitBM + rl;
+        __syncwarp();
+        for (int j = lane; j < ngroups * 4; j += 32) {
+          const bool in = n0 + j < sc.N;
+          ws->col[j] = in ? __ldg(reinterpret_cast<const int2 *>(ep.cols + se.col_off + n0 + j)) : make_int2(-1, 0);
+          ws->fexp[j] = in ? __ldg(eb + sc.eb_off + n0 + j) : 0;
+        }
+        ws->row[lane] = row < sc.M ? __ldg(reinterpret_cast<const int2 *>(ep.rows + se.row_off + row)) : make_int2(-1, 0);
+        __syncwarp();
+        if (row < sc.M) {
+          const int ei = ea[sc.ea_off + row];
+          const int2 ri = ws->row[lane];
+          const EpiBlock *bt = ep.blk + se.blk_off + (int64_t)ri.x * se.ncs;
+          int seg = -1;
+          double *dst = nullptr;
+#pragma unroll
+          for (int j = 0; j < 48; j++) {
+            if (j < ngroups * 4) {
+              const int2 cj = ws->col[j];   // (segment, local column); segment -1 past N
+              if (cj.x >= 0) {
+                if (cj.x != seg) {
+                  seg = cj.x;
+                  const EpiBlock b = bt[seg];
+                  dst = b.off >= 0 ? wc + b.off + (int64_t)ri.y * b.ld : nullptr;
+                }
+                if (dst) dst[cj.y] = scaled_double(acc[j], ei + ws->fexp[j] - 40);
+              }
+            }
+          }
+        }
         continue;
       }
       const int row = tl.mt * kSplitBM + rl;

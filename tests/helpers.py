@@ -27,8 +27,9 @@ def random_legs(rng, mods, rank, max_sectors=3, max_dim=3):
     return legs
 
 
-def random_pair(rng, mods, rankA, rankB, ncon, **kw):
-    """Random A, B whose first ``ncon`` legs of B are dual to ``ncon`` random legs of A."""
+def random_pair(rng, mods, rankA, rankB, ncon, dtype="f64", **kw):
+    """Random A, B whose first ``ncon`` legs of B are dual to ``ncon`` random legs of A
+    (``dtype`` "f64" or "c128" for both)."""
     legsA = random_legs(rng, mods, rankA, **kw)
     axa = tuple(int(a) for a in rng.permutation(rankA)[:ncon])
     legsB = random_legs(rng, mods, rankB, **kw)
@@ -38,8 +39,8 @@ def random_pair(rng, mods, rankA, rankB, ncon, **kw):
     nA = tuple(int(rng.integers(0, m)) if m else int(rng.integers(-1, 2)) for m in mods)
     nB = tuple(int(rng.integers(0, m)) if m else int(rng.integers(-1, 2)) for m in mods)
     seed = int(rng.integers(1 << 30))
-    A = W.random_tensor(mods, legsA, nA, seed)
-    B = W.random_tensor(mods, legsB, nB, seed + 1)
+    A = W.random_tensor(mods, legsA, nA, seed, dtype=dtype)
+    B = W.random_tensor(mods, legsB, nB, seed + 1, dtype=dtype)
     return A, B, axa, axb, legsA, legsB
 
 
@@ -74,7 +75,14 @@ def random_network(rng, mods, kind):
     """A random network: legs, tensors and ncon labels. kind: 'chain' (three tensors
     in a loop), 'trace' (a tensor with a traced pair), 'outer' (two disconnected
     pieces)."""
-    L = random_legs(rng, mods, 7, max_sectors=3, max_dim=3)
+    # small charges so that the blocks of neighbouring tensors meet
+    pool = {(0,): [(-1,), (0,), (1,)], (2,): [(0,), (1,)],
+            (0, 0): [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, -1)]}[tuple(mods)]
+    L = []
+    for _ in range(7):
+        k = int(rng.integers(2, len(pool) + 1))
+        qs = sorted(pool[int(i)] for i in rng.choice(len(pool), size=k, replace=False))
+        L.append(W.Leg(int(rng.choice([-1, 1])), qs, [int(d) for d in rng.integers(1, 4, size=k)]))
     n0 = (0,) * len(mods)
     if kind == "chain":
         legs = [[L[0], L[1], L[2]], [L[1].conj(), L[3], L[4]], [L[2].conj(), L[4].conj(), L[5]]]

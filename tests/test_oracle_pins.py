@@ -626,3 +626,73 @@ def test_ncon_label_errors():
     for labels in ([[1, 1, 2]], [[1, -1]], [[-1, -3]], [[0, -1]], [[1, 2]]):
         with pytest.raises(O.InvalidError):
             O.ncon([A], labels)
+
+
+# ---------------------------------------------------------------- complex128
+
+def _parts(T):
+    """Real and imaginary parts of a complex OTensor as real OTensors."""
+    re = O.OTensor(T.mods, T.sig, T.n, {k: v.real.copy() for k, v in T.blocks.items()}, list(T.fus), np.float64)
+    im = O.OTensor(T.mods, T.sig, T.n, {k: v.imag.copy() for k, v in T.blocks.items()}, list(T.fus), np.float64)
+    return re, im
+
+
+@pytest.mark.parametrize("sym", list(SYMS))
+@pytest.mark.parametrize("case", range(6))
+def test_complex_tensordot_equals_dense(sym, case):
+    """Complex data (Sec. II.A footnote): tensordot == numpy.tensordot of the complex
+    dense embeddings, and == the four real products (re re - im im) + i (re im + im re)
+    of the real oracle."""
+    mods = SYMS[sym]
+    rng = np.random.default_rng(9900 + 13 * case + len(sym))
+    rankA, rankB = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+    ncon = int(rng.integers(0, min(rankA, rankB) + 1))
+    A, B, axa, axb, legsA, legsB = random_pair(rng, mods, rankA, rankB, ncon, dtype="c128")
+    oA, oB = O.from_record(A), O.from_record(B)
+    assert oA.dtype == np.complex128 and oB.dtype == np.complex128
+    C = O.tensordot(oA, oB, axa, axb)
+    lmA, lmB = [leg_map(l) for l in legsA], [leg_map(l) for l in legsB]
+    want = np.tensordot(O.to_dense(oA, lmA), O.to_dense(oB, lmB), axes=(axa, axb))
+    freeA = [lmA[i] for i in range(rankA) if i not in axa]
+    freeB = [lmB[i] for i in range(rankB) if i not in axb]
+    np.testing.assert_allclose(O.to_dense(C, freeA + freeB), want, rtol=1e-12, atol=1e-12)
+    (ar, ai), (br, bi) = _parts(oA), _parts(oB)
+    rr, ii = O.tensordot(ar, br, axa, axb), O.tensordot(ai, bi, axa, axb)
+    ri, ir = O.tensordot(ar, bi, axa, axb), O.tensordot(ai, br, axa, axb)
+    for k in C.blocks:
+        np.testing.assert_allclose(C.blocks[k].real, rr.blocks[k] - ii.blocks[k], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(C.blocks[k].imag, ri.blocks[k] + ir.blocks[k], rtol=1e-12, atol=1e-12)
+
+
+def test_complex_conj_vdot_fuse_trace_swap():
+    """conj conjugates the elements (and flips the structure); <A, B> = sum conj(a) b
+    (numpy.vdot of the dense embeddings), <A, B> = conj(<B, A>), <A, A> = ||A||^2 > 0;
+    fuse/unfuse round trip, trace and swap gate keep the complex values."""
+    rng = np.random.default_rng(41)
+    legs = random_legs(rng, (0,), 4, max_sectors=3, max_dim=3)
+    A = O.from_record(W.random_tensor((0,), legs, (0,), 1, dtype="c128"))
+    B = O.from_record(W.random_tensor((0,), legs, (0,), 2, dtype="c128"))
+    lm = [leg_map(l) for l in legs]
+    dA, dB = O.to_dense(A, lm), O.to_dense(B, lm)
+    Ac = O.conj(A)
+    np.testing.assert_array_equal(O.to_dense(Ac, lm), np.conj(dA))
+    assert Ac.sig == tuple(-s for s in A.sig)
+    assert O.vdot(A, B) == pytest.approx(np.vdot(dA, dB), rel=1e-12, abs=1e-12)
+    assert O.vdot(A, B) == pytest.approx(np.conj(O.vdot(B, A)), rel=1e-13, abs=1e-13)
+    nrm = O.vdot(A, A)
+    assert abs(nrm.imag) < 1e-12 and nrm.real == pytest.approx(float(np.sum(np.abs(dA) ** 2)), rel=1e-12)
+    F = O.fuse(A, ((0, 2), (1, 3)))
+    assert F.dtype == np.complex128
+    U = O.unfuse(F, (0, 1))     # legs now in the order 0, 2, 1, 3
+    for k, v in A.blocks.items():
+        np.testing.assert_array_equal(U.blocks[(k[0], k[2], k[1], k[3])], np.transpose(v, (0, 2, 1, 3)))
+    S = O.swap_gate(A, (0,), (1, 2))
+    par = [np.concatenate([np.full(lm[a][q], q[0] % 2) for q in sorted(lm[a])]) for a in range(4)]
+    g = np.meshgrid(*par, indexing="ij")
+    sign = np.where((g[0] * ((g[1] + g[2]) % 2)) % 2 == 1, -1.0, 1.0)
+    np.testing.assert_array_equal(O.to_dense(S, lm), dA * sign)
+    l = W.Leg(1, [(0,), (1,)], [2, 3])
+    T = O.from_record(W.random_tensor((0,), [l, l.conj(), legs[0]], (0,), 3, dtype="c128"))
+    tr = O.trace(T, (0,), (1,))
+    dT = O.to_dense(T, [leg_map(l), leg_map(l), lm[0]])
+    np.testing.assert_allclose(O.to_dense(tr, [lm[0]]), np.einsum("iik->k", dT), rtol=1e-13, atol=1e-13)

@@ -74,7 +74,7 @@ def _reduce(q, mods):
     return tuple((c % m) if m else c for c, m in zip(q, mods))
 
 
-def random_tensor(mods, legs, n, seed, fill="normal"):
+def random_tensor(mods, legs, n, seed, fill="normal", dtype="f64"):
     """A symmetric tensor with every charge-conserving block stored.
 
     A block (rho_1..rho_N) is allowed when sum_i s_i rho_i == n, component-wise and
@@ -85,6 +85,9 @@ def random_tensor(mods, legs, n, seed, fill="normal"):
     ``fill``: "normal" draws N(0,1) (PCG64, ``default_rng(seed)``), "integer" draws
     integers uniform in [-8, 8] (exactly representable and exactly summable, used to
     test the split-precision path), "ones" fills with 1.0.
+    ``dtype``: "f64", or "c128" (complex: real and imaginary parts drawn alike, as
+    consecutive pairs of the same stream; the record gets ``dtype: "c128"`` and a
+    complex128 data array, stored interleaved).
     """
     mods = tuple(int(m) for m in mods)
     nsym = len(mods)
@@ -93,16 +96,24 @@ def random_tensor(mods, legs, n, seed, fill="normal"):
     t, D = _allowed_blocks(mods, legs, n)
     size = int(np.prod(D, axis=1).sum()) if len(D) else 0
     rng = np.random.default_rng(seed)
+    cplx = dtype == "c128"
+    if dtype not in ("f64", "c128"):
+        raise ValueError(dtype)
+    m = 2 * size if cplx else size
     if fill == "normal":
-        data = rng.standard_normal(size)
+        data = rng.standard_normal(m)
     elif fill == "integer":
-        data = rng.integers(-8, 9, size).astype(np.float64)
+        data = rng.integers(-8, 9, m).astype(np.float64)
     elif fill == "ones":
-        data = np.ones(size)
+        data = np.ones(m)
     else:
         raise ValueError(fill)
-    return {"mods": mods, "sig": tuple(l.s for l in legs), "n": n, "t": t, "D": D,
-            "data": np.ascontiguousarray(data, dtype=np.float64)}
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    rec = {"mods": mods, "sig": tuple(l.s for l in legs), "n": n, "t": t, "D": D,
+           "data": data.view(np.complex128) if cplx else data}
+    if cplx:
+        rec["dtype"] = "c128"
+    return rec
 
 
 def _allowed_blocks(mods, legs, n):
