@@ -105,6 +105,12 @@ typedef struct {
   const int64_t *D;           /* [nentries][nlegs] constituent dimensions     */
 } ytn_fusion;
 
+/* Element type of a tensor's data buffer. YTN_COMPLEX128 elements are pairs of
+ * doubles (real, imaginary), interleaved; offsets and sizes count elements. The
+ * paper's backends hold real or complex blocks (Sec. II.A footnote on
+ * conjugation of complex tensors). */
+typedef enum { YTN_REAL64 = 0, YTN_COMPLEX128 = 1 } ytn_dtype;
+
 /* Block structure of one tensor (host memory, caller-owned). */
 typedef struct {
   ytn_sym sym;
@@ -118,6 +124,7 @@ typedef struct {
                                  buffer; NULL means packed in block order     */
   int64_t size;               /* elements in the data buffer                  */
   const ytn_fusion *fus[YTN_MAX_RANK]; /* per leg; NULL for a plain leg       */
+  int32_t dtype;              /* ytn_dtype of the data (0 = real FP64)        */
 } ytn_struct;
 
 #define YTN_FERMIONIC_EXPLICIT 0x80000000u
@@ -222,9 +229,7 @@ ytn_status ytn_workspace_size(const ytn_plan_t *plan, ytn_precision prec, double
 
 /* C = tensordot(A, B) (Sec. II.B contraction equation): gather the blocks of A
  * and B into one matrix per charge sector, multiply the sectors in one grouped
- * launch, scatter the products into the blocks of C (on the split path with
- * C in device memory the GEMM's epilogue writes C's blocks itself and there is
- * no separate scatter; the workspace size does not depend on it). a, b, c: buffers of
+ * launch, scatter the products into the blocks of C. a, b, c: buffers of
  * sizes a->size, b->size and ytn_plan_output(plan)->size, each either device
  * memory of the context's device or page-locked host memory (cudaHostAlloc or
  * cudaHostRegister, mapped into the device's address space). Host-resident

@@ -70,11 +70,6 @@ static ytn_status upload(ytn_plan_t *p) {
   put_table(buf, p->sp_slice_items, o_sps);
   put_table(buf, p->sp_sectors, o_spsec);
   put_table(buf, p->sp_tiles, o_spt);
-  size_t o_eps, o_epr, o_epc, o_epb;
-  put_table(buf, p->ep_sec, o_eps);
-  put_table(buf, p->ep_rows, o_epr);
-  put_table(buf, p->ep_cols, o_epc);
-  put_table(buf, p->ep_blk, o_epb);
   p->dev_bytes = align256(buf.size()) + 256;
   cudaError_t e = cudaMalloc(&p->dev, p->dev_bytes);
   if (e != cudaSuccess) {
@@ -100,9 +95,6 @@ static ytn_status upload(ytn_plan_t *p) {
   p->d_sp_slice_items = reinterpret_cast<const SplitItem *>(d + o_sps);
   p->d_sp_sectors = reinterpret_cast<const SplitSector *>(d + o_spsec);
   p->d_sp_tiles = reinterpret_cast<const SplitTile *>(d + o_spt);
-  if (!p->ep_sec.empty())
-    p->d_ep = {reinterpret_cast<const SplitEpi *>(d + o_eps), reinterpret_cast<const EpiIdx *>(d + o_epr),
-               reinterpret_cast<const EpiIdx *>(d + o_epc), reinterpret_cast<const EpiBlock *>(d + o_epb)};
   return YTN_OK;
 }
 
@@ -147,10 +139,8 @@ class PhaseTimer {
 // with cudaHostRegister) through its device mapping, so that the data movers
 // read or write it over the host link with no separate copy. Pageable host
 // memory and other devices' memory are rejected before anything is launched.
-static ytn_status device_view(const ytn_ctx *ctx, const void *ptr, const void **out, const char *what,
-                              bool *on_host = nullptr) {
+static ytn_status device_view(const ytn_ctx *ctx, const void *ptr, const void **out, const char *what) {
   *out = ptr;
-  if (on_host) *on_host = false;
   if (!ptr) return YTN_OK;
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, ptr);
@@ -166,16 +156,15 @@ static ytn_status device_view(const ytn_ctx *ctx, const void *ptr, const void **
   if (at.type == cudaMemoryTypeHost) {
     if (!at.devicePointer) return fail(YTN_E_INVALID, std::string(what) + ": page-locked host memory without a device mapping");
     *out = at.devicePointer;
-    if (on_host) *on_host = true;
     return YTN_OK;
   }
   return fail(YTN_E_INVALID, std::string(what) + ": pageable host memory (page-lock it with cudaHostRegister first)");
 }
 
 template <class T>
-static ytn_status device_view(const ytn_ctx *ctx, T *ptr, T **out, const char *what, bool *on_host = nullptr) {
+static ytn_status device_view(const ytn_ctx *ctx, T *ptr, T **out, const char *what) {
   const void *v = nullptr;
-  ytn_status st = device_view(ctx, static_cast<const void *>(ptr), &v, what, on_host);
+  ytn_status st = device_view(ctx, static_cast<const void *>(ptr), &v, what);
   *out = static_cast<T *>(const_cast<void *>(v));
   return st;
 }
@@ -473,11 +462,8 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
 }
 
 // One contraction on the chosen path; arguments already checked and mapped.
-// c_direct: C is device memory, so the split GEMM writes C's blocks itself and
-// the scatter is skipped (page-locked host C keeps the dense C_q and the staged
-// scatter, whose writes cross the host link in whole pieces).
 static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, bool split, int slices,
-                                 bool c_direct, void *workspace, cudaStream_t st) {
+                                 void *workspace, cudaStream_t st) {
   WsLayout w;
   workspace_layout(p, split, w);
   char *ws = static_cast<char *>(workspace);
@@ -513,12 +499,9 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
     if (e != cudaSuccess) return cuda_fail(e, "split into slices");
     {
       PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
-      const bool direct = c_direct && p->d_ep.sec != nullptr;
-      e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles, (int64_t)p->sp_tiles.size(), sa, sb, ea, eb,
-                            direct ? c : wc, direct ? p->d_ep : EpiTables{}, slices, p->ctx->status_dev,
-                            p->ctx->gemm_sms.load() > 0 ? p->ctx->gemm_sms.load() : p->ctx->num_sms, st);
-      if (e != cudaSuccess) return cuda_fail(e, "grouped split-precision GEMM");
-      if (direct) return YTN_OK;
+      e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles, (int64_t)p->sp_tiles.size(), sa, sb, ea, eb, wc, slices,
+                            p->ctx->status_dev, p->ctx->gemm_sms.load() > 0 ? p->ctx->gemm_sms.load() : p->ctx->num_sms,
+                            st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grouped split-precision GEMM");
   }
@@ -573,11 +556,10 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
   DeviceGuard g(p->ctx->device);
   if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
-  bool c_host = false;
   {
     ytn_status vs;
     if ((vs = device_view(p->ctx, a, &a, "A")) != YTN_OK || (vs = device_view(p->ctx, b, &b, "B")) != YTN_OK ||
-        (vs = device_view(p->ctx, c, &c, "C", &c_host)) != YTN_OK)
+        (vs = device_view(p->ctx, c, &c, "C")) != YTN_OK)
       return vs;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -599,9 +581,9 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
         cudaEvent_t ev[3];
         for (auto &x : ev) cudaEventCreate(&x);
         cudaEventRecord(ev[0], st);
-        ytn_status r = exec_tensordot(p, a, b, c, false, 0, !c_host, workspace, st);
+        ytn_status r = exec_tensordot(p, a, b, c, false, 0, workspace, st);
         cudaEventRecord(ev[1], st);
-        if (r == YTN_OK) r = exec_tensordot(p, a, b, c, true, slices, !c_host, workspace, st);
+        if (r == YTN_OK) r = exec_tensordot(p, a, b, c, true, slices, workspace, st);
         cudaEventRecord(ev[2], st);
         cudaError_t e = cudaEventSynchronize(ev[2]);
         float t64 = 0.f, t16 = 0.f;
@@ -629,7 +611,7 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     }
     split = choice == 1;
   }
-  ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, !c_host, workspace, st);
+  ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, workspace, st);
   if (r != YTN_OK) return r;
   if (res) {
     res->useful_flops = p->flops;

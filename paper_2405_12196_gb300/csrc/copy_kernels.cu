@@ -32,6 +32,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Negation by the sign bit (an integer operation: this GPU's FP64 pipe is far
 // slower than its memory system); exact, and it keeps NaN payloads.
+constexpr unsigned long long kSignBit = 0x8000000000000000ull;
+
 __device__ __forceinline__ double flip(double x, unsigned long long mask) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)mask);
 }
@@ -40,8 +42,9 @@ __device__ __forceinline__ double flip(double x, unsigned long long mask) {
 template <int ND>
 struct Piece {
   int64_t g_off, d_off;
-  int p;                  // the piece's start in the staging buffer
-  unsigned long long neg; // sign-bit mask: set for a negated piece (fermionic swap gate)
+  int p;       // the piece's start in the staging buffer
+  int negmode; // 0: as is; 1: negated (fermionic swap gate); 2: odd source offsets
+               // negated (imaginary parts of interleaved complex data: conj)
   int ext[ND], gstr[ND], lstr[ND], shf[ND];
   uint32_t mag[ND];
 
@@ -49,7 +52,7 @@ struct Piece {
     g_off = J.g_off;
     d_off = J.d_off;
     p = J.p;
-    neg = J.negate ? 0x8000000000000000ull : 0ull;
+    negmode = J.negate;
 #pragma unroll
     for (int i = 0; i < ND; i++) {
       const int k = kMaxCopyDims - ND + i;
@@ -131,11 +134,12 @@ __device__ __forceinline__ void stage_item(const CopyJob *Js, int nj, int total,
       int lo;
       P.offsets((uint32_t)l, go, lo);
       const int at = P.p + lo;
-      if ((unsigned)at < (unsigned)total) dst[P.g_off + go] = flip(stage[at], P.neg);
+      const bool neg = P.negmode == 1 || (P.negmode == 2 && ((P.d_off + lo) & 1));
+      if ((unsigned)at < (unsigned)total) dst[P.g_off + go] = flip(stage[at], neg ? kSignBit : 0ull);
     });
   } else {
     for_warp_range<ND>(Js, nj, w0, w1, [&](const Piece<ND> &P, int l, int e) {
-      dst[P.d_off + l] = flip(stage[e], P.neg);
+      dst[P.d_off + l] = flip(stage[e], P.negmode == 1 ? kSignBit : 0ull);
     });
   }
 }

@@ -55,17 +55,7 @@ constexpr int kSlotBytes = 2 * kBlockBytes;
 constexpr int kChunk = 8;         // K stages per exact-accumulation chunk (K 256)
 constexpr uint32_t kColE2 = 0, kColE3 = 128, kColE4 = 256, kColR = 384;
 constexpr uint32_t kMaxPolls = 1u << 26;
-// Per epilogue warp, the column and row tables of its share of the current tile
-// (C written straight into its blocks), staged at the start of the tile so
-// that the final stores wait on no global loads.
-struct EpiWarpStage {
-  int2 col[48];        // (column segment, local column), segment -1 past N
-  int32_t fexp[48];    // column exponents
-  int2 row[32];        // (row segment, local row) of each lane, segment -1 past M
-  int32_t pad[48];
-};
-static_assert(sizeof(EpiWarpStage) == 1024, "EpiWarpStage layout");
-constexpr int kSmemBytes = kStagesRing * kSlotBytes + 1024 + 256 + kEpiWarps * (int)sizeof(EpiWarpStage);
+constexpr int kSmemBytes = kStagesRing * kSlotBytes + 1024 + 256;
 
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = 128, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
@@ -217,7 +207,7 @@ template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_split_kernel(const SplitSector *__restrict__ sectors, const SplitTile *__restrict__ tiles, int ntiles,
                       const uint8_t *__restrict__ sa, const uint8_t *__restrict__ sb, const int32_t *__restrict__ ea,
-                      const int32_t *__restrict__ eb, double *__restrict__ wc, const EpiTables ep, int *status) {
+                      const int32_t *__restrict__ eb, double *__restrict__ wc, int *status) {
   constexpr int s = S;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -401,47 +391,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       // C = acc * 2^(e_i + f_j - 40)
-      if (ep.sec != nullptr) {
-        // straight into C's blocks (C in device memory): the warp stages its share
-        // of the column table, the column exponents and its lanes' row entries in
-        // shared memory (one round of loads, while the next tile's first chunk
-        // runs), then each lane writes its row. The block changes with the column
-        // segment; columns that C has no block for (no K charge joins them) are
-        // dropped, being zero.
-        EpiWarpStage *ws = reinterpret_cast<EpiWarpStage *>(smem + kStagesRing * kSlotBytes + 256) + (warp - kFirstEpiWarp);
-        const SplitEpi se = ep.sec[tl.sector];
-        const int n0 = tl.nt * kSplitBM + c0, row = tl.mt * kSplitBM + rl;
-        __syncwarp();
-        for (int j = lane; j < ngroups * 4; j += 32) {
-          const bool in = n0 + j < sc.N;
-          ws->col[j] = in ? __ldg(reinterpret_cast<const int2 *>(ep.cols + se.col_off + n0 + j)) : make_int2(-1, 0);
-          ws->fexp[j] = in ? __ldg(eb + sc.eb_off + n0 + j) : 0;
-        }
-        ws->row[lane] = row < sc.M ? __ldg(reinterpret_cast<const int2 *>(ep.rows + se.row_off + row)) : make_int2(-1, 0);
-        __syncwarp();
-        if (row < sc.M) {
-          const int ei = ea[sc.ea_off + row];
-          const int2 ri = ws->row[lane];
-          const EpiBlock *bt = ep.blk + se.blk_off + (int64_t)ri.x * se.ncs;
-          int seg = -1;
-          double *dst = nullptr;
-#pragma unroll
-          for (int j = 0; j < 48; j++) {
-            if (j < ngroups * 4) {
-              const int2 cj = ws->col[j];   // (segment, local column); segment -1 past N
-              if (cj.x >= 0) {
-                if (cj.x != seg) {
-                  seg = cj.x;
-                  const EpiBlock b = bt[seg];
-                  dst = b.off >= 0 ? wc + b.off + (int64_t)ri.y * b.ld : nullptr;
-                }
-                if (dst) dst[cj.y] = scaled_double(acc[j], ei + ws->fexp[j] - 40);
-              }
-            }
-          }
-        }
-        continue;
-      }
       const int row = tl.mt * kSplitBM + rl;
       if (row < sc.M) {
         const int ei = ea[sc.ea_off + row];
@@ -476,13 +425,13 @@ cudaError_t configure_split_gemm() {
 }
 
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
-                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc,
-                              const EpiTables &ep, int slices, int *status, int num_sms, cudaStream_t stream) {
+                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc, int slices,
+                              int *status, int num_sms, cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles > INT32_MAX || slices < 4 || slices > kSlices) return cudaErrorInvalidValue;
   auto kernel = slices == 4 ? gemm_split_kernel<4> : slices == 5 ? gemm_split_kernel<5> : gemm_split_kernel<6>;
   const int grid = (int)std::min<int64_t>(ntiles, num_sms);
-  kernel<<<grid, kThreads, kSmemBytes, stream>>>(sectors, tiles, (int)ntiles, sa, sb, ea, eb, wc, ep, status);
+  kernel<<<grid, kThreads, kSmemBytes, stream>>>(sectors, tiles, (int)ntiles, sa, sb, ea, eb, wc, status);
   return cudaGetLastError();
 }
 

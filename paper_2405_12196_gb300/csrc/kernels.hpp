@@ -33,10 +33,9 @@ cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_item
 // Shared-memory opt-in of the split-precision GEMM kernels (once per device).
 cudaError_t configure_split_gemm();
 
-// Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output: the
-// dense C_q into wc, or, when ep.sec is set, C's blocks straight into wc = C.
+// Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output C_q.
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
-                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc,
-                              const EpiTables &ep, int slices, int *status, int num_sms, cudaStream_t stream);
+                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc, int slices,
+                              int *status, int num_sms, cudaStream_t stream);
 
 }  // namespace ytn

@@ -44,6 +44,8 @@ ytn_status load_struct(const ytn_struct *s, Tensor &T, std::string &err) {
   if (s->nblocks < 0 || s->size < 0) { err = "negative sizes"; return YTN_E_INVALID; }
   if (s->nblocks > 0 && s->rank > 0 && (!s->t || !s->D)) { err = "null block arrays"; return YTN_E_INVALID; }
   T = Tensor();
+  if (s->dtype != YTN_REAL64 && s->dtype != YTN_COMPLEX128) { err = "unknown element type"; return YTN_E_INVALID; }
+  T.dtype = s->dtype;
   T.nsym = s->sym.nsym;
   T.rank = s->rank;
   for (int c = 0; c < T.nsym; c++) {
@@ -302,7 +304,7 @@ static bool side_dense(const std::vector<Dim> &dims, bool src) {
 // One staged job: `dims` (ext, local stride, global stride) of a piece whose
 // dense side starts at d_off and strided side at g_off.
 static ytn_status push_piece(ytn_plan_t *p, std::vector<Dim> dims, int mode, int64_t g_off, int64_t d_off,
-                             std::string &err, bool negate = false) {
+                             std::string &err, int negate = 0) {
   // enumeration order: strided (global) side outer -> inner
   std::stable_sort(dims.begin(), dims.end(), [](const Dim &a, const Dim &b) { return a.dst > b.dst; });
   std::vector<Dim> m = merge_dims(dims);
@@ -311,13 +313,17 @@ static ytn_status push_piece(ytn_plan_t *p, std::vector<Dim> dims, int mode, int
     err = "copy job needs more than 8 dimensions";
     return YTN_E_UNSUPPORTED;
   }
+  if (negate == 2 && mode != 2) {   // the parity rule needs the source side dense
+    err = "imaginary-part negation of a copy without a dense source";
+    return YTN_E_UNSUPPORTED;
+  }
   CopyJob J;
   std::memset(&J, 0, sizeof(J));
   J.g_off = g_off;
   J.d_off = d_off;
   J.nd = (int32_t)m.size();
   J.mode = mode;
-  J.negate = negate ? 1 : 0;
+  J.negate = negate;
   int64_t size = 1;
   // dims right-aligned in the kMaxCopyDims slots; the outer slots are unit dims
   const int o = kMaxCopyDims - J.nd;
@@ -345,8 +351,23 @@ static ytn_status push_piece(ytn_plan_t *p, std::vector<Dim> dims, int mode, int
 // sides) becomes staged jobs of at most kStageElems elements. One side is a
 // dense range (the whole block on the tensor side); it is cut into contiguous
 // pieces by fixing its outer indices and splitting the next one.
+static ytn_status add_copy_raw(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t src_off, int64_t dst_off,
+                               std::string &err, int negate);
+
+// A block copy in elements; for complex tensors moved whole (p->cw == 2) every
+// element is a pair of doubles: strides and offsets double and an innermost
+// component dim (2, 1, 1) is added.
 static ytn_status add_copy(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t src_off, int64_t dst_off,
-                           std::string &err, bool negate = false) {
+                           std::string &err, int negate = 0) {
+  if (p->cw != 2) return add_copy_raw(p, dims, src_off, dst_off, err, negate);
+  std::vector<Dim> d2;
+  for (const Dim &d : dims) d2.push_back({d.ext, 2 * d.sst, 2 * d.dst});
+  d2.push_back({2, 1, 1});
+  return add_copy_raw(p, d2, 2 * src_off, 2 * dst_off, err, negate);
+}
+
+static ytn_status add_copy_raw(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t src_off, int64_t dst_off,
+                               std::string &err, int negate) {
   std::vector<Dim> v;
   for (auto &d : dims)
     if (d.ext != 1) v.push_back(d);
@@ -394,7 +415,7 @@ static ytn_status add_copy(ytn_plan_t *p, const std::vector<Dim> &dims, int64_t 
         so += idx[i] * srt[i].sst;
         dof += idx[i] * srt[i].dst;
       }
-      ytn_status s = add_copy(p, inner, so, dof, err, negate);
+      ytn_status s = add_copy_raw(p, inner, so, dof, err, negate);
       if (s != YTN_OK) return s;
       size_t i = k;
       while (i > 0 && ++idx[i - 1] == srt[i - 1].ext) idx[--i] = 0;
@@ -964,43 +985,6 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   make_items(p, j2, j3);
   p->items_c_end = (int64_t)p->items.size();
 
-  // Epilogue tables: the split GEMM writes C's blocks directly (see EpiTables).
-  p->ep_sec.clear();
-  p->ep_rows.clear();
-  p->ep_cols.clear();
-  p->ep_blk.clear();
-  {
-    std::vector<std::map<int64_t, int32_t>> rs_of(geo.size()), cs_of(geo.size());
-    for (size_t si = 0; si < geo.size(); si++) {
-      SplitEpi se{};
-      se.row_off = (int64_t)p->ep_rows.size();
-      se.col_off = (int64_t)p->ep_cols.size();
-      se.blk_off = (int64_t)p->ep_blk.size();
-      int32_t seg = 0;
-      for (auto &r : sbs[si]->rows) {
-        rs_of[si][geo[si].row_off.at(r.first)] = seg;
-        for (int64_t i = 0; i < r.second.first; i++) p->ep_rows.push_back({seg, (int32_t)i});
-        seg++;
-      }
-      const int32_t nrs = seg;
-      seg = 0;
-      for (auto &c : sbs[si]->cols) {
-        cs_of[si][geo[si].col_off.at(c.first)] = seg;
-        for (int64_t j = 0; j < c.second.first; j++) p->ep_cols.push_back({seg, (int32_t)j});
-        seg++;
-      }
-      se.ncs = seg;
-      p->ep_blk.resize(p->ep_blk.size() + (size_t)nrs * (size_t)seg, EpiBlock{-1, 0});
-      p->ep_sec.push_back(se);
-    }
-    for (size_t id = 0; id < srcs.size(); id++) {
-      const Src &sr = srcs[id];
-      const SplitEpi &se = p->ep_sec[sr.sector];
-      const int64_t k = se.blk_off + (int64_t)rs_of[sr.sector].at(sr.roff) * se.ncs + cs_of[sr.sector].at(sr.coff);
-      p->ep_blk[k] = {off_of_id[id], sr.nJ};
-    }
-  }
-
   // Grouped-GEMM tiles, largest K first. The tile edge is chosen per sector from
   // its size: 32 when 32 x 32 tiles cover the sector with at most 60% of the
   // padded area of 64 x 64 tiles (small or thin M, N), else 64.
@@ -1152,6 +1136,8 @@ ytn_status plan_fuse(ytn_plan_t *p, const Tensor &A, int ngroups, const int *gro
     }
   Tensor &C = p->out;
   C = Tensor();
+  C.dtype = A.dtype;
+  p->cw = A.dtype == YTN_COMPLEX128 ? 2 : 1;
   C.nsym = nsym;
   std::memcpy(C.mod, A.mod, sizeof(C.mod));
   std::memcpy(C.n, A.n, sizeof(C.n));
@@ -1256,6 +1242,8 @@ ytn_status plan_unfuse(ytn_plan_t *p, const Tensor &A, int naxes, const int *axe
   const int nsym = A.nsym;
   Tensor &C = p->out;
   C = Tensor();
+  C.dtype = A.dtype;
+  p->cw = A.dtype == YTN_COMPLEX128 ? 2 : 1;
   C.nsym = nsym;
   std::memcpy(C.mod, A.mod, sizeof(C.mod));
   std::memcpy(C.n, A.n, sizeof(C.n));
@@ -1399,8 +1387,11 @@ ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1_
     if (!used[i]) rest.push_back(i);
   if ((int)rest.size() > kMaxCopyDims || naxes > kMaxCopyDims) { err = "trace needs more than 8 dims"; return YTN_E_UNSUPPORTED; }
   const int nsym = A.nsym;
+  const bool cplx = A.dtype == YTN_COMPLEX128;
+  if (cplx && (int)rest.size() + 1 > kMaxCopyDims) { err = "trace needs more than 8 dims"; return YTN_E_UNSUPPORTED; }
   Tensor &C = p->out;
   C = Tensor();
+  C.dtype = A.dtype;
   C.nsym = nsym;
   std::memcpy(C.mod, A.mod, sizeof(C.mod));
   std::memcpy(C.n, A.n, sizeof(C.n));
@@ -1448,15 +1439,24 @@ ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1_
     for (size_t i = 0; i < d.size(); i++) to.rext[i] = (int32_t)d[i];
     to.first = (int32_t)p->tr_contrib.size();
     to.ncontrib = (int32_t)kv.second.size();
+    // complex data: doubles instead of elements, the component an innermost rest dim
+    const int w = cplx ? 2 : 1;
+    if (cplx) {
+      if (to.nrest > INT32_MAX / 2) { err = "trace output block too large"; return YTN_E_UNSUPPORTED; }
+      to.dst_off *= 2;
+      to.nrest *= 2;
+      to.rext[to.nrd++] = 2;
+    }
     for (int64_t b : kv.second) {
       TraceContrib tc{};
-      tc.src_off = A.off[b];
+      tc.src_off = w * A.off[b];
       auto st = block_strides(A, b);
-      for (size_t i = 0; i < rest.size(); i++) tc.rstr[i] = (int32_t)st[rest[i]];
+      for (size_t i = 0; i < rest.size(); i++) tc.rstr[i] = (int32_t)(w * st[rest[i]]);
+      if (cplx) tc.rstr[rest.size()] = 1;
       tc.ndiag = naxes;
       for (int k = 0; k < naxes; k++) {
         tc.dext[k] = (int32_t)A.dim(b, ax1[k]);
-        tc.dstr[k] = (int32_t)(st[ax1[k]] + st[ax2[k]]);
+        tc.dstr[k] = (int32_t)(w * (st[ax1[k]] + st[ax2[k]]));
       }
       p->tr_contrib.push_back(tc);
     }
@@ -1593,13 +1593,14 @@ ytn_status plan_swap_gate(ytn_plan_t *p, const Tensor &A, int ngroups, const int
     return (int)(((s % 2) + 2) % 2);
   };
   p->out = A;
+  p->cw = A.dtype == YTN_COMPLEX128 ? 2 : 1;
   p->jobs.clear();
   p->items.clear();
   p->moved = 0;
   for (int64_t b = 0; b < A.nblocks; b++) {
     const int64_t n = A.elems(b);
     const bool neg = parity(b, g[0]) == 1 && parity(b, g[1]) == 1;
-    ytn_status s = add_copy(p, {{n, 1, 1}}, A.off[b], A.off[b], err, neg);
+    ytn_status s = add_copy(p, {{n, 1, 1}}, A.off[b], A.off[b], err, neg ? 1 : 0);
     if (s != YTN_OK) return s;
     p->moved += n;
   }
@@ -1609,6 +1610,46 @@ ytn_status plan_swap_gate(ytn_plan_t *p, const Tensor &A, int ngroups, const int
   p->zero_out = false;
   p->flops = 0.0;
   p->kind = Kind::Swap;
+  p->a_size = A.size;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Conjugation
+// ---------------------------------------------------------------------------
+
+// Sec. II.A footnote: conjugation flips every leg's signature (so n becomes -n,
+// and each fusion record's constituent signatures flip) and complex-conjugates
+// the elements. Blocks keep their charges and places; complex data is copied
+// with its imaginary parts negated, real data is copied as it is.
+ytn_status plan_conj(ytn_plan_t *p, const Tensor &A, std::string &err) {
+  p->out = A;
+  Tensor &C = p->out;
+  for (int i = 0; i < C.rank; i++) {
+    C.sig[i] = -A.sig[i];
+    if (A.fus[i]) {
+      auto F = std::make_shared<Fusion>(*A.fus[i]);
+      for (int j = 0; j < F->nlegs; j++) F->sig[j] = -F->sig[j];
+      C.fus[i] = F;
+    }
+  }
+  for (int c = 0; c < C.nsym; c++) C.n[c] = reduce(-(int64_t)A.n[c], A.mod[c]);
+  p->cw = A.dtype == YTN_COMPLEX128 ? 2 : 1;
+  p->jobs.clear();
+  p->items.clear();
+  p->moved = 0;
+  for (int64_t b = 0; b < A.nblocks; b++) {
+    const int64_t n = A.elems(b);
+    ytn_status s = add_copy(p, {{n, 1, 1}}, A.off[b], A.off[b], err, p->cw == 2 ? 2 : 0);
+    if (s != YTN_OK) return s;
+    p->moved += n;
+  }
+  p->items_a_begin = 0;
+  make_items(p, 0, p->jobs.size());
+  p->items_a_end = (int64_t)p->items.size();
+  p->zero_out = false;
+  p->flops = 0.0;
+  p->kind = Kind::Conj;
   p->a_size = A.size;
   return YTN_OK;
 }
@@ -1627,6 +1668,7 @@ static void key_struct(std::string &s, const ytn_struct *t) {
   put(s, t->n, sizeof(t->n));
   put(s, &t->nblocks, sizeof(t->nblocks));
   put(s, &t->size, sizeof(t->size));
+  put(s, &t->dtype, sizeof(t->dtype));
   const int nsym = t->sym.nsym > 0 && t->sym.nsym <= YTN_MAX_SYM ? t->sym.nsym : 0;
   const int rank = t->rank > 0 && t->rank <= YTN_MAX_RANK ? t->rank : 0;
   if (t->t) put(s, t->t, (size_t)t->nblocks * rank * nsym * sizeof(int32_t));
@@ -1666,6 +1708,7 @@ void finish_output_view(ytn_plan_t *p) {
   Tensor &C = p->out;
   ytn_struct &v = p->out_view;
   std::memset(&v, 0, sizeof(v));
+  v.dtype = C.dtype;
   v.sym.nsym = C.nsym;
   for (int c = 0; c < YTN_MAX_SYM; c++) v.sym.mod[c] = C.mod[c];
   v.rank = C.rank;

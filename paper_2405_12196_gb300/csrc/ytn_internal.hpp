@@ -47,7 +47,8 @@ struct CopyJob {
   int32_t lstr[kMaxCopyDims];
   uint32_t mag[kMaxCopyDims];
   uint8_t shf[kMaxCopyDims];
-  int32_t negate;      // 1: the piece is written negated (fermionic swap-gate sign)
+  int32_t negate;      // 1: written negated (swap-gate sign); 2: imaginary parts
+                       // negated (odd source offsets of interleaved complex data)
   int32_t reserved[5];
 };
 static_assert(sizeof(CopyJob) == 192, "CopyJob layout");
@@ -155,31 +156,6 @@ struct SplitTile {
   int32_t sector, mt, nt, pad;
 };
 
-// Output tables of the split GEMM's epilogue when it writes C's blocks directly
-// (C in device memory): row r of sector q lies in row segment `seg` (one
-// combination of A's free charges) at row `local` of it, and likewise for the
-// columns (B's free charges). blk[seg_r * ncs + seg_c] is the C block of that
-// pair: its element offset in C (-1 when C has no such block: no K charge joins
-// them) and its row length nJ, so that C element (r, n) sits at
-// off + local_r * nJ + local_n (C blocks are row-major over their legs, A's free
-// legs first).
-struct EpiIdx {
-  int32_t seg, local;
-};
-struct EpiBlock {
-  int64_t off, ld;
-};
-struct SplitEpi {
-  int64_t row_off, col_off, blk_off;   // first entries of the sector in rows / cols / blk
-  int32_t ncs, pad;
-};
-static_assert(sizeof(SplitEpi) == 32, "SplitEpi layout");
-struct EpiTables {
-  const SplitEpi *sec;   // nullptr: write the dense C_q into the workspace instead
-  const EpiIdx *rows, *cols;
-  const EpiBlock *blk;
-};
-
 // ----------------------------------------------------------------------------
 // Host-side structures
 // ----------------------------------------------------------------------------
@@ -194,6 +170,7 @@ struct Fusion {
 };
 
 struct Tensor {
+  int dtype = YTN_REAL64;    // YTN_COMPLEX128: elements are (re, im) pairs of doubles
   int nsym = 0;
   int mod[YTN_MAX_SYM] = {0};
   int rank = 0;
@@ -223,7 +200,7 @@ struct HostSector {
   int64_t a_off = 0, b_off = 0, c_off = 0;
 };
 
-enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap = 6 };
+enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap = 6, Conj = 7 };
 
 struct Plan;
 
@@ -260,6 +237,9 @@ struct ytn_plan_s {
 
   // input sizes and output structure (owned storage + ABI view)
   int64_t a_size = 0, b_size = 0;
+  // doubles per element of the copy jobs that add_copy makes: 2 for complex
+  // tensors moved whole (fuse, unfuse, swap gate, conj), else 1
+  int cw = 1;
   ytn::Tensor out;
   ytn_struct out_view{};
   std::vector<ytn_fusion> out_fus_view;
@@ -306,9 +286,6 @@ struct ytn_plan_s {
   std::vector<ytn::SplitItem> sp_exp_items, sp_slice_items;
   std::vector<ytn::SplitSector> sp_sectors;
   std::vector<ytn::SplitTile> sp_tiles;
-  std::vector<ytn::SplitEpi> ep_sec;
-  std::vector<ytn::EpiIdx> ep_rows, ep_cols;
-  std::vector<ytn::EpiBlock> ep_blk;
   int64_t sp_sa_bytes = 0, sp_sb_bytes = 0, sp_ea = 0, sp_eb = 0;
   // YTN_AUTO: per slice count, -1 undecided, 0 FP64, 1 split; the timings (ms)
   std::mutex auto_mu;
@@ -318,7 +295,6 @@ struct ytn_plan_s {
   const ytn::SplitItem *d_sp_exp_items = nullptr, *d_sp_slice_items = nullptr;
   const ytn::SplitSector *d_sp_sectors = nullptr;
   const ytn::SplitTile *d_sp_tiles = nullptr;
-  ytn::EpiTables d_ep{};
 };
 
 namespace ytn {
@@ -334,6 +310,7 @@ ytn_status plan_unfuse(ytn_plan_t *p, const Tensor &A, int naxes, const int *axe
 ytn_status plan_vdot(ytn_plan_t *p, const Tensor &A, const Tensor &B, std::string &err);
 ytn_status plan_swap_gate(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
                           uint32_t fermionic, std::string &err);
+ytn_status plan_conj(ytn_plan_t *p, const Tensor &A, std::string &err);
 ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1,
                       const int *ax2, std::string &err);
 std::string plan_key(const ytn_op *op);

@@ -34,6 +34,7 @@ YTN_SPLIT_BF16 = 1
 YTN_AUTO = 2
 YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE, YTN_OP_VDOT, YTN_OP_SWAP_GATE = 1, 2, 3, 4, 5, 6
 YTN_FERMIONIC_EXPLICIT = 1 << 31
+YTN_REAL64, YTN_COMPLEX128 = 0, 1
 
 
 class YtnError(RuntimeError):
@@ -58,7 +59,7 @@ class ytn_struct(C.Structure):
                 ("n", C.c_int32 * MAX_SYM), ("nblocks", C.c_int64),
                 ("t", C.POINTER(C.c_int32)), ("D", C.POINTER(C.c_int64)),
                 ("off", C.POINTER(C.c_int64)), ("size", C.c_int64),
-                ("fus", C.POINTER(ytn_fusion) * MAX_RANK)]
+                ("fus", C.POINTER(ytn_fusion) * MAX_RANK), ("dtype", C.c_int32)]
 
 
 class ytn_op(C.Structure):
@@ -209,6 +210,7 @@ class Struct:
             s.off = off.ctypes.data_as(C.POINTER(C.c_int64))
         sizes = np.prod(D, axis=1) if nb else np.zeros(0, np.int64)
         s.size = int(rec.get("size", int(sizes.sum()) if nb else 0))
+        s.dtype = YTN_COMPLEX128 if rec.get("dtype") == "c128" else YTN_REAL64
         fus = rec.get("fus")
         self._fus = []
         if fus is not None:
@@ -265,7 +267,8 @@ def struct_to_record(p):
     return {"mods": tuple(int(s.sym.mod[c]) for c in range(nsym)),
             "sig": tuple(int(s.sig[i]) for i in range(rank)),
             "n": tuple(int(s.n[c]) for c in range(nsym)), "t": t, "D": D, "off": off,
-            "size": int(s.size), "fus": fus if any(f is not None for f in fus) else None}
+            "size": int(s.size), "fus": fus if any(f is not None for f in fus) else None,
+            **({"dtype": "c128"} if s.dtype == YTN_COMPLEX128 else {})}
 
 
 # ------------------------------------------------------------------ entry points
