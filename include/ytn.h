@@ -135,7 +135,8 @@ typedef enum {
   YTN_OP_UNFUSE = 3,     /* undo the fusion of legs axa[0..naxes), Sec. II.B      */
   YTN_OP_TRACE = 4,      /* sum the diagonals of leg pairs (axa[k], axb[k]) of a  */
   YTN_OP_VDOT = 5,       /* scalar product <a, b> of two tensors on the same legs */
-  YTN_OP_SWAP_GATE = 6   /* fermionic swap gate between two groups of legs, Sec. IV */
+  YTN_OP_SWAP_GATE = 6,  /* fermionic swap gate between two groups of legs, Sec. IV */
+  YTN_OP_CONJ = 7        /* conjugate: signatures flip, elements conjugated       */
 } ytn_op_kind;
 
 /* A planned operation.
@@ -162,7 +163,10 @@ typedef enum {
  *             YTN_FERMIONIC_EXPLICIT | (bit c for component c), so that an
  *             explicit empty set (all components bosonic) is expressible. Each
  *             fermionic component must be U(1) or Z_m with m even. Output
- *             structure = a's. */
+ *             structure = a's.
+ *  CONJ:      a. Sec. II.A footnote: every leg's signature flips (n becomes
+ *             -n, fusion records' constituent signatures flip) and complex
+ *             elements are conjugated; blocks keep their charges and places. */
 typedef struct {
   ytn_op_kind kind;
   const ytn_struct *a;
@@ -229,7 +233,11 @@ ytn_status ytn_workspace_size(const ytn_plan_t *plan, ytn_precision prec, double
 
 /* C = tensordot(A, B) (Sec. II.B contraction equation): gather the blocks of A
  * and B into one matrix per charge sector, multiply the sectors in one grouped
- * launch, scatter the products into the blocks of C. a, b, c: buffers of
+ * launch, scatter the products into the blocks of C. Complex operands
+ * (YTN_COMPLEX128) are contracted as real sector matrices with doubled rows
+ * (A: real parts, then imaginary) or columns (B): one real GEMM gives the four
+ * real products, which the scatter combines (re = re.re - im.im, im = re.im +
+ * im.re); C is complex when either operand is. a, b, c: buffers of
  * sizes a->size, b->size and ytn_plan_output(plan)->size, each either device
  * memory of the context's device or page-locked host memory (cudaHostAlloc or
  * cudaHostRegister, mapped into the device's address space). Host-resident
@@ -280,16 +288,19 @@ ytn_status ytn_unfuse(ytn_plan_t *plan, const double *a, double *out, ytn_stream
 /* out = trace of a over the planned leg pairs. Same buffer rules as ytn_fuse. */
 ytn_status ytn_trace(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
 
-/* out[0] = <A, B>, the sum over the elements of the blocks present in both
- * tensors of A's element times B's, in FP64 (a VDOT plan; ||A||^2 = <A, A>).
- * The paper leaves norms, overlaps and expectation values to its backend; they
- * are FP64 reductions here. a, b: buffers of the planned sizes; out: one double;
- * each device memory or page-locked host memory, as for ytn_tensordot.
- * workspace: device buffer of ytn_workspace_size bytes (8 bytes per 8192 common
- * elements), 256-byte aligned. Deterministic: the same call gives the same bits.
+/* out = <A, B>, the sum over the elements of the blocks present in both
+ * tensors of conj(A's element) times B's, in FP64 (a VDOT plan; ||A||^2 =
+ * <A, A>). The paper leaves norms, overlaps and expectation values to its
+ * backend; they are FP64 reductions here. a, b: buffers of the planned sizes;
+ * out: one double (real tensors) or two, real and imaginary part (complex
+ * tensors; both operands must have the same element type); each device memory
+ * or page-locked host memory, as for ytn_tensordot. workspace: device buffer of
+ * ytn_workspace_size bytes (8 bytes, 16 for complex, per CTA share of 8192
+ * doubles), 256-byte aligned. Deterministic: the same call gives the same bits.
  * Asynchronous on stream. Errors: YTN_E_INVALID (wrong plan kind, null buffer),
  * YTN_E_WORKSPACE, YTN_E_CUDA. Planning errors (YTN_E_SIGNATURE,
- * YTN_E_DIM_MISMATCH, YTN_E_FUSION_MISMATCH, YTN_E_INVALID) come from ytn_plan. */
+ * YTN_E_DIM_MISMATCH, YTN_E_FUSION_MISMATCH, YTN_E_INVALID, YTN_E_UNSUPPORTED
+ * for a real and a complex tensor) come from ytn_plan. */
 ytn_status ytn_vdot(ytn_plan_t *plan, const double *a, const double *b, double *out, void *workspace,
                     size_t workspace_bytes, ytn_stream stream);
 
@@ -300,6 +311,12 @@ ytn_status ytn_vdot(ytn_plan_t *plan, const double *a, const double *b, double *
  * Asynchronous on stream. Errors: YTN_E_INVALID (wrong plan kind, null
  * buffer), YTN_E_CUDA. */
 ytn_status ytn_swap_gate(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
+
+/* out = conj(a) (a CONJ plan): each block copied to its place with the
+ * imaginary parts of complex elements negated (real data copied as it is).
+ * out may be a itself. Buffers as for ytn_swap_gate. Bit-exact. Asynchronous on
+ * stream. Errors: YTN_E_INVALID (wrong plan kind, null buffer), YTN_E_CUDA. */
+ytn_status ytn_conj(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
 
 /* Number of CTAs (one per SM) of the persistent split-precision GEMM of this
  * context; 0 (the default) uses every SM. Leaving some SMs free lets the data

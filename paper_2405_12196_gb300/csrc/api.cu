@@ -60,6 +60,8 @@ static ytn_status upload(ytn_plan_t *p) {
   put_table(buf, p->sectors_dev, o_sec);
   put_table(buf, p->tiles, o_tiles);
   put_table(buf, p->tr_out, o_tro);
+  size_t o_csj;
+  put_table(buf, p->cs_jobs, o_csj);
   put_table(buf, p->tr_contrib, o_trc);
   size_t o_vdp, o_vdc;
   put_table(buf, p->vd_pieces, o_vdp);
@@ -87,6 +89,7 @@ static ytn_status upload(ytn_plan_t *p) {
   p->d_sectors = reinterpret_cast<const SectorDev *>(d + o_sec);
   p->d_tiles = reinterpret_cast<const GemmTile *>(d + o_tiles);
   p->d_tr_out = reinterpret_cast<const TraceOut *>(d + o_tro);
+  p->d_cs_jobs = reinterpret_cast<const CScatterJob *>(d + o_csj);
   p->d_tr_contrib = reinterpret_cast<const TraceContrib *>(d + o_trc);
   p->d_vd_pieces = reinterpret_cast<const VdotPiece *>(d + o_vdp);
   p->d_vd_chunks = reinterpret_cast<const VdotChunk *>(d + o_vdc);
@@ -349,6 +352,9 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
             st = plan_unfuse(p, A, op->naxes, op->axa, err);
           }
           break;
+        case YTN_OP_CONJ:
+          st = plan_conj(p, A, err);
+          break;
         case YTN_OP_SWAP_GATE:
           st = plan_swap_gate(p, A, op->ngroups, op->group_size, op->order, op->fermionic, err);
           break;
@@ -434,7 +440,7 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
   if (!p || !bytes) return fail(YTN_E_INVALID, "null argument");
   *bytes = 0;
   if (p->kind == Kind::Vdot) {
-    *bytes = align256(p->vd_chunks.size() * sizeof(double));
+    *bytes = align256(p->vd_chunks.size() * sizeof(double) * p->cw);
     return YTN_OK;
   }
   if (p->kind != Kind::Tensordot) return YTN_OK;
@@ -507,7 +513,10 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
   }
   {
     PhaseTimer t(p->ctx, YTN_PHASE_SCATTER, st);
-    e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, wc, c, st);
+    if (p->ca * p->cb > 1)
+      e = launch_cscatter(p->d_cs_jobs, (int64_t)p->cs_jobs.size(), wc, c, st);
+    else
+      e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, wc, c, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "scatter C");
   return YTN_OK;
@@ -638,7 +647,8 @@ static ytn_status run_move(ytn_plan_t *p, Kind k, const double *a, double *out, 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   note_capture(p, st);
   cudaError_t e;
-  if (p->zero_out && (e = cudaMemsetAsync(out, 0, (size_t)p->out.size * 8, st)) != cudaSuccess)
+  const size_t elem_bytes = p->out.dtype == YTN_COMPLEX128 ? 16 : 8;
+  if (p->zero_out && (e = cudaMemsetAsync(out, 0, (size_t)p->out.size * elem_bytes, st)) != cudaSuccess)
     return cuda_fail(e, "memset output");
   PhaseTimer t(p->ctx, YTN_PHASE_MOVE, st);
   if (k == Kind::Trace) {
@@ -668,13 +678,17 @@ ytn_status ytn_swap_gate(ytn_plan_t *p, const double *a, double *out, ytn_stream
   return run_move(p, Kind::Swap, a, out, stream, "swap-gate");
 }
 
+ytn_status ytn_conj(ytn_plan_t *p, const double *a, double *out, ytn_stream stream) {
+  return run_move(p, Kind::Conj, a, out, stream, "conj");
+}
+
 ytn_status ytn_vdot(ytn_plan_t *p, const double *a, const double *b, double *out, void *workspace,
                     size_t workspace_bytes, ytn_stream stream) {
   if (!p) return fail(YTN_E_INVALID, "null plan");
   if (p->kind != Kind::Vdot) return fail(YTN_E_INVALID, "plan is not a scalar-product plan");
   if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
   if ((p->a_size && !a) || (p->b_size && !b) || !out) return fail(YTN_E_INVALID, "null data buffer");
-  const size_t need = align256(p->vd_chunks.size() * sizeof(double));
+  const size_t need = align256(p->vd_chunks.size() * sizeof(double) * p->cw);
   if (need && (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)))
     return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
   DeviceGuard g(p->ctx->device);
@@ -691,7 +705,7 @@ ytn_status ytn_vdot(ytn_plan_t *p, const double *a, const double *b, double *out
   {
     PhaseTimer t(p->ctx, YTN_PHASE_REDUCE, st);
     e = launch_vdot(p->d_vd_chunks, (int64_t)p->vd_chunks.size(), p->d_vd_pieces, a, b,
-                    static_cast<double *>(workspace), out, st);
+                    static_cast<double *>(workspace), out, p->cw == 2, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "scalar product");
   return YTN_OK;

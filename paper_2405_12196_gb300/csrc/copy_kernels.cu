@@ -216,7 +216,40 @@ __global__ void __launch_bounds__(128) trace_kernel(const TraceOut *__restrict__
   }
 }
 
+// Scatter-combine of a complex product: the doubled real C_q holds the four
+// real products in quadrants; one CTA per C block writes re = P00 - P11 and
+// im = P01 + P10 (absent quadrants, from a real operand, count as zero) as
+// interleaved complex elements. Reads follow the block's innermost dim along a
+// row of C_q; the writes are consecutive 16-byte pairs.
+__global__ void __launch_bounds__(256) cscatter_kernel(const CScatterJob *__restrict__ jobs,
+                                                       const double *__restrict__ P, double *__restrict__ C) {
+  const CScatterJob J = jobs[blockIdx.x];
+  double2 *out = reinterpret_cast<double2 *>(C) + J.dst;
+  for (int e = threadIdx.x; e < J.n; e += blockDim.x) {
+    int r = e;
+    int64_t so = J.src;
+    for (int i = J.nd - 1; i >= 0; i--) {
+      const int x = r % J.ext[i];
+      r /= J.ext[i];
+      so += (int64_t)x * J.sstr[i];
+    }
+    double re = P[so], im = 0.0;
+    if (J.q11 >= 0) re -= P[so + J.q11];
+    if (J.q01 >= 0) im += P[so + J.q01];
+    if (J.q10 >= 0) im += P[so + J.q10];
+    out[e] = make_double2(re, im);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_cscatter(const CScatterJob *jobs, int64_t njobs, const double *wc, double *c,
+                            cudaStream_t stream) {
+  if (njobs <= 0) return cudaSuccess;
+  if (njobs > INT32_MAX) return cudaErrorInvalidValue;
+  cscatter_kernel<<<(unsigned)njobs, 256, 0, stream>>>(jobs, wc, c);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_copy(const CopyJob *jobs, const CopyItem *items, int64_t nitems, const double *src,
                         double *dst, cudaStream_t stream) {

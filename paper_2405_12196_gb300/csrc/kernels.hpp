@@ -18,7 +18,7 @@ cudaError_t launch_trace(const TraceOut *outs, int64_t nout, const TraceContrib 
 // Scalar product <A, B> over the planned common elements (FP64, deterministic):
 // one partial per chunk into `partials`, then their fixed-order sum into out[0].
 cudaError_t launch_vdot(const VdotChunk *chunks, int64_t nchunks, const VdotPiece *pieces, const double *a,
-                        const double *b, double *partials, double *out, cudaStream_t stream);
+                        const double *b, double *partials, double *out, bool complex_data, cudaStream_t stream);
 
 // Grouped FP64 GEMM (DMMA) over 64x64 tiles: C_q = A_q B_q.
 cudaError_t launch_gemm_fp64(const SectorDev *sectors, const GemmTile *tiles, int64_t ntiles,
@@ -32,6 +32,11 @@ cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_item
 
 // Shared-memory opt-in of the split-precision GEMM kernels (once per device).
 cudaError_t configure_split_gemm();
+
+// Scatter-combine of complex products: C blocks (interleaved complex) from the
+// quadrants of the doubled real C_q (one CTA per job).
+cudaError_t launch_cscatter(const CScatterJob *jobs, int64_t njobs, const double *wc, double *c,
+                            cudaStream_t stream);
 
 // Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output C_q.
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,

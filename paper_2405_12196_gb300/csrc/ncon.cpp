@@ -65,7 +65,7 @@ static ytn_status plan_step(ytn_ncon_t *nc, ytn_op &op, StepKind kind, int in0, 
   nc->flops += info.useful_flops;
   const ytn_struct *o = ytn_plan_output(p);
   nc->slot_off.push_back(nc->slots_bytes);
-  nc->slots_bytes += align256((size_t)o->size * sizeof(double));
+  nc->slots_bytes += align256((size_t)o->size * sizeof(double) * (o->dtype == YTN_COMPLEX128 ? 2 : 1));
   const int out = nc->n + (int)nc->slot_off.size() - 1;
   nc->steps.push_back({kind, p, in0, in1, out});
   res.id = out;

@@ -536,6 +536,7 @@ static ytn_status unfuse_view(const Tensor &T, const std::vector<int> &legs, Ten
   if (rank > YTN_MAX_RANK) { err = "unfused view exceeds the maximum rank"; return YTN_E_UNSUPPORTED; }
   const int nsym = T.nsym;
   V = Tensor();
+  V.dtype = T.dtype;
   V.nsym = nsym;
   std::memcpy(V.mod, T.mod, sizeof(V.mod));
   std::memcpy(V.n, T.n, sizeof(V.n));
@@ -715,9 +716,19 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   for (int i = 0; i < B.rank; i++)
     if (std::find(axb.begin(), axb.end(), i) == axb.end()) freeB.push_back(i);
 
+  // Complex operands: each becomes a real sector matrix twice as tall (A: rows of
+  // the real parts, then of the imaginary parts) or twice as wide (B: columns of
+  // real, then imaginary parts), so that one real grouped GEMM gives the four
+  // products re.re, re.im, im.re, im.im as quadrants of C_q; the scatter combines
+  // them into complex C (re = P00 - P11, im = P01 + P10).
+  const int ca = A.dtype == YTN_COMPLEX128 ? 2 : 1, cb = B.dtype == YTN_COMPLEX128 ? 2 : 1;
+  p->ca = ca;
+  p->cb = cb;
+
   // Output tensor: A's free legs then B's; n_C = n_A + n_B.
   Tensor &C = p->out;
   C = Tensor();
+  C.dtype = ca * cb > 1 ? YTN_COMPLEX128 : YTN_REAL64;
   C.nsym = nsym;
   std::memcpy(C.mod, A.mod, sizeof(C.mod));
   C.rank = (int)(freeA.size() + freeB.size());
@@ -769,7 +780,7 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
     }
     flops += 2.0 * si * (double)kx * sj;
   }
-  p->flops = flops;
+  p->flops = flops * ca * cb;
 
   // Sector geometry: rows, K and columns in ascending charge order.
   struct SG {
@@ -823,21 +834,22 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   int64_t a_cov = 0, b_cov = 0;
   p->max_m = p->max_n = p->max_k = 0;
   for (auto &g : geo) {
-    HostSector h;
-    h.M = g.M; h.N = g.N; h.K = g.K;
+    HostSector h;   // the GEMM's (real, possibly doubled) geometry
+    h.M = ca * g.M; h.N = cb * g.N; h.K = g.K;
+    if (h.M > INT32_MAX || h.N > INT32_MAX) { err = "sector too large"; return YTN_E_UNSUPPORTED; }
     h.a_off = ao; h.b_off = bo; h.c_off = co;
-    ao += align32(g.M * g.K);
-    bo += align32(g.K * g.N);
-    co += align32(g.M * g.N);
+    ao += align32(h.M * h.K);
+    bo += align32(h.K * h.N);
+    co += align32(h.M * h.N);
     p->sectors.push_back(h);
     SectorDev d{};
     d.a_off = h.a_off; d.b_off = h.b_off; d.c_off = h.c_off;
-    d.M = (int32_t)g.M; d.N = (int32_t)g.N; d.K = (int32_t)g.K;
+    d.M = (int32_t)h.M; d.N = (int32_t)h.N; d.K = (int32_t)h.K;
     d.a_kmajor = p->a_kmajor; d.b_kmajor = p->b_kmajor;
     p->sectors_dev.push_back(d);
-    p->max_m = std::max(p->max_m, g.M);
-    p->max_n = std::max(p->max_n, g.N);
-    p->max_k = std::max(p->max_k, g.K);
+    p->max_m = std::max(p->max_m, h.M);
+    p->max_n = std::max(p->max_n, h.N);
+    p->max_k = std::max(p->max_k, h.K);
   }
   p->a_elems = ao;
   p->b_elems = bo;
@@ -861,7 +873,8 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
           auto it = offmap.find(fk);
           if (it == offmap.end()) continue;
           const int64_t foff = it->second, xoff = xk.second;
-          const int64_t F = isA ? g.M : g.N;  // free extent of the sector
+          const int cw = isA ? ca : cb;         // 2: complex operand
+          const int64_t F = isA ? h.M : h.N;    // free extent of the (doubled) sector matrix
           const int64_t base = isA ? h.a_off : h.b_off;
           auto st = block_strides(T, b);
           // strides of the free and contracted sub-indices inside their fused index
@@ -883,7 +896,16 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
             for (size_t i = 0; i < freeL.size(); i++) dims.push_back({T.dim(b, freeL[i]), st[freeL[i]], fstr[i]});
             dst_off = base + xoff * ldk + foff;
           }
-          ytn_status s = add_copy(p, dims, T.off[b], dst_off, err);
+          int64_t src_off = T.off[b];
+          if (cw == 2) {
+            // interleaved (re, im) source: element strides double; the component
+            // selects the row block (A) or column block (B) of the sector matrix
+            for (auto &d : dims) d.sst *= 2;
+            src_off *= 2;
+            const int64_t half = isA ? g.M : g.N;
+            dims.push_back({2, 1, kmajor ? half * g.K : half});
+          }
+          ytn_status s = add_copy(p, dims, src_off, dst_off, err);
           if (s != YTN_OK) return s;
           covered += T.elems(b);
           p->moved += T.elems(b);
@@ -957,7 +979,38 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   std::vector<int64_t> off_of_id;
   finalize_out(C, outb, off_of_id);
   // Scatter C: block (I, J) = C_q[row_off(I) + i, col_off(J) + j], row-major per leg.
-  for (size_t id = 0; id < srcs.size(); id++) {
+  p->cs_jobs.clear();
+  for (size_t id = 0; id < srcs.size() && ca * cb > 1; id++) {
+    // complex product: combine the quadrants of the doubled C_q
+    const Src &sr = srcs[id];
+    const HostSector &h = p->sectors[sr.sector];
+    const SG &g = geo[sr.sector];
+    std::vector<int64_t> cd;
+    for (int l : freeA) cd.push_back(A.dim(sr.a_blk, l));
+    for (int l : freeB) cd.push_back(B.dim(sr.b_blk, l));
+    if ((int)cd.size() > kMaxCopyDims) { err = "output block with more than 8 dims"; return YTN_E_UNSUPPORTED; }
+    CScatterJob J{};
+    J.src = h.c_off + sr.roff * h.N + sr.coff;
+    J.dst = off_of_id[id];
+    J.q01 = cb == 2 ? g.N : -1;
+    J.q10 = ca == 2 ? g.M * h.N : -1;
+    J.q11 = (ca == 2 && cb == 2) ? g.M * h.N + g.N : -1;
+    J.nd = (int32_t)cd.size();
+    int64_t acc = 1;
+    for (int i = (int)freeA.size() - 1; i >= 0; i--) { J.sstr[i] = acc * h.N; acc *= cd[i]; }
+    acc = 1;
+    for (int i = (int)cd.size() - 1; i >= (int)freeA.size(); i--) { J.sstr[i] = acc; acc *= cd[i]; }
+    int64_t n = 1;
+    for (size_t i = 0; i < cd.size(); i++) {
+      J.ext[i] = (int32_t)cd[i];
+      n *= cd[i];
+    }
+    if (n > INT32_MAX) { err = "output block too large"; return YTN_E_UNSUPPORTED; }
+    J.n = (int32_t)n;
+    p->cs_jobs.push_back(J);
+    p->moved += n;
+  }
+  for (size_t id = 0; id < srcs.size() && ca * cb == 1; id++) {
     const Src &sr = srcs[id];
     const HostSector &h = p->sectors[sr.sector];
     std::vector<Dim> dims;
@@ -990,7 +1043,7 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   // padded area of 64 x 64 tiles (small or thin M, N), else 64.
   p->tiles.clear();
   for (size_t si = 0; si < geo.size(); si++) {
-    const int64_t M = geo[si].M, N = geo[si].N;
+    const int64_t M = p->sectors[si].M, N = p->sectors[si].N;
     const int64_t a64 = ((M + 63) / 64) * ((N + 63) / 64) * 4096, a32 = ((M + 31) / 32) * ((N + 31) / 32) * 1024;
     const int T = 10 * a32 <= 6 * a64 ? 32 : 64;
     const int64_t mt = (M + T - 1) / T, nt = (N + T - 1) / T;
@@ -1505,6 +1558,10 @@ ytn_status plan_vdot(ytn_plan_t *p, const Tensor &A, const Tensor &B, std::strin
       return YTN_E_FUSION_MISMATCH;
     }
   }
+  if (A.dtype != B.dtype) { err = "scalar product of a real and a complex tensor"; return YTN_E_UNSUPPORTED; }
+  // complex: runs of doubles (pairs), <A, B> = sum conj(a) b
+  const int cw = A.dtype == YTN_COMPLEX128 ? 2 : 1;
+  p->cw = cw;
   // common blocks: both block lists are in canonical (ascending) order
   const size_t w = (size_t)A.rank * A.nsym;
   auto key_of = [w](const Tensor &T, int64_t b) { return Key(T.t.begin() + b * w, T.t.begin() + (b + 1) * w); };
@@ -1515,9 +1572,9 @@ ytn_status plan_vdot(ytn_plan_t *p, const Tensor &A, const Tensor &B, std::strin
     const Key ka = key_of(A, i), kb = key_of(B, j);
     if (ka < kb) { i++; continue; }
     if (kb < ka) { j++; continue; }
-    const int64_t n = A.elems(i);
-    for (int64_t e = 0; e < n; e += kVdotPiece)
-      p->vd_pieces.push_back({A.off[i] + e, B.off[j] + e, (int32_t)std::min<int64_t>(kVdotPiece, n - e), 0});
+    const int64_t n = A.elems(i), nd = cw * n;
+    for (int64_t e = 0; e < nd; e += kVdotPiece)
+      p->vd_pieces.push_back({cw * A.off[i] + e, cw * B.off[j] + e, (int32_t)std::min<int64_t>(kVdotPiece, nd - e), 0});
     common += n;
     i++;
     j++;
@@ -1537,10 +1594,11 @@ ytn_status plan_vdot(ytn_plan_t *p, const Tensor &A, const Tensor &B, std::strin
   C.nsym = A.nsym;
   for (int c = 0; c < A.nsym; c++) C.mod[c] = A.mod[c];
   C.rank = 0;
+  C.dtype = A.dtype;
   C.nblocks = 1;
   C.off.push_back(0);
   C.size = 1;
-  p->flops = 2.0 * (double)common;
+  p->flops = 2.0 * (double)common * (cw == 2 ? 4 : 1);
   p->moved = common;
   p->kind = Kind::Vdot;
   p->a_size = A.size;

@@ -31,29 +31,47 @@ __device__ __forceinline__ double block_sum(double v, double *ws) {
   return t;
 }
 
+// CPLX: the pieces run over interleaved (re, im) doubles, and <A, B> = sum conj(a) b:
+// re = sum over all doubles of a b; im = sum over pairs of a_re b_im - a_im b_re.
+template <bool CPLX>
 __global__ void __launch_bounds__(kThreads) vdot_partial_kernel(const VdotChunk *__restrict__ chunks,
                                                                 const VdotPiece *__restrict__ pieces,
                                                                 const double *a, const double *b,
                                                                 double *__restrict__ partials) {
   __shared__ double ws[kThreads / 32];
   const VdotChunk ch = chunks[blockIdx.x];
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, t0 = 0.0, t1 = 0.0;
   for (int k = ch.first; k < ch.first + ch.count; k++) {
     const VdotPiece pc = pieces[k];
     const double *pa = a + pc.a_off, *pb = b + pc.b_off;
     int e = threadIdx.x;
-    for (; e + 3 * kThreads < pc.len; e += 4 * kThreads) {
-      const double a0 = pa[e], a1 = pa[e + kThreads], a2 = pa[e + 2 * kThreads], a3 = pa[e + 3 * kThreads];
-      const double b0 = pb[e], b1 = pb[e + kThreads], b2 = pb[e + 2 * kThreads], b3 = pb[e + 3 * kThreads];
-      s0 = fma(a0, b0, s0);
-      s1 = fma(a1, b1, s1);
-      s2 = fma(a2, b2, s2);
-      s3 = fma(a3, b3, s3);
+    if (!CPLX) {
+      for (; e + 3 * kThreads < pc.len; e += 4 * kThreads) {
+        const double a0 = pa[e], a1 = pa[e + kThreads], a2 = pa[e + 2 * kThreads], a3 = pa[e + 3 * kThreads];
+        const double b0 = pb[e], b1 = pb[e + kThreads], b2 = pb[e + 2 * kThreads], b3 = pb[e + 3 * kThreads];
+        s0 = fma(a0, b0, s0);
+        s1 = fma(a1, b1, s1);
+        s2 = fma(a2, b2, s2);
+        s3 = fma(a3, b3, s3);
+      }
+      for (; e < pc.len; e += kThreads) s0 = fma(pa[e], pb[e], s0);
+    } else {
+      // thread e takes one double; its pair's other half comes from the same cache line
+      for (; e < pc.len; e += kThreads) {
+        const double x = pa[e], y = pb[e], z = pb[e ^ 1];
+        s0 = fma(x, y, s0);
+        if (e & 1) t1 = fma(x, z, t1);   // a_im b_re
+        else t0 = fma(x, z, t0);         // a_re b_im
+      }
     }
-    for (; e < pc.len; e += kThreads) s0 = fma(pa[e], pb[e], s0);
   }
   const double t = block_sum((s0 + s1) + (s2 + s3), ws);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (CPLX) {
+    __syncthreads();
+    const double u = block_sum(t0 - t1, ws);
+    if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = u;
+  }
 }
 
 __global__ void __launch_bounds__(kFinalThreads) vdot_final_kernel(const double *__restrict__ partials, int n,
@@ -68,12 +86,18 @@ __global__ void __launch_bounds__(kFinalThreads) vdot_final_kernel(const double 
 }  // namespace
 
 cudaError_t launch_vdot(const VdotChunk *chunks, int64_t nchunks, const VdotPiece *pieces, const double *a,
-                        const double *b, double *partials, double *out, cudaStream_t stream) {
-  if (nchunks > INT32_MAX) return cudaErrorInvalidValue;
-  if (nchunks > 0) vdot_partial_kernel<<<(unsigned)nchunks, kThreads, 0, stream>>>(chunks, pieces, a, b, partials);
+                        const double *b, double *partials, double *out, bool complex_data, cudaStream_t stream) {
+  if (nchunks > INT32_MAX / 2) return cudaErrorInvalidValue;
+  if (nchunks > 0) {
+    if (complex_data)
+      vdot_partial_kernel<true><<<(unsigned)nchunks, kThreads, 0, stream>>>(chunks, pieces, a, b, partials);
+    else
+      vdot_partial_kernel<false><<<(unsigned)nchunks, kThreads, 0, stream>>>(chunks, pieces, a, b, partials);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   vdot_final_kernel<<<1, kFinalThreads, 0, stream>>>(partials, (int)nchunks, out);
+  if (complex_data) vdot_final_kernel<<<1, kFinalThreads, 0, stream>>>(partials + nchunks, (int)nchunks, out + 1);
   return cudaGetLastError();
 }
 

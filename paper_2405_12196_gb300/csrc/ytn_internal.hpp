@@ -156,6 +156,19 @@ struct SplitTile {
   int32_t sector, mt, nt, pad;
 };
 
+// Scatter of a complex product: one C block from the quadrants of the doubled
+// C_q (P = [[re.re, re.im], [im.re, im.im]] in rows x columns): element e of the
+// block (row-major over its nd dims) reads P at src + sum idx_i sstr_i plus the
+// quadrant offsets q01, q10, q11 (-1: quadrant absent, a real operand), and
+// writes re = P00 - P11, im = P01 + P10 at complex element dst + e.
+struct CScatterJob {
+  int64_t src, dst;
+  int64_t q01, q10, q11;
+  int32_t nd, n;
+  int32_t ext[kMaxCopyDims];
+  int64_t sstr[kMaxCopyDims];
+};
+
 // ----------------------------------------------------------------------------
 // Host-side structures
 // ----------------------------------------------------------------------------
@@ -237,6 +250,7 @@ struct ytn_plan_s {
 
   // input sizes and output structure (owned storage + ABI view)
   int64_t a_size = 0, b_size = 0;
+  int ca = 1, cb = 1;   // tensordot: 2 when A (B) is complex (doubled sector matrices)
   // doubles per element of the copy jobs that add_copy makes: 2 for complex
   // tensors moved whole (fuse, unfuse, swap gate, conj), else 1
   int cw = 1;
@@ -265,6 +279,7 @@ struct ytn_plan_s {
 
   // trace
   std::vector<ytn::TraceOut> tr_out;
+  std::vector<ytn::CScatterJob> cs_jobs;   // complex tensordot: the scatter-combine
   std::vector<ytn::TraceContrib> tr_contrib;
   std::vector<ytn::VdotPiece> vd_pieces;
   std::vector<ytn::VdotChunk> vd_chunks;
@@ -277,6 +292,7 @@ struct ytn_plan_s {
   const ytn::SectorDev *d_sectors = nullptr;
   const ytn::GemmTile *d_tiles = nullptr;
   const ytn::TraceOut *d_tr_out = nullptr;
+  const ytn::CScatterJob *d_cs_jobs = nullptr;
   const ytn::TraceContrib *d_tr_contrib = nullptr;
   const ytn::VdotPiece *d_vd_pieces = nullptr;
   const ytn::VdotChunk *d_vd_chunks = nullptr;

@@ -32,7 +32,8 @@ STATUS = {
 YTN_FP64 = 0
 YTN_SPLIT_BF16 = 1
 YTN_AUTO = 2
-YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE, YTN_OP_VDOT, YTN_OP_SWAP_GATE = 1, 2, 3, 4, 5, 6
+YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE, YTN_OP_VDOT, YTN_OP_SWAP_GATE, YTN_OP_CONJ = \
+    1, 2, 3, 4, 5, 6, 7
 YTN_FERMIONIC_EXPLICIT = 1 << 31
 YTN_REAL64, YTN_COMPLEX128 = 0, 1
 
@@ -110,6 +111,7 @@ SYMBOLS = {
     "ytn_unfuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_swap_gate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ytn_conj": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_ncon_plan": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.POINTER(ytn_struct)), C.POINTER(C.c_int32),
                                 C.POINTER(C.c_void_p)]),
     "ytn_ncon_output": (C.POINTER(ytn_struct), [C.c_void_p]),
@@ -428,6 +430,11 @@ def ytn_trace(plan, a, out, stream=None):
 def ytn_swap_gate(plan, a, out, stream=None):
     """out = swap_gate(a) for a SWAP_GATE plan; ``out`` may be ``a`` (in place)."""
     _check(_lib.ytn_swap_gate(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ytn_conj(plan, a, out, stream=None):
+    """out = conj(a) for a CONJ plan; ``out`` may be ``a`` (in place)."""
+    _check(_lib.ytn_conj(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
 
 
 def ytn_vdot(plan, a, b, out, workspace=None, workspace_bytes=None, stream=None):

@@ -54,6 +54,7 @@ def run_move(ctx, kind, A, **kw):
 
 
 def same_structure(rec, ref):
+    assert rec.get("dtype", "f64") == ref.get("dtype", "f64")
     assert tuple(rec["sig"]) == tuple(ref["sig"])
     assert tuple(rec["n"]) == tuple(ref["n"])
     np.testing.assert_array_equal(rec["t"], np.asarray(ref["t"]).reshape(rec["t"].shape))
@@ -62,8 +63,8 @@ def same_structure(rec, ref):
 
 
 def rel_frobenius(got, want):
-    got = np.asarray(got, dtype=np.float64)
-    want = np.asarray(want, dtype=np.float64)
+    got = np.asarray(got)     # real or complex
+    want = np.asarray(want)
     nw = np.linalg.norm(want)
     if nw == 0.0:
         return float(np.linalg.norm(got))

@@ -39,6 +39,7 @@ def hctx():
 
 def same_structure(rec, ref):
     """Compare a library output record with an oracle record, bit for bit."""
+    assert rec.get("dtype", "f64") == ref.get("dtype", "f64")
     assert tuple(rec["mods"]) == tuple(ref["mods"])
     assert tuple(rec["sig"]) == tuple(ref["sig"])
     assert tuple(rec["n"]) == tuple(ref["n"])
@@ -291,3 +292,41 @@ def test_fusion_mismatch_errors_as_status_codes(hctx):
         with pytest.raises(ytn.YtnError) as ei:
             ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, O.to_record(A), O.to_record(other), (0,), (0,))
         assert ei.value.name == name
+
+
+@pytest.mark.parametrize("dts", [("c128", "c128"), ("c128", "f64"), ("f64", "c128")])
+@pytest.mark.parametrize("case", range(6))
+def test_complex_plans_match_the_oracle(hctx, dts, case):
+    """Complex operands (real and complex mixed too): tensordot's structure and
+    element type equal the oracle's; its FLOPs count the real products of the
+    doubled sector matrices; fuse, unfuse, trace, swap gate and conj keep the
+    complex element type."""
+    rng = np.random.default_rng(12000 + 17 * case + len(dts[0]) + 3 * len(dts[1]))
+    mods = [(0,), (2,), (0, 0)][case % 3]
+    A, _, axa, axb, legsA, legsB = random_pair(rng, mods, 3, 3, 1 + case % 2, dtype=dts[0])
+    B = W.random_tensor(mods, legsB, (0,) * len(mods), 77 + case, dtype=dts[1])
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    oA, oB = O.from_record(A), O.from_record(B)
+    same_structure(plan.out, O.to_record(O.tensordot(oA, oB, axa, axb)))
+    mult = (2 if dts[0] == "c128" else 1) * (2 if dts[1] == "c128" else 1)
+    assert plan.info["useful_flops"] == mult * O.useful_flops(oA, oB, axa, axb)
+    if dts[0] == "c128":
+        same_structure(ytn.ytn_plan(hctx, ytn.YTN_OP_FUSE, A, groups=((0, 1), (2,))).out,
+                       O.to_record(O.fuse(oA, ((0, 1), (2,)))))
+        same_structure(ytn.ytn_plan(hctx, ytn.YTN_OP_CONJ, A).out, O.to_record(O.conj(oA)))
+        same_structure(ytn.ytn_plan(hctx, ytn.YTN_OP_SWAP_GATE, A, groups=((0,), (1, 2))).out,
+                       O.to_record(O.swap_gate(oA, (0,), (1, 2))))
+
+
+def test_complex_vdot_and_trace_planning(hctx):
+    l = W.Leg(1, [(0,), (1,)], [2, 3])
+    A = W.random_tensor((0,), [l, l.conj(), l], (1,), 1, dtype="c128")
+    B = W.random_tensor((0,), [l, l.conj(), l], (1,), 2, dtype="c128")
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_VDOT, A, B)
+    assert plan.out.get("dtype") == "c128" and plan.info["moved_elems"] == A["data"].size
+    assert ytn.ytn_workspace_size(plan) == 256
+    with pytest.raises(ytn.YtnError) as ei:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_VDOT, A, W.random_tensor((0,), [l, l.conj(), l], (1,), 3))
+    assert ei.value.name == "YTN_E_UNSUPPORTED"
+    tr = ytn.ytn_plan(hctx, ytn.YTN_OP_TRACE, A, axa=(0,), axb=(1,))
+    same_structure(tr.out, O.to_record(O.trace(O.from_record(A), (0,), (1,))))
