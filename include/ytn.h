@@ -343,6 +343,14 @@ ytn_status ytn_ctx_set_gemm_sms(ytn_ctx *ctx, int nsms);
  * tensor). Release with ytn_ncon_release. */
 ytn_status ytn_ncon_plan(ytn_ctx *ctx, int32_t ntensors, const ytn_struct *const *tensors,
                          const int32_t *labels, ytn_ncon_t **out);
+/* The same network from einsum subscripts (Sec. II.B: einsum and ncon differ
+ * only by syntax), e.g. "abc,cd->adb": one letter per leg; a letter on two legs
+ * is summed (twice on one tensor: a trace), a letter on one leg is an output leg,
+ * in the order after "->" (alphabetical without it). Summed letters become ncon
+ * labels 1, 2, ... in the order of their first appearance. Errors: YTN_E_INVALID
+ * (subscripts), then as ytn_ncon_plan. */
+ytn_status ytn_einsum_plan(ytn_ctx *ctx, const char *subscripts, int32_t ntensors,
+                           const ytn_struct *const *tensors, ytn_ncon_t **out);
 /* Output structure (library-owned, valid until the network is released). */
 const ytn_struct *ytn_ncon_output(const ytn_ncon_t *nc);
 /* Useful FLOPs of all contractions and the number of library calls. */

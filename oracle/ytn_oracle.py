@@ -44,7 +44,7 @@ __all__ = [
     "OTensor", "OracleError", "SignatureError", "DimMismatchError", "FusionMismatchError",
     "ChargeError", "InvalidError", "UnsupportedError",
     "from_record", "to_record", "conj", "tensordot", "fuse", "unfuse", "trace",
-    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon",
+    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon", "einsum",
 ]
 
 
@@ -603,6 +603,38 @@ def ncon(tensors, labels):
     T, lab = items[0]
     order = [lab.index(-k) for k in range(1, len(lab) + 1)]
     return fuse(T, [(a,) for a in order]) if T.rank else OTensor(T.mods, (), T.n, dict(T.blocks), dtype=T.dtype)
+
+
+def einsum(subscripts, *tensors):
+    """einsum front end (Sec. II.B: einsum and ncon differ only by syntax).
+
+    ``subscripts`` like "abc,cd->adb": one letter per leg. A letter on two legs is
+    summed (twice on one tensor: a trace); a letter on one leg is an output leg. The
+    output order is the part after "->", or, without it, the once-used letters in
+    alphabetical order. Translation to ncon labels: summed letters get 1, 2, ... in
+    the order of their first appearance, output letters -1, -2, ... in output order."""
+    s = subscripts.replace(" ", "")
+    lhs, arrow, rhs = s.partition("->")
+    ins = lhs.split(",")
+    if len(ins) != len(tensors) or not all(x.isalpha() for x in "".join(ins)):
+        raise InvalidError("one letter group per tensor")
+    count = {}
+    for grp in ins:
+        for c in grp:
+            count[c] = count.get(c, 0) + 1
+    if any(v > 2 for v in count.values()):
+        raise InvalidError("a letter on more than two legs")
+    out = rhs if arrow else "".join(sorted(c for c, v in count.items() if v == 1))
+    if sorted(out) != sorted(c for c, v in count.items() if v == 1) or len(set(out)) != len(out):
+        raise InvalidError("the output must list every once-used letter once")
+    lab = {c: -(k + 1) for k, c in enumerate(out)}
+    nxt = 1
+    for grp in ins:
+        for c in grp:
+            if c not in lab:
+                lab[c] = nxt
+                nxt += 1
+    return ncon(list(tensors), [[lab[c] for c in grp] for grp in ins])
 
 
 # ------------------------------------------------------------------ fermionic swap gate

@@ -226,6 +226,56 @@ extern "C" ytn_status ytn_ncon_plan(ytn_ctx *ctx, int32_t ntensors, const ytn_st
   return YTN_OK;
 }
 
+// einsum subscripts -> ncon labels: a letter on two legs is summed (numbered 1, 2,
+// ... by first appearance), a letter on one leg is an output leg (-1, -2, ... in
+// the order after "->", or alphabetical without it).
+extern "C" ytn_status ytn_einsum_plan(ytn_ctx *ctx, const char *subscripts, int32_t ntensors,
+                                      const ytn_struct *const *tensors, ytn_ncon_t **out) {
+  if (!subscripts || !tensors || ntensors < 1) return invalid("null argument or empty network");
+  std::string s;
+  for (const char *c = subscripts; *c; c++)
+    if (*c != ' ') s += *c;
+  const size_t arrow = s.find("->");
+  const std::string lhs = s.substr(0, arrow);
+  std::vector<std::string> ins(1);
+  for (char c : lhs) {
+    if (c == ',') ins.emplace_back();
+    else if ((c >= 'a' && c <= 'z') || (c >= 'A' && c <= 'Z')) ins.back() += c;
+    else return invalid("einsum subscripts: letters, commas and one arrow only");
+  }
+  if ((int)ins.size() != ntensors) return invalid("einsum subscripts: one letter group per tensor");
+  std::map<char, int> count;
+  for (auto &g : ins)
+    for (char c : g) count[c]++;
+  std::string outl;
+  if (arrow != std::string::npos) {
+    outl = s.substr(arrow + 2);
+  } else {
+    for (auto &kv : count)
+      if (kv.second == 1) outl += kv.first;
+  }
+  std::set<char> once, seen;
+  for (auto &kv : count) {
+    if (kv.second > 2) return invalid("einsum subscripts: a letter on more than two legs");
+    if (kv.second == 1) once.insert(kv.first);
+  }
+  for (char c : outl)
+    if (!once.count(c) || !seen.insert(c).second) return invalid("einsum output must list every once-used letter once");
+  if (seen.size() != once.size()) return invalid("einsum output must list every once-used letter once");
+  std::map<char, int> lab;
+  for (size_t k = 0; k < outl.size(); k++) lab[outl[k]] = -(int)(k + 1);
+  int next = 1;
+  std::vector<int32_t> labels;
+  for (int i = 0; i < ntensors; i++) {
+    if (!tensors[i] || tensors[i]->rank != (int)ins[i].size()) return invalid("einsum subscripts: one letter per leg");
+    for (char c : ins[i]) {
+      if (!lab.count(c)) lab[c] = next++;
+      labels.push_back(lab[c]);
+    }
+  }
+  return ytn_ncon_plan(ctx, ntensors, tensors, labels.data(), out);
+}
+
 extern "C" const ytn_struct *ytn_ncon_output(const ytn_ncon_t *nc) { return nc ? nc->out : nullptr; }
 
 extern "C" ytn_status ytn_ncon_info(const ytn_ncon_t *nc, double *useful_flops, int32_t *ncalls) {

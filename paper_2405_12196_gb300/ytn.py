@@ -114,6 +114,8 @@ SYMBOLS = {
     "ytn_conj": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_ncon_plan": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.POINTER(ytn_struct)), C.POINTER(C.c_int32),
                                 C.POINTER(C.c_void_p)]),
+    "ytn_einsum_plan": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int32, C.POINTER(C.POINTER(ytn_struct)),
+                                  C.POINTER(C.c_void_p)]),
     "ytn_ncon_output": (C.POINTER(ytn_struct), [C.c_void_p]),
     "ytn_ncon_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "ytn_ncon_workspace_size": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
@@ -392,6 +394,15 @@ def ytn_ncon_plan(ctx, records, labels):
     _check(_lib.ytn_ncon_plan(ctx.handle, len(structs), arr, flat.ctypes.data_as(C.POINTER(C.c_int32)),
                               C.byref(h)))
     return Ncon(ctx, h.value, (structs, arr, flat))
+
+
+def ytn_einsum_plan(ctx, subscripts, records):
+    """Plan the network of tensor ``records`` given by einsum ``subscripts``."""
+    structs = [Struct(r) for r in records]
+    arr = (C.POINTER(ytn_struct) * len(structs))(*[C.pointer(x.c) for x in structs])
+    h = C.c_void_p()
+    _check(_lib.ytn_einsum_plan(ctx.handle, subscripts.encode(), len(structs), arr, C.byref(h)))
+    return Ncon(ctx, h.value, (structs, arr))
 
 
 def ytn_ncon_workspace_size(nc, prec=YTN_FP64, rtol=0.0):

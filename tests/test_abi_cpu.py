@@ -330,3 +330,17 @@ def test_complex_vdot_and_trace_planning(hctx):
     assert ei.value.name == "YTN_E_UNSUPPORTED"
     tr = ytn.ytn_plan(hctx, ytn.YTN_OP_TRACE, A, axa=(0,), axb=(1,))
     same_structure(tr.out, O.to_record(O.trace(O.from_record(A), (0,), (1,))))
+
+
+def test_einsum_plans_equal_the_oracle(hctx):
+    from helpers import random_network
+    rng = np.random.default_rng(61)
+    for spec, kind in (("abc,bde,cef->adf", "chain"), ("abbc,cd->da", "trace"), ("ab,bc,de", "outer")):
+        _, ts, _ = random_network(rng, (0,), kind)
+        nc = ytn.ytn_einsum_plan(hctx, spec, ts)
+        same_structure(nc.out, O.to_record(O.einsum(spec, *[O.from_record(t) for t in ts])))
+    _, ts, _ = random_network(rng, (0,), "chain")
+    for bad in ("abc,bde->adf", "abc,bde,cee->a", "abc,bde,cef->ad", "abc,bde,c1f->adf"):
+        with pytest.raises(ytn.YtnError) as ei:
+            ytn.ytn_einsum_plan(hctx, bad, ts)
+        assert ei.value.name == "YTN_E_INVALID"

@@ -89,3 +89,23 @@ def test_host_inputs_and_label_errors(ctx, corner):
         with pytest.raises(ytn.YtnError) as ei:
             ytn.ytn_ncon_plan(ctx, ts, bad)
         assert ei.value.name == "YTN_E_INVALID"
+
+
+def test_einsum_front_end_gives_the_ncon_bits(ctx, corner):
+    """The enlarged corner from einsum subscripts: the same calls as the ncon labels
+    (summed letters numbered by first appearance), so the same bits."""
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    ts, labels, want = corner
+    nc = ytn.ytn_einsum_plan(ctx, "ab,bcw,xda,cdyz->wxyz", ts)
+    assert nc.info["ncalls"] == 4
+    data = [to_dev(t["data"]) for t in ts]
+    out = torch.full((nc.out["size"],), float("nan"), dtype=torch.float64, device=device())
+    ws = torch.empty(max(ytn.ytn_ncon_workspace_size(nc), 1), dtype=torch.uint8, device=device())
+    ytn.ytn_ncon(nc, data, out, workspace=ws)
+    ytn.ytn_sync(ctx)
+    rec = dict(nc.out)
+    rec["data"] = out.cpu().numpy()
+    _, ref = _run(ctx, ts, labels, ytn.YTN_FP64, 0.0)
+    np.testing.assert_array_equal(rec["data"], ref["data"])
+    check_against_oracle(rec, want)

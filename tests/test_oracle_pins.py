@@ -696,3 +696,23 @@ def test_complex_conj_vdot_fuse_trace_swap():
     tr = O.trace(T, (0,), (1,))
     dT = O.to_dense(T, [leg_map(l), leg_map(l), lm[0]])
     np.testing.assert_allclose(O.to_dense(tr, [lm[0]]), np.einsum("iik->k", dT), rtol=1e-13, atol=1e-13)
+
+
+def test_einsum_equals_numpy_einsum():
+    """einsum subscripts (Sec. II.B: einsum and ncon differ only by syntax) against
+    numpy.einsum of the dense embeddings: a chain, a trace, implicit output order."""
+    rng = np.random.default_rng(61)
+    for spec, kind in (("abc,bde,cef->adf", "chain"), ("abbc,cd->da", "trace"), ("ab,bc,de", "outer")):
+        legs, ts, labels = random_network(rng, (0,), kind)
+        C = O.einsum(spec, *[O.from_record(t) for t in ts])
+        dense = [O.to_dense(O.from_record(t), [leg_map(l) for l in lg]) for t, lg in zip(ts, legs)]
+        want = np.einsum(spec, *dense)
+        lhs = spec.split("->")[0].split(",")
+        where = {c: leg_map(legs[i][k]) for i, grp in enumerate(lhs) for k, c in enumerate(grp)}
+        out = spec.split("->")[1] if "->" in spec else "".join(sorted(c for c in where if "".join(lhs).count(c) == 1))
+        np.testing.assert_allclose(O.to_dense(C, [where[c] for c in out]), want, rtol=1e-12, atol=1e-12)
+    l = W.Leg(1, [(0,), (1,)], [2, 3])
+    A = O.from_record(W.random_tensor((0,), [l, l.conj()], (0,), 1))
+    for bad in ("aa->a", "ab,ab,ab->", "ab->abc", "a1,b"):
+        with pytest.raises(O.InvalidError):
+            O.einsum(bad, A, A) if bad.count(",") == 1 else O.einsum(bad, A)
