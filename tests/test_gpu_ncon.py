@@ -97,7 +97,7 @@ def test_einsum_front_end_gives_the_ncon_bits(ctx, corner):
     import torch
     from paper_2405_12196_gb300 import ytn
     ts, labels, want = corner
-    nc = ytn.ytn_einsum_plan(ctx, "ab,bcw,xda,cdyz->wxyz", ts)
+    nc = ytn.ytn_einsum_plan(ctx, "pq,qrw,xsp,ryzs->wxyz", ts)
     assert nc.info["ncalls"] == 4
     data = [to_dev(t["data"]) for t in ts]
     out = torch.full((nc.out["size"],), float("nan"), dtype=torch.float64, device=device())
