@@ -44,7 +44,7 @@ __all__ = [
     "OTensor", "OracleError", "SignatureError", "DimMismatchError", "FusionMismatchError",
     "ChargeError", "InvalidError", "UnsupportedError",
     "from_record", "to_record", "conj", "tensordot", "fuse", "unfuse", "trace",
-    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon", "einsum",
+    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon", "einsum", "svd", "truncation", "slice_leg",
 ]
 
 
@@ -635,6 +635,102 @@ def einsum(subscripts, *tensors):
                 lab[c] = nxt
                 nxt += 1
     return ncon(list(tensors), [[lab[c] for c in grp] for grp in ins])
+
+
+# ------------------------------------------------------------------ block-diagonal SVD
+
+def svd(A, row_legs, col_legs):
+    """Block-diagonal singular value decomposition (Sec. III, CTM: the SVD of a fused
+    enlarged corner is block diagonal in the charge sectors, one dense SVD per
+    block; the paper leaves it to the backend's linear algebra).
+
+    The legs of A are split into rows and columns; rows whose charges sum (with
+    signatures) to c meet only columns that complete the total charge, so A is
+    block diagonal with one matrix M_c per c: rows are the row-charge tuples with
+    sum c in ascending order (each row-major over its legs), columns likewise.
+    M_c = U_c diag(S_c) V_c with k_c = min(rows, cols) and S_c descending (numpy's
+    SVD). Returns (U, S, V): U on (row legs, new leg of signature -1), S on (new leg
+    +1, new leg -1) with a diagonal k_c x k_c block per sector, V on (new leg +1, col
+    legs); the new leg carries charge c with dimension k_c. tensordot(tensordot(U, S,
+    (last,), (0,)), V, (last,), (0,)) == A (the legs in order rows, cols)."""
+    row_legs, col_legs = tuple(int(a) for a in row_legs), tuple(int(b) for b in col_legs)
+    if sorted(row_legs + col_legs) != list(range(A.rank)) or not row_legs or not col_legs:
+        raise InvalidError("rows and columns must split the legs into two nonempty groups")
+    mods = A.mods
+    rows, cols, sect = {}, {}, {}
+    for key, blk in A.blocks.items():
+        rk, ck = tuple(key[a] for a in row_legs), tuple(key[b] for b in col_legs)
+        c = tuple([0] * A.nsym)
+        for a in row_legs:
+            c = _add(c, _scale(A.sig[a], key[a], mods), mods)
+        rows.setdefault(c, {})[rk] = int(np.prod([blk.shape[a] for a in row_legs]))
+        cols.setdefault(c, {})[ck] = int(np.prod([blk.shape[b] for b in col_legs]))
+        sect.setdefault(c, []).append(key)
+    U = OTensor(mods, tuple(A.sig[a] for a in row_legs) + (-1,), tuple([0] * A.nsym),
+                fus=[A.fus[a] for a in row_legs] + [None], dtype=A.dtype)
+    S = OTensor(mods, (1, -1), tuple([0] * A.nsym), dtype=np.float64)
+    V = OTensor(mods, (1,) + tuple(A.sig[b] for b in col_legs), A.n,
+                fus=[None] + [A.fus[b] for b in col_legs], dtype=A.dtype)
+    for c in sorted(sect):
+        roff, coff, m, n = {}, {}, 0, 0
+        for rk in sorted(rows[c]):
+            roff[rk] = m
+            m += rows[c][rk]
+        for ck in sorted(cols[c]):
+            coff[ck] = n
+            n += cols[c][ck]
+        M = np.zeros((m, n), dtype=A.dtype)
+        rshape, cshape = {}, {}
+        for key in sect[c]:
+            blk = A.blocks[key]
+            rk, ck = tuple(key[a] for a in row_legs), tuple(key[b] for b in col_legs)
+            sub = np.transpose(blk, row_legs + col_legs).reshape(rows[c][rk], cols[c][ck])
+            M[roff[rk]:roff[rk] + sub.shape[0], coff[ck]:coff[ck] + sub.shape[1]] = sub
+            rshape[rk] = tuple(blk.shape[a] for a in row_legs)
+            cshape[ck] = tuple(blk.shape[b] for b in col_legs)
+        u, sv, vh = np.linalg.svd(M, full_matrices=False)
+        k = sv.size
+        for rk, o in roff.items():
+            U.blocks[rk + (c,)] = u[o:o + rows[c][rk], :].reshape(rshape[rk] + (k,))
+        S.blocks[(c, c)] = np.diag(sv)
+        for ck, o in coff.items():
+            V.blocks[(c,) + ck] = vh[:, o:o + cols[c][ck]].reshape((k,) + cshape[ck])
+    return U, S, V
+
+
+def truncation(S, D_total, tol=0.0):
+    """Kept singular values per sector: the D_total largest over all sectors among
+    those >= tol times the largest (ties kept in sector order); returns {c: kept}."""
+    vals = []
+    for (c, _), blk in sorted(S.blocks.items()):
+        for i, v in enumerate(np.diag(blk)):
+            vals.append((-float(v), c, i))
+    if not vals:
+        return {}
+    smax = -min(v for v, _, _ in vals)
+    vals = sorted(x for x in vals if -x[0] >= tol * smax)[:int(D_total)]
+    keep = {c: 0 for (c, _) in S.blocks}
+    for _, c, _ in vals:
+        keep[c] += 1
+    return keep
+
+
+def slice_leg(T, legs, keep):
+    """The first keep[c] indices of every sector c of the given legs (all other legs
+    whole): the truncation of U, S and V to the kept singular values. Sectors kept
+    at 0 drop their blocks."""
+    out = OTensor(T.mods, T.sig, T.n, fus=list(T.fus), dtype=T.dtype)
+    for key, blk in T.blocks.items():
+        sl = [slice(None)] * T.rank
+        ok = True
+        for a in legs:
+            k = keep.get(key[a], 0)
+            if k == 0:
+                ok = False
+            sl[a] = slice(0, k)
+        if ok:
+            out.blocks[key] = np.array(blk[tuple(sl)])
+    return out
 
 
 # ------------------------------------------------------------------ fermionic swap gate

@@ -716,3 +716,64 @@ def test_einsum_equals_numpy_einsum():
     for bad in ("aa->a", "ab,ab,ab->", "ab->abc", "a1,b"):
         with pytest.raises(O.InvalidError):
             O.einsum(bad, A, A) if bad.count(",") == 1 else O.einsum(bad, A)
+
+
+# ---------------------------------------------------------------- block-diagonal SVD
+
+def _svd_case(seed, mods=(0,), dtype="f64"):
+    rng = np.random.default_rng(seed)
+    pool = [(0,), (1,), (-1,)] if mods == (0,) else [(0, 0), (1, 0), (0, 1), (-1, 0)]
+    legs = [W.Leg(s, pool[:3], [int(d) for d in rng.integers(1, 5, 3)]) for s in (1, 1, -1, -1)]
+    return legs, O.from_record(W.random_tensor(mods, legs, (0,) * len(mods), seed, dtype=dtype))
+
+
+def _dense_matrix(A, legs, rows, cols):
+    d = O.to_dense(A, [leg_map(l) for l in legs])
+    d = np.transpose(d, rows + cols)
+    r = int(np.prod([d.shape[i] for i in range(len(rows))]))
+    return d.reshape(r, -1)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+@pytest.mark.parametrize("seed", range(4))
+def test_svd_reconstructs_and_is_orthonormal(seed, dtype):
+    """CTM's SVD (Sec. III) block by block: U S V == A, U^H U = 1 and V V^H = 1 per
+    sector, S real, non-negative and descending."""
+    legs, A = _svd_case(100 + seed, (0,) if seed % 2 == 0 else (0, 0), dtype)
+    rows, cols = (0, 2), (1, 3)
+    U, S, V = O.svd(A, rows, cols)
+    R = O.tensordot(O.tensordot(U, S, (2,), (0,)), V, (2,), (0,))
+    R = O.fuse(R, ((0,), (2,), (1,), (3,)))
+    for k in A.blocks:
+        np.testing.assert_allclose(R.blocks[k], A.blocks[k], rtol=1e-12, atol=1e-12)
+    UU = O.tensordot(O.conj(U), U, (0, 1), (0, 1))
+    VV = O.tensordot(V, O.conj(V), (1, 2), (1, 2))
+    for (c, _), blk in S.blocks.items():
+        sv = np.diag(blk)
+        assert np.all(sv >= 0) and np.all(np.diff(sv) <= 0)
+        np.testing.assert_allclose(UU.blocks[(c, c)], np.eye(sv.size), atol=1e-12)
+        np.testing.assert_allclose(VV.blocks[(c, c)], np.eye(sv.size), atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_svd_values_and_truncation_match_the_dense_svd(seed):
+    """The singular values of all sectors are those of the dense matrix (rows = row
+    legs); truncating to the D largest leaves the Frobenius error sqrt(sum of the
+    discarded s^2) (Eckart-Young), equal to the dense rank-D error."""
+    legs, A = _svd_case(200 + seed)
+    rows, cols = (0, 3), (1, 2)
+    U, S, V = O.svd(A, rows, cols)
+    ours = np.sort(np.concatenate([np.diag(b) for b in S.blocks.values()]))[::-1]
+    dense = np.linalg.svd(_dense_matrix(A, legs, rows, cols), compute_uv=False)
+    nz = ours[ours > 1e-10]
+    np.testing.assert_allclose(nz, dense[:nz.size], rtol=1e-12)
+    assert np.all(dense[nz.size:] < 1e-10)
+    D = max(1, nz.size // 2)
+    keep = O.truncation(S, D)
+    assert sum(keep.values()) == D
+    Ut, St, Vt = O.slice_leg(U, (2,), keep), O.slice_leg(S, (0, 1), keep), O.slice_leg(V, (0,), keep)
+    R = O.fuse(O.tensordot(O.tensordot(Ut, St, (2,), (0,)), Vt, (2,), (0,)), ((0,), (2,), (3,), (1,)))
+    err = np.linalg.norm(O.to_dense(R, [leg_map(l) for l in legs]) - O.to_dense(A, [leg_map(l) for l in legs]))
+    assert err == pytest.approx(float(np.sqrt(np.sum(dense[D:] ** 2))), rel=1e-9, abs=1e-12)
+    keep_tol = O.truncation(S, 10 ** 6, tol=0.5)
+    assert sum(keep_tol.values()) == int(np.sum(dense >= 0.5 * dense[0]))
