@@ -136,7 +136,9 @@ typedef enum {
   YTN_OP_TRACE = 4,      /* sum the diagonals of leg pairs (axa[k], axb[k]) of a  */
   YTN_OP_VDOT = 5,       /* scalar product <a, b> of two tensors on the same legs */
   YTN_OP_SWAP_GATE = 6,  /* fermionic swap gate between two groups of legs, Sec. IV */
-  YTN_OP_CONJ = 7        /* conjugate: signatures flip, elements conjugated       */
+  YTN_OP_CONJ = 7,       /* conjugate: signatures flip, elements conjugated       */
+  YTN_OP_SVD = 8,        /* block-diagonal SVD: rows | columns, Sec. III (CTM)    */
+  YTN_OP_SLICE = 9       /* keep the first keep[c] indices of sectors of legs     */
 } ytn_op_kind;
 
 /* A planned operation.
@@ -166,7 +168,17 @@ typedef enum {
  *             structure = a's.
  *  CONJ:      a. Sec. II.A footnote: every leg's signature flips (n becomes
  *             -n, fusion records' constituent signatures flip) and complex
- *             elements are conjugated; blocks keep their charges and places. */
+ *             elements are conjugated; blocks keep their charges and places.
+ *  SVD:       a (real), ngroups = 2: the row legs, then the column legs (every
+ *             leg once). Three outputs (ytn_plan_output_at 0, 1, 2): U on (row
+ *             legs, new leg, signature -1), S on (new leg +1, new leg -1) with a
+ *             k x k diagonal block per sector, V on (new leg +1, column legs);
+ *             the new leg carries the signed sum c of the row charges, with
+ *             k_c = min(rows, columns) of sector c. U S V = a.
+ *  SLICE:     a, naxes legs axa[]; nkeep rows of (keep_t[nsym] charge,
+ *             keep_D dimension): every sector of those legs keeps its first
+ *             keep_D indices (charges not listed keep 0: their blocks go).
+ *             Truncation of U, S, V to the kept singular values. */
 typedef struct {
   ytn_op_kind kind;
   const ytn_struct *a;
@@ -179,6 +191,9 @@ typedef struct {
   int32_t order[YTN_MAX_RANK];
   uint32_t fermionic;         /* SWAP_GATE only: 0 = all components fermionic, else
                                  YTN_FERMIONIC_EXPLICIT | component bits      */
+  int64_t nkeep;              /* SLICE only: rows of the keep table           */
+  const int32_t *keep_t;      /* SLICE: [nkeep][nsym] charges                 */
+  const int64_t *keep_D;      /* SLICE: [nkeep] kept dimensions               */
 } ytn_op;
 
 /* Sizes of a plan. */
@@ -222,6 +237,8 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan);
 
 /* Output structure of a plan (library-owned, valid until the plan is released). */
 const ytn_struct *ytn_plan_output(const ytn_plan_t *plan);
+/* Output i of a plan with several (SVD: 0 = U, 1 = S, 2 = V); NULL past the last. */
+const ytn_struct *ytn_plan_output_at(const ytn_plan_t *plan, int32_t i);
 ytn_status ytn_plan_get_info(const ytn_plan_t *plan, ytn_plan_info *info);
 void ytn_plan_release(ytn_plan_t *plan);
 
@@ -311,6 +328,21 @@ ytn_status ytn_vdot(ytn_plan_t *plan, const double *a, const double *b, double *
  * Asynchronous on stream. Errors: YTN_E_INVALID (wrong plan kind, null
  * buffer), YTN_E_CUDA. */
 ytn_status ytn_swap_gate(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
+
+/* Block-diagonal SVD (an SVD plan): every sector matrix of a is gathered into the
+ * workspace and factored by the dense solver of the CUDA toolkit (Jacobi SVD,
+ * one call per sector on stream; the paper leaves this to the backend), then U,
+ * S and V are written to u, s, v (buffers of their planned sizes; device or
+ * page-locked host memory). Singular vectors are unique up to sign (and rotation
+ * within repeated values). workspace: ytn_workspace_size bytes (the sector
+ * matrices, the factors, the solver's buffer). The first SVD plan of a context
+ * creates the solver handle. Errors: YTN_E_INVALID, YTN_E_WORKSPACE, YTN_E_CUDA
+ * (a solver error included). */
+ytn_status ytn_svd(ytn_plan_t *plan, const double *a, double *u, double *s, double *v, void *workspace,
+                   size_t workspace_bytes, ytn_stream stream);
+
+/* out = slice of a (a SLICE plan). Bit-exact copies. Asynchronous on stream. */
+ytn_status ytn_slice(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
 
 /* out = conj(a) (a CONJ plan): each block copied to its place with the
  * imaginary parts of complex elements negated (real data copied as it is).

@@ -74,7 +74,10 @@ def build(verbose=False):
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + ".tmp"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
+        libdir = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+        # the dense solver (block-diagonal SVD) is the toolkit's shared library
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-L", libdir, "-lcusolver",
+               "-Xlinker", "-rpath=" + libdir, "-lrt", "-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

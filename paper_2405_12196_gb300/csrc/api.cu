@@ -304,6 +304,7 @@ void ytn_ctx_destroy(ytn_ctx *ctx) {
     DeviceGuard g(ctx->device);
     for (void *ev : ctx->ev_pool) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
     if (ctx->status_dev) cudaFree(ctx->status_dev);
+    svd_release(ctx);
   }
   delete ctx;
 }
@@ -354,6 +355,17 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
           break;
         case YTN_OP_CONJ:
           st = plan_conj(p, A, err);
+          break;
+        case YTN_OP_SVD:
+          st = plan_svd(p, A, op->ngroups, op->group_size, op->order, err);
+          if (st == YTN_OK && ctx->device >= 0) {
+            DeviceGuard g(ctx->device);
+            st = svd_prepare(p);
+            if (st != YTN_OK) err = "dense solver set-up failed";
+          }
+          break;
+        case YTN_OP_SLICE:
+          st = plan_slice(p, A, op->naxes, op->axa, op->nkeep, op->keep_t, op->keep_D, err);
           break;
         case YTN_OP_SWAP_GATE:
           st = plan_swap_gate(p, A, op->ngroups, op->group_size, op->order, op->fermionic, err);
@@ -412,6 +424,12 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
 
 const ytn_struct *ytn_plan_output(const ytn_plan_t *plan) { return plan ? &plan->out_view : nullptr; }
 
+const ytn_struct *ytn_plan_output_at(const ytn_plan_t *plan, int32_t i) {
+  if (!plan || i < 0) return nullptr;
+  if (i == 0) return &plan->out_view;
+  return (size_t)i <= plan->outs_view.size() ? &plan->outs_view[(size_t)i - 1] : nullptr;
+}
+
 ytn_status ytn_plan_get_info(const ytn_plan_t *p, ytn_plan_info *info) {
   if (!p || !info) return fail(YTN_E_INVALID, "null argument");
   std::memset(info, 0, sizeof(*info));
@@ -441,6 +459,10 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
   *bytes = 0;
   if (p->kind == Kind::Vdot) {
     *bytes = align256(p->vd_chunks.size() * sizeof(double) * p->cw);
+    return YTN_OK;
+  }
+  if (p->kind == Kind::Svd) {
+    *bytes = align256((p->svd_ws_doubles + p->svd_lwork) * sizeof(double));
     return YTN_OK;
   }
   if (p->kind != Kind::Tensordot) return YTN_OK;
@@ -680,6 +702,50 @@ ytn_status ytn_swap_gate(ytn_plan_t *p, const double *a, double *out, ytn_stream
 
 ytn_status ytn_conj(ytn_plan_t *p, const double *a, double *out, ytn_stream stream) {
   return run_move(p, Kind::Conj, a, out, stream, "conj");
+}
+
+ytn_status ytn_slice(ytn_plan_t *p, const double *a, double *out, ytn_stream stream) {
+  return run_move(p, Kind::Slice, a, out, stream, "slice");
+}
+
+ytn_status ytn_svd(ytn_plan_t *p, const double *a, double *u, double *s, double *v, void *workspace,
+                   size_t workspace_bytes, ytn_stream stream) {
+  if (!p) return fail(YTN_E_INVALID, "null plan");
+  if (p->kind != Kind::Svd) return fail(YTN_E_INVALID, "plan is not an SVD plan");
+  if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
+  if ((p->a_size && !a) || (p->out.size && !u) || (p->outs[0].size && !s) || (p->outs[1].size && !v))
+    return fail(YTN_E_INVALID, "null data buffer");
+  const size_t need = align256((p->svd_ws_doubles + p->svd_lwork) * sizeof(double));
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))
+    return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
+  DeviceGuard g(p->ctx->device);
+  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  {
+    ytn_status vs;
+    if ((vs = device_view(p->ctx, a, &a, "A")) != YTN_OK || (vs = device_view(p->ctx, u, &u, "U")) != YTN_OK ||
+        (vs = device_view(p->ctx, s, &s, "S")) != YTN_OK || (vs = device_view(p->ctx, v, &v, "V")) != YTN_OK)
+      return vs;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double *ws = static_cast<double *>(workspace);
+  cudaError_t e;
+  if (p->svd_zero_m && (e = cudaMemsetAsync(ws, 0, p->svd_m_doubles * sizeof(double), st)) != cudaSuccess)
+    return cuda_fail(e, "memset sector matrices");
+  if ((e = launch_copy(p->d_jobs, p->d_items + p->items_a_begin, p->items_a_end - p->items_a_begin, a, ws, st)) !=
+      cudaSuccess)
+    return cuda_fail(e, "gather sector matrices");
+  ytn_status r = svd_factor(p, ws, st);
+  if (r != YTN_OK) return r;
+  if (p->outs[0].size && (e = cudaMemsetAsync(s, 0, (size_t)p->outs[0].size * sizeof(double), st)) != cudaSuccess)
+    return cuda_fail(e, "memset S");
+  if ((e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, ws, u, st)) !=
+          cudaSuccess ||
+      (e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, ws, v, st)) !=
+          cudaSuccess ||
+      (e = launch_copy(p->d_jobs, p->d_items + p->items_s_begin, p->items_s_end - p->items_s_begin, ws, s, st)) !=
+          cudaSuccess)
+    return cuda_fail(e, "write U, S, V");
+  return YTN_OK;
 }
 
 ytn_status ytn_vdot(ytn_plan_t *p, const double *a, const double *b, double *out, void *workspace,

@@ -1713,6 +1713,277 @@ ytn_status plan_conj(ytn_plan_t *p, const Tensor &A, std::string &err) {
 }
 
 // ---------------------------------------------------------------------------
+// Block-diagonal SVD and leg slicing
+// ---------------------------------------------------------------------------
+
+// Sec. III (CTM): the fused enlarged corner is block diagonal in the charge
+// sectors and its SVD is one dense SVD per block. Rows are the combinations of
+// the row legs' charges, grouped by their signed sum c (ascending, each row-major
+// over its legs), columns likewise; M_c is gathered row-major into the workspace
+// and factored by the dense solver. Outputs: U (row legs, new leg of signature -1),
+// S (new leg +1, new leg -1; a k x k diagonal block per sector), V (new leg +1,
+// col legs); the new leg has charge c and dimension k_c = min(m_c, n_c).
+ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
+                    std::string &err) {
+  if (A.dtype != YTN_REAL64) { err = "SVD of complex data is not built"; return YTN_E_UNSUPPORTED; }
+  if (ngroups != 2 || group_size[0] < 1 || group_size[1] < 1 || group_size[0] + group_size[1] != A.rank) {
+    err = "an SVD takes two nonempty groups of legs: rows and columns";
+    return YTN_E_INVALID;
+  }
+  std::vector<int> rowL(order, order + group_size[0]), colL(order + group_size[0], order + A.rank);
+  {
+    std::vector<int> seen(A.rank, 0);
+    for (int l : rowL) if (l < 0 || l >= A.rank || seen[l]++) { err = "row/column legs must split the legs"; return YTN_E_INVALID; }
+    for (int l : colL) if (l < 0 || l >= A.rank || seen[l]++) { err = "row/column legs must split the legs"; return YTN_E_INVALID; }
+  }
+  if ((int)rowL.size() + 1 > YTN_MAX_RANK || (int)colL.size() + 1 > YTN_MAX_RANK) {
+    err = "SVD output rank too large";
+    return YTN_E_UNSUPPORTED;
+  }
+  const int nsym = A.nsym;
+  struct Sec {
+    std::map<Key, std::pair<int64_t, int64_t>> rows, cols;   // key -> (size, any block)
+    std::vector<int64_t> blocks;
+  };
+  std::map<Key, Sec> secs;
+  for (int64_t b = 0; b < A.nblocks; b++) {
+    Key c(nsym, 0);
+    for (int l : rowL)
+      for (int q = 0; q < nsym; q++) c[q] = reduce((int64_t)c[q] + (int64_t)A.sig[l] * A.charge(b, l)[q], A.mod[q]);
+    Sec &sc = secs[c];
+    sc.rows.emplace(sub_charges(A, b, rowL), std::make_pair(sub_elems(A, b, rowL), b));
+    sc.cols.emplace(sub_charges(A, b, colL), std::make_pair(sub_elems(A, b, colL), b));
+    sc.blocks.push_back(b);
+  }
+  // output structures
+  Tensor U, S, V;
+  for (Tensor *T : {&U, &S, &V}) {
+    T->nsym = nsym;
+    std::memcpy(T->mod, A.mod, sizeof(T->mod));
+  }
+  U.rank = (int)rowL.size() + 1;
+  for (size_t i = 0; i < rowL.size(); i++) {
+    U.sig[i] = A.sig[rowL[i]];
+    copy_fusion(A.fus[rowL[i]].get(), U.fus[i]);
+  }
+  U.sig[rowL.size()] = -1;
+  S.rank = 2;
+  S.sig[0] = 1;
+  S.sig[1] = -1;
+  V.rank = (int)colL.size() + 1;
+  V.sig[0] = 1;
+  for (size_t i = 0; i < colL.size(); i++) {
+    V.sig[i + 1] = A.sig[colL[i]];
+    copy_fusion(A.fus[colL[i]].get(), V.fus[i + 1]);
+  }
+  std::memcpy(V.n, A.n, sizeof(V.n));
+  std::vector<OutBlock> ub, sb, vb;
+  struct Place { int64_t sec; int64_t off; int64_t blk; };
+  std::vector<Place> uplace, vplace;   // per output block id: its sector, row/col offset, a source block
+  p->svd_sec.clear();
+  size_t off = 0;
+  auto align32 = [](int64_t e) { return (e + 31) / 32 * 32; };
+  std::vector<std::map<Key, int64_t>> roff(secs.size()), coff(secs.size());
+  int64_t si = 0;
+  int64_t covered = 0, need = 0;
+  for (auto &kv : secs) {
+    SvdSector sv{};
+    for (auto &r : kv.second.rows) { roff[si][r.first] = sv.m; sv.m += r.second.first; }
+    for (auto &c : kv.second.cols) { coff[si][c.first] = sv.n; sv.n += c.second.first; }
+    sv.k = std::min(sv.m, sv.n);
+    if (sv.m > INT32_MAX || sv.n > INT32_MAX) { err = "sector too large"; return YTN_E_UNSUPPORTED; }
+    sv.m_off = (int64_t)off;
+    off += align32(sv.m * sv.n);
+    need += sv.m * sv.n;
+    p->svd_sec.push_back(sv);
+    for (auto &r : kv.second.rows) {
+      OutBlock ob;
+      ob.key = r.first;
+      ob.key.insert(ob.key.end(), kv.first.begin(), kv.first.end());
+      for (int l : rowL) ob.D.push_back(A.dim(r.second.second, l));
+      ob.D.push_back(sv.k);
+      ob.id = (int64_t)uplace.size();
+      ub.push_back(ob);
+      uplace.push_back({si, roff[si][r.first], r.second.second});
+    }
+    {
+      OutBlock ob;
+      ob.key = kv.first;
+      ob.key.insert(ob.key.end(), kv.first.begin(), kv.first.end());
+      ob.D = {sv.k, sv.k};
+      ob.id = (int64_t)sb.size();
+      sb.push_back(ob);
+    }
+    for (auto &c : kv.second.cols) {
+      OutBlock ob;
+      ob.key = kv.first;
+      ob.key.insert(ob.key.end(), c.first.begin(), c.first.end());
+      ob.D.push_back(sv.k);
+      for (int l : colL) ob.D.push_back(A.dim(c.second.second, l));
+      ob.id = (int64_t)vplace.size();
+      vb.push_back(ob);
+      vplace.push_back({si, coff[si][c.first], c.second.second});
+    }
+    si++;
+  }
+  p->svd_m_doubles = off;
+  for (auto &sv : p->svd_sec) { sv.up_off = (int64_t)off; off += align32(sv.n * sv.k); }
+  for (auto &sv : p->svd_sec) { sv.vp_off = (int64_t)off; off += align32(sv.m * sv.k); }
+  for (auto &sv : p->svd_sec) { sv.s_off = (int64_t)off; off += align32(sv.k); }
+  p->svd_info_off = off;                       // one int per sector (as doubles: rounded up)
+  off += align32(((int64_t)p->svd_sec.size() + 1) / 2 + 1);
+  p->svd_ws_doubles = off;                     // the solver's buffer follows (size set by the device side)
+  std::vector<int64_t> uo, so, vo;
+  finalize_out(U, ub, uo);
+  finalize_out(S, sb, so);
+  finalize_out(V, vb, vo);
+  p->jobs.clear();
+  p->items.clear();
+  p->moved = 0;
+  // gather A -> M_c (row-major, ld = n)
+  si = 0;
+  for (auto &kv : secs) {
+    const SvdSector &sv = p->svd_sec[si];
+    for (int64_t b : kv.second.blocks) {
+      const auto st = block_strides(A, b);
+      std::vector<Dim> dims;
+      int64_t acc = 1;
+      std::vector<int64_t> rs(rowL.size()), cs(colL.size());
+      for (int i = (int)rowL.size() - 1; i >= 0; i--) { rs[i] = acc; acc *= A.dim(b, rowL[i]); }
+      acc = 1;
+      for (int i = (int)colL.size() - 1; i >= 0; i--) { cs[i] = acc; acc *= A.dim(b, colL[i]); }
+      for (size_t i = 0; i < rowL.size(); i++) dims.push_back({A.dim(b, rowL[i]), st[rowL[i]], rs[i] * sv.n});
+      for (size_t i = 0; i < colL.size(); i++) dims.push_back({A.dim(b, colL[i]), st[colL[i]], cs[i]});
+      const int64_t dst = sv.m_off + roff[si][sub_charges(A, b, rowL)] * sv.n + coff[si][sub_charges(A, b, colL)];
+      ytn_status s = add_copy(p, dims, A.off[b], dst, err);
+      if (s != YTN_OK) return s;
+      covered += A.elems(b);
+      p->moved += A.elems(b);
+    }
+    si++;
+  }
+  p->svd_zero_m = covered < need;
+  const size_t j0 = 0, j1 = p->jobs.size();
+  p->items_a_begin = 0;
+  make_items(p, j0, j1);
+  p->items_a_end = (int64_t)p->items.size();
+  // U blocks from V' (m x k, column-major): element (row r, j) at vp_off + j*m + r
+  for (size_t id = 0; id < uplace.size(); id++) {
+    const Place &pl = uplace[id];
+    const SvdSector &sv = p->svd_sec[pl.sec];
+    const int64_t rows = sub_elems(A, pl.blk, rowL);
+    ytn_status s = add_copy(p, {{rows, 1, sv.k}, {sv.k, sv.m, 1}}, sv.vp_off + pl.off, uo[id], err);
+    if (s != YTN_OK) return s;
+  }
+  const size_t j2 = p->jobs.size();
+  p->items_b_begin = (int64_t)p->items.size();
+  make_items(p, j1, j2);
+  p->items_b_end = (int64_t)p->items.size();
+  // V blocks from U' (n x k, column-major): element (j, col c) at up_off + j*n + c
+  for (size_t id = 0; id < vplace.size(); id++) {
+    const Place &pl = vplace[id];
+    const SvdSector &sv = p->svd_sec[pl.sec];
+    const int64_t cols = sub_elems(A, pl.blk, colL);
+    ytn_status s = add_copy(p, {{sv.k, sv.n, cols}, {cols, 1, 1}}, sv.up_off + pl.off, vo[id], err);
+    if (s != YTN_OK) return s;
+  }
+  const size_t j3 = p->jobs.size();
+  p->items_c_begin = (int64_t)p->items.size();
+  make_items(p, j2, j3);
+  p->items_c_end = (int64_t)p->items.size();
+  // S diagonals from the singular-value vectors (the rest of S is zero)
+  for (size_t id = 0; id < p->svd_sec.size(); id++) {
+    const SvdSector &sv = p->svd_sec[id];
+    if (sv.k == 0) continue;
+    ytn_status s = add_copy(p, {{sv.k, 1, sv.k + 1}}, sv.s_off, so[id], err);
+    if (s != YTN_OK) return s;
+  }
+  p->items_s_begin = (int64_t)p->items.size();
+  make_items(p, j3, p->jobs.size());
+  p->items_s_end = (int64_t)p->items.size();
+  p->out = U;
+  p->outs = {S, V};
+  p->kind = Kind::Svd;
+  p->a_size = A.size;
+  double fl = 0.0;
+  for (auto &sv : p->svd_sec) fl += 4.0 * (double)sv.m * sv.n * sv.k;   // nominal dense SVD work
+  p->flops = fl;
+  return YTN_OK;
+}
+
+// The first keep[c] indices of every sector c of the legs `axes` (other legs
+// whole); blocks with a sector kept at 0 are dropped. Truncates U, S and V to the
+// kept singular values.
+ytn_status plan_slice(ytn_plan_t *p, const Tensor &A, int naxes, const int *axes, int64_t nkeep,
+                      const int32_t *keep_t, const int64_t *keep_D, std::string &err) {
+  if (naxes < 1 || naxes > A.rank) { err = "naxes out of range"; return YTN_E_INVALID; }
+  if (nkeep < 0 || (nkeep > 0 && (!keep_t || !keep_D))) { err = "null keep table"; return YTN_E_INVALID; }
+  std::vector<int> ax(axes, axes + naxes);
+  for (int a : ax)
+    if (a < 0 || a >= A.rank || std::count(ax.begin(), ax.end(), a) != 1) { err = "bad sliced legs"; return YTN_E_INVALID; }
+  std::map<Key, int64_t> keep;
+  for (int64_t i = 0; i < nkeep; i++) {
+    if (keep_D[i] < 0) { err = "negative kept dimension"; return YTN_E_INVALID; }
+    Key q(keep_t + i * A.nsym, keep_t + (i + 1) * A.nsym);
+    for (int c = 0; c < A.nsym; c++) q[c] = reduce(q[c], A.mod[c]);
+    keep[q] = keep_D[i];
+  }
+  Tensor &C = p->out;
+  C = A;
+  C.t.clear();
+  C.D.clear();
+  C.off.clear();
+  C.bstr.clear();
+  p->cw = A.dtype == YTN_COMPLEX128 ? 2 : 1;
+  std::vector<OutBlock> ob;
+  std::vector<int64_t> src;
+  for (int64_t b = 0; b < A.nblocks; b++) {
+    OutBlock o;
+    o.key = Key(&A.t[(size_t)b * A.rank * A.nsym], &A.t[(size_t)(b + 1) * A.rank * A.nsym]);
+    bool ok = true;
+    for (int i = 0; i < A.rank; i++) {
+      int64_t d = A.dim(b, i);
+      if (std::find(ax.begin(), ax.end(), i) != ax.end()) {
+        auto it = keep.find(Key(A.charge(b, i), A.charge(b, i) + A.nsym));
+        d = std::min(d, it == keep.end() ? 0 : it->second);
+      }
+      if (d == 0) ok = false;
+      o.D.push_back(d);
+    }
+    if (!ok) continue;
+    o.id = (int64_t)src.size();
+    src.push_back(b);
+    ob.push_back(o);
+  }
+  std::vector<int64_t> off_of_id;
+  std::vector<OutBlock> sorted = ob;
+  finalize_out(C, sorted, off_of_id);
+  p->jobs.clear();
+  p->items.clear();
+  p->moved = 0;
+  for (size_t id = 0; id < ob.size(); id++) {
+    const int64_t b = src[id];
+    const auto st = block_strides(A, b);
+    std::vector<Dim> dims;
+    int64_t acc = 1;
+    std::vector<int64_t> ds(A.rank);
+    for (int i = A.rank - 1; i >= 0; i--) { ds[i] = acc; acc *= ob[id].D[i]; }
+    for (int i = 0; i < A.rank; i++) dims.push_back({ob[id].D[i], st[i], ds[i]});
+    ytn_status s = add_copy(p, dims, A.off[b], off_of_id[id], err);
+    if (s != YTN_OK) return s;
+    p->moved += acc;
+  }
+  p->items_a_begin = 0;
+  make_items(p, 0, p->jobs.size());
+  p->items_a_end = (int64_t)p->items.size();
+  p->zero_out = false;
+  p->flops = 0.0;
+  p->kind = Kind::Slice;
+  p->a_size = A.size;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Cache key and output view
 // ---------------------------------------------------------------------------
 
@@ -1757,14 +2028,25 @@ std::string plan_key(const ytn_op *op) {
   put(s, op->group_size, sizeof(op->group_size));
   put(s, op->order, sizeof(op->order));
   if (op->kind == YTN_OP_SWAP_GATE) put(s, &op->fermionic, sizeof(op->fermionic));
+  if (op->kind == YTN_OP_SLICE) {
+    put(s, &op->nkeep, sizeof(op->nkeep));
+    const int nsym = op->a && op->a->sym.nsym > 0 && op->a->sym.nsym <= YTN_MAX_SYM ? op->a->sym.nsym : 0;
+    if (op->nkeep > 0 && op->keep_t) put(s, op->keep_t, (size_t)op->nkeep * nsym * sizeof(int32_t));
+    if (op->nkeep > 0 && op->keep_D) put(s, op->keep_D, (size_t)op->nkeep * sizeof(int64_t));
+  }
   key_struct(s, op->a);
   key_struct(s, op->b);
   return s;
 }
 
 void finish_output_view(ytn_plan_t *p) {
-  Tensor &C = p->out;
-  ytn_struct &v = p->out_view;
+  make_view(p->out, p->out_view, p->out_fus_view);
+  p->outs_view.assign(p->outs.size(), ytn_struct{});
+  p->outs_fus_view.assign(p->outs.size(), {});
+  for (size_t i = 0; i < p->outs.size(); i++) make_view(p->outs[i], p->outs_view[i], p->outs_fus_view[i]);
+}
+
+void make_view(const Tensor &C, ytn_struct &v, std::vector<ytn_fusion> &fv) {
   std::memset(&v, 0, sizeof(v));
   v.dtype = C.dtype;
   v.sym.nsym = C.nsym;
@@ -1777,10 +2059,10 @@ void finish_output_view(ytn_plan_t *p) {
   v.D = C.D.data();
   v.off = C.off.data();
   v.size = C.size;
-  p->out_fus_view.assign(C.rank, ytn_fusion{});
+  fv.assign(C.rank, ytn_fusion{});
   for (int i = 0; i < C.rank; i++) {
     if (!C.fus[i]) continue;
-    ytn_fusion &f = p->out_fus_view[i];
+    ytn_fusion &f = fv[i];
     const Fusion &F = *C.fus[i];
     f.nlegs = F.nlegs;
     for (int j = 0; j < F.nlegs; j++) f.sig[j] = (int8_t)F.sig[j];

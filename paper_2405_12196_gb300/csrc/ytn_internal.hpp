@@ -213,7 +213,16 @@ struct HostSector {
   int64_t a_off = 0, b_off = 0, c_off = 0;
 };
 
-enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap = 6, Conj = 7 };
+enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap = 6, Conj = 7, Svd = 8, Slice = 9 };
+
+// One charge sector of a block-diagonal SVD: the dense m x n matrix M (row-major;
+// column-major it is M^T, n x m, which is what the solver factors: M^T = U' S V'^T,
+// so M = V' S U'^T), and where its factors live in the workspace (offsets in
+// doubles): M, U' (n x k, column-major), V' (m x k, column-major), S (k).
+struct SvdSector {
+  int64_t m, n, k;
+  int64_t m_off, up_off, vp_off, s_off;
+};
 
 struct Plan;
 
@@ -240,6 +249,10 @@ struct ytn_ctx {
   void *cap_stream = nullptr;
   std::vector<ytn_plan_s *> cap_plans;
   std::mutex cap_mu;
+  // dense solver handle and Jacobi SVD parameters (created by the first SVD plan)
+  void *solver = nullptr;
+  void *svd_params = nullptr;
+  std::mutex solver_mu;
 };
 
 struct ytn_plan_s {
@@ -251,6 +264,15 @@ struct ytn_plan_s {
   // input sizes and output structure (owned storage + ABI view)
   int64_t a_size = 0, b_size = 0;
   int ca = 1, cb = 1;   // tensordot: 2 when A (B) is complex (doubled sector matrices)
+  // further outputs (SVD: S and V after U in `out`) and their ABI views
+  std::vector<ytn::Tensor> outs;
+  std::vector<ytn_struct> outs_view;
+  std::vector<std::vector<ytn_fusion>> outs_fus_view;
+  // SVD: sectors, the copy-item ranges of the output scatters, workspace layout
+  std::vector<ytn::SvdSector> svd_sec;
+  int64_t items_s_begin = 0, items_s_end = 0;   // S vectors -> S diagonals
+  size_t svd_m_doubles = 0, svd_ws_doubles = 0, svd_info_off = 0, svd_lwork = 0;
+  bool svd_zero_m = false;
   // doubles per element of the copy jobs that add_copy makes: 2 for complex
   // tensors moved whole (fuse, unfuse, swap gate, conj), else 1
   int cw = 1;
@@ -327,6 +349,11 @@ ytn_status plan_vdot(ytn_plan_t *p, const Tensor &A, const Tensor &B, std::strin
 ytn_status plan_swap_gate(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
                           uint32_t fermionic, std::string &err);
 ytn_status plan_conj(ytn_plan_t *p, const Tensor &A, std::string &err);
+ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
+                    std::string &err);
+ytn_status plan_slice(ytn_plan_t *p, const Tensor &A, int naxes, const int *axes, int64_t nkeep,
+                      const int32_t *keep_t, const int64_t *keep_D, std::string &err);
+void make_view(const Tensor &C, ytn_struct &v, std::vector<ytn_fusion> &fv);
 ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1,
                       const int *ax2, std::string &err);
 std::string plan_key(const ytn_op *op);
@@ -335,5 +362,10 @@ void plan_split_tables(ytn_plan_t *p);
 
 // error reporting (api.cu)
 ytn_status fail(ytn_status st, const std::string &msg);
+
+// dense solver of the block-diagonal SVD (svd.cpp)
+ytn_status svd_prepare(ytn_plan_t *p);
+ytn_status svd_factor(ytn_plan_t *p, double *ws, void *stream);
+void svd_release(ytn_ctx *ctx);
 
 }  // namespace ytn

@@ -34,6 +34,7 @@ YTN_SPLIT_BF16 = 1
 YTN_AUTO = 2
 YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE, YTN_OP_VDOT, YTN_OP_SWAP_GATE, YTN_OP_CONJ = \
     1, 2, 3, 4, 5, 6, 7
+YTN_OP_SVD, YTN_OP_SLICE = 8, 9
 YTN_FERMIONIC_EXPLICIT = 1 << 31
 YTN_REAL64, YTN_COMPLEX128 = 0, 1
 
@@ -67,7 +68,8 @@ class ytn_op(C.Structure):
     _fields_ = [("kind", C.c_int), ("a", C.POINTER(ytn_struct)), ("b", C.POINTER(ytn_struct)),
                 ("naxes", C.c_int32), ("axa", C.c_int32 * MAX_RANK), ("axb", C.c_int32 * MAX_RANK),
                 ("ngroups", C.c_int32), ("group_size", C.c_int32 * MAX_RANK),
-                ("order", C.c_int32 * MAX_RANK), ("fermionic", C.c_uint32)]
+                ("order", C.c_int32 * MAX_RANK), ("fermionic", C.c_uint32), ("nkeep", C.c_int64),
+                ("keep_t", C.POINTER(C.c_int32)), ("keep_D", C.POINTER(C.c_int64))]
 
 
 class ytn_plan_info(C.Structure):
@@ -101,6 +103,10 @@ SYMBOLS = {
     "ytn_ctx_destroy": (None, [C.c_void_p]),
     "ytn_plan": (C.c_int, [C.c_void_p, C.POINTER(ytn_op), C.POINTER(C.c_void_p)]),
     "ytn_plan_output": (C.POINTER(ytn_struct), [C.c_void_p]),
+    "ytn_plan_output_at": (C.POINTER(ytn_struct), [C.c_void_p, C.c_int32]),
+    "ytn_svd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                          C.c_void_p]),
+    "ytn_slice": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(ytn_plan_info)]),
     "ytn_plan_release": (None, [C.c_void_p]),
     "ytn_workspace_size": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
@@ -293,6 +299,14 @@ class Plan:
         self.handle = handle
         self._keep = keep
         self.out = struct_to_record(_lib.ytn_plan_output(handle))
+        self.outs = [self.out]
+        i = 1
+        while True:   # further outputs (SVD: U, S, V)
+            ptr = _lib.ytn_plan_output_at(handle, i)
+            if not ptr:
+                break
+            self.outs.append(struct_to_record(ptr))
+            i += 1
         info = ytn_plan_info()
         _check(_lib.ytn_plan_get_info(handle, C.byref(info)))
         self.info = {k: getattr(info, k) for k, _ in ytn_plan_info._fields_}
@@ -337,7 +351,7 @@ def ytn_ctx_create(device=0):
     return Ctx(h.value)
 
 
-def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None):
+def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None, keep=None):
     """Plan an operation. ``a``/``b``: tensor records. ``kind``: one of YTN_OP_*.
     TENSORDOT: pairs (axa[k], axb[k]); FUSE: ``groups`` (list of leg tuples);
     UNFUSE: legs ``axa``; TRACE: pairs (axa[k], axb[k]) of ``a``; SWAP_GATE: two
@@ -363,9 +377,17 @@ def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None):
             op.order[k] = x
     if fermionic is not None:
         op.fermionic = YTN_FERMIONIC_EXPLICIT | sum(1 << c for c, f in enumerate(fermionic) if f)
+    keep_arrays = ()
+    if keep is not None:   # SLICE: {charge tuple: kept dimension}
+        kt = np.ascontiguousarray([list(q) for q in keep] or [[0]], dtype=np.int32)
+        kd = np.ascontiguousarray(list(keep.values()) or [0], dtype=np.int64)
+        op.nkeep = len(keep)
+        op.keep_t = kt.ctypes.data_as(C.POINTER(C.c_int32))
+        op.keep_D = kd.ctypes.data_as(C.POINTER(C.c_int64))
+        keep_arrays = (kt, kd)
     h = C.c_void_p()
     _check(_lib.ytn_plan(ctx.handle, C.byref(op), C.byref(h)))
-    return Plan(ctx, h.value, (sa, sb))
+    return Plan(ctx, h.value, (sa, sb, keep_arrays))
 
 
 def ytn_workspace_size(plan, prec=YTN_FP64, rtol=0.0):
@@ -441,6 +463,18 @@ def ytn_trace(plan, a, out, stream=None):
 def ytn_swap_gate(plan, a, out, stream=None):
     """out = swap_gate(a) for a SWAP_GATE plan; ``out`` may be ``a`` (in place)."""
     _check(_lib.ytn_swap_gate(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
+
+
+def ytn_svd(plan, a, u, s, v, workspace=None, workspace_bytes=None, stream=None):
+    """U, S, V of an SVD plan into ``u``, ``s``, ``v`` (sizes of ``plan.outs``)."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.ytn_svd(plan.handle, _ptr(a), _ptr(u), _ptr(s), _ptr(v), _ptr(workspace), int(workspace_bytes),
+                        _stream(stream)))
+
+
+def ytn_slice(plan, a, out, stream=None):
+    _check(_lib.ytn_slice(plan.handle, _ptr(a), _ptr(out), _stream(stream)))
 
 
 def ytn_conj(plan, a, out, stream=None):

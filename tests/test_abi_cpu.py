@@ -344,3 +344,30 @@ def test_einsum_plans_equal_the_oracle(hctx):
         with pytest.raises(ytn.YtnError) as ei:
             ytn.ytn_einsum_plan(hctx, bad, ts)
         assert ei.value.name == "YTN_E_INVALID"
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_svd_and_slice_planning(hctx, seed):
+    """SVD plans: U, S and V have the oracle's structures (sectors, new-leg charges
+    and dimensions, signatures); a SLICE plan keeps the oracle's truncated blocks."""
+    rng = np.random.default_rng(300 + seed)
+    mods = (0,) if seed % 2 == 0 else (0, 0)
+    pool = [(0,), (1,), (-1,)] if mods == (0,) else [(0, 0), (1, 0), (0, 1)]
+    legs = [W.Leg(s, pool, [int(d) for d in rng.integers(1, 5, 3)]) for s in (1, 1, -1, -1)]
+    A = W.random_tensor(mods, legs, (0,) * len(mods), seed)
+    rows, cols = (0, 2), (1, 3)
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_SVD, A, groups=(rows, cols))
+    U, S, V = O.svd(O.from_record(A), rows, cols)
+    for got, want in zip(plan.outs, (U, S, V)):
+        same_structure(got, O.to_record(want))
+    keep = O.truncation(S, max(1, sum(S.blocks[k].shape[0] for k in S.blocks) // 2))
+    ps = ytn.ytn_plan(hctx, ytn.YTN_OP_SLICE, plan.outs[0], axa=(2,), keep=keep)
+    same_structure(ps.out, O.to_record(O.slice_leg(U, (2,), keep)))
+    ps2 = ytn.ytn_plan(hctx, ytn.YTN_OP_SLICE, plan.outs[1], axa=(0, 1), keep=keep)
+    same_structure(ps2.out, O.to_record(O.slice_leg(S, (0, 1), keep)))
+    with pytest.raises(ytn.YtnError):
+        ytn.ytn_plan(hctx, ytn.YTN_OP_SVD, A, groups=((0, 1), (1, 2, 3)))
+    with pytest.raises(ytn.YtnError) as ei:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_SVD, W.random_tensor(mods, legs, (0,) * len(mods), 1, dtype="c128"),
+                     groups=(rows, cols))
+    assert ei.value.name == "YTN_E_UNSUPPORTED"
