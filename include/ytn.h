@@ -248,6 +248,15 @@ void ytn_plan_release(ytn_plan_t *plan);
 ytn_status ytn_workspace_size(const ytn_plan_t *plan, ytn_precision prec, double rtol,
                               size_t *bytes);
 
+/* Workspace (bytes) with which a ytn_tensordot call stages page-locked host
+ * operands on the device: ytn_workspace_size plus device copies of A, B and C.
+ * Given at least this much, a call whose a, b or c is host memory moves them
+ * with the copy engines (cudaMemcpyAsync on its stream, no SM time, so that a
+ * call on another stream keeps every SM) instead of reading and writing host
+ * memory from the data-mover kernels. Tensordot plans only (YTN_E_INVALID). */
+ytn_status ytn_workspace_size_staged(const ytn_plan_t *plan, ytn_precision prec, double rtol,
+                                     size_t *bytes);
+
 /* C = tensordot(A, B) (Sec. II.B contraction equation): gather the blocks of A
  * and B into one matrix per charge sector, multiply the sectors in one grouped
  * launch, scatter the products into the blocks of C. Complex operands

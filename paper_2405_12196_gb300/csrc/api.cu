@@ -142,8 +142,10 @@ class PhaseTimer {
 // with cudaHostRegister) through its device mapping, so that the data movers
 // read or write it over the host link with no separate copy. Pageable host
 // memory and other devices' memory are rejected before anything is launched.
-static ytn_status device_view(const ytn_ctx *ctx, const void *ptr, const void **out, const char *what) {
+static ytn_status device_view(const ytn_ctx *ctx, const void *ptr, const void **out, const char *what,
+                              bool *on_host = nullptr) {
   *out = ptr;
+  if (on_host) *on_host = false;
   if (!ptr) return YTN_OK;
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, ptr);
@@ -159,15 +161,16 @@ static ytn_status device_view(const ytn_ctx *ctx, const void *ptr, const void **
   if (at.type == cudaMemoryTypeHost) {
     if (!at.devicePointer) return fail(YTN_E_INVALID, std::string(what) + ": page-locked host memory without a device mapping");
     *out = at.devicePointer;
+    if (on_host) *on_host = true;
     return YTN_OK;
   }
   return fail(YTN_E_INVALID, std::string(what) + ": pageable host memory (page-lock it with cudaHostRegister first)");
 }
 
 template <class T>
-static ytn_status device_view(const ytn_ctx *ctx, T *ptr, T **out, const char *what) {
+static ytn_status device_view(const ytn_ctx *ctx, T *ptr, T **out, const char *what, bool *on_host = nullptr) {
   const void *v = nullptr;
-  ytn_status st = device_view(ctx, static_cast<const void *>(ptr), &v, what);
+  ytn_status st = device_view(ctx, static_cast<const void *>(ptr), &v, what, on_host);
   *out = static_cast<T *>(const_cast<void *>(v));
   return st;
 }
@@ -454,6 +457,22 @@ void ytn_plan_release(ytn_plan_t *plan) {
   if (--plan->refs == 0) destroy_plan(plan);
 }
 
+// Staging of page-locked host operands through the workspace (copy engines):
+// device copies of A, B and C after the contraction's own workspace.
+static size_t staging_bytes(const ytn_plan_t *p) {
+  const size_t wa = p->a_size * (p->ca == 2 ? 16 : 8), wb = p->b_size * (p->cb == 2 ? 16 : 8);
+  const size_t wc = (size_t)p->out.size * (p->out.dtype == YTN_COMPLEX128 ? 16 : 8);
+  return align256(wa) + align256(wb) + align256(wc);
+}
+
+ytn_status ytn_workspace_size_staged(const ytn_plan_t *p, ytn_precision prec, double rtol, size_t *bytes) {
+  ytn_status st = ytn_workspace_size(p, prec, rtol, bytes);
+  if (st != YTN_OK) return st;
+  if (p->kind != Kind::Tensordot) return fail(YTN_E_INVALID, "staging is for tensordot plans");
+  *bytes = align256(*bytes) + staging_bytes(p);
+  return YTN_OK;
+}
+
 ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rtol, size_t *bytes) {
   if (!p || !bytes) return fail(YTN_E_INVALID, "null argument");
   *bytes = 0;
@@ -587,14 +606,44 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
   DeviceGuard g(p->ctx->device);
   if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  const double *a_host = a, *b_host = b;
+  double *c_host_ptr = c;
+  bool ha = false, hb = false, hc = false;
   {
     ytn_status vs;
-    if ((vs = device_view(p->ctx, a, &a, "A")) != YTN_OK || (vs = device_view(p->ctx, b, &b, "B")) != YTN_OK ||
-        (vs = device_view(p->ctx, c, &c, "C")) != YTN_OK)
+    if ((vs = device_view(p->ctx, a, &a, "A", &ha)) != YTN_OK || (vs = device_view(p->ctx, b, &b, "B", &hb)) != YTN_OK ||
+        (vs = device_view(p->ctx, c, &c, "C", &hc)) != YTN_OK)
       return vs;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   note_capture(p, st);
+  // Host operands with a workspace large enough for staging: copy engines move
+  // them (no SM time, so calls in flight on other streams keep every SM);
+  // otherwise the data movers read and write host memory directly.
+  bool staged = false;
+  if (ha || hb || hc) {
+    const size_t base = align256(need);
+    staged = workspace && workspace_bytes >= base + staging_bytes(p);
+    if (staged) {
+      char *sw = static_cast<char *>(workspace) + base;
+      const size_t wa = p->a_size * (p->ca == 2 ? 16 : 8), wb = p->b_size * (p->cb == 2 ? 16 : 8);
+      double *sa = reinterpret_cast<double *>(sw), *sb = reinterpret_cast<double *>(sw + align256(wa));
+      double *sc = reinterpret_cast<double *>(sw + align256(wa) + align256(wb));
+      cudaError_t e = cudaSuccess;
+      if (ha && wa) e = cudaMemcpyAsync(sa, a_host, wa, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess && hb && wb) e = cudaMemcpyAsync(sb, b_host, wb, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "staging copy to the device");
+      if (ha) a = sa;
+      if (hb) b = sb;
+      if (hc) c = sc;
+    }
+  }
+  auto unstage = [&]() -> ytn_status {
+    if (!staged || !hc || !p->out.size) return YTN_OK;
+    const size_t wc = (size_t)p->out.size * (p->out.dtype == YTN_COMPLEX128 ? 16 : 8);
+    cudaError_t e = cudaMemcpyAsync(c_host_ptr, c, wc, cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? YTN_OK : cuda_fail(e, "staging copy to the host");
+  };
   bool split = prec == YTN_SPLIT_BF16;
   if (prec == YTN_AUTO && split_ok) {
     // the choice is made once per plan and slice count and cached on the plan
@@ -635,7 +684,7 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
           res->slices = slices;
           res->err_est = est;
         }
-        return YTN_OK;
+        return unstage();
       }
       std::lock_guard<std::mutex> lk(p->auto_mu);
       if (p->auto_choice[slices] < 0) p->auto_choice[slices] = choice;
@@ -644,6 +693,7 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
   }
   ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, workspace, st);
   if (r != YTN_OK) return r;
+  if ((r = unstage()) != YTN_OK) return r;
   if (res) {
     res->useful_flops = p->flops;
     res->precision = split ? YTN_SPLIT_BF16 : YTN_FP64;

@@ -110,6 +110,7 @@ SYMBOLS = {
     "ytn_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(ytn_plan_info)]),
     "ytn_plan_release": (None, [C.c_void_p]),
     "ytn_workspace_size": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
+    "ytn_workspace_size_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
     "ytn_tensordot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                 C.c_void_p, C.c_size_t, C.POINTER(ytn_result), C.c_void_p]),
     "ytn_tensordot_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -393,6 +394,13 @@ def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None, 
 def ytn_workspace_size(plan, prec=YTN_FP64, rtol=0.0):
     n = C.c_size_t()
     _check(_lib.ytn_workspace_size(plan.handle, prec, float(rtol), C.byref(n)))
+    return n.value
+
+
+def ytn_workspace_size_staged(plan, prec=YTN_FP64, rtol=0.0):
+    """Workspace with which host operands are staged by the copy engines."""
+    n = C.c_size_t()
+    _check(_lib.ytn_workspace_size_staged(plan.handle, prec, float(rtol), C.byref(n)))
     return n.value
 
 

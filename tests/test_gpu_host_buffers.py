@@ -133,3 +133,53 @@ def test_split_gemm_on_a_subset_of_the_sms(ctx):
             np.testing.assert_array_equal(rec["data"], ref["data"])
     finally:
         ytn.ytn_ctx_set_gemm_sms(ctx, 0)
+
+
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("where", ["host_all", "host_a", "host_c"])
+def test_host_buffers_staged_by_copy_engines(ctx, split, where):
+    """With a staging workspace (ytn_workspace_size_staged) host operands move with
+    the copy engines: same bits as the device-buffer path."""
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    prec, rtol = (ytn.YTN_SPLIT_BF16, 1e-10) if split else (ytn.YTN_FP64, 0.0)
+    rng = np.random.default_rng(654)
+    A, B, axa, axb, _, _ = random_pair(rng, (0, 0), 4, 3, 2, max_sectors=3, max_dim=7)
+    plan, ref_dev, _ = run_tensordot(ctx, A, B, axa, axb, prec=prec, rtol=rtol)
+    n = plan.out["size"]
+    dev = device()
+    a = _pinned(A["data"]) if where in ("host_all", "host_a") else torch.from_numpy(A["data"]).to(dev)
+    b = _pinned(B["data"]) if where == "host_all" else torch.from_numpy(B["data"]).to(dev)
+    if where in ("host_all", "host_c"):
+        c = torch.full((max(n, 1),), float("nan"), dtype=torch.float64).pin_memory()
+    else:
+        c = torch.full((max(n, 1),), float("nan"), dtype=torch.float64, device=dev)
+    nb = ytn.ytn_workspace_size_staged(plan, prec, rtol)
+    assert nb > ytn.ytn_workspace_size(plan, prec, rtol)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    ytn.ytn_tensordot(plan, a, b, c, prec=prec, rtol=rtol, workspace=ws)
+    ytn.ytn_sync(ctx)
+    np.testing.assert_array_equal(c[:n].cpu().numpy(), ref_dev["data"])
+
+
+def test_full_size_workload_staged_from_host(ctx):
+    """The D = 14 environment contraction from and to page-locked host memory through
+    the staging workspace: every element equals the device-buffer path."""
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    cfg = W.config5(D=14)
+    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    n = plan.out["size"]
+    a, b = _pinned(A["data"]), _pinned(B["data"])
+    c = torch.full((n,), float("nan"), dtype=torch.float64).pin_memory()
+    ws = torch.empty(ytn.ytn_workspace_size_staged(plan, ytn.YTN_SPLIT_BF16, 1e-10), dtype=torch.uint8,
+                     device=device())
+    ytn.ytn_tensordot(plan, a, b, c, prec=ytn.YTN_SPLIT_BF16, rtol=1e-10, workspace=ws)
+    ytn.ytn_sync(ctx)
+    da, db = a.to(device()), b.to(device())
+    dc = torch.empty(n, dtype=torch.float64, device=device())
+    ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_SPLIT_BF16, rtol=1e-10, workspace=ws)
+    ytn.ytn_sync(ctx)
+    np.testing.assert_array_equal(c.numpy(), dc.cpu().numpy())
+
