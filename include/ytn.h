@@ -339,10 +339,10 @@ ytn_status ytn_vdot(ytn_plan_t *plan, const double *a, const double *b, double *
 ytn_status ytn_swap_gate(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);
 
 /* Block-diagonal SVD (an SVD plan): every sector matrix of a is gathered into the
- * workspace and factored by the dense solver of the CUDA toolkit (Jacobi SVD,
- * one call per sector on stream; the paper leaves this to the backend), then U,
- * S and V are written to u, s, v (buffers of their planned sizes; device or
- * page-locked host memory). Singular vectors are unique up to sign (and rotation
+ * workspace and factored by the dense solver of the CUDA toolkit (SVD by polar
+ * decomposition, one call per sector on stream, which waits for the host part of
+ * each call; the paper leaves this to the backend), then U, S and V are written
+ * to u, s, v (buffers of their planned sizes; device or page-locked host memory). Singular vectors are unique up to sign (and rotation
  * within repeated values). workspace: ytn_workspace_size bytes (the sector
  * matrices, the factors, the solver's buffer). The first SVD plan of a context
  * creates the solver handle. Errors: YTN_E_INVALID, YTN_E_WORKSPACE, YTN_E_CUDA

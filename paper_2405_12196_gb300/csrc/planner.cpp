@@ -1791,6 +1791,7 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
     for (auto &r : kv.second.rows) { roff[si][r.first] = sv.m; sv.m += r.second.first; }
     for (auto &c : kv.second.cols) { coff[si][c.first] = sv.n; sv.n += c.second.first; }
     sv.k = std::min(sv.m, sv.n);
+    sv.trans = sv.n < sv.m ? 1 : 0;
     if (sv.m > INT32_MAX || sv.n > INT32_MAX) { err = "sector too large"; return YTN_E_UNSUPPORTED; }
     sv.m_off = (int64_t)off;
     off += align32(sv.m * sv.n);
@@ -1840,7 +1841,7 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
   p->jobs.clear();
   p->items.clear();
   p->moved = 0;
-  // gather A -> M_c (row-major, ld = n)
+  // gather A -> M_c (row-major, ld = n; column-major, ld = m, when trans)
   si = 0;
   for (auto &kv : secs) {
     const SvdSector &sv = p->svd_sec[si];
@@ -1852,9 +1853,10 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
       for (int i = (int)rowL.size() - 1; i >= 0; i--) { rs[i] = acc; acc *= A.dim(b, rowL[i]); }
       acc = 1;
       for (int i = (int)colL.size() - 1; i >= 0; i--) { cs[i] = acc; acc *= A.dim(b, colL[i]); }
-      for (size_t i = 0; i < rowL.size(); i++) dims.push_back({A.dim(b, rowL[i]), st[rowL[i]], rs[i] * sv.n});
-      for (size_t i = 0; i < colL.size(); i++) dims.push_back({A.dim(b, colL[i]), st[colL[i]], cs[i]});
-      const int64_t dst = sv.m_off + roff[si][sub_charges(A, b, rowL)] * sv.n + coff[si][sub_charges(A, b, colL)];
+      const int64_t rstep = sv.trans ? 1 : sv.n, cstep = sv.trans ? sv.m : 1;
+      for (size_t i = 0; i < rowL.size(); i++) dims.push_back({A.dim(b, rowL[i]), st[rowL[i]], rs[i] * rstep});
+      for (size_t i = 0; i < colL.size(); i++) dims.push_back({A.dim(b, colL[i]), st[colL[i]], cs[i] * cstep});
+      const int64_t dst = sv.m_off + roff[si][sub_charges(A, b, rowL)] * rstep + coff[si][sub_charges(A, b, colL)] * cstep;
       ytn_status s = add_copy(p, dims, A.off[b], dst, err);
       if (s != YTN_OK) return s;
       covered += A.elems(b);
@@ -1867,7 +1869,7 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
   p->items_a_begin = 0;
   make_items(p, j0, j1);
   p->items_a_end = (int64_t)p->items.size();
-  // U blocks from V' (m x k, column-major): element (row r, j) at vp_off + j*m + r
+  // U blocks from F_m (m x k, column-major): element (row r, j) at vp_off + j*m + r
   for (size_t id = 0; id < uplace.size(); id++) {
     const Place &pl = uplace[id];
     const SvdSector &sv = p->svd_sec[pl.sec];
@@ -1879,7 +1881,7 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
   p->items_b_begin = (int64_t)p->items.size();
   make_items(p, j1, j2);
   p->items_b_end = (int64_t)p->items.size();
-  // V blocks from U' (n x k, column-major): element (j, col c) at up_off + j*n + c
+  // V blocks from F_n (n x k, column-major): element (j, col c) at up_off + j*n + c
   for (size_t id = 0; id < vplace.size(); id++) {
     const Place &pl = vplace[id];
     const SvdSector &sv = p->svd_sec[pl.sec];

@@ -215,13 +215,14 @@ struct HostSector {
 
 enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap = 6, Conj = 7, Svd = 8, Slice = 9 };
 
-// One charge sector of a block-diagonal SVD: the dense m x n matrix M (row-major;
-// column-major it is M^T, n x m, which is what the solver factors: M^T = U' S V'^T,
-// so M = V' S U'^T), and where its factors live in the workspace (offsets in
-// doubles): M, U' (n x k, column-major), V' (m x k, column-major), S (k).
+// One charge sector of a block-diagonal SVD: the dense m x n matrix M and where
+// its factors live in the workspace (offsets in doubles). The solver factors a
+// column-major X with at least as many rows as columns: X = M^T (M stored
+// row-major) when n >= m, else X = M (stored column-major; trans = 1). Either
+// way M = F_m diag(S) F_n^T with F_m (m x k) and F_n (n x k) column-major.
 struct SvdSector {
-  int64_t m, n, k;
-  int64_t m_off, up_off, vp_off, s_off;
+  int64_t m, n, k, trans;
+  int64_t m_off, up_off, vp_off, s_off;   // X, F_n, F_m, S
 };
 
 struct Plan;
@@ -272,6 +273,7 @@ struct ytn_plan_s {
   std::vector<ytn::SvdSector> svd_sec;
   int64_t items_s_begin = 0, items_s_end = 0;   // S vectors -> S diagonals
   size_t svd_m_doubles = 0, svd_ws_doubles = 0, svd_info_off = 0, svd_lwork = 0;
+  std::vector<char> svd_host_ws;   // the solver's host buffer (one call at a time)
   bool svd_zero_m = false;
   // doubles per element of the copy jobs that add_copy makes: 2 for complex
   // tensors moved whole (fuse, unfuse, swap gate, conj), else 1

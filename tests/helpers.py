@@ -7,19 +7,22 @@ import workloads as W
 
 
 def random_legs(rng, mods, rank, max_sectors=3, max_dim=3):
-    """Random legs for the given symmetry: a few charges per leg, small dimensions."""
+    """Random legs for the given symmetry: a few charges per leg, small dimensions.
+    U(1) components range over -2..2 alone and over -1..1 in product groups (so that
+    blocks of several legs still meet often)."""
     nsym = len(mods)
+    span = 2 if nsym == 1 else 1
     legs = []
     for _ in range(rank):
         avail = 1
         for m in mods:
-            avail *= m if m else 5
+            avail *= m if m else 2 * span + 1
         ns = int(rng.integers(1, min(max_sectors, avail) + 1))
         charges = set()
         while len(charges) < ns:
             q = []
             for m in mods:
-                q.append(int(rng.integers(0, m)) if m else int(rng.integers(-2, 3)))
+                q.append(int(rng.integers(0, m)) if m else int(rng.integers(-span, span + 1)))
             charges.add(tuple(q))
         ts = sorted(charges)
         ds = [int(rng.integers(1, max_dim + 1)) for _ in ts]

@@ -35,9 +35,10 @@ def test_tensordot_with_host_buffers(ctx, split, where):
     import torch
     from paper_2405_12196_gb300 import ytn
     prec, rtol = (ytn.YTN_SPLIT_BF16, 1e-10) if split else (ytn.YTN_FP64, 0.0)
-    rng = np.random.default_rng(321)
-    A, B, axa, axb, _, _ = random_pair(rng, (0,), 4, 3, 2, max_sectors=3, max_dim=7)
+    cfg = W.config1()
+    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
     plan, ref_dev, _ = run_tensordot(ctx, A, B, axa, axb, prec=prec, rtol=rtol)
+    assert plan.out["size"] > 0
     n = plan.out["size"]
     dev = device()
     a = _pinned(A["data"]) if where in ("host_all", "host_a") else torch.from_numpy(A["data"]).to(dev)
@@ -120,9 +121,12 @@ def test_split_gemm_on_a_subset_of_the_sms(ctx):
     """The persistent split GEMM on fewer CTAs than SMs gives the same bits."""
     import torch
     from paper_2405_12196_gb300 import ytn
-    rng = np.random.default_rng(77)
-    A, B, axa, axb, _, _ = random_pair(rng, (0, 0), 3, 3, 2, max_sectors=4, max_dim=9)
+    cfg = W.config2()
+    A = cfg["A"]
+    B = dict(A, sig=tuple(-s for s in A["sig"]), n=tuple(-q for q in A["n"]))
+    axa = axb = (4,)
     plan, ref, _ = run_tensordot(ctx, A, B, axa, axb, prec=ytn.YTN_SPLIT_BF16, rtol=1e-10)
+    assert plan.info["useful_flops"] > 0
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     with pytest.raises(ytn.YtnError):
         ytn.ytn_ctx_set_gemm_sms(ctx, nsm + 1)
@@ -143,9 +147,10 @@ def test_host_buffers_staged_by_copy_engines(ctx, split, where):
     import torch
     from paper_2405_12196_gb300 import ytn
     prec, rtol = (ytn.YTN_SPLIT_BF16, 1e-10) if split else (ytn.YTN_FP64, 0.0)
-    rng = np.random.default_rng(654)
-    A, B, axa, axb, _, _ = random_pair(rng, (0, 0), 4, 3, 2, max_sectors=3, max_dim=7)
+    cfg = W.config1()
+    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
     plan, ref_dev, _ = run_tensordot(ctx, A, B, axa, axb, prec=prec, rtol=rtol)
+    assert plan.out["size"] > 0
     n = plan.out["size"]
     dev = device()
     a = _pinned(A["data"]) if where in ("host_all", "host_a") else torch.from_numpy(A["data"]).to(dev)

@@ -398,3 +398,30 @@ def test_config5_full_size_split_vs_fp64(ctx):
         got = rsp["data"][rsp["off"][b]:rsp["off"][b] + sizes[b]].reshape(want.shape)
         assert rel_frobenius(got, want) <= SPLIT_RTOL
     del torch
+
+
+def _u1u1_pair(seed, ncon):
+    """A, B on U(1)xU(1) legs over {(0,0), (+-1,0), (0,+-1)} with total charge 0, so
+    that many blocks meet (random legs of a product group rarely do)."""
+    rng = np.random.default_rng(seed)
+    pool = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1)]
+
+    def leg():
+        return W.Leg(int(rng.choice([-1, 1])), pool, [int(d) for d in rng.integers(1, 7, len(pool))])
+    la = [leg() for _ in range(3)]
+    lb = [la[i].conj() for i in range(ncon)] + [leg() for _ in range(3 - ncon)]
+    A = W.random_tensor((0, 0), la, (0, 0), seed + 1)
+    B = W.random_tensor((0, 0), lb, (0, 0), seed + 2)
+    return A, B, tuple(range(ncon)), tuple(range(ncon))
+
+
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("case", range(4))
+def test_u1u1_tensordot(ctx, case, split):
+    A, B, axa, axb = _u1u1_pair(71000 + case, 1 + case % 2)
+    if split:
+        _, rec, res = _split(ctx, A, B, axa, axb)
+    else:
+        _, rec, res = run_tensordot(ctx, A, B, axa, axb)
+    assert res["useful_flops"] > 0
+    check_against_oracle(rec, oracle_tensordot(A, B, axa, axb), rtol=SPLIT_RTOL if split else FP64_RTOL)
