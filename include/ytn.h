@@ -169,8 +169,8 @@ typedef enum {
  *  CONJ:      a. Sec. II.A footnote: every leg's signature flips (n becomes
  *             -n, fusion records' constituent signatures flip) and complex
  *             elements are conjugated; blocks keep their charges and places.
- *  SVD:       a (real), ngroups = 2: the row legs, then the column legs (every
- *             leg once). Three outputs (ytn_plan_output_at 0, 1, 2): U on (row
+ *  SVD:       a (real or complex), ngroups = 2: the row legs, then the
+ *             column legs (every leg once). Three outputs (ytn_plan_output_at 0, 1, 2): U on (row
  *             legs, new leg, signature -1), S on (new leg +1, new leg -1) with a
  *             k x k diagonal block per sector, V on (new leg +1, column legs);
  *             the new leg carries the signed sum c of the row charges, with

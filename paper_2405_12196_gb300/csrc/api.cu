@@ -788,6 +788,9 @@ ytn_status ytn_svd(ytn_plan_t *p, const double *a, double *u, double *s, double 
   if (r != YTN_OK) return r;
   if (p->outs[0].size && (e = cudaMemsetAsync(s, 0, (size_t)p->outs[0].size * sizeof(double), st)) != cudaSuccess)
     return cuda_fail(e, "memset S");
+  if ((e = launch_copy(p->d_jobs, p->d_items + p->items_h_begin, p->items_h_end - p->items_h_begin, ws, ws, st)) !=
+      cudaSuccess)
+    return cuda_fail(e, "conjugate a factor");
   if ((e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, ws, u, st)) !=
           cudaSuccess ||
       (e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, ws, v, st)) !=

@@ -1725,7 +1725,8 @@ ytn_status plan_conj(ytn_plan_t *p, const Tensor &A, std::string &err) {
 // col legs); the new leg has charge c and dimension k_c = min(m_c, n_c).
 ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
                     std::string &err) {
-  if (A.dtype != YTN_REAL64) { err = "SVD of complex data is not built"; return YTN_E_UNSUPPORTED; }
+  const int w = A.dtype == YTN_COMPLEX128 ? 2 : 1;   // doubles per element
+  p->cw = w;   // the gathers and scatters below move whole (complex) elements
   if (ngroups != 2 || group_size[0] < 1 || group_size[1] < 1 || group_size[0] + group_size[1] != A.rank) {
     err = "an SVD takes two nonempty groups of legs: rows and columns";
     return YTN_E_INVALID;
@@ -1767,6 +1768,7 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
     copy_fusion(A.fus[rowL[i]].get(), U.fus[i]);
   }
   U.sig[rowL.size()] = -1;
+  U.dtype = V.dtype = A.dtype;   // S is real
   S.rank = 2;
   S.sig[0] = 1;
   S.sig[1] = -1;
@@ -1827,9 +1829,10 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
     }
     si++;
   }
-  p->svd_m_doubles = off;
+  p->svd_m_doubles = w * off;
   for (auto &sv : p->svd_sec) { sv.up_off = (int64_t)off; off += align32(sv.n * sv.k); }
   for (auto &sv : p->svd_sec) { sv.vp_off = (int64_t)off; off += align32(sv.m * sv.k); }
+  off *= w;   // from here on, doubles
   for (auto &sv : p->svd_sec) { sv.s_off = (int64_t)off; off += align32(sv.k); }
   p->svd_info_off = off;                       // one int per sector (as doubles: rounded up)
   off += align32(((int64_t)p->svd_sec.size() + 1) / 2 + 1);
@@ -1893,16 +1896,32 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
   p->items_c_begin = (int64_t)p->items.size();
   make_items(p, j2, j3);
   p->items_c_end = (int64_t)p->items.size();
-  // S diagonals from the singular-value vectors (the rest of S is zero)
+  // S diagonals from the singular-value vectors (real; the rest of S is zero)
+  p->cw = 1;
   for (size_t id = 0; id < p->svd_sec.size(); id++) {
     const SvdSector &sv = p->svd_sec[id];
     if (sv.k == 0) continue;
     ytn_status s = add_copy(p, {{sv.k, 1, sv.k + 1}}, sv.s_off, so[id], err);
     if (s != YTN_OK) return s;
   }
+  const size_t j4 = p->jobs.size();
   p->items_s_begin = (int64_t)p->items.size();
-  make_items(p, j3, p->jobs.size());
+  make_items(p, j3, j4);
   p->items_s_end = (int64_t)p->items.size();
+  // complex data: the solver factors X = M^T (or M) as U_x S V_x^H, so that
+  // M = conj(V_x) S U_x^T (or U_x S conj(V_x)^T): the factor F_m (or F_n) is
+  // conjugated in place before the scatters (imaginary parts negated)
+  p->cw = w;
+  if (w == 2)
+    for (const SvdSector &sv : p->svd_sec) {
+      if (sv.k == 0) continue;
+      const int64_t o = sv.trans ? sv.up_off : sv.vp_off, n = sv.trans ? sv.n * sv.k : sv.m * sv.k;
+      ytn_status s = add_copy(p, {{n, 1, 1}}, o, o, err, 2);
+      if (s != YTN_OK) return s;
+    }
+  p->items_h_begin = (int64_t)p->items.size();
+  make_items(p, j4, p->jobs.size());
+  p->items_h_end = (int64_t)p->items.size();
   p->out = U;
   p->outs = {S, V};
   p->kind = Kind::Svd;

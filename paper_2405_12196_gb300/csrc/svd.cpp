@@ -46,13 +46,14 @@ ytn_status svd_prepare(ytn_plan_t *p) {
   auto h = static_cast<cusolverDnHandle_t>(ctx->solver);
   auto prm = static_cast<cusolverDnParams_t>(ctx->svd_params);
   size_t dev_bytes = 0, host_bytes = 0;
+  const cudaDataType T = p->out.dtype == YTN_COMPLEX128 ? CUDA_C_64F : CUDA_R_64F;
   for (const SvdSector &sv : p->svd_sec) {
     if (sv.k == 0) continue;
     const int64_t rows = std::max(sv.m, sv.n), cols = sv.k;
     size_t d = 0, hb = 0;
-    cusolverStatus_t s = cusolverDnXgesvdp_bufferSize(h, prm, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, CUDA_R_64F,
-                                                      nullptr, rows, CUDA_R_64F, nullptr, CUDA_R_64F, nullptr, rows,
-                                                      CUDA_R_64F, nullptr, cols, CUDA_R_64F, &d, &hb);
+    cusolverStatus_t s = cusolverDnXgesvdp_bufferSize(h, prm, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, T, nullptr,
+                                                      rows, CUDA_R_64F, nullptr, T, nullptr, rows, T, nullptr, cols, T,
+                                                      &d, &hb);
     if (s != CUSOLVER_STATUS_SUCCESS) return fail(YTN_E_CUDA, std::string("buffer size: ") + solver_error(s));
     dev_bytes = std::max(dev_bytes, d);
     host_bytes = std::max(host_bytes, hb);
@@ -75,17 +76,19 @@ ytn_status svd_factor(ytn_plan_t *p, double *ws, void *stream) {
   if (s != CUSOLVER_STATUS_SUCCESS) return fail(YTN_E_CUDA, std::string("set stream: ") + solver_error(s));
   int *info = reinterpret_cast<int *>(ws + p->svd_info_off);
   double *work = ws + p->svd_ws_doubles;
+  const bool cplx = p->out.dtype == YTN_COMPLEX128;
+  const cudaDataType T = cplx ? CUDA_C_64F : CUDA_R_64F;
+  const int64_t w = cplx ? 2 : 1;   // element offsets -> doubles
   for (size_t i = 0; i < p->svd_sec.size(); i++) {
     const SvdSector &sv = p->svd_sec[i];
     if (sv.k == 0) continue;
     const int64_t rows = std::max(sv.m, sv.n), cols = sv.k;
-    double *ux = sv.trans ? ws + sv.vp_off : ws + sv.up_off;   // rows x k
-    double *vx = sv.trans ? ws + sv.up_off : ws + sv.vp_off;   // cols x k
+    double *ux = ws + w * (sv.trans ? sv.vp_off : sv.up_off);   // rows x k
+    double *vx = ws + w * (sv.trans ? sv.up_off : sv.vp_off);   // cols x k
     double err_sigma = 0.0;
-    s = cusolverDnXgesvdp(h, prm, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, CUDA_R_64F, ws + sv.m_off, rows,
-                          CUDA_R_64F, ws + sv.s_off, CUDA_R_64F, ux, rows, CUDA_R_64F, vx, cols, CUDA_R_64F, work,
-                          p->svd_lwork * sizeof(double), p->svd_host_ws.data(), p->svd_host_ws.size(), info + i,
-                          &err_sigma);
+    s = cusolverDnXgesvdp(h, prm, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, T, ws + w * sv.m_off, rows, CUDA_R_64F,
+                          ws + sv.s_off, T, ux, rows, T, vx, cols, T, work, p->svd_lwork * sizeof(double),
+                          p->svd_host_ws.data(), p->svd_host_ws.size(), info + i, &err_sigma);
     if (s != CUSOLVER_STATUS_SUCCESS) return fail(YTN_E_CUDA, std::string("polar-decomposition SVD: ") + solver_error(s));
   }
   return YTN_OK;

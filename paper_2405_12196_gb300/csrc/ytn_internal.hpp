@@ -222,7 +222,8 @@ enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap
 // way M = F_m diag(S) F_n^T with F_m (m x k) and F_n (n x k) column-major.
 struct SvdSector {
   int64_t m, n, k, trans;
-  int64_t m_off, up_off, vp_off, s_off;   // X, F_n, F_m, S
+  int64_t m_off, up_off, vp_off;   // X, F_n, F_m: offsets in elements (complex: pairs)
+  int64_t s_off;                   // S (real): offset in doubles
 };
 
 struct Plan;
@@ -272,6 +273,7 @@ struct ytn_plan_s {
   // SVD: sectors, the copy-item ranges of the output scatters, workspace layout
   std::vector<ytn::SvdSector> svd_sec;
   int64_t items_s_begin = 0, items_s_end = 0;   // S vectors -> S diagonals
+  int64_t items_h_begin = 0, items_h_end = 0;   // complex: conjugate one factor in place
   size_t svd_m_doubles = 0, svd_ws_doubles = 0, svd_info_off = 0, svd_lwork = 0;
   std::vector<char> svd_host_ws;   // the solver's host buffer (one call at a time)
   bool svd_zero_m = false;

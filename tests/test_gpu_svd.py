@@ -118,3 +118,31 @@ def test_svd_of_the_ctm_enlarged_corner(ctx):
     _, ref_S, _ = O.svd(O.from_record(corner), rows, cols)
     _check(corner, rows, cols, U, S, V, ref_S)
     assert max(b.shape[0] for b in S.blocks.values()) > 500
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_complex_svd(ctx, seed):
+    """Complex tensors: complex U and V, real S; the same checks with conjugate
+    transposes."""
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    rng = np.random.default_rng(450 + seed)
+    pool = [(0,), (1,), (-1,)]
+    legs = [W.Leg(s, pool, [int(d) for d in rng.integers(1, 9, 3)]) for s in (1, 1, -1, -1)]
+    A = W.random_tensor((0,), legs, (0,), seed, dtype="c128")
+    rows, cols = ((0, 2), (1, 3)) if seed == 0 else ((0,), (1, 2, 3))
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_SVD, A, groups=(rows, cols))
+    dts = [torch.complex128, torch.float64, torch.complex128]
+    bufs = [torch.full((max(o["size"], 1),), float("nan"), dtype=dt, device=device()) for o, dt in zip(plan.outs, dts)]
+    ws = torch.empty(ytn.ytn_workspace_size(plan), dtype=torch.uint8, device=device())
+    ytn.ytn_svd(plan, torch.from_numpy(A["data"]).to(device()), *bufs, workspace=ws)
+    ytn.ytn_sync(ctx)
+    recs = []
+    for o, b in zip(plan.outs, bufs):
+        r = dict(o)
+        r["data"] = b[:o["size"]].cpu().numpy()
+        recs.append(O.from_record(r))
+    U, S, V = recs
+    _, ref_S, _ = O.svd(O.from_record(A), rows, cols)
+    _check(A, rows, cols, U, S, V, ref_S)
+
