@@ -44,7 +44,7 @@ __all__ = [
     "OTensor", "OracleError", "SignatureError", "DimMismatchError", "FusionMismatchError",
     "ChargeError", "InvalidError", "UnsupportedError",
     "from_record", "to_record", "conj", "tensordot", "fuse", "unfuse", "trace",
-    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon", "einsum", "svd", "truncation", "slice_leg",
+    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon", "einsum", "svd", "eigh", "truncation", "slice_leg",
 ]
 
 
@@ -696,6 +696,51 @@ def svd(A, row_legs, col_legs):
         for ck, o in coff.items():
             V.blocks[(c,) + ck] = vh[:, o:o + cols[c][ck]].reshape((k,) + cshape[ck])
     return U, S, V
+
+
+def eigh(A, row_legs, col_legs):
+    """Block-diagonal eigendecomposition of a Hermitian matrix-shaped tensor (the
+    eigen-variant of the CTM's decompositions, Sec. III; the paper leaves it to the
+    backend's linear algebra). The column legs must be the duals of the row legs,
+    in the same order, and n = 0, so that every sector matrix M_c is square with
+    columns ordered as its rows; M_c = U_c diag(w_c) U_c^H with w_c ascending
+    (numpy's eigh on the lower triangle). Returns (U, S): U on (row legs, new leg of
+    signature -1), S on (new leg +1, new leg -1) with diag(w_c) per sector."""
+    row_legs, col_legs = tuple(int(a) for a in row_legs), tuple(int(b) for b in col_legs)
+    if len(row_legs) != len(col_legs) or sorted(row_legs + col_legs) != list(range(A.rank)):
+        raise InvalidError("rows and columns must split the legs into two groups of equal size")
+    if any(A.sig[a] != -A.sig[b] for a, b in zip(row_legs, col_legs)) or any(A.n):
+        raise SignatureError("eigh needs dual row and column legs and n = 0")
+    U, S, _ = svd(A, row_legs, col_legs)   # structure only: rows, sectors, offsets
+    mods = A.mods
+    Uo = OTensor(mods, U.sig, U.n, fus=list(U.fus), dtype=A.dtype)
+    So = OTensor(mods, S.sig, S.n, dtype=np.float64)
+    rows, sect = {}, {}
+    for key, blk in A.blocks.items():
+        rk, ck = tuple(key[a] for a in row_legs), tuple(key[b] for b in col_legs)
+        c = tuple([0] * A.nsym)
+        for a in row_legs:
+            c = _add(c, _scale(A.sig[a], key[a], mods), mods)
+        rows.setdefault(c, {})[rk] = tuple(blk.shape[a] for a in row_legs)
+        rows[c].setdefault(ck, tuple(blk.shape[b] for b in col_legs))
+        sect.setdefault(c, []).append(key)
+    for c in sorted(sect):
+        off, m = {}, 0
+        for rk in sorted(rows[c]):
+            off[rk] = m
+            m += int(np.prod(rows[c][rk]))
+        M = np.zeros((m, m), dtype=A.dtype)
+        for key in sect[c]:
+            blk = A.blocks[key]
+            rk, ck = tuple(key[a] for a in row_legs), tuple(key[b] for b in col_legs)
+            sub = np.transpose(blk, row_legs + col_legs).reshape(int(np.prod(rows[c][rk])), int(np.prod(rows[c][ck])))
+            M[off[rk]:off[rk] + sub.shape[0], off[ck]:off[ck] + sub.shape[1]] = sub
+        w, u = np.linalg.eigh(M)
+        for rk, o in off.items():
+            if rk + (c,) in U.blocks:
+                Uo.blocks[rk + (c,)] = u[o:o + int(np.prod(rows[c][rk])), :].reshape(rows[c][rk] + (m,))
+        So.blocks[(c, c)] = np.diag(w)
+    return Uo, So
 
 
 def truncation(S, D_total, tol=0.0):

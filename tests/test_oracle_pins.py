@@ -777,3 +777,29 @@ def test_svd_values_and_truncation_match_the_dense_svd(seed):
     assert err == pytest.approx(float(np.sqrt(np.sum(dense[D:] ** 2))), rel=1e-9, abs=1e-12)
     keep_tol = O.truncation(S, 10 ** 6, tol=0.5)
     assert sum(keep_tol.values()) == int(np.sum(dense >= 0.5 * dense[0]))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+@pytest.mark.parametrize("seed", range(3))
+def test_eigh_of_a_hermitian_tensor(seed, dtype):
+    """H = B + B^H on legs (r, r*): U diag(w) U^H == H, U^H U = 1, w ascending and
+    equal to the dense matrix's eigenvalues (numpy.linalg.eigvalsh)."""
+    rng = np.random.default_rng(500 + seed)
+    pool = [(0,), (1,), (-1,)]
+    r = [W.Leg(s, pool, [int(d) for d in rng.integers(1, 5, 3)]) for s in (1, -1)]
+    legs = r + [l.conj() for l in r]
+    B = O.from_record(W.random_tensor((0,), legs, (0,), seed, dtype=dtype))
+    Bh = O.fuse(O.conj(B), ((2,), (3,), (0,), (1,)))   # conj(B) with rows and columns swapped
+    H = O.OTensor(B.mods, B.sig, B.n, {k: B.blocks[k] + Bh.blocks[k] for k in B.blocks}, dtype=B.dtype)
+    U, S = O.eigh(H, (0, 1), (2, 3))
+    R = O.tensordot(O.tensordot(U, S, (2,), (0,)), O.fuse(O.conj(U), ((2,), (0,), (1,))), (2,), (0,))
+    for k in H.blocks:
+        np.testing.assert_allclose(R.blocks[k], H.blocks[k], rtol=1e-12, atol=1e-12)
+    UU = O.tensordot(O.conj(U), U, (0, 1), (0, 1))
+    for (c, _), blk in S.blocks.items():
+        w = np.diag(blk)
+        assert np.all(np.diff(w) >= 0)
+        np.testing.assert_allclose(UU.blocks[(c, c)], np.eye(w.size), atol=1e-12)
+    ours = np.sort(np.concatenate([np.diag(b) for b in S.blocks.values()]))
+    d = _dense_matrix(H, legs, (0, 1), (2, 3))
+    np.testing.assert_allclose(ours, np.linalg.eigvalsh(d), rtol=1e-10, atol=1e-12)
