@@ -138,7 +138,8 @@ typedef enum {
   YTN_OP_SWAP_GATE = 6,  /* fermionic swap gate between two groups of legs, Sec. IV */
   YTN_OP_CONJ = 7,       /* conjugate: signatures flip, elements conjugated       */
   YTN_OP_SVD = 8,        /* block-diagonal SVD: rows | columns, Sec. III (CTM)    */
-  YTN_OP_SLICE = 9       /* keep the first keep[c] indices of sectors of legs     */
+  YTN_OP_SLICE = 9,      /* keep the first keep[c] indices of sectors of legs     */
+  YTN_OP_EIGH = 10       /* block-diagonal Hermitian eigendecomposition           */
 } ytn_op_kind;
 
 /* A planned operation.
@@ -175,6 +176,11 @@ typedef enum {
  *             k x k diagonal block per sector, V on (new leg +1, column legs);
  *             the new leg carries the signed sum c of the row charges, with
  *             k_c = min(rows, columns) of sector c. U S V = a.
+ *  EIGH:      a (Hermitian), ngroups = 2: row legs, then column legs dual
+ *             to them in the same order, n = 0. Two outputs: U (row legs,
+ *             new leg -1) and S (new leg +1, new leg -1; diagonal eigenvalues
+ *             per sector, ascending); a = U S U^H. The lower triangle of each
+ *             sector matrix is read.
  *  SLICE:     a, naxes legs axa[]; nkeep rows of (keep_t[nsym] charge,
  *             keep_D dimension): every sector of those legs keeps its first
  *             keep_D indices (charges not listed keep 0: their blocks go).
@@ -349,6 +355,11 @@ ytn_status ytn_swap_gate(ytn_plan_t *plan, const double *a, double *out, ytn_str
  * (a solver error included). */
 ytn_status ytn_svd(ytn_plan_t *plan, const double *a, double *u, double *s, double *v, void *workspace,
                    size_t workspace_bytes, ytn_stream stream);
+
+/* Block-diagonal Hermitian eigendecomposition (an EIGH plan): as ytn_svd, with
+ * the toolkit's divide-and-conquer eigensolver per sector and outputs U and S. */
+ytn_status ytn_eigh(ytn_plan_t *plan, const double *a, double *u, double *s, void *workspace,
+                    size_t workspace_bytes, ytn_stream stream);
 
 /* out = slice of a (a SLICE plan). Bit-exact copies. Asynchronous on stream. */
 ytn_status ytn_slice(ytn_plan_t *plan, const double *a, double *out, ytn_stream stream);

@@ -367,6 +367,14 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
             if (st != YTN_OK) err = "dense solver set-up failed";
           }
           break;
+        case YTN_OP_EIGH:
+          st = plan_eigh(p, A, op->ngroups, op->group_size, op->order, err);
+          if (st == YTN_OK && ctx->device >= 0) {
+            DeviceGuard g(ctx->device);
+            st = svd_prepare(p);
+            if (st != YTN_OK) err = "dense solver set-up failed";
+          }
+          break;
         case YTN_OP_SLICE:
           st = plan_slice(p, A, op->naxes, op->axa, op->nkeep, op->keep_t, op->keep_D, err);
           break;
@@ -480,7 +488,7 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
     *bytes = align256(p->vd_chunks.size() * sizeof(double) * p->cw);
     return YTN_OK;
   }
-  if (p->kind == Kind::Svd) {
+  if (p->kind == Kind::Svd || p->kind == Kind::Eigh) {
     *bytes = align256((p->svd_ws_doubles + p->svd_lwork) * sizeof(double));
     return YTN_OK;
   }
@@ -758,12 +766,13 @@ ytn_status ytn_slice(ytn_plan_t *p, const double *a, double *out, ytn_stream str
   return run_move(p, Kind::Slice, a, out, stream, "slice");
 }
 
-ytn_status ytn_svd(ytn_plan_t *p, const double *a, double *u, double *s, double *v, void *workspace,
-                   size_t workspace_bytes, ytn_stream stream) {
+static ytn_status run_decomp(ytn_plan_t *p, Kind kind, const double *a, double *u, double *s, double *v,
+                             void *workspace, size_t workspace_bytes, ytn_stream stream) {
   if (!p) return fail(YTN_E_INVALID, "null plan");
-  if (p->kind != Kind::Svd) return fail(YTN_E_INVALID, "plan is not an SVD plan");
+  if (p->kind != kind) return fail(YTN_E_INVALID, kind == Kind::Svd ? "plan is not an SVD plan" : "plan is not an eigh plan");
   if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
-  if ((p->a_size && !a) || (p->out.size && !u) || (p->outs[0].size && !s) || (p->outs[1].size && !v))
+  const bool has_v = p->outs.size() > 1;
+  if ((p->a_size && !a) || (p->out.size && !u) || (p->outs[0].size && !s) || (has_v && p->outs[1].size && !v))
     return fail(YTN_E_INVALID, "null data buffer");
   const size_t need = align256((p->svd_ws_doubles + p->svd_lwork) * sizeof(double));
   if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))
@@ -793,12 +802,23 @@ ytn_status ytn_svd(ytn_plan_t *p, const double *a, double *u, double *s, double 
     return cuda_fail(e, "conjugate a factor");
   if ((e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, ws, u, st)) !=
           cudaSuccess ||
-      (e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, ws, v, st)) !=
-          cudaSuccess ||
+      (has_v &&
+       (e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, ws, v, st)) !=
+           cudaSuccess) ||
       (e = launch_copy(p->d_jobs, p->d_items + p->items_s_begin, p->items_s_end - p->items_s_begin, ws, s, st)) !=
           cudaSuccess)
-    return cuda_fail(e, "write U, S, V");
+    return cuda_fail(e, "write the factors");
   return YTN_OK;
+}
+
+ytn_status ytn_svd(ytn_plan_t *p, const double *a, double *u, double *s, double *v, void *workspace,
+                   size_t workspace_bytes, ytn_stream stream) {
+  return run_decomp(p, Kind::Svd, a, u, s, v, workspace, workspace_bytes, stream);
+}
+
+ytn_status ytn_eigh(ytn_plan_t *p, const double *a, double *u, double *s, void *workspace, size_t workspace_bytes,
+                    ytn_stream stream) {
+  return run_decomp(p, Kind::Eigh, a, u, s, nullptr, workspace, workspace_bytes, stream);
 }
 
 ytn_status ytn_vdot(ytn_plan_t *p, const double *a, const double *b, double *out, void *workspace,

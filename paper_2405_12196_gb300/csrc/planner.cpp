@@ -1723,8 +1723,24 @@ ytn_status plan_conj(ytn_plan_t *p, const Tensor &A, std::string &err) {
 // and factored by the dense solver. Outputs: U (row legs, new leg of signature -1),
 // S (new leg +1, new leg -1; a k x k diagonal block per sector), V (new leg +1,
 // col legs); the new leg has charge c and dimension k_c = min(m_c, n_c).
+// eig: the Hermitian eigendecomposition instead (column legs dual to the row
+// legs, n = 0, square sectors; M_c = U_c diag(w_c) U_c^H, w ascending): M_c is
+// gathered column-major, the solver overwrites it with U_c, and there is no V.
+static ytn_status plan_decomp(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
+                              bool eig, std::string &err);
+
 ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
                     std::string &err) {
+  return plan_decomp(p, A, ngroups, group_size, order, false, err);
+}
+
+ytn_status plan_eigh(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
+                     std::string &err) {
+  return plan_decomp(p, A, ngroups, group_size, order, true, err);
+}
+
+static ytn_status plan_decomp(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
+                              bool eig, std::string &err) {
   const int w = A.dtype == YTN_COMPLEX128 ? 2 : 1;   // doubles per element
   p->cw = w;   // the gathers and scatters below move whole (complex) elements
   if (ngroups != 2 || group_size[0] < 1 || group_size[1] < 1 || group_size[0] + group_size[1] != A.rank) {
@@ -1740,6 +1756,13 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
   if ((int)rowL.size() + 1 > YTN_MAX_RANK || (int)colL.size() + 1 > YTN_MAX_RANK) {
     err = "SVD output rank too large";
     return YTN_E_UNSUPPORTED;
+  }
+  if (eig) {
+    if (rowL.size() != colL.size()) { err = "eigh needs as many column legs as row legs"; return YTN_E_INVALID; }
+    for (size_t i = 0; i < rowL.size(); i++)
+      if (A.sig[rowL[i]] != -A.sig[colL[i]]) { err = "eigh needs column legs dual to the row legs"; return YTN_E_SIGNATURE; }
+    for (int c = 0; c < A.nsym; c++)
+      if (A.n[c] != 0) { err = "eigh needs total charge 0"; return YTN_E_CHARGE; }
   }
   const int nsym = A.nsym;
   struct Sec {
@@ -1792,8 +1815,15 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
     SvdSector sv{};
     for (auto &r : kv.second.rows) { roff[si][r.first] = sv.m; sv.m += r.second.first; }
     for (auto &c : kv.second.cols) { coff[si][c.first] = sv.n; sv.n += c.second.first; }
+    if (eig) {
+      // square, columns in the order of the rows (dual legs: the same tuples)
+      bool same = kv.second.rows.size() == kv.second.cols.size();
+      for (auto r = kv.second.rows.begin(), c = kv.second.cols.begin(); same && r != kv.second.rows.end(); ++r, ++c)
+        same = r->first == c->first && r->second.first == c->second.first;
+      if (!same) { err = "eigh: a sector whose columns do not match its rows"; return YTN_E_DIM_MISMATCH; }
+    }
     sv.k = std::min(sv.m, sv.n);
-    sv.trans = sv.n < sv.m ? 1 : 0;
+    sv.trans = (eig || sv.n < sv.m) ? 1 : 0;
     if (sv.m > INT32_MAX || sv.n > INT32_MAX) { err = "sector too large"; return YTN_E_UNSUPPORTED; }
     sv.m_off = (int64_t)off;
     off += align32(sv.m * sv.n);
@@ -1818,6 +1848,7 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
       sb.push_back(ob);
     }
     for (auto &c : kv.second.cols) {
+      if (eig) break;
       OutBlock ob;
       ob.key = kv.first;
       ob.key.insert(ob.key.end(), c.first.begin(), c.first.end());
@@ -1830,8 +1861,16 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
     si++;
   }
   p->svd_m_doubles = w * off;
-  for (auto &sv : p->svd_sec) { sv.up_off = (int64_t)off; off += align32(sv.n * sv.k); }
-  for (auto &sv : p->svd_sec) { sv.vp_off = (int64_t)off; off += align32(sv.m * sv.k); }
+  for (auto &sv : p->svd_sec) {
+    if (eig) { sv.up_off = sv.vp_off = sv.m_off; continue; }   // U overwrites the matrix
+    sv.up_off = (int64_t)off;
+    off += align32(sv.n * sv.k);
+  }
+  for (auto &sv : p->svd_sec) {
+    if (eig) continue;
+    sv.vp_off = (int64_t)off;
+    off += align32(sv.m * sv.k);
+  }
   off *= w;   // from here on, doubles
   for (auto &sv : p->svd_sec) { sv.s_off = (int64_t)off; off += align32(sv.k); }
   p->svd_info_off = off;                       // one int per sector (as doubles: rounded up)
@@ -1912,7 +1951,7 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
   // M = conj(V_x) S U_x^T (or U_x S conj(V_x)^T): the factor F_m (or F_n) is
   // conjugated in place before the scatters (imaginary parts negated)
   p->cw = w;
-  if (w == 2)
+  if (w == 2 && !eig)
     for (const SvdSector &sv : p->svd_sec) {
       if (sv.k == 0) continue;
       const int64_t o = sv.trans ? sv.up_off : sv.vp_off, n = sv.trans ? sv.n * sv.k : sv.m * sv.k;
@@ -1923,8 +1962,9 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
   make_items(p, j4, p->jobs.size());
   p->items_h_end = (int64_t)p->items.size();
   p->out = U;
-  p->outs = {S, V};
-  p->kind = Kind::Svd;
+  if (eig) p->outs = {S};
+  else p->outs = {S, V};
+  p->kind = eig ? Kind::Eigh : Kind::Svd;
   p->a_size = A.size;
   double fl = 0.0;
   for (auto &sv : p->svd_sec) fl += 4.0 * (double)sv.m * sv.n * sv.k;   // nominal dense SVD work

@@ -51,9 +51,12 @@ ytn_status svd_prepare(ytn_plan_t *p) {
     if (sv.k == 0) continue;
     const int64_t rows = std::max(sv.m, sv.n), cols = sv.k;
     size_t d = 0, hb = 0;
-    cusolverStatus_t s = cusolverDnXgesvdp_bufferSize(h, prm, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, T, nullptr,
-                                                      rows, CUDA_R_64F, nullptr, T, nullptr, rows, T, nullptr, cols, T,
-                                                      &d, &hb);
+    cusolverStatus_t s =
+        p->kind == Kind::Eigh
+            ? cusolverDnXsyevd_bufferSize(h, prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, sv.m, T, nullptr,
+                                          sv.m, CUDA_R_64F, nullptr, T, &d, &hb)
+            : cusolverDnXgesvdp_bufferSize(h, prm, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, T, nullptr, rows,
+                                           CUDA_R_64F, nullptr, T, nullptr, rows, T, nullptr, cols, T, &d, &hb);
     if (s != CUSOLVER_STATUS_SUCCESS) return fail(YTN_E_CUDA, std::string("buffer size: ") + solver_error(s));
     dev_bytes = std::max(dev_bytes, d);
     host_bytes = std::max(host_bytes, hb);
@@ -86,9 +89,14 @@ ytn_status svd_factor(ytn_plan_t *p, double *ws, void *stream) {
     double *ux = ws + w * (sv.trans ? sv.vp_off : sv.up_off);   // rows x k
     double *vx = ws + w * (sv.trans ? sv.up_off : sv.vp_off);   // cols x k
     double err_sigma = 0.0;
-    s = cusolverDnXgesvdp(h, prm, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, T, ws + w * sv.m_off, rows, CUDA_R_64F,
-                          ws + sv.s_off, T, ux, rows, T, vx, cols, T, work, p->svd_lwork * sizeof(double),
-                          p->svd_host_ws.data(), p->svd_host_ws.size(), info + i, &err_sigma);
+    if (p->kind == Kind::Eigh)   // M (column-major, Hermitian: its lower triangle) -> eigenvectors in place
+      s = cusolverDnXsyevd(h, prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, sv.m, T, ws + w * sv.m_off, sv.m,
+                           CUDA_R_64F, ws + sv.s_off, T, work, p->svd_lwork * sizeof(double), p->svd_host_ws.data(),
+                           p->svd_host_ws.size(), info + i);
+    else
+      s = cusolverDnXgesvdp(h, prm, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, T, ws + w * sv.m_off, rows, CUDA_R_64F,
+                            ws + sv.s_off, T, ux, rows, T, vx, cols, T, work, p->svd_lwork * sizeof(double),
+                            p->svd_host_ws.data(), p->svd_host_ws.size(), info + i, &err_sigma);
     if (s != CUSOLVER_STATUS_SUCCESS) return fail(YTN_E_CUDA, std::string("polar-decomposition SVD: ") + solver_error(s));
   }
   return YTN_OK;

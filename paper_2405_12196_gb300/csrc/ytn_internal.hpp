@@ -213,7 +213,8 @@ struct HostSector {
   int64_t a_off = 0, b_off = 0, c_off = 0;
 };
 
-enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap = 6, Conj = 7, Svd = 8, Slice = 9 };
+enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap = 6, Conj = 7, Svd = 8, Slice = 9,
+                  Eigh = 10 };
 
 // One charge sector of a block-diagonal SVD: the dense m x n matrix M and where
 // its factors live in the workspace (offsets in doubles). The solver factors a
@@ -355,6 +356,8 @@ ytn_status plan_swap_gate(ytn_plan_t *p, const Tensor &A, int ngroups, const int
 ytn_status plan_conj(ytn_plan_t *p, const Tensor &A, std::string &err);
 ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
                     std::string &err);
+ytn_status plan_eigh(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
+                     std::string &err);
 ytn_status plan_slice(ytn_plan_t *p, const Tensor &A, int naxes, const int *axes, int64_t nkeep,
                       const int32_t *keep_t, const int64_t *keep_D, std::string &err);
 void make_view(const Tensor &C, ytn_struct &v, std::vector<ytn_fusion> &fv);

@@ -34,7 +34,7 @@ YTN_SPLIT_BF16 = 1
 YTN_AUTO = 2
 YTN_OP_TENSORDOT, YTN_OP_FUSE, YTN_OP_UNFUSE, YTN_OP_TRACE, YTN_OP_VDOT, YTN_OP_SWAP_GATE, YTN_OP_CONJ = \
     1, 2, 3, 4, 5, 6, 7
-YTN_OP_SVD, YTN_OP_SLICE = 8, 9
+YTN_OP_SVD, YTN_OP_SLICE, YTN_OP_EIGH = 8, 9, 10
 YTN_FERMIONIC_EXPLICIT = 1 << 31
 YTN_REAL64, YTN_COMPLEX128 = 0, 1
 
@@ -107,6 +107,7 @@ SYMBOLS = {
     "ytn_svd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                           C.c_void_p]),
     "ytn_slice": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ytn_eigh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "ytn_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(ytn_plan_info)]),
     "ytn_plan_release": (None, [C.c_void_p]),
     "ytn_workspace_size": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
@@ -479,6 +480,14 @@ def ytn_svd(plan, a, u, s, v, workspace=None, workspace_bytes=None, stream=None)
         workspace_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(_lib.ytn_svd(plan.handle, _ptr(a), _ptr(u), _ptr(s), _ptr(v), _ptr(workspace), int(workspace_bytes),
                         _stream(stream)))
+
+
+def ytn_eigh(plan, a, u, s, workspace=None, workspace_bytes=None, stream=None):
+    """U, S of an EIGH plan into ``u``, ``s`` (sizes of ``plan.outs``)."""
+    if workspace_bytes is None:
+        workspace_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.ytn_eigh(plan.handle, _ptr(a), _ptr(u), _ptr(s), _ptr(workspace), int(workspace_bytes),
+                         _stream(stream)))
 
 
 def ytn_slice(plan, a, out, stream=None):

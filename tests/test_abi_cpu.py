@@ -371,3 +371,21 @@ def test_svd_and_slice_planning(hctx, seed):
     pc = ytn.ytn_plan(hctx, ytn.YTN_OP_SVD, Ac, groups=(rows, cols))
     for got, want in zip(pc.outs, O.svd(O.from_record(Ac), rows, cols)):
         same_structure(got, O.to_record(want))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+def test_eigh_planning(hctx, dtype):
+    """EIGH plans: U and S have the oracle's structures; non-dual legs or n != 0 are
+    rejected."""
+    rng = np.random.default_rng(77)
+    pool = [(0,), (1,), (-1,)]
+    r = [W.Leg(s, pool, [int(d) for d in rng.integers(1, 5, 3)]) for s in (1, -1)]
+    H = W.random_tensor((0,), r + [l.conj() for l in r], (0,), 3, dtype=dtype)
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_EIGH, H, groups=((0, 1), (2, 3)))
+    U, S = O.eigh(O.from_record(H), (0, 1), (2, 3))
+    assert len(plan.outs) == 2
+    same_structure(plan.outs[0], O.to_record(U))
+    same_structure(plan.outs[1], O.to_record(S))
+    with pytest.raises(ytn.YtnError) as ei:
+        ytn.ytn_plan(hctx, ytn.YTN_OP_EIGH, H, groups=((0, 2), (1, 3)))
+    assert ei.value.name == "YTN_E_SIGNATURE"

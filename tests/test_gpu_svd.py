@@ -146,3 +146,35 @@ def test_complex_svd(ctx, seed):
     _, ref_S, _ = O.svd(O.from_record(A), rows, cols)
     _check(A, rows, cols, U, S, V, ref_S)
 
+
+
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+def test_eigh_of_a_hermitian_tensor(ctx, dtype):
+    """H = B + B^H on legs (r, r*): eigenvalues against the oracle's, U S U^H == H and
+    U^H U = 1 per sector."""
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    rng = np.random.default_rng(610)
+    pool = [(0,), (1,), (-1,)]
+    r = [W.Leg(s, pool, [int(d) for d in rng.integers(2, 12, 3)]) for s in (1, -1)]
+    B = O.from_record(W.random_tensor((0,), r + [l.conj() for l in r], (0,), 5, dtype=dtype))
+    Bh = O.fuse(O.conj(B), ((2,), (3,), (0,), (1,)))
+    Ho = O.OTensor(B.mods, B.sig, B.n, {k: B.blocks[k] + Bh.blocks[k] for k in B.blocks}, dtype=B.dtype)
+    H = O.to_record(Ho)
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_EIGH, H, groups=((0, 1), (2, 3)))
+    dts = [torch.complex128 if dtype == "c128" else torch.float64, torch.float64]
+    bufs = [torch.full((max(o["size"], 1),), float("nan"), dtype=dt, device=device()) for o, dt in zip(plan.outs, dts)]
+    ws = torch.empty(ytn.ytn_workspace_size(plan), dtype=torch.uint8, device=device())
+    ytn.ytn_eigh(plan, torch.from_numpy(H["data"]).to(device()), *bufs, workspace=ws)
+    ytn.ytn_sync(ctx)
+    U, S = [O.from_record(dict(o, data=b[:o["size"]].cpu().numpy())) for o, b in zip(plan.outs, bufs)]
+    _, ref_S = O.eigh(Ho, (0, 1), (2, 3))
+    scale = max(np.max(np.abs(b)) for b in Ho.blocks.values())
+    for k, blk in ref_S.blocks.items():
+        np.testing.assert_allclose(np.diag(S.blocks[k]), np.diag(blk), rtol=1e-10, atol=1e-12 * scale)
+    R = O.tensordot(O.tensordot(U, S, (2,), (0,)), O.fuse(O.conj(U), ((2,), (0,), (1,))), (2,), (0,))
+    for k in Ho.blocks:
+        np.testing.assert_allclose(R.blocks[k], Ho.blocks[k], rtol=0, atol=1e-11 * scale)
+    UU = O.tensordot(O.conj(U), U, (0, 1), (0, 1))
+    for (c, _), blk in S.blocks.items():
+        np.testing.assert_allclose(UU.blocks[(c, c)], np.eye(blk.shape[0]), atol=1e-11)
