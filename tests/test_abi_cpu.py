@@ -387,5 +387,5 @@ def test_eigh_planning(hctx, dtype):
     same_structure(plan.outs[0], O.to_record(U))
     same_structure(plan.outs[1], O.to_record(S))
     with pytest.raises(ytn.YtnError) as ei:
-        ytn.ytn_plan(hctx, ytn.YTN_OP_EIGH, H, groups=((0, 2), (1, 3)))
+        ytn.ytn_plan(hctx, ytn.YTN_OP_EIGH, H, groups=((0, 1), (3, 2)))
     assert ei.value.name == "YTN_E_SIGNATURE"
