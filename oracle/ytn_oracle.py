@@ -44,7 +44,7 @@ __all__ = [
     "OTensor", "OracleError", "SignatureError", "DimMismatchError", "FusionMismatchError",
     "ChargeError", "InvalidError", "UnsupportedError",
     "from_record", "to_record", "conj", "tensordot", "fuse", "unfuse", "trace",
-    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon", "einsum", "svd", "eigh", "truncation", "slice_leg",
+    "to_dense", "leg_sectors", "useful_flops", "tensordot_block", "vdot", "swap_gate", "charge_parity", "ncon", "einsum", "svd", "eigh", "truncation", "slice_leg", "philox4x32", "normal_fill",
 ]
 
 
@@ -635,6 +635,47 @@ def einsum(subscripts, *tensors):
                 lab[c] = nxt
                 nxt += 1
     return ncon(list(tensors), [[lab[c] for c in grp] for grp in ins])
+
+
+# ------------------------------------------------------------------ random data
+
+def philox4x32(ctr, key, rounds=10):
+    """Philox4x32 counter-based generator (Salmon, Moraes, Dror, Shaw, "Parallel
+    random numbers: as easy as 1, 2, 3", SC'11): ``rounds`` rounds of two 32x32 ->
+    64-bit multiplications (multipliers 0xD2511F53, 0xCD9E8D57) with the key added
+    by XOR, the key bumped by the Weyl constants (0x9E3779B9, 0xBB67AE85) between
+    rounds. ctr: four uint32, key: two uint32; returns four uint32."""
+    c = [int(x) & 0xFFFFFFFF for x in ctr]
+    k = [int(x) & 0xFFFFFFFF for x in key]
+    for r in range(rounds):
+        if r:
+            k = [(k[0] + 0x9E3779B9) & 0xFFFFFFFF, (k[1] + 0xBB67AE85) & 0xFFFFFFFF]
+        p0 = 0xD2511F53 * c[0]
+        p1 = 0xCD9E8D57 * c[2]
+        c = [((p1 >> 32) ^ c[1] ^ k[0]) & 0xFFFFFFFF, p1 & 0xFFFFFFFF,
+             ((p0 >> 32) ^ c[3] ^ k[1]) & 0xFFFFFFFF, p0 & 0xFFFFFFFF]
+    return c
+
+
+def normal_fill(seed, size):
+    """N(0, 1) numbers of a random tensor's data (the paper's rand, Sec. II.A): element
+    i takes word i mod 4 of Philox4x32-10 at counter (i div 4 low 32 bits, high 32
+    bits, 0, 0) and key (seed low, seed high); each pair of words (x, y) gives, by
+    the Box-Muller transform with u = (x + 1) 2^-32 in (0, 1] and v = y 2^-32,
+    sqrt(-2 ln u) cos(2 pi v) and sqrt(-2 ln u) sin(2 pi v)."""
+    out = np.zeros(size)
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    for q in range((size + 3) // 4):
+        w = philox4x32((q & 0xFFFFFFFF, q >> 32, 0, 0), key)
+        for h in range(2):
+            u = (w[2 * h] + 1.0) * 2.0 ** -32
+            v = w[2 * h + 1] * 2.0 ** -32
+            r = np.sqrt(-2.0 * np.log(u))
+            for j, z in enumerate((r * np.cos(2 * np.pi * v), r * np.sin(2 * np.pi * v))):
+                i = 4 * q + 2 * h + j
+                if i < size:
+                    out[i] = z
+    return out
 
 
 # ------------------------------------------------------------------ block-diagonal SVD

@@ -803,3 +803,28 @@ def test_eigh_of_a_hermitian_tensor(seed, dtype):
     ours = np.sort(np.concatenate([np.diag(b) for b in S.blocks.values()]))
     d = _dense_matrix(H, legs, (0, 1), (2, 3))
     np.testing.assert_allclose(ours, np.linalg.eigvalsh(d), rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- random data
+
+def test_philox_known_answers():
+    """Philox4x32-10 against the known-answer vectors published with the generator
+    (Salmon et al., SC'11, Random123): zero counter and key, all-ones, and the pi
+    digits."""
+    assert O.philox4x32((0, 0, 0, 0), (0, 0)) == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+    assert O.philox4x32((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2) == [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]
+    assert O.philox4x32((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0)) == \
+        [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+def test_normal_fill_is_box_muller_of_philox():
+    """Each pair is sqrt(-2 ln u) (cos, sin)(2 pi v) of one pair of Philox words, so
+    z0^2 + z1^2 = -2 ln u exactly in the words; over 4e4 numbers the mean and
+    variance are those of N(0, 1) within 5 standard errors."""
+    z = O.normal_fill(12345, 40000)
+    w = O.philox4x32((0, 0, 0, 0), (12345, 0))
+    np.testing.assert_allclose(z[0] ** 2 + z[1] ** 2, -2 * np.log((w[0] + 1.0) * 2.0 ** -32), rtol=1e-14)
+    np.testing.assert_allclose(z[2] ** 2 + z[3] ** 2, -2 * np.log((w[2] + 1.0) * 2.0 ** -32), rtol=1e-14)
+    assert abs(z.mean()) < 5 / np.sqrt(z.size)
+    assert abs(z.var() - 1) < 5 * np.sqrt(2 / z.size)
+    np.testing.assert_array_equal(O.normal_fill(12345, 7), z[:7])
