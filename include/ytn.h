@@ -241,6 +241,30 @@ void ytn_ctx_destroy(ytn_ctx *ctx);
  * YTN_E_CUDA. */
 ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan);
 
+/* A leg V(s, t, D) (Sec. II.A): signature, and its charge sectors with their
+ * dimensions, in ascending charge order. */
+typedef struct {
+  int8_t sig;
+  int32_t ncharges;
+  const int32_t *t;           /* [ncharges][nsym] */
+  const int64_t *D;           /* [ncharges], >= 1 */
+} ytn_leg;
+
+/* The structure of a tensor on the given legs with total charge n (Sec. II.A,
+ * the paper's rand(legs, n)): every block allowed by the conservation rule
+ * sum_i s_i rho_i = n (modulo m for Z_m components), canonical order, packed.
+ * The plan's output structure is that tensor; ytn_fill_normal fills its data.
+ * Errors: YTN_E_INVALID (legs, charges), YTN_E_UNSUPPORTED (more than 2^31 blocks). */
+ytn_status ytn_plan_blocks(ytn_ctx *ctx, ytn_sym sym, int32_t rank, const ytn_leg *legs, const int32_t *n,
+                           ytn_plan_t **plan);
+
+/* out (the plan's output size, real FP64; device or page-locked host memory) = N(0, 1)
+ * numbers: element i is word i mod 4 of Philox4x32-10 (Salmon et al., SC'11) at
+ * counter (i div 4, 0, 0) and key seed, each pair of words (x, y) turned by the
+ * Box-Muller transform into sqrt(-2 ln u) (cos, sin)(2 pi v), u = (x + 1) 2^-32,
+ * v = y 2^-32. Deterministic. Asynchronous on stream. */
+ytn_status ytn_fill_normal(ytn_plan_t *plan, uint64_t seed, double *out, ytn_stream stream);
+
 /* Output structure of a plan (library-owned, valid until the plan is released). */
 const ytn_struct *ytn_plan_output(const ytn_plan_t *plan);
 /* Output i of a plan with several (SVD: 0 = U, 1 = S, 2 = V); NULL past the last. */

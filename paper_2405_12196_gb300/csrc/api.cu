@@ -433,6 +433,56 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
   return YTN_OK;
 }
 
+// Structure from legs: not cached (the caller holds the only reference).
+ytn_status ytn_plan_blocks(ytn_ctx *ctx, ytn_sym sym, int32_t rank, const ytn_leg *legs, const int32_t *n,
+                           ytn_plan_t **plan) {
+  if (!ctx || !plan) return fail(YTN_E_INVALID, "null argument");
+  *plan = nullptr;
+  ytn_plan_t *p = new (std::nothrow) ytn_plan_t;
+  if (!p) return fail(YTN_E_NOMEM, "host allocation failed");
+  p->ctx = ctx;
+  std::string err;
+  ytn_status st;
+  try {
+    st = plan_blocks(p, sym, rank, legs, n, err);
+    if (st == YTN_OK) finish_output_view(p);
+  } catch (const std::bad_alloc &) {
+    st = YTN_E_NOMEM;
+    err = "host allocation failed";
+  }
+  if (st != YTN_OK) {
+    delete p;
+    return fail(st, err);
+  }
+  if (ctx->device >= 0) {
+    DeviceGuard g(ctx->device);
+    if (!g.ok()) {
+      delete p;
+      return fail(YTN_E_CUDA, "cannot select device");
+    }
+    if ((st = upload(p)) != YTN_OK) {
+      destroy_plan(p);
+      return st;
+    }
+  }
+  p->refs = 1;
+  *plan = p;
+  return YTN_OK;
+}
+
+ytn_status ytn_fill_normal(ytn_plan_t *p, uint64_t seed, double *out, ytn_stream stream) {
+  if (!p) return fail(YTN_E_INVALID, "null plan");
+  if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
+  if (p->out.dtype != YTN_REAL64) return fail(YTN_E_UNSUPPORTED, "normal fill of complex data");
+  if (p->out.size && !out) return fail(YTN_E_INVALID, "null data buffer");
+  DeviceGuard g(p->ctx->device);
+  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  ytn_status vs = device_view(p->ctx, out, &out, "output");
+  if (vs != YTN_OK) return vs;
+  cudaError_t e = launch_fill_normal(seed, p->out.size, out, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? YTN_OK : cuda_fail(e, "normal fill");
+}
+
 const ytn_struct *ytn_plan_output(const ytn_plan_t *plan) { return plan ? &plan->out_view : nullptr; }
 
 const ytn_struct *ytn_plan_output_at(const ytn_plan_t *plan, int32_t i) {

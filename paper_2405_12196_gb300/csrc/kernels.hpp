@@ -38,6 +38,9 @@ cudaError_t configure_split_gemm();
 cudaError_t launch_cscatter(const CScatterJob *jobs, int64_t njobs, const double *wc, double *c,
                             cudaStream_t stream);
 
+// N(0, 1) numbers: Philox4x32-10 words turned by Box-Muller (see ytn_fill_normal).
+cudaError_t launch_fill_normal(uint64_t seed, int64_t n, double *out, cudaStream_t stream);
+
 // Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output C_q.
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
                               const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc, int slices,

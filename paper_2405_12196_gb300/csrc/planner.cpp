@@ -2045,6 +2045,87 @@ ytn_status plan_slice(ytn_plan_t *p, const Tensor &A, int naxes, const int *axes
 }
 
 // ---------------------------------------------------------------------------
+// Tensor structure from legs (the paper's rand)
+// ---------------------------------------------------------------------------
+
+// Every block (rho_1 .. rho_r) with sum_i s_i rho_i = n: the first r - 1 legs are
+// enumerated, the last leg's charge follows from the rule and is looked up.
+ytn_status plan_blocks(ytn_plan_t *p, const ytn_sym &sym, int rank, const ytn_leg *legs, const int32_t *n,
+                       std::string &err) {
+  if (sym.nsym < 1 || sym.nsym > YTN_MAX_SYM) { err = "nsym out of range"; return YTN_E_INVALID; }
+  if (rank < 1 || rank > YTN_MAX_RANK || !legs || !n) { err = "rank out of range or null legs"; return YTN_E_INVALID; }
+  const int nsym = sym.nsym;
+  Tensor C;
+  C.nsym = nsym;
+  for (int c = 0; c < nsym; c++) {
+    if (sym.mod[c] < 0 || sym.mod[c] == 1) { err = "modulus must be 0 (U(1)) or >= 2"; return YTN_E_INVALID; }
+    C.mod[c] = sym.mod[c];
+    C.n[c] = reduce(n[c], C.mod[c]);
+  }
+  C.rank = rank;
+  std::vector<std::vector<Key>> ch(rank);
+  std::vector<std::vector<int64_t>> dims(rank);
+  for (int l = 0; l < rank; l++) {
+    const ytn_leg &L = legs[l];
+    if ((L.sig != 1 && L.sig != -1) || L.ncharges < 0 || (L.ncharges > 0 && (!L.t || !L.D))) {
+      err = "bad leg " + std::to_string(l);
+      return YTN_E_INVALID;
+    }
+    C.sig[l] = L.sig;
+    for (int i = 0; i < L.ncharges; i++) {
+      Key q(L.t + (size_t)i * nsym, L.t + (size_t)(i + 1) * nsym);
+      for (int c = 0; c < nsym; c++) q[c] = reduce(q[c], C.mod[c]);
+      if (L.D[i] < 1 || L.D[i] > ((int64_t)1 << 30)) { err = "leg dimension out of range"; return YTN_E_INVALID; }
+      if (i > 0 && !(ch[l].back() < q)) { err = "leg charges must ascend and be distinct"; return YTN_E_INVALID; }
+      ch[l].push_back(q);
+      dims[l].push_back(L.D[i]);
+    }
+  }
+  std::map<Key, int> last;
+  for (size_t i = 0; i < ch[rank - 1].size(); i++) last[ch[rank - 1][i]] = (int)i;
+  std::vector<OutBlock> ob;
+  std::vector<int> idx(rank, 0);
+  const int r1 = rank - 1;
+  bool empty = false;
+  for (int l = 0; l < r1; l++) empty = empty || ch[l].empty();
+  while (!empty) {
+    // the last leg's charge: s_last q = n - sum_{l < last} s_l q_l
+    Key need(nsym, 0);
+    for (int c = 0; c < nsym; c++) {
+      int64_t acc = C.n[c];
+      for (int l = 0; l < r1; l++) acc -= (int64_t)C.sig[l] * ch[l][idx[l]][c];
+      need[c] = reduce(acc * C.sig[r1], C.mod[c]);
+    }
+    auto it = last.find(need);
+    if (it != last.end()) {
+      OutBlock o;
+      o.id = (int64_t)ob.size();
+      for (int l = 0; l < r1; l++) {
+        o.key.insert(o.key.end(), ch[l][idx[l]].begin(), ch[l][idx[l]].end());
+        o.D.push_back(dims[l][idx[l]]);
+      }
+      o.key.insert(o.key.end(), need.begin(), need.end());
+      o.D.push_back(dims[r1][it->second]);
+      ob.push_back(o);
+      if (ob.size() > (size_t)INT32_MAX) { err = "too many blocks"; return YTN_E_UNSUPPORTED; }
+    }
+    int l = r1 - 1;
+    for (; l >= 0; l--) {
+      if (++idx[l] < (int)ch[l].size()) break;
+      idx[l] = 0;
+    }
+    if (l < 0) break;
+  }
+  std::vector<int64_t> off;
+  finalize_out(C, ob, off);
+  p->out = C;
+  p->kind = Kind::Blocks;
+  p->a_size = 0;
+  p->flops = 0.0;
+  return YTN_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Cache key and output view
 // ---------------------------------------------------------------------------
 

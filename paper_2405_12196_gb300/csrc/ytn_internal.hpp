@@ -214,7 +214,7 @@ struct HostSector {
 };
 
 enum class Kind { Tensordot = 1, Fuse = 2, Unfuse = 3, Trace = 4, Vdot = 5, Swap = 6, Conj = 7, Svd = 8, Slice = 9,
-                  Eigh = 10 };
+                  Eigh = 10, Blocks = 11 };
 
 // One charge sector of a block-diagonal SVD: the dense m x n matrix M and where
 // its factors live in the workspace (offsets in doubles). The solver factors a
@@ -358,6 +358,8 @@ ytn_status plan_svd(ytn_plan_t *p, const Tensor &A, int ngroups, const int *grou
                     std::string &err);
 ytn_status plan_eigh(ytn_plan_t *p, const Tensor &A, int ngroups, const int *group_size, const int *order,
                      std::string &err);
+ytn_status plan_blocks(ytn_plan_t *p, const ytn_sym &sym, int rank, const ytn_leg *legs, const int32_t *n,
+                       std::string &err);
 ytn_status plan_slice(ytn_plan_t *p, const Tensor &A, int naxes, const int *axes, int64_t nkeep,
                       const int32_t *keep_t, const int64_t *keep_D, std::string &err);
 void make_view(const Tensor &C, ytn_struct &v, std::vector<ytn_fusion> &fv);

@@ -64,6 +64,10 @@ class ytn_struct(C.Structure):
                 ("fus", C.POINTER(ytn_fusion) * MAX_RANK), ("dtype", C.c_int32)]
 
 
+class ytn_leg(C.Structure):
+    _fields_ = [("sig", C.c_int8), ("ncharges", C.c_int32), ("t", C.POINTER(C.c_int32)), ("D", C.POINTER(C.c_int64))]
+
+
 class ytn_op(C.Structure):
     _fields_ = [("kind", C.c_int), ("a", C.POINTER(ytn_struct)), ("b", C.POINTER(ytn_struct)),
                 ("naxes", C.c_int32), ("axa", C.c_int32 * MAX_RANK), ("axb", C.c_int32 * MAX_RANK),
@@ -103,6 +107,9 @@ SYMBOLS = {
     "ytn_ctx_destroy": (None, [C.c_void_p]),
     "ytn_plan": (C.c_int, [C.c_void_p, C.POINTER(ytn_op), C.POINTER(C.c_void_p)]),
     "ytn_plan_output": (C.POINTER(ytn_struct), [C.c_void_p]),
+    "ytn_plan_blocks": (C.c_int, [C.c_void_p, ytn_sym, C.c_int32, C.POINTER(ytn_leg), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_void_p)]),
+    "ytn_fill_normal": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
     "ytn_plan_output_at": (C.POINTER(ytn_struct), [C.c_void_p, C.c_int32]),
     "ytn_svd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                           C.c_void_p]),
@@ -390,6 +397,32 @@ def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None, 
     h = C.c_void_p()
     _check(_lib.ytn_plan(ctx.handle, C.byref(op), C.byref(h)))
     return Plan(ctx, h.value, (sa, sb, keep_arrays))
+
+
+def ytn_plan_blocks(ctx, mods, legs, n):
+    """The structure of a tensor on ``legs`` (objects with ``s``, ``t``, ``D``: sig,
+    charge tuples, dims) with total charge ``n``: every allowed block."""
+    sym = ytn_sym()
+    sym.nsym = len(mods)
+    for c, m in enumerate(mods):
+        sym.mod[c] = m
+    arrs, cl = [], (ytn_leg * len(legs))()
+    for i, l in enumerate(legs):
+        t = np.ascontiguousarray(np.asarray(l.t, dtype=np.int32).reshape(-1, len(mods)))
+        d = np.ascontiguousarray(l.D, dtype=np.int64)
+        arrs += [t, d]
+        cl[i].sig, cl[i].ncharges = int(l.s), len(d)
+        cl[i].t = t.ctypes.data_as(C.POINTER(C.c_int32))
+        cl[i].D = d.ctypes.data_as(C.POINTER(C.c_int64))
+    nn = (C.c_int32 * MAX_SYM)(*[int(x) for x in n])
+    h = C.c_void_p()
+    _check(_lib.ytn_plan_blocks(ctx.handle, sym, len(legs), cl, nn, C.byref(h)))
+    return Plan(ctx, h.value, (arrs, cl))
+
+
+def ytn_fill_normal(plan, seed, out, stream=None):
+    """N(0, 1) numbers (Philox4x32-10, Box-Muller) into ``out`` (the plan's output size)."""
+    _check(_lib.ytn_fill_normal(plan.handle, int(seed), _ptr(out), _stream(stream)))
 
 
 def ytn_workspace_size(plan, prec=YTN_FP64, rtol=0.0):

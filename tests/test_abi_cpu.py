@@ -389,3 +389,28 @@ def test_eigh_planning(hctx, dtype):
     with pytest.raises(ytn.YtnError) as ei:
         ytn.ytn_plan(hctx, ytn.YTN_OP_EIGH, H, groups=((0, 1), (3, 2)))
     assert ei.value.name == "YTN_E_SIGNATURE"
+
+
+@pytest.mark.parametrize("sym", ["U1", "Z2", "Z3", "U1xU1"])
+@pytest.mark.parametrize("case", range(4))
+def test_blocks_from_legs_match_the_generator(hctx, sym, case):
+    """ytn_plan_blocks (the paper's rand(legs, n) structure) == every block the input
+    generator allows (an independent enumeration), canonical and packed."""
+    mods = SYMS[sym]
+    rng = np.random.default_rng(900 + 7 * case + len(sym))
+    legs = random_legs(rng, mods, int(rng.integers(1, 5)), max_sectors=4, max_dim=4)
+    n = tuple(int(rng.integers(0, m)) if m else int(rng.integers(-1, 2)) for m in mods)
+    plan = ytn.ytn_plan_blocks(hctx, mods, legs, n)
+    want = W.random_tensor(mods, legs, n, 1)
+    same_structure(plan.out, dict(want, data=np.zeros(want["data"].size)))
+    O.from_record(dict(want, t=plan.out["t"], D=plan.out["D"]))   # validates conservation
+
+
+def test_blocks_from_legs_errors(hctx):
+    from types import SimpleNamespace
+    for bad in (SimpleNamespace(s=1, t=[(1,), (0,)], D=[2, 3]),     # charges not ascending
+                SimpleNamespace(s=2, t=[(0,)], D=[2]),              # signature
+                SimpleNamespace(s=1, t=[(0,)], D=[0])):             # dimension
+        with pytest.raises(ytn.YtnError) as ei:
+            ytn.ytn_plan_blocks(hctx, (0,), [bad], (0,))
+        assert ei.value.name == "YTN_E_INVALID"
