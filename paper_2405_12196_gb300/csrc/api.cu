@@ -539,7 +539,7 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
     return YTN_OK;
   }
   if (p->kind == Kind::Svd || p->kind == Kind::Eigh) {
-    *bytes = align256((p->svd_ws_doubles + p->svd_lwork) * sizeof(double));
+    *bytes = align256((p->svd_ws_doubles + kSolverLanes * p->svd_lwork) * sizeof(double));
     return YTN_OK;
   }
   if (p->kind != Kind::Tensordot) return YTN_OK;
@@ -824,7 +824,7 @@ static ytn_status run_decomp(ytn_plan_t *p, Kind kind, const double *a, double *
   const bool has_v = p->outs.size() > 1;
   if ((p->a_size && !a) || (p->out.size && !u) || (p->outs[0].size && !s) || (has_v && p->outs[1].size && !v))
     return fail(YTN_E_INVALID, "null data buffer");
-  const size_t need = align256((p->svd_ws_doubles + p->svd_lwork) * sizeof(double));
+  const size_t need = align256((p->svd_ws_doubles + kSolverLanes * p->svd_lwork) * sizeof(double));
   if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))
     return fail(YTN_E_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
   DeviceGuard g(p->ctx->device);

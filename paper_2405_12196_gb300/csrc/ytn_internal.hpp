@@ -252,9 +252,9 @@ struct ytn_ctx {
   void *cap_stream = nullptr;
   std::vector<ytn_plan_s *> cap_plans;
   std::mutex cap_mu;
-  // dense solver handle and Jacobi SVD parameters (created by the first SVD plan)
-  void *solver = nullptr;
-  void *svd_params = nullptr;
+  // dense solver: kSolverLanes handles, parameter sets, streams and events
+  // (created by the first SVD / eigh plan); sectors are factored concurrently
+  std::vector<void *> solvers, solver_params, solver_streams, solver_events;
   std::mutex solver_mu;
 };
 
@@ -276,7 +276,7 @@ struct ytn_plan_s {
   int64_t items_s_begin = 0, items_s_end = 0;   // S vectors -> S diagonals
   int64_t items_h_begin = 0, items_h_end = 0;   // complex: conjugate one factor in place
   size_t svd_m_doubles = 0, svd_ws_doubles = 0, svd_info_off = 0, svd_lwork = 0;
-  std::vector<char> svd_host_ws;   // the solver's host buffer (one call at a time)
+  std::vector<std::vector<char>> svd_host_ws;   // the solver's host buffer, per lane
   bool svd_zero_m = false;
   // doubles per element of the copy jobs that add_copy makes: 2 for complex
   // tensors moved whole (fuse, unfuse, swap gate, conj), else 1
@@ -372,7 +372,9 @@ void plan_split_tables(ytn_plan_t *p);
 // error reporting (api.cu)
 ytn_status fail(ytn_status st, const std::string &msg);
 
-// dense solver of the block-diagonal SVD (svd.cpp)
+// dense solver of the block-diagonal SVD (svd.cpp): sectors are factored on
+// kSolverLanes handles and streams at once, each with its own device buffer
+constexpr int kSolverLanes = 4;
 ytn_status svd_prepare(ytn_plan_t *p);
 ytn_status svd_factor(ytn_plan_t *p, double *ws, void *stream);
 void svd_release(ytn_ctx *ctx);
