@@ -864,7 +864,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--workload", default="cfg5", choices=sorted(WORKLOAD_DESC))
-    ap.add_argument("--e2e-steps", type=int, default=9)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
