@@ -598,6 +598,11 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
     uint8_t *sa = reinterpret_cast<uint8_t *>(ws + w.sa), *sb = reinterpret_cast<uint8_t *>(ws + w.sb);
     {
       PhaseTimer t(p->ctx, YTN_PHASE_SPLIT, st);
+      // the exponent kernel max-combines into EA / EB: start from a value below
+      // every exponent (bytes 0x80: 0x80808080 as int32)
+      e = cudaMemsetAsync(ea, 0x80, (size_t)p->sp_ea * 4, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(eb, 0x80, (size_t)p->sp_eb * 4, st);
+      if (e == cudaSuccess)
       e = launch_split_prep(p->d_sp_ops, p->d_sp_exp_items, (int64_t)p->sp_exp_items.size(), p->d_sp_slice_items,
                             (int64_t)p->sp_slice_items.size(), wa, wb, ea, eb, sa, sb, slices, st);
     }

@@ -1096,7 +1096,8 @@ void plan_split_tables(ytn_plan_t *p) {
     for (int which = 0; which < 2; which++) {
       const int64_t tiles = which == 0 ? tm : tn;
       for (int64_t rt = 0; rt < tiles; rt++) {
-        p->sp_exp_items.push_back({ia + which, (int32_t)rt, 0, (int32_t)ks});
+        for (int64_t k0 = 0; k0 < ks; k0 += 8)   // row maxima per 256 of K, combined by atomicMax
+          p->sp_exp_items.push_back({ia + which, (int32_t)rt, (int32_t)k0, (int32_t)std::min<int64_t>(8, ks - k0)});
         for (int64_t k0 = 0; k0 < ks; k0 += 8)
           p->sp_slice_items.push_back({ia + which, (int32_t)rt, (int32_t)k0, (int32_t)std::min<int64_t>(8, ks - k0)});
       }

@@ -33,7 +33,11 @@ __device__ __forceinline__ int biased_exp(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// Row exponents: e_r = maxE - 1021 over the row (maxE = largest biased exponent).
+// Row exponents: e_r = maxE - 1021 over the row (maxE = largest biased exponent,
+// 0 for a zero row). An item covers 128 rows and up to 256 of K; its per-row
+// maxima are combined into E with atomicMax (exact and order-independent), E
+// having been set below every exponent beforehand. Rows past the operand are
+// left alone (no kernel reads them).
 __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__restrict__ ops,
                                                         const SplitItem *__restrict__ items,
                                                         const double *__restrict__ wa,
@@ -45,36 +49,33 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__re
   const double *X = (isA ? wa : wb) + o.src_off;
   int32_t *E = (isA ? ea : eb) + o.exp_off;
   const int r0 = it.rt * kSplitBM;
+  const int k_lo = it.kt0 * kSplitBK, k_hi = min(o.K, (it.kt0 + it.nkt) * kSplitBK);
   __shared__ int red[2][kSplitBM];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (o.kmajor) {
     // rows of K contiguous elements: one warp per row
     for (int rr = warp; rr < kSplitBM; rr += 8) {
       const int r = r0 + rr;
+      if (r >= o.rows) break;   // uniform in the warp
+      const double *row = X + (int64_t)r * o.K;
       int m = 0;
-      if (r < o.rows) {
-        const double *row = X + (int64_t)r * o.K;
-        for (int k = lane; k < o.K; k += 32) m = max(m, biased_exp(__ldg(row + k)));
-      }
+#pragma unroll 8
+      for (int k = k_lo + lane; k < k_hi; k += 32) m = max(m, biased_exp(__ldg(row + k)));
 #pragma unroll
       for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
-      if (lane == 0) red[0][rr] = m;
+      if (lane == 0) atomicMax(E + r, m - 1021);
     }
-    __syncthreads();
-    if (tid < kSplitBM) E[r0 + tid] = (r0 + tid < o.rows && red[0][tid] > 0) ? red[0][tid] - 1021 : -1021;
   } else {
-    // K rows of `rows` contiguous elements: thread per row, two halves of K
+    // K rows of `rows` contiguous elements: thread per row, two halves of the K range
     const int rr = tid & (kSplitBM - 1), half = tid >> 7;
     const int r = r0 + rr;
     int m = 0;
     if (r < o.rows)
-      for (int k = half; k < o.K; k += 2) m = max(m, biased_exp(__ldg(X + (int64_t)k * o.rows + r)));
+#pragma unroll 4
+      for (int k = k_lo + half; k < k_hi; k += 2) m = max(m, biased_exp(__ldg(X + (int64_t)k * o.rows + r)));
     red[half][rr] = m;
     __syncthreads();
-    if (tid < kSplitBM) {
-      const int mm = max(red[0][tid], red[1][tid]);
-      E[r0 + tid] = (r0 + tid < o.rows && mm > 0) ? mm - 1021 : -1021;
-    }
+    if (tid < kSplitBM && r0 + tid < o.rows) atomicMax(E + r0 + tid, max(red[0][tid], red[1][tid]) - 1021);
   }
 }
 
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256) split_slice_kernel(const SplitOperand *__
   uint8_t *S = (isA ? sa : sb) + o.slice_off;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = it.rt * kSplitBM;
-  if (tid < kSplitBM) rexp[tid] = E[r0 + tid];
+  if (tid < kSplitBM) rexp[tid] = r0 + tid < o.rows ? E[r0 + tid] : -1021;
   for (int kt = it.kt0; kt < it.kt0 + it.nkt; kt++) {
     const int k0 = kt * kSplitBK;
     __syncthreads();
