@@ -344,6 +344,44 @@ def test_split_wide_dynamic_range(ctx):
     assert rel_frobenius(got / np.abs(want).max(axis=1, keepdims=True), want / np.abs(want).max(axis=1, keepdims=True)) <= SPLIT_RTOL
 
 
+@pytest.mark.parametrize("axes", [((1,), (0,)), ((0,), (1,))])
+def test_split_row_maximum_in_a_late_chunk(ctx, axes):
+    """In each row of A_q one K chunk of 256 is scaled by 2^8 (in each column of B_q
+    one by 2^6), the chunk depending on the row: the row exponent must be the maximum
+    over every chunk, whichever holds it, in both operand orientations (K contiguous,
+    or the rows contiguous). An exponent taken from fewer chunks would push digits
+    far outside their range. (Whole chunks are scaled, not single elements, so that
+    |c_ij| stays within a small factor of the scale 2^(e_i + f_j) that the slice
+    arithmetic works at.)"""
+    M, K, N = 140, 1000, 70
+    axa, axb = axes
+    rng = np.random.default_rng(5)
+    a_mat = rng.standard_normal((M, K))
+    b_mat = rng.standard_normal((K, N))
+    for i in range(M):
+        c = (i * 7) % 4
+        a_mat[i, c * 256:(c + 1) * 256] *= 2.0 ** 8
+    for j in range(N):
+        c = (j * 5 + 1) % 4
+        b_mat[c * 256:(c + 1) * 256, j] *= 2.0 ** 6
+    l_m, l_k, l_n = W.Leg(1, [(0,)], [M]), W.Leg(1, [(0,)], [K]), W.Leg(1, [(0,)], [N])
+    if axa == (1,):
+        A = W.random_tensor((0,), [l_m, l_k], (0,), 1)
+        A["data"] = a_mat.ravel().copy()
+    else:
+        A = W.random_tensor((0,), [l_k, l_m], (0,), 1)
+        A["data"] = a_mat.T.ravel().copy()
+    if axb == (0,):
+        B = W.random_tensor((0,), [l_k.conj(), l_n], (0,), 2)
+        B["data"] = b_mat.ravel().copy()
+    else:
+        B = W.random_tensor((0,), [l_n, l_k.conj()], (0,), 2)
+        B["data"] = b_mat.T.ravel().copy()
+    _, rec, _ = _split(ctx, A, B, axa, axb)
+    err = rel_frobenius(rec["data"], (a_mat @ b_mat).ravel())
+    assert err <= SPLIT_RTOL, err
+
+
 def test_split_slice_count_follows_tolerance(ctx):
     from paper_2405_12196_gb300 import ytn
     cfg = W.config1()
