@@ -374,7 +374,7 @@ ytn_status fail(ytn_status st, const std::string &msg);
 
 // dense solver of the block-diagonal SVD (svd.cpp): sectors are factored on
 // kSolverLanes handles and streams at once, each with its own device buffer
-constexpr int kSolverLanes = 4;
+constexpr int kSolverLanes = 8;
 ytn_status svd_prepare(ytn_plan_t *p);
 ytn_status svd_factor(ytn_plan_t *p, double *ws, void *stream);
 void svd_release(ytn_ctx *ctx);
