@@ -14,6 +14,7 @@
 #include <deque>
 #include <map>
 #include <new>
+#include <system_error>
 #include <thread>
 
 #include "ytn_internal.hpp"
@@ -201,24 +202,36 @@ ytn_status ytn_server_create(ytn_ctx *ctx, int nslots, void *arena, size_t arena
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
+  auto release = [&]() {
+    for (auto x : s->streams) cudaStreamDestroy(x);
+    for (auto x : s->events) cudaEventDestroy(x);
+    cudaSetDevice(prev);
+    delete s;
+  };
   for (int i = 0; i < nslots; i++) {
-    cudaStream_t st;
-    cudaEvent_t ev;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-      for (auto x : s->streams) cudaStreamDestroy(x);
-      for (auto x : s->events) cudaEventDestroy(x);
-      cudaSetDevice(prev);
-      delete s;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      release();
       return fail(YTN_E_CUDA, "cannot create server streams");
+    }
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaStreamDestroy(st);
+      release();
+      return fail(YTN_E_CUDA, "cannot create server events");
     }
     s->streams.push_back(st);
     s->events.push_back(ev);
   }
-  cudaSetDevice(prev);
   s->busy.assign(nslots, false);
   s->running.resize(nslots);
-  s->th = std::thread([s] { s->loop(); });
+  try {
+    s->th = std::thread([s] { s->loop(); });
+  } catch (const std::system_error &) {
+    release();
+    return fail(YTN_E_NOMEM, "cannot start the admission thread");
+  }
+  cudaSetDevice(prev);
   *server = s;
   return YTN_OK;
 }

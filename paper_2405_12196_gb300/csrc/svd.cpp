@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -139,10 +140,20 @@ ytn_status svd_factor(ytn_plan_t *p, double *ws, void *stream) {
     result[l] = s;
   };
   {
+    // a lane whose thread cannot be started runs on the calling thread instead
     std::vector<std::thread> threads;
-    for (int l = 1; l < kSolverLanes; l++)
-      if (!lane[l].empty()) threads.emplace_back(work, l);
-    work(0);
+    std::vector<int> here{0};
+    threads.reserve(kSolverLanes);
+    here.reserve(kSolverLanes);
+    for (int l = 1; l < kSolverLanes; l++) {
+      if (lane[l].empty()) continue;
+      try {
+        threads.emplace_back(work, l);
+      } catch (const std::system_error &) {
+        here.push_back(l);
+      }
+    }
+    for (int l : here) work(l);
     for (auto &t : threads) t.join();
   }
   for (int l = 0; l < kSolverLanes; l++) {
