@@ -1,16 +1,20 @@
 """Continuous-batching server (ytn_server_*), through the C ABI.
 
-Each request's result must be the same alone and in the mix; admission must keep
-the workspaces of concurrently running requests inside the arena (the HBM
-budget); requests that can never fit are rejected.
+Every request's result is checked against the CPU oracle (block structure bit for
+bit, values within 1e-12 on the FP64 path and 1e-10 on the split path), and must be
+the same alone and in the mix; admission must keep the workspaces of concurrently
+running requests inside the arena (the HBM budget); requests that can never fit are
+rejected.
 """
 import numpy as np
 import pytest
 
 import workloads as W
-from gpu_helpers import rel_frobenius
+from gpu_helpers import check_against_oracle, oracle_tensordot, rel_frobenius
 
 pytestmark = pytest.mark.gpu
+
+SPLIT_RTOL = 1e-10
 
 
 @pytest.fixture(scope="module")
@@ -22,16 +26,26 @@ def ctx():
     return ytn.ytn_ctx_create(0)
 
 
-def _requests(ctx, nruns=6):
-    """Independent U(1) environment contractions X2_r . a_r of several sizes."""
+def _runs(per_d=2):
+    """Independent U(1) runs of the serving stream's recipe, ``per_d`` of each of
+    D = 4, 6 and 8 (three bond dimensions in one mix)."""
+    runs = []
+    for i, D in enumerate((4, 6, 8)):
+        runs += W.serving_runs(nruns=per_d, seed=777 + i, Ds=(D,))
+    return runs
+
+
+def _requests(ctx, runs):
+    """One environment contraction X2_r . a_r per run, with its oracle result."""
     import torch
     from paper_2405_12196_gb300 import ytn
     dev = torch.device("cuda:0")
     out = []
-    for run in W.serving_runs(nruns=nruns, seed=777, Ds=(4, 6, 8)):
+    for run in runs:
         X2, a = W.serving_request(run)
         plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, X2, a, (1, 2), (0, 1))
-        out.append({"plan": plan, "a": torch.from_numpy(X2["data"]).to(dev),
+        out.append({"plan": plan, "D": run["D"], "X2": X2, "a_rec": a,
+                    "a": torch.from_numpy(X2["data"]).to(dev),
                     "b": torch.from_numpy(a["data"]).to(dev), "n": plan.out["size"]})
     return out
 
@@ -47,19 +61,15 @@ def _alone(ctx, r, prec, rtol):
     return c[:r["n"]].cpu().numpy()
 
 
-def test_results_same_alone_and_in_the_mix(ctx):
+def _serve(ctx, reqs, precs, arena_bytes, nslots, reps):
+    """Submit every (request, precision) ``reps`` times at once and drain."""
     import torch
     from paper_2405_12196_gb300 import ytn
-    reqs = _requests(ctx)
-    precs = [(ytn.YTN_FP64, 0.0), (ytn.YTN_SPLIT_BF16, 1e-10)]
-    alone = {(i, k): _alone(ctx, r, p, t) for i, r in enumerate(reqs) for k, (p, t) in enumerate(precs)}
-    # arena for about two requests at a time
-    need = max(ytn.ytn_workspace_size(r["plan"], p, t) for r in reqs for p, t in precs)
-    arena = torch.empty(2 * need + (1 << 20), dtype=torch.uint8, device=reqs[0]["a"].device)
-    srv = ytn.Server(ctx, 4, arena)
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device=reqs[0]["a"].device)
+    srv = ytn.Server(ctx, nslots, arena)
     outs = {}
     rid = 0
-    for rep in range(2):
+    for _ in range(reps):
         for i, r in enumerate(reqs):
             for k, (p, t) in enumerate(precs):
                 c = torch.full((max(r["n"], 1),), float("nan"), dtype=torch.float64, device=r["a"].device)
@@ -71,9 +81,29 @@ def test_results_same_alone_and_in_the_mix(ctx):
     srv.close()
     assert len(infos) == rid
     assert all(x["status"] == 0 for x in infos)
+    return outs, infos, arena.numel()
+
+
+def test_results_match_the_oracle_alone_and_in_the_mix(ctx):
+    from paper_2405_12196_gb300 import ytn
+    reqs = _requests(ctx, _runs())
+    assert len({r["D"] for r in reqs}) == 3
+    precs = [(ytn.YTN_FP64, 0.0), (ytn.YTN_SPLIT_BF16, SPLIT_RTOL)]
+    alone = {}
+    for i, r in enumerate(reqs):
+        ref = oracle_tensordot(r["X2"], r["a_rec"], (1, 2), (0, 1))
+        for k, (p, t) in enumerate(precs):
+            got = _alone(ctx, r, p, t)
+            rec = dict(r["plan"].out)
+            rec["data"] = got
+            check_against_oracle(rec, ref, rtol=1e-12 if k == 0 else SPLIT_RTOL)
+            alone[(i, k)] = got
+    # arena for about two requests at a time, four slots: requests queue for memory
+    need = max(ytn.ytn_workspace_size(r["plan"], p, t) for r in reqs for p, t in precs)
+    outs, infos, arena_bytes = _serve(ctx, reqs, precs, 2 * need + (1 << 20), 4, 2)
     for rid_, (i, k, c) in outs.items():
         got = c[:reqs[i]["n"]].cpu().numpy()
-        tol = 1e-12 if k == 0 else 1e-10
+        tol = 1e-12 if k == 0 else SPLIT_RTOL
         assert rel_frobenius(got, alone[(i, k)]) <= tol
         np.testing.assert_array_equal(got, alone[(i, k)])   # deterministic kernels: identical bits
     # admission kept the running workspaces inside the arena
@@ -83,16 +113,34 @@ def test_results_same_alone_and_in_the_mix(ctx):
     for _, w in events:
         used += w
         peak = max(peak, used)
-    assert peak <= arena.numel()
+    assert peak <= arena_bytes
     assert max(x["slot"] for x in infos) <= 3
     # with two slots' worth of arena and four slots, some requests had to wait
     assert any(x["t_admit"] > x["t_arrive"] + 1e-3 for x in infos)
 
 
+def test_mixed_bond_dimensions_and_precisions_in_flight(ctx):
+    """Both precisions and three bond dimensions submitted together into a roomy
+    arena: results equal the alone runs bit for bit, and requests overlapped."""
+    from paper_2405_12196_gb300 import ytn
+    reqs = _requests(ctx, _runs(per_d=1))
+    precs = [(ytn.YTN_FP64, 0.0), (ytn.YTN_SPLIT_BF16, SPLIT_RTOL)]
+    alone = {(i, k): _alone(ctx, r, p, t) for i, r in enumerate(reqs) for k, (p, t) in enumerate(precs)}
+    total = sum(ytn.ytn_workspace_size(r["plan"], p, t) for r in reqs for p, t in precs)
+    outs, infos, _ = _serve(ctx, reqs, precs, total + (1 << 20), 6, 3)
+    for rid_, (i, k, c) in outs.items():
+        np.testing.assert_array_equal(c[:reqs[i]["n"]].cpu().numpy(), alone[(i, k)])
+    by_id = {x["id"]: x for x in infos}
+    kinds = {(reqs[i]["D"], k) for (i, k, _) in outs.values()}
+    assert len({d for d, _ in kinds}) == 3 and len({k for _, k in kinds}) == 2
+    spans = sorted((by_id[r]["t_admit"], by_id[r]["t_done"]) for r in outs)
+    assert any(spans[j + 1][0] < spans[j][1] for j in range(len(spans) - 1)), "no two requests overlapped"
+
+
 def test_request_larger_than_the_arena_is_rejected(ctx):
     import torch
     from paper_2405_12196_gb300 import ytn
-    reqs = _requests(ctx, nruns=2)
+    reqs = _requests(ctx, W.serving_runs(nruns=2, seed=777, Ds=(4, 6, 8)))
     r = reqs[0]
     arena = torch.empty(1 << 16, dtype=torch.uint8, device=r["a"].device)
     srv = ytn.Server(ctx, 2, arena)
