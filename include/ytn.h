@@ -213,15 +213,41 @@ typedef struct {
   int64_t njobs;             /* copy jobs of all data movers                    */
 } ytn_plan_info;
 
-/* Per-call result of ytn_tensordot. */
+/* Per-call result of ytn_tensordot, filled when the call returns (before the
+ * device has run it). */
 typedef struct {
   double useful_flops;
   int32_t precision;         /* ytn_precision used                              */
   int32_t slices;            /* split path: BF16 slices per operand, else 0     */
-  double err_est;            /* split path: a-priori estimate of the relative
-                                Frobenius error of the result (the model that
-                                picks the slice count); 0 for FP64            */
+  double err_est;            /* split path: the a-priori bound of the model that
+                                picks the slice count, which does not see the
+                                data; 0 for FP64. The data-aware estimate of the
+                                result is in ytn_tensordot_report            */
 } ytn_result;
+
+/* Accuracy record of a split-precision ytn_tensordot (no counterpart in the
+ * paper), computed on the device by the call itself and read with
+ * ytn_tensordot_report. Per charge sector q the split products are estimated to
+ * be off, per element, by eta(s) sqrt(K_q) 2^(e_i + f_j), where 2^e_i and 2^f_j
+ * are the power-of-two scales of row i of A_q and column j of B_q (the split's
+ * own scales); the sector's relative Frobenius error is then
+ *   est_q = eta(s) sqrt(K_q sum_i 4^e_i sum_j 4^f_j) / ||C_q||_F,
+ * which grows when the result is small against the scales (cancellation, or
+ * rows whose elements lie far below their largest). Every sector with
+ * est_q > rtol is recomputed on the FP64 path in the same call, so each sector,
+ * and the whole result, stays within rtol unless even FP64 cannot reach it. */
+typedef struct {
+  double err_est;            /* relative Frobenius error of C, after the FP64
+                                recomputation of the flagged sectors            */
+  double split_err_est;      /* the same for the split products alone           */
+  double max_sector_est;     /* largest est_q of the split products             */
+  double fallback_flops;     /* useful FLOPs recomputed on the FP64 path        */
+  double rtol;               /* tolerance of the call                           */
+  int32_t nsectors;
+  int32_t nfallback;         /* sectors recomputed on the FP64 path             */
+  int32_t within;            /* 1 when err_est <= rtol                          */
+  int32_t slices;
+} ytn_error_report;
 
 /* Context bound to one CUDA device; allocates a device status word.
  * device < 0 creates a host-only context: ytn_plan then builds plans (output
@@ -240,6 +266,24 @@ void ytn_ctx_destroy(ytn_ctx *ctx);
  * YTN_E_DIM_MISMATCH, YTN_E_FUSION_MISMATCH, YTN_E_UNSUPPORTED, YTN_E_NOMEM,
  * YTN_E_CUDA. */
 ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan);
+
+/* One rank's part of a contraction split over `world` ranks (a TENSORDOT op; no
+ * counterpart in the paper). The charge sectors of a contraction are independent
+ * matrix products and every block of C lies in exactly one sector (Sec. II.B), so
+ * the sectors can be shared out with no exchange of data: the work units are
+ * whole sectors, except that a sector above a quarter of a rank's share of the
+ * useful FLOPs is cut into runs of consecutive row charge tuples I of about that
+ * size; units go to ranks longest first, each to the least loaded rank (ties to
+ * the lower rank, units of equal FLOPs in sector and row order). Every rank
+ * computes the same partition from the structure alone. The plan is an ordinary
+ * tensordot plan on the whole A and B (replicated on every rank) whose output
+ * structure holds only this rank's blocks of C, in canonical order and packed;
+ * the union over ranks of the output blocks is the output of ytn_plan for the
+ * same op, with the same values. ytn_plan_get_info reports this rank's useful
+ * FLOPs and sectors. world = 1 is ytn_plan. Plans are cached per (op, rank,
+ * world). Errors: as ytn_plan, plus YTN_E_INVALID (rank outside [0, world), or
+ * world > 1 for another kind of op). */
+ytn_status ytn_plan_shard(ytn_ctx *ctx, const ytn_op *op, int32_t rank, int32_t world, ytn_plan_t **plan);
 
 /* A leg V(s, t, D) (Sec. II.A): signature, and its charge sectors with their
  * dimensions, in ascending charge order. */
@@ -310,11 +354,25 @@ ytn_status ytn_workspace_size_staged(const ytn_plan_t *plan, ytn_precision prec,
  * the cached choice. While the stream is being captured into a graph, a cost
  * model of the two kernels' tile-padded work decides instead. res->precision
  * reports the path that wrote c; the workspace is ytn_workspace_size(YTN_AUTO).
+ * On the split path the call also checks its own accuracy on the device (see
+ * ytn_error_report): sectors whose data-aware estimate exceeds rtol are
+ * recomputed on the FP64 path before C is written, and when even that leaves
+ * the estimate above rtol the next ytn_sync on the context returns
+ * YTN_E_TOLERANCE.
  * Errors: YTN_E_INVALID (wrong plan kind), YTN_E_WORKSPACE, YTN_E_TOLERANCE
  * (rtol below what the split path can guarantee), YTN_E_CUDA (launch). */
 ytn_status ytn_tensordot(ytn_plan_t *plan, const double *a, const double *b, double *c,
                          ytn_precision prec, double rtol, void *workspace,
                          size_t workspace_bytes, ytn_result *res, ytn_stream stream);
+
+/* The accuracy record (ytn_error_report) of the last split-precision
+ * ytn_tensordot of `plan` that ran with `workspace` (the record lives in the
+ * workspace, so the next call that uses it overwrites it). Waits for `stream`,
+ * then copies the record to *out. Errors: YTN_E_INVALID (null argument, not a
+ * tensordot plan, or no split-precision call has completed in this workspace),
+ * YTN_E_CUDA. No counterpart in the paper. */
+ytn_status ytn_tensordot_report(const ytn_plan_t *plan, const void *workspace, ytn_error_report *out,
+                                ytn_stream stream);
 
 /* C = tensordot(A, B) on the FP64 path without a caller workspace and without
  * allocating anything. The paper has no counterpart: this is for callers that
@@ -328,8 +386,13 @@ ytn_status ytn_tensordot(ytn_plan_t *plan, const double *a, const double *b, dou
  * the array's device address (cudaGetSymbolAddress, with that device current);
  * make that first call before any stream capture. Every call uses the same
  * array: calls that overlap on the GPU (other streams, other threads) race and
- * must be serialised by the caller. Results are those of ytn_tensordot with
- * YTN_FP64. Errors: as ytn_tensordot, plus YTN_E_WORKSPACE (too large). */
+ * must be serialised by the caller. a, b, c may be device memory or page-locked
+ * host memory, as for ytn_tensordot; host operands are staged through the rest of
+ * the array when they fit beside the workspace, else read over the host link.
+ * Results are those of ytn_tensordot with YTN_FP64. Errors: as ytn_tensordot
+ * (YTN_E_INVALID for a plan that is not a tensordot plan or belongs to a
+ * host-only context), plus YTN_E_WORKSPACE (too large) and YTN_E_UNSUPPORTED
+ * (device index 64 or above). */
 ytn_status ytn_tensordot_noalloc(ytn_plan_t *plan, const double *a, const double *b, double *c,
                                  ytn_stream stream);
 
@@ -452,8 +515,10 @@ ytn_status ytn_selftest_timeout(ytn_ctx *ctx, ytn_stream stream);
 
 /* Wait for the stream (at most timeout_ms; < 0 waits without limit) and report
  * the context's device status word: YTN_E_TIMEOUT if a bounded device wait
- * ran out since the last call (the word is then cleared), YTN_E_CUDA if the
- * stream reported an error. */
+ * ran out since the last call, else YTN_E_TOLERANCE if a split-precision
+ * contraction's result is estimated above its rtol even after the FP64
+ * recomputation (the word is then cleared), YTN_E_CUDA if the stream reported
+ * an error. */
 ytn_status ytn_sync(ytn_ctx *ctx, ytn_stream stream, int64_t timeout_ms);
 
 /* ---------------------------------------------------------------------------
@@ -542,6 +607,7 @@ enum {
   YTN_PHASE_SPLIT = 4,      /* FP64 -> BF16 slices (split path)               */
   YTN_PHASE_MOVE = 5,       /* fuse / unfuse / trace                          */
   YTN_PHASE_REDUCE = 6,     /* scalar products                                */
+  YTN_PHASE_CHECK = 7,      /* split path: accuracy check and FP64 fallback   */
   YTN_NPHASES = 8
 };
 typedef struct {

@@ -187,9 +187,13 @@ static void note_capture(ytn_plan_t *p, cudaStream_t st) {
 }
 
 // Workspace: WA | WB | WC (FP64 sector matrices), then for the split path
-// SA | SB (BF16 slice blocks) | EA | EB (row / column exponents); 256-byte aligned.
+// SA | SB (BF16 slice blocks) | EA | EB (row / column exponents) and the accuracy
+// check: EMAX | NORMSQ | REC | SECV | FLAGGED | TILE_END (see SplitRecord);
+// 256-byte aligned regions, except that EMAX follows EB and REC follows NORMSQ
+// directly so that one memset covers each pair.
 struct WsLayout {
   size_t wa = 0, wb = 0, wc = 0, sa = 0, sb = 0, ea = 0, eb = 0;
+  size_t emax = 0, emax_end = 0, normsq = 0, rec = 0, rec_end = 0, secv = 0, flagged = 0, tile_end = 0;
 };
 
 static size_t workspace_layout(const ytn_plan_t *p, bool split, WsLayout &w) {
@@ -208,7 +212,24 @@ static size_t workspace_layout(const ytn_plan_t *p, bool split, WsLayout &w) {
   w.ea = o;
   o += align256((size_t)p->sp_ea * 4);
   w.eb = o;
-  o += align256((size_t)p->sp_eb * 4);
+  o += (size_t)p->sp_eb * 4;
+  const size_t nsec = p->sp_sectors.size();
+  w.emax = o;
+  o += 2 * nsec * 4;
+  w.emax_end = o;
+  o = align256(o);
+  w.normsq = o;
+  o += align256(nsec * 4);
+  w.rec = o;
+  o += sizeof(SplitRecord);
+  w.rec_end = o;
+  o = align256(o);
+  w.secv = o;
+  o += align256(nsec * 8);
+  w.flagged = o;
+  o += align256(nsec * 4);
+  w.tile_end = o;
+  o += align256(nsec * 4);
   return o;
 }
 
@@ -224,6 +245,19 @@ static size_t workspace_layout(const ytn_plan_t *p, bool split, WsLayout &w) {
 static double split_error_estimate(int s, int64_t kmax) {
   return std::ldexp(1.0, 11 - 8 * s) + std::ldexp(1.0, -43) * std::sqrt((double)std::max<int64_t>(kmax, 1));
 }
+
+// Data-aware estimate (split_check.cu): per element of C_q, the error relative to
+// the product of the row and column scales 2^(e_i + f_j), per square root of K.
+// Digit rounding and the dropped orders contribute about 2^-8s; the FP32
+// rounding of the accumulator of the orders >= 3 about 2^-43 (it is rounded over
+// 256 of K at a time at that accumulator's own magnitude, which the digits bound
+// relative to the scales). Measured on this GPU over seven value distributions
+// (normal, uniform, elements just below a power of two, log-uniform over 2^30,
+// rows scaled over 10^60, one dominant element per row and column, cancelling
+// products), K from 64 to 16384 and s = 4, 5, 6, the split error stayed below
+// 0.42 of this estimate. An FP64 product: 2^-52.
+static double split_eta(int s) { return std::ldexp(1.0, -8 * s) + std::ldexp(1.0, -43); }
+static const double kEtaFp64 = std::ldexp(1.0, -52);
 
 static ytn_status choose_slices(const ytn_plan_t *p, double rtol, int &s, double &est) {
   if (p->max_k > 16384) return fail(YTN_E_UNSUPPORTED, "split path supports K up to 16384 per sector");
@@ -312,12 +346,19 @@ void ytn_ctx_destroy(ytn_ctx *ctx) {
   delete ctx;
 }
 
-ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
+static ytn_status plan_op(ytn_ctx *ctx, const ytn_op *op, int32_t rank, int32_t world, ytn_plan_t **plan) {
   if (!ctx || !op || !plan) return fail(YTN_E_INVALID, "null argument");
   *plan = nullptr;
+  if (world < 1 || rank < 0 || rank >= world) return fail(YTN_E_INVALID, "shard rank outside [0, world)");
+  if (world > 1 && op->kind != YTN_OP_TENSORDOT) return fail(YTN_E_INVALID, "only tensordot plans are sharded");
   std::string key;
   try {
     key = plan_key(op);
+    if (world > 1) {
+      key += "|shard";
+      key.append(reinterpret_cast<const char *>(&rank), sizeof(rank));
+      key.append(reinterpret_cast<const char *>(&world), sizeof(world));
+    }
   } catch (...) {
     return fail(YTN_E_NOMEM, "host allocation failed");
   }
@@ -334,6 +375,8 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
   if (!p) return fail(YTN_E_NOMEM, "host allocation failed");
   p->ctx = ctx;
   p->key = key;
+  p->shard_rank = rank;
+  p->shard_world = world;
   std::string err;
   ytn_status st = YTN_OK;
   try {
@@ -431,6 +474,12 @@ ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) {
   ctx->cache[key] = p;
   *plan = p;
   return YTN_OK;
+}
+
+ytn_status ytn_plan(ytn_ctx *ctx, const ytn_op *op, ytn_plan_t **plan) { return plan_op(ctx, op, 0, 1, plan); }
+
+ytn_status ytn_plan_shard(ytn_ctx *ctx, const ytn_op *op, int32_t rank, int32_t world, ytn_plan_t **plan) {
+  return plan_op(ctx, op, rank, world, plan);
 }
 
 // Structure from legs: not cached (the caller holds the only reference).
@@ -568,7 +617,7 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
 
 // One contraction on the chosen path; arguments already checked and mapped.
 static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, bool split, int slices,
-                                 void *workspace, cudaStream_t st) {
+                                 double rtol, void *workspace, cudaStream_t st) {
   WsLayout w;
   workspace_layout(p, split, w);
   char *ws = static_cast<char *>(workspace);
@@ -595,25 +644,42 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
     if (e != cudaSuccess) return cuda_fail(e, "grouped FP64 GEMM");
   } else {
     int32_t *ea = reinterpret_cast<int32_t *>(ws + w.ea), *eb = reinterpret_cast<int32_t *>(ws + w.eb);
+    int32_t *emax = reinterpret_cast<int32_t *>(ws + w.emax);
+    float *normsq = reinterpret_cast<float *>(ws + w.normsq);
+    SplitRecord *rec = reinterpret_cast<SplitRecord *>(ws + w.rec);
     uint8_t *sa = reinterpret_cast<uint8_t *>(ws + w.sa), *sb = reinterpret_cast<uint8_t *>(ws + w.sb);
     {
       PhaseTimer t(p->ctx, YTN_PHASE_SPLIT, st);
-      // the exponent kernel max-combines into EA / EB: start from a value below
-      // every exponent (bytes 0x80: 0x80808080 as int32)
-      e = cudaMemsetAsync(ea, 0x80, (size_t)p->sp_ea * 4, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(eb, 0x80, (size_t)p->sp_eb * 4, st);
+      // the exponent kernel max-combines into EA, EB and EMAX: start from a value
+      // below every exponent (bytes 0x80: 0x80808080 as int32); the epilogue sums
+      // into NORMSQ and the check counts in the record: start from zero
+      e = cudaMemsetAsync(ea, 0x80, w.emax_end - w.ea, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(normsq, 0, w.rec_end - w.normsq, st);
       if (e == cudaSuccess)
-      e = launch_split_prep(p->d_sp_ops, p->d_sp_exp_items, (int64_t)p->sp_exp_items.size(), p->d_sp_slice_items,
-                            (int64_t)p->sp_slice_items.size(), wa, wb, ea, eb, sa, sb, slices, st);
+        e = launch_split_prep(p->d_sp_ops, p->d_sp_exp_items, (int64_t)p->sp_exp_items.size(),
+                              p->d_sp_slice_items, (int64_t)p->sp_slice_items.size(), wa, wb, ea, eb, emax, sa, sb,
+                              slices, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "split into slices");
+    const int sms = p->ctx->gemm_sms.load() > 0 ? p->ctx->gemm_sms.load() : p->ctx->num_sms;
     {
       PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
-      e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles, (int64_t)p->sp_tiles.size(), sa, sb, ea, eb, wc, slices,
-                            p->ctx->status_dev, p->ctx->gemm_sms.load() > 0 ? p->ctx->gemm_sms.load() : p->ctx->num_sms,
-                            st);
+      e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles, (int64_t)p->sp_tiles.size(), sa, sb, ea, eb, emax,
+                            normsq, wc, slices, p->ctx->status_dev, sms, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grouped split-precision GEMM");
+    {
+      // data-aware error estimate per sector; sectors above rtol recomputed in FP64
+      PhaseTimer t(p->ctx, YTN_PHASE_CHECK, st);
+      int32_t *flagged = reinterpret_cast<int32_t *>(ws + w.flagged);
+      int32_t *tile_end = reinterpret_cast<int32_t *>(ws + w.tile_end);
+      e = launch_split_check(p->d_sp_sectors, (int64_t)p->sp_sectors.size(), ea, eb, emax, normsq,
+                             reinterpret_cast<double *>(ws + w.secv), flagged, tile_end, rec, split_eta(slices),
+                             kEtaFp64, rtol, slices, p->ctx->status_dev, st);
+      if (e == cudaSuccess && !p->sp_sectors.empty())
+        e = launch_gemm_fp64_redo(p->d_sectors, flagged, tile_end, rec, wa, wb, wc, p->ctx->num_sms, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "accuracy check of the split products");
   }
   {
     PhaseTimer t(p->ctx, YTN_PHASE_SCATTER, st);
@@ -724,9 +790,9 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
         cudaEvent_t ev[3];
         for (auto &x : ev) cudaEventCreate(&x);
         cudaEventRecord(ev[0], st);
-        ytn_status r = exec_tensordot(p, a, b, c, false, 0, workspace, st);
+        ytn_status r = exec_tensordot(p, a, b, c, false, 0, rtol, workspace, st);
         cudaEventRecord(ev[1], st);
-        if (r == YTN_OK) r = exec_tensordot(p, a, b, c, true, slices, workspace, st);
+        if (r == YTN_OK) r = exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st);
         cudaEventRecord(ev[2], st);
         cudaError_t e = cudaEventSynchronize(ev[2]);
         float t64 = 0.f, t16 = 0.f;
@@ -754,7 +820,7 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     }
     split = choice == 1;
   }
-  ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, workspace, st);
+  ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, rtol, workspace, st);
   if (r != YTN_OK) return r;
   if ((r = unstage()) != YTN_OK) return r;
   if (res) {
@@ -975,10 +1041,47 @@ ytn_status ytn_sync(ytn_ctx *ctx, ytn_stream stream, int64_t timeout_ms) {
   int word[4] = {0, 0, 0, 0};
   cudaError_t e = cudaMemcpy(word, ctx->status_dev, sizeof(word), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "read status word");
-  if (word[0] != 0) {
-    cudaMemset(ctx->status_dev, 0, sizeof(word));
+  if (word[0] != 0 || word[1] != 0) cudaMemset(ctx->status_dev, 0, sizeof(word));
+  if (word[0] != 0)
     return fail(YTN_E_TIMEOUT, "a bounded device wait ran out (status " + std::to_string(word[0]) + ")");
+  if (word[1] != 0)
+    return fail(YTN_E_TOLERANCE,
+                "a split-precision result is estimated above its rtol even after the FP64 recomputation "
+                "(ytn_tensordot_report gives the estimate)");
+  return YTN_OK;
+}
+
+ytn_status ytn_tensordot_report(const ytn_plan_t *p, const void *workspace, ytn_error_report *out,
+                                ytn_stream stream) {
+  if (!p || !out) return fail(YTN_E_INVALID, "null argument");
+  if (p->kind != Kind::Tensordot) return fail(YTN_E_INVALID, "plan is not a tensordot plan");
+  if (!p->dev) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
+  std::memset(out, 0, sizeof(*out));
+  if (p->sp_sectors.empty()) {   // nothing to multiply: exact
+    out->within = 1;
+    return YTN_OK;
   }
+  if (!workspace) return fail(YTN_E_INVALID, "null workspace");
+  DeviceGuard g(p->ctx->device);
+  if (!g.ok()) return fail(YTN_E_CUDA, "cannot select device");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream");
+  WsLayout w;
+  workspace_layout(p, true, w);
+  SplitRecord r;
+  e = cudaMemcpy(&r, static_cast<const char *>(workspace) + w.rec, sizeof(r), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read the accuracy record");
+  if (r.valid != 1) return fail(YTN_E_INVALID, "no split-precision call has completed in this workspace");
+  out->err_est = r.err_est;
+  out->split_err_est = r.split_err_est;
+  out->max_sector_est = r.max_sector_est;
+  out->fallback_flops = r.fallback_flops;
+  out->rtol = r.rtol;
+  out->nsectors = r.nsectors;
+  out->nfallback = r.nfallback;
+  out->within = r.within;
+  out->slices = r.slices;
   return YTN_OK;
 }
 

@@ -16,6 +16,8 @@
 // prefetch of the next K step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kernels.hpp"
 
 namespace ytn {
@@ -154,7 +156,47 @@ __global__ void __launch_bounds__(kThreads) gemm_fp64_kernel(const SectorDev *__
   else gemm_tile<64>(s, tl, wa, wb, wc, As, Bs);
 }
 
+// FP64 recomputation of the sectors that the split path's accuracy check
+// flagged: a persistent grid walks the flagged sectors' 64 x 64 tiles, whose list
+// the check wrote on the device (tile_end: running tile counts per flagged
+// sector). With no flagged sector every CTA returns at once.
+__global__ void __launch_bounds__(kThreads) gemm_fp64_redo_kernel(const SectorDev *__restrict__ sectors,
+                                                                  const int32_t *__restrict__ flagged,
+                                                                  const int32_t *__restrict__ tile_end,
+                                                                  const SplitRecord *__restrict__ rec,
+                                                                  const double *__restrict__ wa,
+                                                                  const double *__restrict__ wb,
+                                                                  double *__restrict__ wc) {
+  __shared__ double As[2][BK][64 + PAD];
+  __shared__ double Bs[2][BK][64 + PAD];
+  const int nflag = rec->nfallback;
+  if (nflag <= 0) return;
+  const int total = tile_end[nflag - 1];
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = nflag - 1;   // first flagged sector whose tiles end after t
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (tile_end[mid] > t) hi = mid;
+      else lo = mid + 1;
+    }
+    const int local = t - (lo > 0 ? tile_end[lo - 1] : 0);
+    const SectorDev s = sectors[flagged[lo]];
+    const int nt = (s.N + 63) / 64;
+    const GemmTile tl{flagged[lo], local / nt, local % nt, 64};
+    gemm_tile<64>(s, tl, wa, wb, wc, As, Bs);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_gemm_fp64_redo(const SectorDev *sectors, const int32_t *flagged, const int32_t *tile_end,
+                                  const SplitRecord *rec, const double *wa, const double *wb, double *wc,
+                                  int num_sms, cudaStream_t stream) {
+  gemm_fp64_redo_kernel<<<(unsigned)std::max(1, num_sms) * 4, kThreads, 0, stream>>>(sectors, flagged, tile_end, rec,
+                                                                                    wa, wb, wc);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_fp64(const SectorDev *sectors, const GemmTile *tiles, int64_t ntiles,
                              const double *wa, const double *wb, double *wc, cudaStream_t stream) {

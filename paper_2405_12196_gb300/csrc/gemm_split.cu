@@ -203,11 +203,15 @@ __device__ __forceinline__ void issue_rest(uint32_t tmem, uint64_t a0, uint64_t 
   }
 }
 
+// 2^k as an FP32 value for k <= 0 (0 below the normal range).
+__device__ __forceinline__ float pow2f(int k) { return k >= -126 ? __int_as_float((k + 127) << 23) : 0.0f; }
+
 template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_split_kernel(const SplitSector *__restrict__ sectors, const SplitTile *__restrict__ tiles, int ntiles,
                       const uint8_t *__restrict__ sa, const uint8_t *__restrict__ sb, const int32_t *__restrict__ ea,
-                      const int32_t *__restrict__ eb, double *__restrict__ wc, int *status) {
+                      const int32_t *__restrict__ eb, const int32_t *__restrict__ emax, float *__restrict__ normsq,
+                      double *__restrict__ wc, int *status) {
   constexpr int s = S;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -390,20 +394,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(bar(kREmpty));
       }
       if (!ok) break;
-      // C = acc * 2^(e_i + f_j - 40)
+      // C = acc * 2^(e_i + f_j - 40); beside it, the tile's share of the sector's
+      // ||C_q||^2 relative to 4^(emax_A + emax_B) for the accuracy check, in FP32
+      // (acc * 2^-40 from its two 32-bit halves, squared, scaled by powers of two)
       const int row = tl.mt * kSplitBM + rl;
+      float ss = 0.0f;
       if (row < sc.M) {
         const int ei = ea[sc.ea_off + row];
+        const int fmax = __ldg(emax + 2 * tl.sector + 1);
         double *crow = wc + sc.c_off + (int64_t)row * sc.N;
         const int n0 = tl.nt * kSplitBM + c0;
         const int32_t *fcol = eb + sc.eb_off + n0;
 #pragma unroll
         for (int j = 0; j < 48; j++) {
           if (j < ngroups * 4 && n0 + j < sc.N) {
-            crow[n0 + j] = scaled_double(acc[j], ei + __ldg(fcol + j) - 40);
+            const int fj = __ldg(fcol + j);
+            crow[n0 + j] = scaled_double(acc[j], ei + fj - 40);
+            const float v = fmaf((float)(int)(acc[j] >> 32), 0x1p-8f, (float)(uint32_t)acc[j] * 0x1p-40f) *
+                            pow2f(fj - fmax);
+            ss = fmaf(v, v, ss);
           }
         }
+        ss *= pow2f(2 * (ei - __ldg(emax + 2 * tl.sector)));
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0 && ss > 0.0f) atomicAdd(normsq + tl.sector, ss);
     }
   }
   tc_fence_before();
@@ -425,13 +441,14 @@ cudaError_t configure_split_gemm() {
 }
 
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
-                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc, int slices,
-                              int *status, int num_sms, cudaStream_t stream) {
+                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, const int32_t *emax,
+                              float *normsq, double *wc, int slices, int *status, int num_sms, cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles > INT32_MAX || slices < 4 || slices > kSlices) return cudaErrorInvalidValue;
   auto kernel = slices == 4 ? gemm_split_kernel<4> : slices == 5 ? gemm_split_kernel<5> : gemm_split_kernel<6>;
   const int grid = (int)std::min<int64_t>(ntiles, num_sms);
-  kernel<<<grid, kThreads, kSmemBytes, stream>>>(sectors, tiles, (int)ntiles, sa, sb, ea, eb, wc, status);
+  kernel<<<grid, kThreads, kSmemBytes, stream>>>(sectors, tiles, (int)ntiles, sa, sb, ea, eb, emax, normsq, wc,
+                                                 status);
   return cudaGetLastError();
 }
 

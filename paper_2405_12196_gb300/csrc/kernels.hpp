@@ -25,9 +25,10 @@ cudaError_t launch_gemm_fp64(const SectorDev *sectors, const GemmTile *tiles, in
                              const double *wa, const double *wb, double *wc, cudaStream_t stream);
 
 // Split-precision path: row exponents and BF16 slices of every sector operand.
+// emax[op] receives each operand's largest row exponent.
 cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_items, int64_t nexp,
                               const SplitItem *slice_items, int64_t nslice, const double *wa, const double *wb,
-                              int32_t *ea, int32_t *eb, uint8_t *sa, uint8_t *sb, int slices,
+                              int32_t *ea, int32_t *eb, int32_t *emax, uint8_t *sa, uint8_t *sb, int slices,
                               cudaStream_t stream);
 
 // Shared-memory opt-in of the split-precision GEMM kernels (once per device).
@@ -41,9 +42,28 @@ cudaError_t launch_cscatter(const CScatterJob *jobs, int64_t njobs, const double
 // N(0, 1) numbers: Philox4x32-10 words turned by Box-Muller (see ytn_fill_normal).
 cudaError_t launch_fill_normal(uint64_t seed, int64_t n, double *out, cudaStream_t stream);
 
-// Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output C_q.
+// Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output C_q;
+// the epilogue adds each sector's scaled ||C_q||^2 into normsq (emax: the
+// operands' largest exponents).
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
-                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, double *wc, int slices,
-                              int *status, int num_sms, cudaStream_t stream);
+                              const uint8_t *sb, const int32_t *ea, const int32_t *eb, const int32_t *emax,
+                              float *normsq, double *wc, int slices, int *status, int num_sms, cudaStream_t stream);
+
+// Accuracy check of the split products (one CTA per sector, the last one
+// finalises): per-sector estimates from the exponents and normsq, the list of
+// sectors above rtol with their 64 x 64 tile counts, the call's record, and the
+// status word's tolerance flag (status[1]) when the fallback cannot reach rtol.
+// eta_split / eta_fp64: per-element error of the split / FP64 products relative
+// to the row and column scales, per square root of K.
+cudaError_t launch_split_check(const SplitSector *sectors, int64_t nsec, const int32_t *ea, const int32_t *eb,
+                               const int32_t *emax, const float *normsq, double *secv, int32_t *flagged,
+                               int32_t *tile_end, SplitRecord *rec, double eta_split, double eta_fp64, double rtol,
+                               int slices, int *status, cudaStream_t stream);
+
+// FP64 recomputation of the flagged sectors (persistent, 64 x 64 DMMA tiles):
+// the sector list and tile counts come from the accuracy check on the device.
+cudaError_t launch_gemm_fp64_redo(const SectorDev *sectors, const int32_t *flagged, const int32_t *tile_end,
+                                  const SplitRecord *rec, const double *wa, const double *wb, double *wc,
+                                  int num_sms, cudaStream_t stream);
 
 }  // namespace ytn

@@ -38,6 +38,11 @@ using namespace ytn;
 extern "C" ytn_status ytn_tensordot_noalloc(ytn_plan_t *plan, const double *a, const double *b, double *c,
                                             ytn_stream stream) {
   if (!plan) return fail(YTN_E_INVALID, "null plan");
+  if (plan->kind != Kind::Tensordot) return fail(YTN_E_INVALID, "plan is not a tensordot plan");
+  const int dev = plan->ctx ? plan->ctx->device : -1;
+  if (dev < 0) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
+  if (dev >= kMaxDevices)
+    return fail(YTN_E_UNSUPPORTED, "ytn_tensordot_noalloc serves devices 0.." + std::to_string(kMaxDevices - 1));
   size_t need = 0;
   ytn_status st = ytn_workspace_size(plan, YTN_FP64, 0.0, &need);
   if (st != YTN_OK) return st;
@@ -45,8 +50,6 @@ extern "C" ytn_status ytn_tensordot_noalloc(ytn_plan_t *plan, const double *a, c
     return fail(YTN_E_WORKSPACE, "contraction needs " + std::to_string(need) +
                                      " bytes of workspace, more than the 64 MiB static scratch of "
                                      "ytn_tensordot_noalloc; use ytn_tensordot with a caller workspace");
-  const int dev = plan->ctx ? plan->ctx->device : -1;
-  if (dev < 0 || dev >= kMaxDevices) return fail(YTN_E_INVALID, "plan of a host-only context cannot run");
   void *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -58,9 +61,11 @@ extern "C" ytn_status ytn_tensordot_noalloc(ytn_plan_t *plan, const double *a, c
         return fail(YTN_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (prev != dev) cudaSetDevice(prev);
+      const cudaError_t er = prev != dev ? cudaSetDevice(prev) : cudaSuccess;
       if (e != cudaSuccess || !p)
         return fail(YTN_E_CUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+      if (er != cudaSuccess)
+        return fail(YTN_E_CUDA, std::string("restoring the caller's device: ") + cudaGetErrorString(er));
       g_noalloc_ptr[dev] = p;
     }
     scratch = g_noalloc_ptr[dev];

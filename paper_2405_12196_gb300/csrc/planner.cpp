@@ -653,6 +653,105 @@ static ytn_status check_resolvable(const Fusion &a, const Fusion &b, int nsym, s
   return YTN_OK;
 }
 
+// One sector of a contraction while it is being planned: its contracted charge
+// tuples x (with |x|), its rows I (with |I| and one A block carrying it) and its
+// columns J (with |J| and one B block).
+struct SB {
+  std::map<Key, int64_t> xs;
+  std::map<Key, std::pair<int64_t, int64_t>> rows;
+  std::map<Key, std::pair<int64_t, int64_t>> cols;
+};
+
+// Partition of one contraction over p->shard_world ranks (its sectors are
+// independent matrix products, and each block of C lies in exactly one sector):
+// the work units are whole sectors, except that a sector above a quarter of a
+// rank's share is cut into runs of consecutive rows I of about that size; the
+// units go to ranks by longest-processing-time first (largest useful FLOPs first,
+// each to the least loaded rank, ties to the lower rank; units of equal FLOPs in
+// sector and row order), the same on every rank since it is integer structure
+// and a fixed order. The plan keeps p->shard_rank's rows of each sector (A and B
+// stay whole; C's blocks are those of the kept rows) and its useful FLOPs.
+static void shard_sectors(ytn_plan_t *p, const Tensor &A, const Tensor &B,
+                          std::map<Key, std::vector<int64_t>> &Ax, std::map<Key, std::vector<int64_t>> &Bx,
+                          const std::vector<int> &freeA, const std::vector<int> &freeB, std::map<Key, SB> &secs) {
+  const int world = p->shard_world, rank = p->shard_rank;
+  // useful FLOPs per row of each sector: 2 |I| |x| sum_{B(x, J)} |J| over the x of A(I, x)
+  std::vector<std::vector<double>> row_fl;
+  double total = 0;
+  for (auto &kv : secs) {
+    const SB &sb = kv.second;
+    std::map<Key, size_t> ridx;
+    for (auto &r : sb.rows) ridx.emplace(r.first, ridx.size());
+    std::vector<double> fl(sb.rows.size(), 0.0);
+    for (auto &x : sb.xs) {
+      double nj = 0;
+      for (int64_t b : Bx[x.first]) nj += (double)sub_elems(B, b, freeB);
+      for (int64_t a : Ax[x.first]) {
+        auto it = ridx.find(sub_charges(A, a, freeA));
+        if (it != ridx.end()) fl[it->second] += 2.0 * (double)sub_elems(A, a, freeA) * (double)x.second * nj;
+      }
+    }
+    for (double f : fl) total += f;
+    row_fl.push_back(std::move(fl));
+  }
+  struct Unit { size_t sec, r0, r1; double fl; };
+  std::vector<Unit> units;
+  const double cap = total / world / 4.0;
+  for (size_t si = 0; si < row_fl.size(); si++) {
+    const auto &fl = row_fl[si];
+    double sf = 0;
+    for (double f : fl) sf += f;
+    if (sf <= cap || fl.size() < 2) {
+      units.push_back({si, 0, fl.size(), sf});
+      continue;
+    }
+    size_t r0 = 0;
+    double acc = 0;
+    for (size_t r = 0; r < fl.size(); r++) {
+      acc += fl[r];
+      if (acc >= cap || r + 1 == fl.size()) {
+        units.push_back({si, r0, r + 1, acc});
+        r0 = r + 1;
+        acc = 0;
+      }
+    }
+  }
+  std::stable_sort(units.begin(), units.end(), [](const Unit &x, const Unit &y) { return x.fl > y.fl; });
+  std::vector<double> load(world, 0.0);
+  std::vector<std::vector<std::pair<size_t, size_t>>> mine(row_fl.size());
+  for (const Unit &u : units) {
+    int best = 0;
+    for (int r = 1; r < world; r++)
+      if (load[r] < load[best]) best = r;
+    load[best] += u.fl;
+    if (best == rank) mine[u.sec].push_back({u.r0, u.r1});
+  }
+  // keep this rank's rows; drop sectors with none
+  double kept = 0;
+  size_t si = 0;
+  for (auto it = secs.begin(); it != secs.end(); si++) {
+    auto &ranges = mine[si];
+    if (ranges.empty()) {
+      it = secs.erase(it);
+      continue;
+    }
+    std::vector<char> keep(row_fl[si].size(), 0);
+    for (auto &rg : ranges)
+      for (size_t r = rg.first; r < rg.second; r++) keep[r] = 1;
+    size_t r = 0;
+    for (auto rit = it->second.rows.begin(); rit != it->second.rows.end(); r++) {
+      if (keep[r]) {
+        kept += row_fl[si][r];
+        ++rit;
+      } else {
+        rit = it->second.rows.erase(rit);
+      }
+    }
+    ++it;
+  }
+  p->flops = kept * p->ca * p->cb;
+}
+
 ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int naxes,
                           const int *axa_in, const int *axb_in, std::string &err) {
   if (A.nsym != B.nsym || std::memcmp(A.mod, B.mod, sizeof(A.mod)) != 0) {
@@ -749,11 +848,6 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
 
   // Sector key q = sum_k s_A[axa_k] x_k (reduced): every x, every row I of A and
   // every column J of B belongs to exactly one sector.
-  struct SB {
-    std::map<Key, int64_t> xs;                      // x -> |x|
-    std::map<Key, std::pair<int64_t, int64_t>> rows; // I -> (|I|, any A block)
-    std::map<Key, std::pair<int64_t, int64_t>> cols; // J -> (|J|, any B block)
-  };
   std::map<Key, SB> secs;
   double flops = 0;
   for (auto &kv : Ax) {
@@ -781,6 +875,7 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
     flops += 2.0 * si * (double)kx * sj;
   }
   p->flops = flops * ca * cb;
+  if (p->shard_world > 1) shard_sectors(p, A, B, Ax, Bx, freeA, freeB, secs);
 
   // Sector geometry: rows, K and columns in ascending charge order.
   struct SG {

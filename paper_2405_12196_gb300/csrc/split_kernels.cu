@@ -37,12 +37,14 @@ __device__ __forceinline__ int biased_exp(double x) {
 // 0 for a zero row). An item covers 128 rows and up to 256 of K; its per-row
 // maxima are combined into E with atomicMax (exact and order-independent), E
 // having been set below every exponent beforehand. Rows past the operand are
-// left alone (no kernel reads them).
+// left alone (no kernel reads them). The item's largest exponent also goes into
+// emax[op], the operand's largest (the reference scale of the accuracy check).
 __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__restrict__ ops,
                                                         const SplitItem *__restrict__ items,
                                                         const double *__restrict__ wa,
                                                         const double *__restrict__ wb,
-                                                        int32_t *__restrict__ ea, int32_t *__restrict__ eb) {
+                                                        int32_t *__restrict__ ea, int32_t *__restrict__ eb,
+                                                        int32_t *__restrict__ emax) {
   const SplitItem it = items[blockIdx.x];
   const SplitOperand o = ops[it.op];
   const bool isA = (it.op & 1) == 0;
@@ -51,7 +53,9 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__re
   const int r0 = it.rt * kSplitBM;
   const int k_lo = it.kt0 * kSplitBK, k_hi = min(o.K, (it.kt0 + it.nkt) * kSplitBK);
   __shared__ int red[2][kSplitBM];
+  __shared__ int wmax[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int mine = 0;   // largest biased exponent this thread saw
   if (o.kmajor) {
     // rows of K contiguous elements: one warp per row
     for (int rr = warp; rr < kSplitBM; rr += 8) {
@@ -64,6 +68,7 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__re
 #pragma unroll
       for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
       if (lane == 0) atomicMax(E + r, m - 1021);
+      mine = max(mine, m);
     }
   } else {
     // K rows of `rows` contiguous elements: thread per row, two halves of the K range
@@ -74,8 +79,19 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__re
 #pragma unroll 4
       for (int k = k_lo + half; k < k_hi; k += 2) m = max(m, biased_exp(__ldg(X + (int64_t)k * o.rows + r)));
     red[half][rr] = m;
+    mine = m;
     __syncthreads();
     if (tid < kSplitBM && r0 + tid < o.rows) atomicMax(E + r0 + tid, max(red[0][tid], red[1][tid]) - 1021);
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) mine = max(mine, __shfl_xor_sync(0xffffffffu, mine, s));
+  if (lane == 0) wmax[warp] = mine;
+  __syncthreads();
+  if (tid == 0) {
+    int m = wmax[0];
+#pragma unroll
+    for (int w = 1; w < 8; w++) m = max(m, wmax[w]);
+    atomicMax(emax + it.op, m - 1021);
   }
 }
 
@@ -180,10 +196,10 @@ __global__ void __launch_bounds__(256) split_slice_kernel(const SplitOperand *__
 
 cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_items, int64_t nexp,
                               const SplitItem *slice_items, int64_t nslice, const double *wa, const double *wb,
-                              int32_t *ea, int32_t *eb, uint8_t *sa, uint8_t *sb, int slices,
+                              int32_t *ea, int32_t *eb, int32_t *emax, uint8_t *sa, uint8_t *sb, int slices,
                               cudaStream_t stream) {
   if (nexp > INT32_MAX || nslice > INT32_MAX || slices < 1 || slices > kSlices) return cudaErrorInvalidValue;
-  if (nexp > 0) split_exp_kernel<<<(unsigned)nexp, 256, 0, stream>>>(ops, exp_items, wa, wb, ea, eb);
+  if (nexp > 0) split_exp_kernel<<<(unsigned)nexp, 256, 0, stream>>>(ops, exp_items, wa, wb, ea, eb, emax);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (nslice > 0) split_slice_kernel<<<(unsigned)nslice, 256, 0, stream>>>(ops, slice_items, wa, wb, ea, eb, sa, sb, slices);

@@ -156,6 +156,33 @@ struct SplitTile {
   int32_t sector, mt, nt, pad;
 };
 
+// Accuracy check of a split-precision call, written into the workspace after the
+// column exponents (see split_check.cu):
+//   emax    int32 [2 * nsec]  largest row exponent of each operand (A of sector q
+//                             at 2q, B at 2q + 1), max-combined by the exponent kernel
+//   normsq  float [nsec]      ||C_q||_F^2 times 4^-(emax_A + emax_B), summed by the
+//                             GEMM epilogue
+//   SplitRecord               the call's totals (below)
+//   secv    double [nsec]     K_q sum_i 4^(e_i - emax_A) sum_j 4^(f_j - emax_B)
+//   flagged int32 [nsec]      sectors recomputed on the FP64 path, in sector order
+//   tile_end int32 [nsec]     running count of their 64 x 64 FP64 tiles
+// emax is filled with bytes 0x80 and normsq / the record with zeros before the
+// call's kernels run.
+struct SplitRecord {
+  double err_est;          // relative Frobenius error of C after the FP64 fallback
+  double split_err_est;    // the same for the split products alone (no fallback)
+  double max_sector_est;   // largest per-sector estimate of the split products
+  double fallback_flops;   // useful FLOPs recomputed on the FP64 path
+  double rtol;             // tolerance the call was made with
+  int32_t nsectors;
+  int32_t nfallback;       // sectors recomputed on the FP64 path
+  int32_t within;          // 1 when err_est <= rtol
+  int32_t valid;           // 1 once the check has run
+  int32_t done_blocks;     // per-sector CTAs finished (the last one finalises)
+  int32_t slices;
+};
+static_assert(sizeof(SplitRecord) == 64, "SplitRecord layout");
+
 // Scatter of a complex product: one C block from the quadrants of the doubled
 // C_q (P = [[re.re, re.im], [im.re, im.im]] in rows x columns): element e of the
 // block (row-major over its nd dims) reads P at src + sum idx_i sstr_i plus the
@@ -263,6 +290,9 @@ struct ytn_plan_s {
   ytn_ctx *ctx = nullptr;
   ytn::Kind kind = ytn::Kind::Tensordot;
   std::string key;
+  // tensordot shard (ytn_plan_shard): this plan keeps the work units that the
+  // partition of the whole contraction over shard_world ranks gives shard_rank
+  int32_t shard_rank = 0, shard_world = 1;
 
   // input sizes and output structure (owned storage + ABI view)
   int64_t a_size = 0, b_size = 0;

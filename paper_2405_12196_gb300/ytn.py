@@ -84,7 +84,7 @@ class ytn_plan_info(C.Structure):
 
 
 NPHASES = 8
-PHASES = {0: "gather_a", 1: "gather_b", 2: "gemm", 3: "scatter", 4: "split", 5: "move", 6: "reduce"}
+PHASES = {0: "gather_a", 1: "gather_b", 2: "gemm", 3: "scatter", 4: "split", 5: "move", 6: "reduce", 7: "check"}
 
 
 class ytn_profile(C.Structure):
@@ -94,6 +94,12 @@ class ytn_profile(C.Structure):
 class ytn_result(C.Structure):
     _fields_ = [("useful_flops", C.c_double), ("precision", C.c_int32), ("slices", C.c_int32),
                 ("err_est", C.c_double)]
+
+
+class ytn_error_report(C.Structure):
+    _fields_ = [("err_est", C.c_double), ("split_err_est", C.c_double), ("max_sector_est", C.c_double),
+                ("fallback_flops", C.c_double), ("rtol", C.c_double), ("nsectors", C.c_int32),
+                ("nfallback", C.c_int32), ("within", C.c_int32), ("slices", C.c_int32)]
 
 
 class ytn_request_info(C.Structure):
@@ -106,6 +112,7 @@ SYMBOLS = {
     "ytn_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
     "ytn_ctx_destroy": (None, [C.c_void_p]),
     "ytn_plan": (C.c_int, [C.c_void_p, C.POINTER(ytn_op), C.POINTER(C.c_void_p)]),
+    "ytn_plan_shard": (C.c_int, [C.c_void_p, C.POINTER(ytn_op), C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
     "ytn_plan_output": (C.POINTER(ytn_struct), [C.c_void_p]),
     "ytn_plan_blocks": (C.c_int, [C.c_void_p, ytn_sym, C.c_int32, C.POINTER(ytn_leg), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_void_p)]),
@@ -121,6 +128,7 @@ SYMBOLS = {
     "ytn_workspace_size_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
     "ytn_tensordot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                 C.c_void_p, C.c_size_t, C.POINTER(ytn_result), C.c_void_p]),
+    "ytn_tensordot_report": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ytn_error_report), C.c_void_p]),
     "ytn_tensordot_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_fuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_unfuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -360,11 +368,12 @@ def ytn_ctx_create(device=0):
     return Ctx(h.value)
 
 
-def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None, keep=None):
+def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None, keep=None, shard=None):
     """Plan an operation. ``a``/``b``: tensor records. ``kind``: one of YTN_OP_*.
     TENSORDOT: pairs (axa[k], axb[k]); FUSE: ``groups`` (list of leg tuples);
     UNFUSE: legs ``axa``; TRACE: pairs (axa[k], axb[k]) of ``a``; SWAP_GATE: two
-    ``groups`` and ``fermionic`` (one flag per symmetry component; None = all)."""
+    ``groups`` and ``fermionic`` (one flag per symmetry component; None = all).
+    ``shard=(rank, world)``: this rank's part of a TENSORDOT (ytn_plan_shard)."""
     sa = Struct(a)
     sb = Struct(b) if b is not None else None
     op = ytn_op()
@@ -395,7 +404,10 @@ def ytn_plan(ctx, kind, a, b=None, axa=(), axb=(), groups=None, fermionic=None, 
         op.keep_D = kd.ctypes.data_as(C.POINTER(C.c_int64))
         keep_arrays = (kt, kd)
     h = C.c_void_p()
-    _check(_lib.ytn_plan(ctx.handle, C.byref(op), C.byref(h)))
+    if shard is None:
+        _check(_lib.ytn_plan(ctx.handle, C.byref(op), C.byref(h)))
+    else:
+        _check(_lib.ytn_plan_shard(ctx.handle, C.byref(op), int(shard[0]), int(shard[1]), C.byref(h)))
     return Plan(ctx, h.value, (sa, sb, keep_arrays))
 
 
@@ -482,6 +494,15 @@ def ytn_ncon(nc, data, out, prec=YTN_FP64, rtol=0.0, workspace=None, workspace_b
     ptrs = (C.c_void_p * len(data))(*[_ptr(d) for d in data])
     _check(_lib.ytn_ncon(nc.handle, ptrs, _ptr(out), prec, float(rtol), _ptr(workspace), int(workspace_bytes),
                          _stream(stream)))
+
+
+def ytn_tensordot_report(plan, workspace, stream=None):
+    """Accuracy record of the last split-precision call of ``plan`` in ``workspace``
+    (waits for ``stream``): data-aware error estimate after the FP64 fallback, the
+    split products' estimate, recomputed sectors."""
+    r = ytn_error_report()
+    _check(_lib.ytn_tensordot_report(plan.handle, _ptr(workspace), C.byref(r), _stream(stream)))
+    return {k: getattr(r, k) for k, _ in ytn_error_report._fields_}
 
 
 def ytn_tensordot_noalloc(plan, a, b, c, stream=None):

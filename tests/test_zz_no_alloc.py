@@ -61,6 +61,66 @@ def test_noalloc_matches_tensordot_on_consecutive_calls():
             assert _rel(got, want) <= FP64_RTOL
 
 
+def test_noalloc_host_buffers_and_side_stream_match_the_oracle():
+    """Page-locked host A, B and C (staged through the static array beside the
+    workspace) and a call on a non-default stream, each compared with the oracle and
+    with ytn_tensordot on device buffers."""
+    import torch
+    import oracle as O
+    from paper_2405_12196_gb300 import ytn
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device")
+    dev = torch.device("cuda:0")
+    ctx = ytn.ytn_ctx_create(0)
+    cfg = W.config1()
+    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    n = plan.out["size"]
+    assert ytn.ytn_workspace_size_staged(plan, ytn.YTN_FP64, 0.0) < 64 << 20
+    want = O.to_record(O.tensordot(O.from_record(A), O.from_record(B), axa, axb))["data"]
+    da = torch.from_numpy(A["data"]).to(dev)
+    db = torch.from_numpy(B["data"]).to(dev)
+    ref = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    ws = torch.empty(max(ytn.ytn_workspace_size(plan, ytn.YTN_FP64), 1), dtype=torch.uint8, device=dev)
+    ytn.ytn_tensordot(plan, da, db, ref, prec=ytn.YTN_FP64, workspace=ws)
+    ytn.ytn_sync(ctx)
+    ref = ref.cpu().numpy()
+    ha = torch.from_numpy(A["data"].copy()).pin_memory()
+    hb = torch.from_numpy(B["data"].copy()).pin_memory()
+    for _ in range(2):
+        hc = torch.full((n,), float("nan"), dtype=torch.float64).pin_memory()
+        ytn.ytn_tensordot_noalloc(plan, ha, hb, hc)
+        ytn.ytn_sync(ctx)
+        got = hc.numpy().copy()
+        assert np.all(np.isfinite(got))
+        assert _rel(got, want) <= FP64_RTOL
+        np.testing.assert_array_equal(got, ref)
+    side = torch.cuda.Stream(device=dev)
+    out = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    ytn.ytn_tensordot_noalloc(plan, da, db, out, stream=side)
+    ytn.ytn_sync(ctx, stream=side)
+    got = out.cpu().numpy()
+    assert _rel(got, want) <= FP64_RTOL
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_noalloc_rejects_other_plan_kinds():
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device")
+    ctx = ytn.ytn_ctx_create(0)
+    A = W.config1()["A"]
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_FUSE, A, groups=((0, 1), (2,)))
+    dev = torch.device("cuda:0")
+    da = torch.from_numpy(A["data"]).to(dev)
+    out = torch.empty(max(plan.out["size"], 1), dtype=torch.float64, device=dev)
+    with pytest.raises(ytn.YtnError) as e:
+        ytn.ytn_tensordot_noalloc(plan, da, da, out)
+    assert e.value.name == "YTN_E_INVALID"
+
+
 def test_noalloc_rejects_contractions_beyond_its_scratch():
     import torch
     from paper_2405_12196_gb300 import ytn
