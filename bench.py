@@ -15,9 +15,11 @@ warm-up steps; the FP64 tensor-core path is timed beside it (--fp64-steps) and t
 relative Frobenius difference of the two results is reported.
 python bench.py --impl reference ...   (the CPU oracle, timed on host cores)
 
-Multi-GPU (torchrun, one rank per GPU): every rank contracts its own independent
-problem (its own seed); there is no data-path collective. value = all ranks' useful
-FLOPs / max-over-ranks time ("scaling": "weak").
+Multi-GPU (torchrun, one rank per GPU): the one contraction is shared out over the
+ranks by charge sectors (ytn_plan_shard: longest-first partition of the sectors, the
+largest cut by rows); A and B are replicated, every rank writes its own blocks of C,
+and there is no data-path collective. value = the whole contraction's useful FLOPs /
+the slowest rank's time ("scaling": "strong").
 """
 import os
 
@@ -192,6 +194,240 @@ def oracle_sample(cfg, budget_s, seed=0):
     return flops, secs, desc
 
 
+def host_cores():
+    """CPU cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_POOL_CFG = {}
+
+
+def _pool_init(meta):
+    """Worker start-up: the workload's structure, and its data as views of the parent's
+    shared memory (no copy)."""
+    from multiprocessing import shared_memory
+    cfg = {"axa": meta["axa"], "axb": meta["axb"]}
+    shms = []
+    for k in ("A", "B"):
+        m = meta[k]
+        shm = shared_memory.SharedMemory(name=m["shm"])
+        shms.append(shm)
+        rec = dict(m["rec"])
+        rec["data"] = np.ndarray((m["n"],), dtype=np.float64, buffer=shm.buf)
+        cfg[k] = rec
+    _POOL_CFG["cfg"] = cfg
+    _POOL_CFG["shm"] = shms
+
+
+def _pool_ping(_):
+    return os.getpid()
+
+
+def _pool_oracle(xs):
+    """Oracle tensordot over the block pairs of the given contracted charge tuples;
+    returns (useful FLOPs, seconds)."""
+    import oracle as O
+    cfg = _POOL_CFG["cfg"]
+    sa, sb = _restrict(cfg, xs)
+    oA, oB = O.from_record(sa), O.from_record(sb)
+    t0 = time.perf_counter()
+    O.tensordot(oA, oB, cfg["axa"], cfg["axb"])
+    return O.useful_flops(oA, oB, cfg["axa"], cfg["axb"]), time.perf_counter() - t0
+
+
+class CpuPool:
+    """Worker processes on every host core (started with spawn), sharing the workload's
+    data with this process through shared memory."""
+
+    def __init__(self, cfg):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        self.ncores = host_cores()
+        self.shms = []
+        meta = {"axa": cfg["axa"], "axb": cfg["axb"]}
+        for k in ("A", "B"):
+            rec = cfg[k]
+            n = int(rec["data"].size)
+            shm = shared_memory.SharedMemory(create=True, size=max(8, 8 * n))
+            np.ndarray((n,), dtype=np.float64, buffer=shm.buf)[:] = rec["data"]
+            self.shms.append(shm)
+            meta[k] = {"shm": shm.name, "n": n, "rec": {kk: v for kk, v in rec.items() if kk != "data"}}
+        self.ex = cf.ProcessPoolExecutor(max_workers=self.ncores, mp_context=mp.get_context("spawn"),
+                                         initializer=_pool_init, initargs=(meta,))
+        self.warm = [self.ex.submit(_pool_ping, k) for k in range(self.ncores)]
+
+    def close(self):
+        self.ex.shutdown(wait=True, cancel_futures=True)
+        for shm in self.shms:
+            shm.close()
+            shm.unlink()
+
+
+def cpu_pool(cfg):
+    return CpuPool(cfg)
+
+
+def _charge_index(cfg):
+    """Contracted charge tuples x common to A and B, and the blocks of each."""
+    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
+    xa = [tuple(map(tuple, A["t"][b, list(axa)])) for b in range(A["t"].shape[0])]
+    xb = [tuple(map(tuple, B["t"][b, list(axb)])) for b in range(B["t"].shape[0])]
+    byxa, byxb = {}, {}
+    for b, x in enumerate(xa):
+        byxa.setdefault(x, []).append(b)
+    for b, x in enumerate(xb):
+        byxb.setdefault(x, []).append(b)
+    xs = sorted(set(byxa) & set(byxb))
+    return xs, byxa, byxb
+
+
+def _restrict(cfg, xs):
+    """Sub-records of A and B holding only the blocks of the contracted tuples xs."""
+    A, B = cfg["A"], cfg["B"]
+    if "_index" not in cfg:
+        cfg["_index"] = _charge_index(cfg)
+    _, byxa, byxb = cfg["_index"]
+    offa, offb = W.block_offsets(A["D"]), W.block_offsets(B["D"])
+    sza, szb = np.prod(A["D"], axis=1), np.prod(B["D"], axis=1)
+
+    def sub(rec, idx, off, sz):
+        idx = sorted(idx)
+        return {"mods": rec["mods"], "sig": rec["sig"], "n": rec["n"], "t": rec["t"][idx], "D": rec["D"][idx],
+                "data": np.concatenate([rec["data"][off[i]:off[i] + sz[i]] for i in idx]) if idx else np.zeros(0)}
+    return (sub(A, [b for x in xs for b in byxa[x]], offa, sza), sub(B, [b for x in xs for b in byxb[x]], offb, szb))
+
+
+def oracle_sample_parallel(pool, cfg, budget_s):
+    """The oracle on every host core: the contracted charge tuples of the workload (in
+    a random order, about budget_s seconds of work per core, at most all of them) shared
+    over the pool's workers in chunks; wall time of the whole batch."""
+    import concurrent.futures as cf
+    for f in pool.warm:
+        f.result()
+    xs, byxa, byxb = _charge_index(cfg)
+    order = np.random.default_rng(1).permutation(len(xs))
+    # calibrate: one chunk per worker, timed
+    chunk = 8
+    probe = [[xs[j] for j in order[k * chunk:(k + 1) * chunk]] for k in range(pool.ncores)]
+    t0 = time.perf_counter()
+    got = list(pool.ex.map(_pool_oracle, probe))
+    t_probe = time.perf_counter() - t0
+    rate = sum(f for f, _ in got) / max(t_probe, 1e-6)
+    # the timed batch: chunks until about budget_s of wall time at that rate
+    per_chunk = max(1.0, sum(f for f, _ in got) / len(got))
+    nchunks = int(min(len(xs) // chunk - pool.ncores, max(pool.ncores, budget_s * rate / per_chunk)))
+    start = pool.ncores * chunk
+    tasks = [[xs[j] for j in order[start + k * chunk:start + (k + 1) * chunk]] for k in range(max(nchunks, 0))]
+    tasks = [t for t in tasks if t]
+    t0 = time.perf_counter()
+    futs = [pool.ex.submit(_pool_oracle, t) for t in tasks]
+    res = [f.result() for f in cf.as_completed(futs)]
+    wall = time.perf_counter() - t0
+    flops = sum(f for f, _ in res)
+    ntx = sum(len(t) for t in tasks)
+    return {"value": flops / wall / 1e12, "unit": "TFLOP/s", "cores": pool.ncores, "kind": "oracle",
+            "seconds": wall,
+            "sample": f"oracle tensordot over {ntx} of {len(xs)} contracted charge tuples ({flops:.3e} useful "
+                      f"FLOPs) in chunks of {chunk} on {pool.ncores} worker processes (1 BLAS thread each)"}
+
+
+def cpu_workflow(cfg, budget_s, ncores):
+    """The paper's own workflow on the host cores (Sec. II.B: fuse the blocks into one
+    matrix per charge sector, multiply per sector, unfuse): NumPy permutes and copies
+    build A_q and B_q, torch multiplies them in FP64 on every core, and the products are
+    cut back into C's blocks. Sectors from the largest down, until about budget_s."""
+    import torch
+    A, B, axa, axb = cfg["A"], cfg["B"], list(cfg["axa"]), list(cfg["axb"])
+    freeA = [i for i in range(A["t"].shape[1]) if i not in axa]
+    freeB = [i for i in range(B["t"].shape[1]) if i not in axb]
+    mods = A["mods"]
+    offa, offb = W.block_offsets(A["D"]), W.block_offsets(B["D"])
+
+    def red(v):
+        return tuple(int(x) % m if m else int(x) for x, m in zip(v, mods))
+
+    # sectors: q = sum_k s_A[axa_k] x_k; rows I, columns J and contracted x per sector
+    secs = {}
+    for b in range(A["t"].shape[0]):
+        t = A["t"][b]
+        q = red(sum(int(A["sig"][a]) * t[a].astype(np.int64) for a in axa))
+        s_ = secs.setdefault(q, {"rows": {}, "cols": {}, "xs": {}, "a": [], "b": []})
+        I = tuple(map(tuple, t[freeA]))
+        x = tuple(map(tuple, t[axa]))
+        s_["rows"][I] = int(np.prod(A["D"][b][freeA])) if freeA else 1
+        s_["xs"][x] = int(np.prod(A["D"][b][axa]))
+        s_["a"].append(b)
+    for b in range(B["t"].shape[0]):
+        t = B["t"][b]
+        x = tuple(map(tuple, t[axb]))
+        q = red(sum(int(A["sig"][a]) * np.asarray(xk, dtype=np.int64) for a, xk in zip(axa, x)))
+        if q not in secs:
+            continue
+        s_ = secs[q]
+        J = tuple(map(tuple, t[freeB]))
+        s_["cols"][J] = int(np.prod(B["D"][b][freeB])) if freeB else 1
+        s_["b"].append(b)
+    order = sorted(secs, key=lambda q: -2.0 * sum(secs[q]["rows"].values()) * sum(secs[q]["cols"].values())
+                   * sum(secs[q]["xs"].values()))
+    prev = torch.get_num_threads()
+    torch.set_num_threads(ncores)
+    flops, t_move, t_mm, nsec = 0.0, 0.0, 0.0, 0
+    t_all = time.perf_counter()
+    for q in order:
+        if time.perf_counter() - t_all > budget_s:
+            break
+        s_ = secs[q]
+        ro, co, xo = {}, {}, {}
+        for d, src in ((ro, s_["rows"]), (co, s_["cols"]), (xo, s_["xs"])):
+            acc = 0
+            for k in sorted(src):
+                d[k] = acc
+                acc += src[k]
+        M, N, K = sum(s_["rows"].values()), sum(s_["cols"].values()), sum(s_["xs"].values())
+        t0 = time.perf_counter()
+        Aq = np.zeros((M, K))
+        for b in s_["a"]:
+            t = A["t"][b]
+            I, x = tuple(map(tuple, t[freeA])), tuple(map(tuple, t[axa]))
+            if x not in xo:
+                continue
+            blk = A["data"][offa[b]:offa[b] + int(np.prod(A["D"][b]))].reshape(A["D"][b])
+            m = blk.transpose(freeA + axa).reshape(s_["rows"][I], s_["xs"][x])
+            Aq[ro[I]:ro[I] + m.shape[0], xo[x]:xo[x] + m.shape[1]] = m
+        Bq = np.zeros((K, N))
+        for b in s_["b"]:
+            t = B["t"][b]
+            J, x = tuple(map(tuple, t[freeB])), tuple(map(tuple, t[axb]))
+            if x not in xo:
+                continue
+            blk = B["data"][offb[b]:offb[b] + int(np.prod(B["D"][b]))].reshape(B["D"][b])
+            m = blk.transpose(axb + freeB).reshape(s_["xs"][x], s_["cols"][J])
+            Bq[xo[x]:xo[x] + m.shape[0], co[J]:co[J] + m.shape[1]] = m
+        t1 = time.perf_counter()
+        Cq = torch.matmul(torch.from_numpy(Aq), torch.from_numpy(Bq)).numpy()
+        t2 = time.perf_counter()
+        out = {}
+        for I, r0 in ro.items():
+            for J, c0 in co.items():
+                out[(I, J)] = Cq[r0:r0 + s_["rows"][I], c0:c0 + s_["cols"][J]].copy()
+        t3 = time.perf_counter()
+        t_move += (t1 - t0) + (t3 - t2)
+        t_mm += t2 - t1
+        flops += 2.0 * M * N * K
+        nsec += 1
+    wall = time.perf_counter() - t_all
+    torch.set_num_threads(prev)
+    return {"value": flops / wall / 1e12, "unit": "TFLOP/s", "cores": ncores, "kind": "paper workflow on CPU",
+            "seconds": wall, "matmul_s": t_mm, "fuse_unfuse_s": t_move,
+            "matmul_tflops": flops / max(t_mm, 1e-9) / 1e12,
+            "sample": f"{nsec} of {len(secs)} charge sectors, largest first ({flops:.3e} useful FLOPs): NumPy "
+                      f"fuse into A_q, B_q, torch FP64 matmul on {ncores} threads, cut into C's blocks"}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -209,7 +445,7 @@ def run_reference(args):
     line = {
         "metric": METRIC, "value": tflops, "unit": "TFLOP/s", "impl": "reference", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD_DESC[args.workload]},
         "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -236,13 +472,262 @@ def max_over_ranks(value, device):
     return float(t.item())
 
 
-def weak_value(flops_per_rank, steps, world, seconds):
-    """Whole-job useful TFLOP/s: every rank contracts its own problem of the same
-    size, the slowest rank's time counts."""
-    return world * flops_per_rank * steps / seconds / 1e12
+def sum_over_ranks(value, device):
+    """The sum of a value over all ranks (bookkeeping of the sharded FLOPs)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def strong_value(total_flops, steps, seconds):
+    """Whole-job useful TFLOP/s of one contraction shared out over the ranks: its
+    whole useful FLOPs per step over the slowest rank's time."""
+    return total_flops * steps / seconds / 1e12
 
 
 # ------------------------------------------------------------------ our arm
+
+def measure_contraction(args, ytn, ctx, dev, cfg, world, rank, local, prec, steps, warmup, e2e_steps, fp64_steps,
+                        nfly=3):
+    """Time one contraction (this rank's part of it when world > 1) through the C ABI:
+    the headline precision on device-resident data (CUDA events on the launching stream,
+    clocks sampled meanwhile), the FP64 path beside it, and end to end with page-locked
+    host A, B and C. Returns the fields of the bench line."""
+    import torch
+    import torch.distributed as dist
+
+    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
+    shard = (rank, world) if world > 1 else None
+    t_plan = time.perf_counter()
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb, shard=shard)
+    t_plan = time.perf_counter() - t_plan
+    t_plan_cached = time.perf_counter()
+    plan2 = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb, shard=shard)
+    t_plan_cached = time.perf_counter() - t_plan_cached
+    assert plan2.handle == plan.handle
+    flops = plan.info["useful_flops"]              # this rank's part
+    total_flops = sum_over_ranks(flops, dev)       # the whole contraction
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        da = torch.from_numpy(A["data"]).to(dev)
+        db = torch.from_numpy(B["data"]).to(dev)
+        dc = torch.empty(max(plan.out["size"], 1), dtype=torch.float64, device=dev)
+        ws_bytes = max(ytn.ytn_workspace_size(plan, p, args.rtol) for p in (prec, ytn.YTN_FP64))
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream.synchronize()
+
+    def step(p):
+        return ytn.ytn_tensordot(plan, da, db, dc, prec=p, rtol=args.rtol, workspace=ws, stream=stream)
+
+    def measure(p, nsteps, nwarm, clocks=False):
+        res = None
+        for _ in range(nwarm):
+            res = step(p)
+        stream.synchronize()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        ytn.ytn_profile_enable(ctx, True)
+        ytn.ytn_profile_read(ctx)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
+        ev[0].record(stream)
+        for k in range(nsteps):
+            res = step(p)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        clk = sampler.stop() if sampler else None
+        prof = ytn.ytn_profile_read(ctx)
+        ytn.ytn_profile_enable(ctx, False)
+        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(nsteps)]
+        total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dev)
+        return {"total_ms": total_ms, "step_ms": step_ms, "prof": prof, "res": res, "clocks": clk,
+                "value": strong_value(total_flops, nsteps, total_ms * 1e-3)}
+
+    peaks, peak_src = load_peaks()
+
+    def roofline(p, m):
+        gemm_calls, gemm_ms = m["prof"].get("gemm", (0, 0.0))
+        kernel_ms = gemm_ms / max(1, gemm_calls)
+        if p == ytn.YTN_FP64:
+            kernel, kflops = "gemm_fp64_kernel", flops
+            peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+            note = (f"{peak_src} dense BF16 burst ({peaks['bf16_tflops']} TFLOP/s) x nominal FP64/BF16 ratio "
+                    f"{NOMINAL['fp64']}/{NOMINAL['bf16']}")
+        else:
+            s_ = m["res"]["slices"]
+            kernel, kflops = "gemm_split_kernel", flops * s_ * (s_ + 1) / 2
+            peak = peaks["bf16_tflops"]
+            note = (f"{peak_src} dense BF16 burst; achieved counts the BF16 slice-product FLOPs "
+                    f"(s(s+1)/2 = {s_ * (s_ + 1) // 2} per useful FLOP, s = {s_} slices)")
+        achieved = kflops / (kernel_ms * 1e-3) / 1e12 if kernel_ms > 0 else None
+        return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": read_traffic(kernel, args.workload),
+                "kernel_ms": kernel_ms,
+                "effective_fp64_tflops": flops / (kernel_ms * 1e-3) / 1e12 if kernel_ms else None,
+                "peak_source": note}
+
+    def phases(m):
+        return {k: {"calls": v[0], "ms_per_call": v[1] / max(1, v[0])} for k, v in m["prof"].items() if k != "dropped"}
+
+    # ---- headline precision: device-resident steps
+    head = measure(prec, steps, warmup, clocks=True)
+    ph = phases(head)
+    # the fused split path reads A's and B's blocks in its slicing kernel (the split
+    # phase): then only the scatter of C is a data mover of its own
+    moved_elems = plan.info["moved_elems"] if "gather_a" in ph else plan.info["out_size"]
+    moved_bytes = 16.0 * moved_elems
+    mover_ms = sum(ph[k]["ms_per_call"] for k in ("gather_a", "gather_b", "scatter") if k in ph)
+    out_head = dc.clone() if prec != ytn.YTN_FP64 else None
+    # the data-aware accuracy record of the last timed split call (the device's own
+    # estimate of its relative error, and the sectors it recomputed in FP64)
+    report = ytn.ytn_tensordot_report(plan, ws, stream) if prec != ytn.YTN_FP64 else None
+
+    # ---- the other precision, for the FP64 vs split comparison
+    other = None
+    if prec != ytn.YTN_FP64 and fp64_steps > 0:
+        m64 = measure(ytn.YTN_FP64, fp64_steps, 1)
+        diff = float(torch.linalg.vector_norm(out_head - dc) / torch.linalg.vector_norm(dc))
+        other = {"precision": "fp64", "value": m64["value"], "unit": "TFLOP/s", "steps": fp64_steps,
+                 "ms_per_step": m64["total_ms"] / fp64_steps, "roofline": roofline(ytn.YTN_FP64, m64),
+                 "split_speedup": head["value"] / m64["value"], "split_vs_fp64_rel_frobenius": diff}
+    del out_head
+
+    # ---- end to end through the C ABI with HOST buffers: A and B are read from page-locked
+    # host memory and C is written back to it, every step
+    ha = torch.from_numpy(A["data"]).pin_memory()
+    hb = torch.from_numpy(B["data"]).pin_memory()
+    hc = torch.empty(max(plan.out["size"], 1), dtype=torch.float64).pin_memory()
+    e2e = {}
+    if e2e_steps > 0:
+        def timed_e2e(body):
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(e2e_steps):
+                body()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return strong_value(total_flops, e2e_steps, max_over_ranks(e0.elapsed_time(e1), dev) * 1e-3)
+
+        def host_call():
+            ytn.ytn_tensordot(plan, ha, hb, hc, prec=prec, rtol=args.rtol, workspace=ws, stream=stream)
+
+        def staged_call():
+            with torch.cuda.stream(stream):
+                da.copy_(ha, non_blocking=True)
+                db.copy_(hb, non_blocking=True)
+                step(prec)
+                hc.copy_(dc, non_blocking=True)
+
+        host_call()
+        e2e["serial_value"] = timed_e2e(host_call)
+        e2e["staged_copies_value"] = timed_e2e(staged_call)
+        if nfly >= 3:
+            # two calls in flight on two streams (own workspace and host result buffer each),
+            # the data movers reading host memory; the GEMM leaves a few SMs free, so that one
+            # call's host-link data movers run beside the other call's GEMM
+            stream2 = torch.cuda.Stream(device=dev)
+            ws2 = torch.empty_like(ws)
+            hc2 = torch.empty_like(hc).pin_memory()
+            k_e2e = [0]
+
+            def pipelined_call():
+                k = k_e2e[0]
+                k_e2e[0] += 1
+                st, w, c = (stream, ws, hc) if k % 2 == 0 else (stream2, ws2, hc2)
+                ytn.ytn_tensordot(plan, ha, hb, c, prec=prec, rtol=args.rtol, workspace=w, stream=st)
+
+            reserve = 8
+            pipelined_call()
+            pipelined_call()
+            torch.cuda.synchronize(dev)
+            ytn.ytn_ctx_set_gemm_sms(ctx, torch.cuda.get_device_properties(dev).multi_processor_count - reserve)
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                pipelined_call()
+            torch.cuda.synchronize(dev)
+            e2e["direct_pipelined_value"] = strong_value(total_flops, e2e_steps,
+                                                         max_over_ranks(time.perf_counter() - t0, dev))
+            ytn.ytn_ctx_set_gemm_sms(ctx, 0)
+            del ws2, hc2
+        # nfly calls in flight, each staging its host operands through its own workspace
+        # with the copy engines (ytn_workspace_size_staged): one call's inputs travel in
+        # and another's result travels out while a third computes on every SM
+        sbytes = ytn.ytn_workspace_size_staged(plan, prec, args.rtol)
+        step(prec)
+        torch.cuda.synchronize(dev)
+        ref_c = dc.cpu()
+        del ws, da, db, dc
+        torch.cuda.empty_cache()
+        s_streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(nfly - 1)]
+        s_ws = [torch.empty(sbytes, dtype=torch.uint8, device=dev) for _ in range(nfly)]
+        s_hc = [hc] + [torch.empty_like(hc).pin_memory() for _ in range(nfly - 1)]
+        k_s = [0]
+
+        def staged_pipelined_call():
+            k = k_s[0] % nfly
+            k_s[0] += 1
+            ytn.ytn_tensordot(plan, ha, hb, s_hc[k], prec=prec, rtol=args.rtol, workspace=s_ws[k],
+                              stream=s_streams[k])
+
+        for _ in range(nfly):
+            staged_pipelined_call()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            staged_pipelined_call()
+        torch.cuda.synchronize(dev)
+        e2e_value = strong_value(total_flops, e2e_steps, max_over_ranks(time.perf_counter() - t0, dev))
+        staged_ok = bool(torch.equal(s_hc[(k_s[0] - 1) % nfly], ref_c))
+        hbm_reserved = nfly * sbytes
+        del s_ws
+        e2e = {"value": e2e_value, "unit": "TFLOP/s", "steps": e2e_steps,
+               "h2d_bytes_per_step": int(world * 8 * (A["data"].size + B["data"].size)),
+               "d2h_bytes_per_step": int(sum_over_ranks(8 * plan.out["size"], dev)),
+               "path": "ytn_tensordot on page-locked host A, B, C with a staging workspace "
+                       f"(ytn_workspace_size_staged): each call copies its inputs in and its result out with "
+                       f"the copy engines; {nfly} calls in flight on {nfly} streams",
+               "hbm_reserved_bytes": int(hbm_reserved),
+               "staged_result_equals_device_result": staged_ok, **e2e}
+    else:
+        del ws, da, db, dc
+    torch.cuda.empty_cache()
+
+    res = head["res"]
+    out = {
+        "value": head["value"], "ms_per_step": head["total_ms"] / steps, "total_flops": total_flops,
+        "plan": plan, "head": head, "phases": ph, "roofline": roofline(prec, head), "e2e": e2e,
+        "latency_ms": {"p50": float(np.percentile(head["step_ms"], 50)),
+                       "p99": float(np.percentile(head["step_ms"], 99))},
+        "data_movers": {"bytes_per_step": moved_bytes, "ms_per_step": mover_ms,
+                        "GB_per_s": moved_bytes / (mover_ms * 1e-3) / 1e9 if mover_ms else None,
+                        "peak_GB_per_s": peaks["hbm_gbs"]},
+        "host": {"plan_s": t_plan, "plan_cached_s": t_plan_cached},
+        "fp64": other,
+    }
+    if prec != ytn.YTN_FP64:
+        out["split"] = {"slices": res["slices"], "a_priori_err_est": res["err_est"],
+                        "err_est": report["err_est"], "split_err_est": report["split_err_est"],
+                        "max_sector_est": report["max_sector_est"], "fp64_fallback_sectors": report["nfallback"],
+                        "fp64_fallback_flops": report["fallback_flops"]}
+    return out
+
 
 def run_ours(args):
     import torch
@@ -257,250 +742,61 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     PREC = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}
     prec = PREC[args.precision]
+    extras = rank == 0 and world == 1 and not args.no_extras and args.workload == "cfg5"
 
     t_gen = time.perf_counter()
-    cfg = make_workload(args.workload, rank)
-    A, B, axa, axb = cfg["A"], cfg["B"], cfg["axa"], cfg["axb"]
+    cfg = make_workload(args.workload, 0)    # one problem, shared out over the ranks
+    A, B = cfg["A"], cfg["B"]
     t_gen = time.perf_counter() - t_gen
     ctx = ytn.ytn_ctx_create(local)
-    t_plan = time.perf_counter()
-    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
-    t_plan = time.perf_counter() - t_plan
-    t_plan_cached = time.perf_counter()
-    plan2 = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
-    t_plan_cached = time.perf_counter() - t_plan_cached
-    assert plan2.handle == plan.handle
-    flops = plan.info["useful_flops"]
-    stream = torch.cuda.Stream(device=dev)
-    with torch.cuda.stream(stream):
-        da = torch.from_numpy(A["data"]).to(dev)
-        db = torch.from_numpy(B["data"]).to(dev)
-        dc = torch.empty(plan.out["size"], dtype=torch.float64, device=dev)
-        ws_bytes = max(ytn.ytn_workspace_size(plan, p, args.rtol) for p in PREC.values())
-        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-    stream.synchronize()
-
-    def step(p):
-        return ytn.ytn_tensordot(plan, da, db, dc, prec=p, rtol=args.rtol, workspace=ws, stream=stream)
-
-    def measure(p, steps, warmup, clocks=False):
-        res = None
-        for _ in range(warmup):
-            res = step(p)
-        stream.synchronize()
-        sampler = ClockSampler(local) if clocks else None
-        if sampler:
-            sampler.start()
-            time.sleep(0.3)
-        ytn.ytn_profile_enable(ctx, True)
-        ytn.ytn_profile_read(ctx)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-        ev[0].record(stream)
-        for k in range(steps):
-            res = step(p)
-            ev[k + 1].record(stream)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
-        clk = sampler.stop() if sampler else None
-        prof = ytn.ytn_profile_read(ctx)
-        ytn.ytn_profile_enable(ctx, False)
-        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
-        total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dev)
-        return {"total_ms": total_ms, "step_ms": step_ms, "prof": prof, "res": res, "clocks": clk,
-                "value": weak_value(flops, steps, world, total_ms * 1e-3)}
-
-    peaks, peak_src = load_peaks()
-
-    def roofline(p, m):
-        gemm_calls, gemm_ms = m["prof"].get("gemm", (0, 0.0))
-        kernel_ms = gemm_ms / max(1, gemm_calls)
-        if p == ytn.YTN_FP64:
-            kernel, kflops = "gemm_fp64_kernel", flops
-            peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
-            note = (f"{peak_src} dense BF16 burst ({peaks['bf16_tflops']} TFLOP/s) x nominal FP64/BF16 ratio "
-                    f"{NOMINAL['fp64']}/{NOMINAL['bf16']}")
-        else:
-            s = m["res"]["slices"]
-            kernel, kflops = "gemm_split_kernel", flops * s * (s + 1) / 2
-            peak = peaks["bf16_tflops"]
-            note = (f"{peak_src} dense BF16 burst; achieved counts the BF16 slice-product FLOPs "
-                    f"(s(s+1)/2 = {s * (s + 1) // 2} per useful FLOP, s = {s} slices)")
-        achieved = kflops / (kernel_ms * 1e-3) / 1e12 if kernel_ms > 0 else None
-        return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": read_traffic(kernel, args.workload),
-                "kernel_ms": kernel_ms, "effective_fp64_tflops": flops / (kernel_ms * 1e-3) / 1e12 if kernel_ms else None,
-                "peak_source": note}
-
-    def phases(m):
-        return {k: {"calls": v[0], "ms_per_call": v[1] / max(1, v[0])} for k, v in m["prof"].items() if k != "dropped"}
-
-    # ---- headline precision: device-resident steps
-    head = measure(prec, args.steps, args.warmup, clocks=True)
-    value = head["value"]
-    ph = phases(head)
-    # the split GEMM writes device-resident C's blocks itself: then only A and B move
-    moved_elems = plan.info["moved_elems"] - (0 if "scatter" in ph else plan.info["out_size"])
-    moved_bytes = 16.0 * moved_elems
-    mover_ms = sum(ph[k]["ms_per_call"] for k in ("gather_a", "gather_b", "scatter") if k in ph)
-    out_head = dc.clone() if prec != ytn.YTN_FP64 else None
-
-    # ---- the other precision, for the FP64 vs split comparison
-    other = None
-    if prec != ytn.YTN_FP64 and args.fp64_steps > 0:
-        m64 = measure(ytn.YTN_FP64, args.fp64_steps, 1)
-        diff = float(torch.linalg.vector_norm(out_head - dc) / torch.linalg.vector_norm(dc))
-        other = {"precision": "fp64", "value": m64["value"], "unit": "TFLOP/s", "steps": args.fp64_steps,
-                 "ms_per_step": m64["total_ms"] / args.fp64_steps, "roofline": roofline(ytn.YTN_FP64, m64),
-                 "split_speedup": value / m64["value"], "split_vs_fp64_rel_frobenius": diff}
-        del out_head
-
-    # ---- end to end through the C ABI with HOST buffers: A and B are read from page-locked
-    # host memory and C is written back to it by the library's data movers, every step
-    ha = torch.from_numpy(A["data"]).pin_memory()
-    hb = torch.from_numpy(B["data"]).pin_memory()
-    hc = torch.empty(plan.out["size"], dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
-
-    def timed_e2e(body):
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e2e_steps):
-            body()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        return weak_value(flops, e2e_steps, world, max_over_ranks(e0.elapsed_time(e1), dev) * 1e-3)
-
-    def host_call():
-        ytn.ytn_tensordot(plan, ha, hb, hc, prec=prec, rtol=args.rtol, workspace=ws, stream=stream)
-
-    def staged_call():
-        with torch.cuda.stream(stream):
-            da.copy_(ha, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            step(prec)
-            hc.copy_(dc, non_blocking=True)
-
-    host_call()
-    e2e_serial = timed_e2e(host_call)
-    e2e_staged = timed_e2e(staged_call)
-    # two calls in flight on two streams (own workspace and host result buffer each):
-    # a step's result travels back over the link while the next step's inputs travel in
-    stream2 = torch.cuda.Stream(device=dev)
-    ws2 = torch.empty_like(ws)
-    hc2 = torch.empty_like(hc).pin_memory()
-    k_e2e = [0]
-
-    def pipelined_call():
-        k = k_e2e[0]
-        k_e2e[0] += 1
-        st, w, c = (stream, ws, hc) if k % 2 == 0 else (stream2, ws2, hc2)
-        ytn.ytn_tensordot(plan, ha, hb, c, prec=prec, rtol=args.rtol, workspace=w, stream=st)
-
-    # the GEMM leaves a few SMs free, so that one call's host-link data movers run
-    # beside the other call's GEMM
-    reserve = 8
-
-    def timed_pipelined():
-        ytn.ytn_ctx_set_gemm_sms(ctx, torch.cuda.get_device_properties(dev).multi_processor_count - reserve)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            pipelined_call()
-        torch.cuda.synchronize(dev)
-        elapsed = time.perf_counter() - t0
-        ytn.ytn_ctx_set_gemm_sms(ctx, 0)
-        return weak_value(flops, e2e_steps, world, max_over_ranks(elapsed, dev))
-
-    pipelined_call()
-    pipelined_call()
-    torch.cuda.synchronize(dev)
-    e2e_direct_pipelined = timed_pipelined()
-    del ws2
-
-    # three calls in flight, each staging its host operands through its own workspace
-    # with the copy engines (ytn_workspace_size_staged): one call's inputs travel in
-    # and another's result travels out while a third computes on every SM
-    nfly = 3
-    sbytes = ytn.ytn_workspace_size_staged(plan, prec, args.rtol)
-    step(prec)
-    torch.cuda.synchronize(dev)
-    ref_c = dc.cpu()
-    del ws
-    torch.cuda.empty_cache()
-    s_streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(nfly - 1)]
-    s_ws = [torch.empty(sbytes, dtype=torch.uint8, device=dev) for _ in range(nfly)]
-    s_hc = [hc] + [torch.empty_like(hc).pin_memory() for _ in range(nfly - 1)]
-    k_s = [0]
-
-    def staged_pipelined_call():
-        k = k_s[0] % nfly
-        k_s[0] += 1
-        ytn.ytn_tensordot(plan, ha, hb, s_hc[k], prec=prec, rtol=args.rtol, workspace=s_ws[k], stream=s_streams[k])
-
-    for _ in range(nfly):
-        staged_pipelined_call()
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        staged_pipelined_call()
-    torch.cuda.synchronize(dev)
-    e2e_value = weak_value(flops, e2e_steps, world, max_over_ranks(time.perf_counter() - t0, dev))
-    staged_ok = bool(torch.equal(s_hc[(k_s[0] - 1) % nfly], ref_c))
-    del s_ws
-
-    res = head["res"]
+    m = measure_contraction(args, ytn, ctx, dev, cfg, world, rank, local, prec, args.steps, args.warmup,
+                            max(1, min(args.steps, args.e2e_steps)), args.fp64_steps)
+    plan, ph = m["plan"], m["phases"]
     line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": m["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None,
         "dtype": "f64" if prec == ytn.YTN_FP64 else "bf16 slices, f32 accumulate, f64 recombine",
         "data": "synthetic", "precision": args.precision,
-        "config": {"workload": WORKLOAD_DESC[args.workload], "useful_flops_per_step": flops,
+        "config": {"workload": WORKLOAD_DESC[args.workload], "useful_flops_per_step": m["total_flops"],
+                   "parallelism": f"sector-sharded x{world}" if world > 1 else "one GPU",
                    "blocks": [int(A["t"].shape[0]), int(B["t"].shape[0]), int(plan.out["t"].shape[0])],
                    "sectors": plan.info["nsectors"],
                    "max_mnk": [plan.info["max_m"], plan.info["max_n"], plan.info["max_k"]],
                    "l2": "inputs larger than L2 (no flush)",
                    "rtol": args.rtol if prec != ytn.YTN_FP64 else None},
-        "latency_ms": {"p50": float(np.percentile(head["step_ms"], 50)),
-                       "p99": float(np.percentile(head["step_ms"], 99))},
-        "clocks": head["clocks"],
-        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "steps": e2e_steps,
-                "h2d_bytes_per_step": int(8 * (A["data"].size + B["data"].size)),
-                "d2h_bytes_per_step": int(8 * plan.out["size"]),
-                "path": "ytn_tensordot on page-locked host A, B, C with a staging workspace "
-                        "(ytn_workspace_size_staged): each call copies its inputs in and its result out with "
-                        "the copy engines; three calls in flight on three streams",
-                "staged_result_equals_device_result": staged_ok,
-                "direct_pipelined_value": e2e_direct_pipelined,
-                "serial_value": e2e_serial, "staged_copies_value": e2e_staged},
-        # kernels of the library per timed region (the split phase launches two)
-        "gpu_launches": int(sum(v["calls"] for v in ph.values()) + ph.get("split", {}).get("calls", 0)),
-        "roofline": roofline(prec, head),
+        "latency_ms": m["latency_ms"],
+        "clocks": m["head"]["clocks"],
+        "e2e": m["e2e"],
+        # kernels of the library per timed region (the split phase launches two, the
+        # accuracy check two)
+        "gpu_launches": int(sum(v["calls"] for v in ph.values()) + ph.get("split", {}).get("calls", 0)
+                            + ph.get("check", {}).get("calls", 0)),
+        "roofline": m["roofline"],
         "phases_ms": ph,
-        "data_movers": {"bytes_per_step": moved_bytes, "ms_per_step": mover_ms,
-                        "GB_per_s": moved_bytes / (mover_ms * 1e-3) / 1e9 if mover_ms else None,
-                        "peak_GB_per_s": peaks["hbm_gbs"]},
-        "host": {"generate_s": t_gen, "plan_s": t_plan, "plan_cached_s": t_plan_cached},
+        "data_movers": m["data_movers"],
+        "host": dict(m["host"], generate_s=t_gen),
     }
-    if prec != ytn.YTN_FP64:
-        line["split"] = {"slices": res["slices"], "err_est": res["err_est"]}
-    if other is not None:
-        line["fp64"] = other
+    if "split" in m:
+        line["split"] = m["split"]
+    if m["fp64"] is not None:
+        line["fp64"] = m["fp64"]
+    del m, plan
+    if extras:
+        line["cfg5b"] = extra_cfg5b(args, ytn, ctx, dev, prec)
+        line["serving"] = serving_summary(args, ytn, ctx, dev, prec, nruns=args.extra_serve_runs,
+                                          nrequests=args.extra_serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f, s, desc = oracle_sample(cfg, args.cpu_budget)
         line["cpu_baseline"] = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                                 "sample": desc}
+        if not args.no_extras:
+            pool = cpu_pool(cfg)
+            try:
+                line["cpu_baseline"]["all_cores"] = oracle_sample_parallel(pool, cfg, args.cpu_budget)
+            finally:
+                pool.close()
+            line["cpu_workflow"] = cpu_workflow(cfg, args.cpu_budget, host_cores())
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -509,22 +805,35 @@ def run_ours(args):
     return 0
 
 
+def extra_cfg5b(args, ytn, ctx, dev, prec):
+    """The 25-sector reading of the large workload (D = 20 over 9 charges, 81 sectors up
+    to 11388^3), a few steps: value, roofline and e2e on the same clock as the headline."""
+    cfg = make_workload("cfg5b", 0)
+    m = measure_contraction(args, ytn, ctx, dev, cfg, 1, 0, 0, prec, args.extra_steps, 3, args.extra_steps, 0,
+                            nfly=2)
+    out = {"workload": WORKLOAD_DESC["cfg5b"], "useful_flops_per_step": m["total_flops"], "value": m["value"],
+           "unit": "TFLOP/s", "steps": args.extra_steps, "warmup": 3, "ms_per_step": m["ms_per_step"],
+           "sectors": m["plan"].info["nsectors"],
+           "max_mnk": [m["plan"].info["max_m"], m["plan"].info["max_n"], m["plan"].info["max_k"]],
+           "clocks": m["head"]["clocks"], "roofline": m["roofline"], "e2e": m["e2e"], "phases_ms": m["phases"]}
+    if "split" in m:
+        out["split"] = m["split"]
+    return out
+
+
 # ------------------------------------------------------------------ serving (continuous batching)
 
-def run_serving(args):
+def serving_summary(args, ytn, ctx, dev, prec, nruns, nrequests, slots=None, budget_gb=None):
     """Poisson stream of tensordot requests from independent U(1) iPEPS runs (D uniform
     in {4,6,8,10,12}, chi in [4D, 8D], random sector splits per run), tensors resident on
     the device, admission by an HBM budget, served by the library's continuous-batching
     server. First the saturation rate is measured (all requests at once), then the
     requests arrive as a Poisson stream at 0.8x that rate; latency = completion time -
-    arrival time."""
+    arrival time. Returns the summary fields."""
     import torch
-
-    from paper_2405_12196_gb300 import ytn
-    dev = torch.device("cuda:0")
-    prec = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}[args.precision]
-    ctx = ytn.ytn_ctx_create(0)
-    runs = W.serving_runs(nruns=args.serve_runs)
+    slots = slots or args.serve_slots
+    budget_gb = budget_gb or args.serve_budget_gb
+    runs = W.serving_runs(nruns=nruns)
     res = []
     resident = 0
     for r in runs:
@@ -536,15 +845,15 @@ def run_serving(args):
         resident += 8 * (da.numel() + db.numel() + dc.numel())
         res.append({"plan": plan, "a": da, "b": db, "c": dc, "flops": plan.info["useful_flops"],
                     "D": r["D"], "chi": r["chi"]})
-    budget = int(args.serve_budget_gb * 1e9)
+    budget = int(budget_gb * 1e9)
     arena_bytes = (budget - resident) // 256 * 256
     arena = torch.empty(arena_bytes, dtype=torch.uint8, device=dev)
     rng = np.random.default_rng(4242)
-    pick = rng.integers(0, len(res), size=args.serve_requests)
+    pick = rng.integers(0, len(res), size=nrequests)
     total_flops = float(sum(res[i]["flops"] for i in pick))
 
     def serve(arrivals):
-        srv = ytn.Server(ctx, args.serve_slots, arena)
+        srv = ytn.Server(ctx, slots, arena)
         t0 = srv.now_ms()
         for k, i in enumerate(pick):
             ta = t0 + arrivals[k]
@@ -575,20 +884,38 @@ def run_serving(args):
     lam = 0.8 * rate
     arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(pick)))
     lat, span = serve(arrivals)
-    line = {
-        "metric": "serving: block-sparse tensordot requests, p50/p99 latency and useful TFLOP/s",
-        "value": total_flops / (span * 1e-3) / 1e12, "unit": "TFLOP/s", "impl": "ours", "n_gpus": 1,
-        "higher_is_better": True, "precision": args.precision, "data": "synthetic",
-        "config": {"workload": f"{len(pick)} requests from {len(res)} independent U(1) iPEPS runs, D in "
-                               f"{{4,6,8,10,12}}, chi in [4D,8D]; X2 . a over two legs",
-                   "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
-                   "resident_gb": resident / 1e9, "arena_gb": arena_bytes / 1e9,
-                   "requests_flops": total_flops},
+    out = {
+        "workload": f"{len(pick)} requests from {len(res)} independent U(1) iPEPS runs, D in {{4,6,8,10,12}}, "
+                    f"chi in [4D,8D]; X2 . a over two legs",
+        "precision": args.precision, "requests": len(pick), "slots": slots, "hbm_budget_gb": budget_gb,
+        "resident_gb": resident / 1e9, "arena_gb": arena_bytes / 1e9, "requests_flops": total_flops,
+        "value": total_flops / (span * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "saturation": {"requests_per_s": rate * 1e3, "tflops": total_flops / (span_sat * 1e-3) / 1e12,
                        "p50_ms": float(np.percentile(lat_sat, 50)), "p99_ms": float(np.percentile(lat_sat, 99))},
         "poisson": {"rate_per_s": lam * 1e3, "p50_ms": float(np.percentile(lat, 50)),
-                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                    "span_ms": span},
+                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "span_ms": span},
+    }
+    del res, arena
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(args):
+    import torch
+
+    from paper_2405_12196_gb300 import ytn
+    dev = torch.device("cuda:0")
+    prec = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}[args.precision]
+    ctx = ytn.ytn_ctx_create(0)
+    sm = serving_summary(args, ytn, ctx, dev, prec, args.serve_runs, args.serve_requests)
+    line = {
+        "metric": "serving: block-sparse tensordot requests, p50/p99 latency and useful TFLOP/s",
+        "value": sm["value"], "unit": "TFLOP/s", "impl": "ours", "n_gpus": 1,
+        "higher_is_better": True, "precision": args.precision, "data": "synthetic",
+        "config": {k: sm[k] for k in ("workload", "slots", "hbm_budget_gb", "resident_gb", "arena_gb",
+                                      "requests_flops")},
+        "saturation": sm["saturation"], "poisson": sm["poisson"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -868,6 +1195,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 25-sector workload and the serving stream of the default line")
+    ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of the 25-sector workload")
+    ap.add_argument("--extra-serve-runs", type=int, default=32)
+    ap.add_argument("--extra-serve-requests", type=int, default=600)
     ap.add_argument("--serving", action="store_true", help="run the continuous-batching serving benchmark")
     ap.add_argument("--chain", action="store_true", help="time the CTMRG-step chain eager and as one CUDA graph")
     ap.add_argument("--reduce", action="store_true", help="time the FP64 scalar product of two D=20 tensors")
