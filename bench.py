@@ -722,7 +722,11 @@ def measure_contraction(args, ytn, ctx, dev, cfg, world, rank, local, prec, step
         "fp64": other,
     }
     if prec != ytn.YTN_FP64:
-        out["split"] = {"slices": res["slices"], "a_priori_err_est": res["err_est"],
+        out["split"] = {"slices": res["slices"],
+                        "variant": {1: "fused: slices straight from the blocks",
+                                    0: "staged: FP64 sector matrices gathered first"}.get(res["split_variant"]),
+                        "narrow_sector_tails": bool(res.get("narrow_tiles", 0)),
+                        "a_priori_err_est": res["err_est"],
                         "err_est": report["err_est"], "split_err_est": report["split_err_est"],
                         "max_sector_est": report["max_sector_est"], "fp64_fallback_sectors": report["nfallback"],
                         "fp64_fallback_flops": report["fallback_flops"]}

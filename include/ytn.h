@@ -211,6 +211,12 @@ typedef struct {
   int64_t moved_elems;       /* elements read (= written) by the data movers    */
   int64_t out_size;          /* elements of the output data buffer              */
   int64_t njobs;             /* copy jobs of all data movers                    */
+  int32_t split_fused;       /* 1: the split path builds its BF16 slices straight
+                                from the blocks (at most three dims per side in
+                                every block once unit dims are dropped and
+                                contiguous ones merged); 0: it gathers FP64
+                                sector matrices first                          */
+  int32_t reserved;
 } ytn_plan_info;
 
 /* Per-call result of ytn_tensordot, filled when the call returns (before the
@@ -223,6 +229,13 @@ typedef struct {
                                 picks the slice count, which does not see the
                                 data; 0 for FP64. The data-aware estimate of the
                                 result is in ytn_tensordot_report            */
+  int32_t split_variant;     /* split path: 1 when the BF16 slices were built
+                                straight from the blocks (fused), 0 when FP64
+                                sector matrices were gathered first (staged);
+                                -1 for FP64                                    */
+  int32_t narrow_tiles;      /* split path: 1 when sectors whose N ends in the
+                                first half of a 128-wide tile had a 64-wide last
+                                column tile, else 0                            */
 } ytn_result;
 
 /* Accuracy record of a split-precision ytn_tensordot (no counterpart in the
@@ -354,6 +367,21 @@ ytn_status ytn_workspace_size_staged(const ytn_plan_t *plan, ytn_precision prec,
  * the cached choice. While the stream is being captured into a graph, a cost
  * model of the two kernels' tile-padded work decides instead. res->precision
  * reports the path that wrote c; the workspace is ytn_workspace_size(YTN_AUTO).
+ * The split path has two variants for plans whose blocks have at most three
+ * dims per side (ytn_plan_info.split_fused): slices built straight from the
+ * blocks (fused), or from FP64 sector matrices gathered first (staged). The
+ * first split-precision call on such a plan (explicit or through YTN_AUTO) times
+ * both on the caller's stream in the same way and caches the faster; under graph
+ * capture the fused one is taken when the blocks are large (an average of at
+ * least 1024 elements per block part). Operands read straight from page-locked
+ * host memory (no staging workspace) always take the staged variant, whose
+ * gathers read every block linearly over the host link. res->split_variant
+ * reports the variant used.
+ * Likewise the split GEMM's tile list: 128 x 128 tiles, or the same with a
+ * 128 x 64 last column tile for every sector whose N ends in the first half of a
+ * 128-wide tile (half of that tile's padded products saved); the first split call
+ * times both when the plan has such sectors (all 128 wide under graph capture);
+ * res->narrow_tiles reports the choice.
  * On the split path the call also checks its own accuracy on the device (see
  * ytn_error_report): sectors whose data-aware estimate exceeds rtol are
  * recomputed on the FP64 path before C is written, and when even that leaves

@@ -41,7 +41,7 @@ def _sources():
 
 def _compile(src, nvcc, verbose):
     obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-    deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".hpp")]
+    deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".hpp") or h.endswith(".cuh")]
     deps.append(os.path.join(INCLUDE, "ytn.h"))
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj, ""

@@ -6,6 +6,8 @@
 #include <chrono>
 #include <cmath>
 #include <algorithm>
+#include <array>
+#include <functional>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -66,12 +68,16 @@ static ytn_status upload(ytn_plan_t *p) {
   size_t o_vdp, o_vdc;
   put_table(buf, p->vd_pieces, o_vdp);
   put_table(buf, p->vd_chunks, o_vdc);
-  size_t o_spo, o_spe, o_sps, o_spsec, o_spt;
+  size_t o_spo, o_spe, o_sps, o_spsec, o_spt, o_spfi, o_spsg;
   put_table(buf, p->sp_ops, o_spo);
   put_table(buf, p->sp_exp_items, o_spe);
   put_table(buf, p->sp_slice_items, o_sps);
   put_table(buf, p->sp_sectors, o_spsec);
   put_table(buf, p->sp_tiles, o_spt);
+  size_t o_sptm;
+  put_table(buf, p->sp_tiles_mix, o_sptm);
+  put_table(buf, p->sp_fitems, o_spfi);
+  put_table(buf, p->sp_segs, o_spsg);
   p->dev_bytes = align256(buf.size()) + 256;
   cudaError_t e = cudaMalloc(&p->dev, p->dev_bytes);
   if (e != cudaSuccess) {
@@ -98,6 +104,9 @@ static ytn_status upload(ytn_plan_t *p) {
   p->d_sp_slice_items = reinterpret_cast<const SplitItem *>(d + o_sps);
   p->d_sp_sectors = reinterpret_cast<const SplitSector *>(d + o_spsec);
   p->d_sp_tiles = reinterpret_cast<const SplitTile *>(d + o_spt);
+  p->d_sp_tiles_mix = reinterpret_cast<const SplitTile *>(d + o_sptm);
+  p->d_sp_fitems = reinterpret_cast<const SliceItem *>(d + o_spfi);
+  p->d_sp_segs = reinterpret_cast<const SliceSeg *>(d + o_spsg);
   return YTN_OK;
 }
 
@@ -194,6 +203,7 @@ static void note_capture(ytn_plan_t *p, cudaStream_t st) {
 struct WsLayout {
   size_t wa = 0, wb = 0, wc = 0, sa = 0, sb = 0, ea = 0, eb = 0;
   size_t emax = 0, emax_end = 0, normsq = 0, rec = 0, rec_end = 0, secv = 0, flagged = 0, tile_end = 0;
+  size_t item_end_a = 0, item_end_b = 0;
 };
 
 static size_t workspace_layout(const ytn_plan_t *p, bool split, WsLayout &w) {
@@ -229,6 +239,10 @@ static size_t workspace_layout(const ytn_plan_t *p, bool split, WsLayout &w) {
   w.flagged = o;
   o += align256(nsec * 4);
   w.tile_end = o;
+  o += align256(nsec * 4);
+  w.item_end_a = o;
+  o += align256(nsec * 4);
+  w.item_end_b = o;
   o += align256(nsec * 4);
   return o;
 }
@@ -268,6 +282,26 @@ static ytn_status choose_slices(const ytn_plan_t *p, double rtol, int &s, double
   }
   est = split_error_estimate(kSlices, p->max_k);
   return fail(YTN_E_TOLERANCE, "rtol below what the split path can reach for this plan");
+}
+
+// Times contraction runs enqueued one after another on st (each a callable) and
+// returns their durations in ms; synchronises the stream.
+static ytn_status time_runs(cudaStream_t st, const std::vector<std::function<ytn_status()>> &runs,
+                            std::vector<float> &ms) {
+  std::vector<cudaEvent_t> ev(runs.size() + 1);
+  for (auto &x : ev) cudaEventCreate(&x);
+  cudaEventRecord(ev[0], st);
+  ytn_status r = YTN_OK;
+  for (size_t i = 0; i < runs.size(); i++) {
+    if (r == YTN_OK) r = runs[i]();
+    cudaEventRecord(ev[i + 1], st);
+  }
+  cudaError_t e = cudaEventSynchronize(ev.back());
+  ms.assign(runs.size(), 0.f);
+  for (size_t i = 0; i < runs.size() && e == cudaSuccess; i++) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (auto &x : ev) cudaEventDestroy(x);
+  if (r != YTN_OK) return r;
+  return e == cudaSuccess ? YTN_OK : cuda_fail(e, "timing the contraction paths");
 }
 
 }  // namespace ytn
@@ -554,6 +588,7 @@ ytn_status ytn_plan_get_info(const ytn_plan_t *p, ytn_plan_info *info) {
   info->moved_elems = p->moved;
   info->out_size = p->out.size;
   info->njobs = (int64_t)p->jobs.size();
+  info->split_fused = p->sp_fused ? 1 : 0;
   return YTN_OK;
 }
 
@@ -617,27 +652,33 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
 
 // One contraction on the chosen path; arguments already checked and mapped.
 static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, bool split, int slices,
-                                 double rtol, void *workspace, cudaStream_t st) {
+                                 double rtol, void *workspace, cudaStream_t st, bool fused_variant = false,
+                                 bool narrow_tails = false) {
   WsLayout w;
   workspace_layout(p, split, w);
   char *ws = static_cast<char *>(workspace);
   double *wa = reinterpret_cast<double *>(ws + w.wa), *wb = reinterpret_cast<double *>(ws + w.wb),
          *wc = reinterpret_cast<double *>(ws + w.wc);
   cudaError_t e;
-  if (p->zero_a && (e = cudaMemsetAsync(wa, 0, (size_t)p->a_elems * 8, st)) != cudaSuccess)
-    return cuda_fail(e, "memset A workspace");
-  if (p->zero_b && (e = cudaMemsetAsync(wb, 0, (size_t)p->b_elems * 8, st)) != cudaSuccess)
-    return cuda_fail(e, "memset B workspace");
-  {
-    PhaseTimer t(p->ctx, YTN_PHASE_GATHER_A, st);
-    e = launch_copy(p->d_jobs, p->d_items + p->items_a_begin, p->items_a_end - p->items_a_begin, a, wa, st);
+  // the fused split builds its slices straight from the blocks and gathers FP64
+  // sector matrices only for the sectors its accuracy check recomputes
+  const bool fused = split && p->sp_fused && fused_variant;
+  if (!fused) {
+    if (p->zero_a && (e = cudaMemsetAsync(wa, 0, (size_t)p->a_elems * 8, st)) != cudaSuccess)
+      return cuda_fail(e, "memset A workspace");
+    if (p->zero_b && (e = cudaMemsetAsync(wb, 0, (size_t)p->b_elems * 8, st)) != cudaSuccess)
+      return cuda_fail(e, "memset B workspace");
+    {
+      PhaseTimer t(p->ctx, YTN_PHASE_GATHER_A, st);
+      e = launch_copy(p->d_jobs, p->d_items + p->items_a_begin, p->items_a_end - p->items_a_begin, a, wa, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gather A");
+    {
+      PhaseTimer t(p->ctx, YTN_PHASE_GATHER_B, st);
+      e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, b, wb, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gather B");
   }
-  if (e != cudaSuccess) return cuda_fail(e, "gather A");
-  {
-    PhaseTimer t(p->ctx, YTN_PHASE_GATHER_B, st);
-    e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, b, wb, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "gather B");
   if (!split) {
     PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
     e = launch_gemm_fp64(p->d_sectors, p->d_tiles, (int64_t)p->tiles.size(), wa, wb, wc, st);
@@ -650,22 +691,29 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
     uint8_t *sa = reinterpret_cast<uint8_t *>(ws + w.sa), *sb = reinterpret_cast<uint8_t *>(ws + w.sb);
     {
       PhaseTimer t(p->ctx, YTN_PHASE_SPLIT, st);
-      // the exponent kernel max-combines into EA, EB and EMAX: start from a value
+      // the exponent kernels max-combine into EA, EB and EMAX: start from a value
       // below every exponent (bytes 0x80: 0x80808080 as int32); the epilogue sums
       // into NORMSQ and the check counts in the record: start from zero
       e = cudaMemsetAsync(ea, 0x80, w.emax_end - w.ea, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(normsq, 0, w.rec_end - w.normsq, st);
-      if (e == cudaSuccess)
-        e = launch_split_prep(p->d_sp_ops, p->d_sp_exp_items, (int64_t)p->sp_exp_items.size(),
-                              p->d_sp_slice_items, (int64_t)p->sp_slice_items.size(), wa, wb, ea, eb, emax, sa, sb,
-                              slices, st);
+      if (e == cudaSuccess) {
+        if (fused)
+          e = launch_split_blocks(p->d_sp_ops, p->d_sp_fitems, (int64_t)p->sp_fitems.size(), p->d_sp_segs, a, b,
+                                  ea, eb, emax, sa, sb, slices, st);
+        else
+          e = launch_split_prep(p->d_sp_ops, p->d_sp_exp_items, (int64_t)p->sp_exp_items.size(),
+                                p->d_sp_slice_items, (int64_t)p->sp_slice_items.size(), wa, wb, ea, eb, emax, sa,
+                                sb, slices, st);
+      }
     }
     if (e != cudaSuccess) return cuda_fail(e, "split into slices");
     const int sms = p->ctx->gemm_sms.load() > 0 ? p->ctx->gemm_sms.load() : p->ctx->num_sms;
     {
       PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
-      e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles, (int64_t)p->sp_tiles.size(), sa, sb, ea, eb, emax,
-                            normsq, wc, slices, p->ctx->status_dev, sms, st);
+      const bool mix = narrow_tails && !p->sp_tiles_mix.empty();
+      e = launch_gemm_split(p->d_sp_sectors, mix ? p->d_sp_tiles_mix : p->d_sp_tiles,
+                            (int64_t)(mix ? p->sp_tiles_mix.size() : p->sp_tiles.size()), sa, sb, ea, eb, emax,
+                            normsq, wc, slices, p->ctx->status_dev, sms, mix, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grouped split-precision GEMM");
     {
@@ -673,9 +721,15 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
       PhaseTimer t(p->ctx, YTN_PHASE_CHECK, st);
       int32_t *flagged = reinterpret_cast<int32_t *>(ws + w.flagged);
       int32_t *tile_end = reinterpret_cast<int32_t *>(ws + w.tile_end);
+      int32_t *item_end_a = reinterpret_cast<int32_t *>(ws + w.item_end_a);
+      int32_t *item_end_b = reinterpret_cast<int32_t *>(ws + w.item_end_b);
       e = launch_split_check(p->d_sp_sectors, (int64_t)p->sp_sectors.size(), ea, eb, emax, normsq,
-                             reinterpret_cast<double *>(ws + w.secv), flagged, tile_end, rec, split_eta(slices),
-                             kEtaFp64, rtol, slices, p->ctx->status_dev, st);
+                             reinterpret_cast<double *>(ws + w.secv), flagged, tile_end, item_end_a, item_end_b, rec,
+                             split_eta(slices), kEtaFp64, rtol, slices, p->ctx->status_dev, st);
+      if (e == cudaSuccess && fused && !p->sp_sectors.empty())
+        e = launch_gather_flagged(p->d_jobs, p->d_items + p->items_a_begin, p->d_items + p->items_b_begin,
+                                  p->d_sp_sectors, p->d_sectors, flagged, item_end_a, item_end_b, rec, a, b, wa, wb,
+                                  p->zero_a, p->zero_b, p->ctx->num_sms, st);
       if (e == cudaSuccess && !p->sp_sectors.empty())
         e = launch_gemm_fp64_redo(p->d_sectors, flagged, tile_end, rec, wa, wb, wc, p->ctx->num_sms, st);
     }
@@ -707,6 +761,18 @@ static bool model_prefers_split(const ytn_plan_t *p, int s) {
   const double t64 = f64 / 1.0e12;
   const double t16 = f16 / 1.3e15 + (double)(p->a_elems + p->b_elems) * (16.0 + 2.0 * s) / 6.0e12 + 5e-6;
   return t16 < t64;
+}
+
+// Split-path variant when it cannot be timed (graph capture): the fused one for
+// large blocks. The fused kernels read each block in runs along its contiguous
+// direction, which pays off once blocks are large; the staged gathers read every
+// block linearly, which wins for many small blocks (measured: 3.2e3 elements per
+// block, fused 5.10 ms vs staged 5.24 ms per D = 20 step; 183 elements per block,
+// fused 0.60 ms vs staged about 0.40 ms at D = 14).
+static bool model_prefers_fused(const ytn_plan_t *p) {
+  if (!p->sp_fused || p->sp_segs.empty()) return false;
+  const double per_seg = (double)(p->a_elems + p->b_elems) / (double)p->sp_segs.size();
+  return per_seg >= 1024.0;
 }
 
 ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, ytn_precision prec,
@@ -774,61 +840,107 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     return e == cudaSuccess ? YTN_OK : cuda_fail(e, "staging copy to the host");
   };
   bool split = prec == YTN_SPLIT_BF16;
-  if (prec == YTN_AUTO && split_ok) {
-    // the choice is made once per plan and slice count and cached on the plan
-    int choice;
-    {
+  auto fill_res = [&](bool sp, int variant) {
+    if (!res) return;
+    res->useful_flops = p->flops;
+    res->precision = sp ? YTN_SPLIT_BF16 : YTN_FP64;
+    res->slices = sp ? slices : 0;
+    res->err_est = sp ? est : 0.0;
+    res->split_variant = sp ? variant : -1;
+    res->narrow_tiles = 0;
+  };
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+  // Choices cached per plan and slice count: YTN_AUTO's FP64 or split, the split
+  // path's variant (staged, or fused when the plan has fused tables) and its tile
+  // list (all 128 wide, or with 64-wide sector tails when the plan has any). The
+  // first call that needs a choice times the candidates on the caller's stream
+  // (this call synchronises it; C holds the last candidate's result, a split
+  // result); under graph capture cost models decide.
+  int choice = 1, variant = 0, tiles = 0;
+  if (prec == YTN_AUTO) {
+    if (!split_ok) {
+      choice = 0;
+    } else {
       std::lock_guard<std::mutex> lk(p->auto_mu);
       choice = p->auto_choice[slices];
     }
-    if (choice < 0) {
-      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-      if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
-        choice = model_prefers_split(p, slices) ? 1 : 0;
-      } else {
-        // time both paths once on the caller's stream (this call synchronises it)
-        cudaEvent_t ev[3];
-        for (auto &x : ev) cudaEventCreate(&x);
-        cudaEventRecord(ev[0], st);
-        ytn_status r = exec_tensordot(p, a, b, c, false, 0, rtol, workspace, st);
-        cudaEventRecord(ev[1], st);
-        if (r == YTN_OK) r = exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st);
-        cudaEventRecord(ev[2], st);
-        cudaError_t e = cudaEventSynchronize(ev[2]);
-        float t64 = 0.f, t16 = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t64, ev[0], ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t16, ev[1], ev[2]);
-        for (auto &x : ev) cudaEventDestroy(x);
-        if (r != YTN_OK) return r;
-        if (e != cudaSuccess) return cuda_fail(e, "timing the two paths");
-        {
-          std::lock_guard<std::mutex> lk(p->auto_mu);
-          p->auto_choice[slices] = t16 < t64 ? 1 : 0;
-          p->auto_ms[slices][0] = t64;
-          p->auto_ms[slices][1] = t16;
-        }
-        if (res) {   // C holds the split result (the last run)
-          res->useful_flops = p->flops;
-          res->precision = YTN_SPLIT_BF16;
-          res->slices = slices;
-          res->err_est = est;
-        }
-        return unstage();
-      }
-      std::lock_guard<std::mutex> lk(p->auto_mu);
-      if (p->auto_choice[slices] < 0) p->auto_choice[slices] = choice;
-    }
-    split = choice == 1;
   }
-  ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, rtol, workspace, st);
+  const bool has_mix = !p->sp_tiles_mix.empty();
+  if (split_ok || split) {
+    std::lock_guard<std::mutex> lk(p->auto_mu);
+    variant = p->sp_fused ? p->split_variant[slices] : 0;
+    tiles = has_mix ? p->tile_policy[slices] : 0;
+  }
+  const bool may_split = split || (prec == YTN_AUTO && split_ok && choice != 0);
+  const bool need_choice = prec == YTN_AUTO && split_ok && choice < 0;
+  const bool need_variant = may_split && p->sp_fused && variant < 0;
+  const bool need_tiles = may_split && has_mix && tiles < 0;
+  if ((need_choice || need_variant || need_tiles) && capturing) {
+    std::lock_guard<std::mutex> lk(p->auto_mu);
+    if (need_choice && p->auto_choice[slices] < 0) p->auto_choice[slices] = model_prefers_split(p, slices) ? 1 : 0;
+    if (p->sp_fused && p->split_variant[slices] < 0) p->split_variant[slices] = model_prefers_fused(p) ? 1 : 0;
+    if (has_mix && p->tile_policy[slices] < 0) p->tile_policy[slices] = 0;
+    choice = prec == YTN_AUTO ? p->auto_choice[slices] : 1;
+    variant = p->sp_fused ? p->split_variant[slices] : 0;
+    tiles = has_mix ? p->tile_policy[slices] : 0;
+  } else if (need_choice || need_variant || need_tiles) {
+    // candidates in a fixed order: FP64 (YTN_AUTO), staged split, fused split (128
+    // wide tiles), then the variant of the previous run with 64-wide tails
+    const bool with64 = need_choice, withfused = p->sp_fused && !((ha || hb) && !staged), withmix = has_mix;
+    std::vector<std::function<ytn_status()>> runs;
+    if (with64) runs.push_back([&]() { return exec_tensordot(p, a, b, c, false, 0, rtol, workspace, st); });
+    runs.push_back([&]() { return exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st, false, false); });
+    if (withfused)
+      runs.push_back([&]() { return exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st, true, false); });
+    if (withmix)
+      runs.push_back(
+          [&]() { return exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st, withfused, true); });
+    std::vector<float> ms;
+    ytn_status r = time_runs(st, runs, ms);
+    if (r != YTN_OK) return r;
+    size_t k = 0;
+    const float t64 = with64 ? ms[k++] : 0.f;
+    const float tst = ms[k++];
+    const float tfu = withfused ? ms[k++] : tst;
+    const float tmx = withmix ? ms[k++] : 0.f;
+    const float t128 = withfused ? tfu : tst;   // the 128-wide run of the variant tried with tails
+    {
+      std::lock_guard<std::mutex> lk(p->auto_mu);
+      if (withfused && p->split_variant[slices] < 0) {
+        p->split_variant[slices] = tfu < tst ? 1 : 0;
+        p->variant_ms[slices][0] = tst;
+        p->variant_ms[slices][1] = tfu;
+      }
+      if (withmix) {
+        p->tile_policy[slices] = tmx < t128 ? 1 : 0;
+        p->tile_ms[slices][0] = t128;
+        p->tile_ms[slices][1] = tmx;
+      }
+      if (with64) {
+        float best = std::min(tst, tfu);
+        if (withmix) best = std::min(best, tmx);
+        p->auto_choice[slices] = best < t64 ? 1 : 0;
+        p->auto_ms[slices][0] = t64;
+        p->auto_ms[slices][1] = best;
+      }
+    }
+    fill_res(true, withfused ? 1 : 0);
+    if (res) res->narrow_tiles = withmix ? 1 : 0;
+    return unstage();
+  }
+  if (prec == YTN_AUTO) split = choice == 1;
+  // operands read straight from host memory go through the staged gathers, which
+  // read every block linearly over the host link (the fused kernels read blocks in
+  // runs, twice)
+  const bool host_direct = (ha || hb) && !staged;
+  const bool use_fused = split && p->sp_fused && variant == 1 && !host_direct;
+  const bool use_mix = split && has_mix && tiles == 1;
+  ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, rtol, workspace, st, use_fused, use_mix);
   if (r != YTN_OK) return r;
   if ((r = unstage()) != YTN_OK) return r;
-  if (res) {
-    res->useful_flops = p->flops;
-    res->precision = split ? YTN_SPLIT_BF16 : YTN_FP64;
-    res->slices = split ? slices : 0;
-    res->err_est = split ? est : 0.0;
-  }
+  fill_res(split, use_fused ? 1 : 0);
+  if (res) res->narrow_tiles = use_mix ? 1 : 0;
   return YTN_OK;
 }
 

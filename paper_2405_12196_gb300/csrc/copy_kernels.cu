@@ -11,6 +11,8 @@
 // HBM-bound: every element is read once and written once.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kernels.hpp"
 
 namespace ytn {
@@ -151,13 +153,10 @@ __device__ __forceinline__ void stage_dispatch(bool dense_src, const CopyJob *Js
   else stage_item<ND, false>(Js, nj, total, src, dst, stage);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) copy_kernel(const CopyJob *__restrict__ jobs,
-                                                           const CopyItem *__restrict__ items,
-                                                           const double *__restrict__ src,
-                                                           double *__restrict__ dst) {
-  __shared__ CopyJob Js[kStageJobs];
-  __shared__ double stage[kStageElems];
-  const CopyItem it = items[blockIdx.x];
+// One work item: its pieces' parameters into shared memory, then the staged move.
+__device__ __forceinline__ void run_item(const CopyJob *__restrict__ jobs, const CopyItem &it,
+                                         const double *__restrict__ src, double *__restrict__ dst, CopyJob *Js,
+                                         double *stage) {
   const int nj = it.njobs, total = it.total, nd = it.kind & 255, mode = it.kind >> 8;
   // the planner never makes other items
   if (nj < 1 || nj > kStageJobs || total < 1 || total > kStageElems || nd < 1 || nd > kMaxCopyDims) return;
@@ -177,6 +176,62 @@ __global__ void __launch_bounds__(kThreads, 4) copy_kernel(const CopyJob *__rest
     case 6: stage_dispatch<6>(dense_src, Js, nj, total, src, dst, stage); break;
     case 7: stage_dispatch<7>(dense_src, Js, nj, total, src, dst, stage); break;
     default: stage_dispatch<8>(dense_src, Js, nj, total, src, dst, stage); break;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) copy_kernel(const CopyJob *__restrict__ jobs,
+                                                           const CopyItem *__restrict__ items,
+                                                           const double *__restrict__ src,
+                                                           double *__restrict__ dst) {
+  __shared__ CopyJob Js[kStageJobs];
+  __shared__ double stage[kStageElems];
+  run_item(jobs, items[blockIdx.x], src, dst, Js, stage);
+}
+
+// Gathers of the sectors that the split path's accuracy check flagged (FP64
+// fallback): a persistent grid walks the flagged sectors' work items (each
+// sector's items are [first[q], first[q] + count), the running counts over the
+// flagged sectors in item_end). With no flagged sector every CTA returns at once.
+__global__ void __launch_bounds__(kThreads, 4) copy_flagged_kernel(const CopyJob *__restrict__ jobs,
+                                                                   const CopyItem *__restrict__ items,
+                                                                   const SplitSector *__restrict__ sectors, int which,
+                                                                   const int32_t *__restrict__ flagged,
+                                                                   const int32_t *__restrict__ item_end,
+                                                                   const SplitRecord *__restrict__ rec,
+                                                                   const double *__restrict__ src,
+                                                                   double *__restrict__ dst) {
+  __shared__ CopyJob Js[kStageJobs];
+  __shared__ double stage[kStageElems];
+  const int nflag = rec->nfallback;
+  if (nflag <= 0) return;
+  const int total = item_end[nflag - 1];
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = nflag - 1;   // first flagged sector whose items end after t
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (item_end[mid] > t) hi = mid;
+      else lo = mid + 1;
+    }
+    const SplitSector &sc = sectors[flagged[lo]];
+    const int first = which == 0 ? sc.ga0 : sc.gb0;
+    const int local = t - (lo > 0 ? item_end[lo - 1] : 0);
+    __syncthreads();   // the previous item's shared memory is no longer read
+    run_item(jobs, items[first + local], src, dst, Js, stage);
+  }
+}
+
+// Zero fill of the flagged sectors' FP64 sector matrices (partially populated
+// operands) before their gathers.
+__global__ void __launch_bounds__(kThreads) zero_flagged_kernel(const SectorDev *__restrict__ sectors,
+                                                                const int32_t *__restrict__ flagged,
+                                                                const SplitRecord *__restrict__ rec, double *wa,
+                                                                double *wb, int zero_a, int zero_b) {
+  const int nflag = rec->nfallback;
+  for (int k = blockIdx.x; k < nflag; k += gridDim.x) {
+    const SectorDev s = sectors[flagged[k]];
+    const int64_t na = zero_a ? (int64_t)s.M * s.K : 0, nb = zero_b ? (int64_t)s.K * s.N : 0;
+    for (int64_t e = threadIdx.x; e < na; e += kThreads) wa[s.a_off + e] = 0.0;
+    for (int64_t e = threadIdx.x; e < nb; e += kThreads) wb[s.b_off + e] = 0.0;
   }
 }
 
@@ -264,6 +319,18 @@ cudaError_t launch_trace(const TraceOut *outs, int64_t nout, const TraceContrib 
   if (nout <= 0) return cudaSuccess;
   if (nout > INT32_MAX) return cudaErrorInvalidValue;
   trace_kernel<<<(unsigned)nout, 128, 0, stream>>>(outs, contribs, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_flagged(const CopyJob *jobs, const CopyItem *items_a, const CopyItem *items_b,
+                                  const SplitSector *sp_sectors, const SectorDev *sectors, const int32_t *flagged,
+                                  const int32_t *item_end_a, const int32_t *item_end_b, const SplitRecord *rec,
+                                  const double *a, const double *b, double *wa, double *wb, bool zero_a, bool zero_b,
+                                  int num_sms, cudaStream_t stream) {
+  const unsigned grid = (unsigned)std::max(1, num_sms) * 4;
+  if (zero_a || zero_b) zero_flagged_kernel<<<grid, kThreads, 0, stream>>>(sectors, flagged, rec, wa, wb, zero_a, zero_b);
+  copy_flagged_kernel<<<grid, kThreads, 0, stream>>>(jobs, items_a, sp_sectors, 0, flagged, item_end_a, rec, a, wa);
+  copy_flagged_kernel<<<grid, kThreads, 0, stream>>>(jobs, items_b, sp_sectors, 1, flagged, item_end_b, rec, b, wb);
   return cudaGetLastError();
 }
 

@@ -57,8 +57,10 @@ constexpr uint32_t kColE2 = 0, kColE3 = 128, kColE4 = 256, kColR = 384;
 constexpr uint32_t kMaxPolls = 1u << 26;
 constexpr int kSmemBytes = kStagesRing * kSlotBytes + 1024 + 256;
 
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = 128, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128; the
+// N field (bits 17..22, N / 8) is set per tile: 128, or 64 for the narrow tiles
+constexpr uint32_t kIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 4) << 24);
+__device__ __forceinline__ uint32_t idesc_for(int bn) { return kIdescBase | ((uint32_t)(bn >> 3) << 17); }
 
 enum Bar { kFull0 = 0, kEmpty0 = 2, kEFull = 4, kEEmpty = 5, kRFull = 6, kREmpty = 7, kDone = 8, kNumBars = 9 };
 
@@ -110,11 +112,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
          ((uint64_t)4 << 61);
 }
 
-__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate));
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -165,29 +167,32 @@ __device__ __forceinline__ double scaled_double(long long acc, int e) {
 }
 
 // Descriptor offsets in the 16-byte units of the start-address field: one slice
-// (8 KB) and one K step of 16 (32 bytes). The shared-memory footprint stays below
-// 256 KB, so additions never carry out of the 14-bit field.
+// of A (8 KB) and one K step of 16 (32 bytes); B's slices lie 8 KB apart in a
+// 128-wide tile and 4 KB apart in a 64-wide one (bsu). The shared-memory footprint
+// stays below 256 KB, so additions never carry out of the 14-bit field.
 constexpr uint64_t kSliceU = kSliceBytes >> 4, kStepU = 2;
 
 // Orders 0, 1, 2 of one 32-wide K stage into the exact accumulators; `fresh`
 // starts a new chunk. a0 / b0: descriptors of slice 0 of the stage.
-__device__ __forceinline__ void issue_exact(uint32_t tmem, uint64_t a0, uint64_t b0, bool fresh) {
+__device__ __forceinline__ void issue_exact(uint32_t tmem, uint64_t a0, uint64_t b0, bool fresh, uint32_t idesc,
+                                            uint64_t bsu) {
 #pragma unroll
   for (int ks = 0; ks < 2; ks++) {
     const uint64_t a = a0 + ks * kStepU, b = b0 + ks * kStepU;
     const uint32_t acc = (fresh && ks == 0) ? 0u : 1u;
-    umma(tmem + kColE2, a, b, acc);
-    umma(tmem + kColE3, a, b + kSliceU, acc);
-    umma(tmem + kColE3, a + kSliceU, b, 1u);
-    umma(tmem + kColE4, a, b + 2 * kSliceU, acc);
-    umma(tmem + kColE4, a + kSliceU, b + kSliceU, 1u);
-    umma(tmem + kColE4, a + 2 * kSliceU, b, 1u);
+    umma(tmem + kColE2, a, b, idesc, acc);
+    umma(tmem + kColE3, a, b + bsu, idesc, acc);
+    umma(tmem + kColE3, a + kSliceU, b, idesc, 1u);
+    umma(tmem + kColE4, a, b + 2 * bsu, idesc, acc);
+    umma(tmem + kColE4, a + kSliceU, b + bsu, idesc, 1u);
+    umma(tmem + kColE4, a + 2 * kSliceU, b, idesc, 1u);
   }
 }
 
 // Orders 3 .. S-1 of one stage into R; `fresh` starts a new chunk.
 template <int S>
-__device__ __forceinline__ void issue_rest(uint32_t tmem, uint64_t a0, uint64_t b0, bool fresh) {
+__device__ __forceinline__ void issue_rest(uint32_t tmem, uint64_t a0, uint64_t b0, bool fresh, uint32_t idesc,
+                                           uint64_t bsu) {
 #pragma unroll
   for (int ks = 0; ks < 2; ks++) {
     const uint64_t a = a0 + ks * kStepU, b = b0 + ks * kStepU;
@@ -197,7 +202,7 @@ __device__ __forceinline__ void issue_rest(uint32_t tmem, uint64_t a0, uint64_t 
       for (int p = 0; p <= L; p++) {
         if (p > S - 1 || L - p > S - 1) continue;
         const uint32_t acc = (fresh && ks == 0 && L == 3 && p == 0) ? 0u : 1u;
-        umma(tmem + kColR, a + p * kSliceU, b + (L - p) * kSliceU, acc);
+        umma(tmem + kColR, a + p * kSliceU, b + (L - p) * bsu, idesc, acc);
       }
     }
   }
@@ -206,7 +211,9 @@ __device__ __forceinline__ void issue_rest(uint32_t tmem, uint64_t a0, uint64_t 
 // 2^k as an FP32 value for k <= 0 (0 below the normal range).
 __device__ __forceinline__ float pow2f(int k) { return k >= -126 ? __int_as_float((k + 127) << 23) : 0.0f; }
 
-template <int S>
+// MIX: the tile list may hold 64-wide tiles (tile width read per tile); without it
+// every tile is 128 wide and the widths are constants.
+template <int S, bool MIX>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_split_kernel(const SplitSector *__restrict__ sectors, const SplitTile *__restrict__ tiles, int ntiles,
                       const uint8_t *__restrict__ sa, const uint8_t *__restrict__ sb, const int32_t *__restrict__ ea,
@@ -253,15 +260,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         const SplitTile tl = tiles[t];
         const SplitSector sc = sectors[tl.sector];
         const uint8_t *ablk = sa + sc.sa_off + (int64_t)tl.mt * sc.ks * kBlockBytes;
-        const uint8_t *bblk = sb + sc.sb_off + (int64_t)tl.nt * sc.ks * kBlockBytes;
+        // a 64-wide tile reads one half (64 rows, 4 KB per slice) of a 128-row B block
+        const bool narrow = MIX && tl.bn == 64;
+        const uint8_t *bblk = sb + sc.sb_off + (int64_t)(narrow ? tl.nt >> 1 : tl.nt) * sc.ks * kBlockBytes +
+                              (narrow ? (tl.nt & 1) * (kSliceBytes / 2) : 0);
         for (int kt = 0; kt < sc.ks && ok; kt++, g++) {
           const int slot = g & 1;
           ok = mbar_wait(bar(kEmpty0 + slot), ((g >> 1) & 1) ^ 1, abort_flag, status, 1);
           if (!ok) break;
           uint8_t *dst = smem + slot * kSlotBytes;
-          mbar_expect_tx(bar(kFull0 + slot), 2 * bytes);
+          mbar_expect_tx(bar(kFull0 + slot), narrow ? bytes + bytes / 2 : 2 * bytes);
           bulk_g2s(smem_u32(dst), ablk + (int64_t)kt * kBlockBytes, bytes, bar(kFull0 + slot));
-          bulk_g2s(smem_u32(dst + kBlockBytes), bblk + (int64_t)kt * kBlockBytes, bytes, bar(kFull0 + slot));
+          if (!narrow) {
+            bulk_g2s(smem_u32(dst + kBlockBytes), bblk + (int64_t)kt * kBlockBytes, bytes, bar(kFull0 + slot));
+          } else {
+            for (int p = 0; p < s; p++)
+              bulk_g2s(smem_u32(dst + kBlockBytes + p * (kSliceBytes / 2)),
+                       bblk + (int64_t)kt * kBlockBytes + p * kSliceBytes, kSliceBytes / 2, bar(kFull0 + slot));
+          }
         }
       }
       // no copy may still be in flight when the CTA exits
@@ -277,8 +293,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       const uint32_t slot_base = smem_u32(smem);
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, tcount++) {
-        const SplitSector sc = sectors[tiles[t].sector];
+        const SplitTile tlm = tiles[t];
+        const SplitSector sc = sectors[tlm.sector];
         const int nchunks = (sc.ks + kChunk - 1) / kChunk;
+        const bool narrow = MIX && tlm.bn == 64;
+        const uint32_t idesc = idesc_for(narrow ? 64 : 128);
+        const uint64_t bsu = narrow ? kSliceU / 2 : kSliceU;
         for (int c = 0; c < nchunks && ok; c++, cc++) {
           const int st0 = c * kChunk, st1 = min(sc.ks, st0 + kChunk);
           for (int st = st0; st < st1; st++, g++) {
@@ -303,18 +323,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (first) {
               wait_e_empty();
               if (!ok) break;
-              issue_exact(tmem, a0, b0, true);
+              issue_exact(tmem, a0, b0, true, idesc, bsu);
               if (last) umma_commit(bar(kEFull));
               if (cc >= 1) {
                 ok = mbar_wait(bar(kREmpty), (cc - 1) & 1, abort_flag, status, 4);
                 if (!ok) break;
                 tc_fence_after();
               }
-              issue_rest<S>(tmem, a0, b0, true);
+              issue_rest<S>(tmem, a0, b0, true, idesc, bsu);
             } else {
-              issue_exact(tmem, a0, b0, false);
+              issue_exact(tmem, a0, b0, false, idesc, bsu);
               if (last) umma_commit(bar(kEFull));
-              issue_rest<S>(tmem, a0, b0, false);
+              issue_rest<S>(tmem, a0, b0, false, idesc, bsu);
             }
             umma_commit(bar(kEmpty0 + slot));
             if (last) umma_commit(bar(kRFull));
@@ -327,18 +347,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp >= kFirstEpiWarp) {
     // ---------------------------------------------------------------- epilogue
-    // three warps per 32-lane quarter of tensor memory; columns [40 t, 40 t + w)
-    // with w = 40, 40, 48 for t = 0, 1, 2
+    // three warps per 32-lane quarter of tensor memory; columns [c0, c0 + w) with
+    // w = 40, 40, 48 in a 128-wide tile and 24, 24, 16 in a 64-wide one
     const int quarter = warp & 3, third = (warp - kFirstEpiWarp) >> 2;
     const int rl = quarter * 32 + lane;          // row inside the tile (tensor memory lane)
-    const int c0 = third * 40;                   // first column of this thread
-    const int ngroups = third == 2 ? 12 : 10;    // groups of 4 columns
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     uint32_t cc = 0, tcount = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, tcount++) {
       const SplitTile tl = tiles[t];
       const SplitSector sc = sectors[tl.sector];
+      const bool narrow = MIX && tl.bn == 64;
+      const int c0 = narrow ? third * 24 : third * 40;                                  // first column
+      const int ngroups = narrow ? (third == 2 ? 4 : 6) : (third == 2 ? 12 : 10);      // groups of 4 columns
       const int nchunks = (sc.ks + kChunk - 1) / kChunk;
       long long acc[48];
 #pragma unroll
@@ -403,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ei = ea[sc.ea_off + row];
         const int fmax = __ldg(emax + 2 * tl.sector + 1);
         double *crow = wc + sc.c_off + (int64_t)row * sc.N;
-        const int n0 = tl.nt * kSplitBM + c0;
+        const int n0 = tl.nt * (narrow ? 64 : kSplitBM) + c0;
         const int32_t *fcol = eb + sc.eb_off + n0;
 #pragma unroll
         for (int j = 0; j < 48; j++) {
@@ -433,7 +454,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Opt the kernels in to their shared-memory size; once per device (a context
 // does it at creation), so that launches stay free of non-stream calls.
 cudaError_t configure_split_gemm() {
-  for (auto kernel : {gemm_split_kernel<4>, gemm_split_kernel<5>, gemm_split_kernel<6>}) {
+  for (auto kernel : {gemm_split_kernel<4, false>, gemm_split_kernel<5, false>, gemm_split_kernel<6, false>,
+                      gemm_split_kernel<4, true>, gemm_split_kernel<5, true>, gemm_split_kernel<6, true>}) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
   }
@@ -442,10 +464,16 @@ cudaError_t configure_split_gemm() {
 
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
                               const uint8_t *sb, const int32_t *ea, const int32_t *eb, const int32_t *emax,
-                              float *normsq, double *wc, int slices, int *status, int num_sms, cudaStream_t stream) {
+                              float *normsq, double *wc, int slices, int *status, int num_sms, bool mixed_widths,
+                              cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles > INT32_MAX || slices < 4 || slices > kSlices) return cudaErrorInvalidValue;
-  auto kernel = slices == 4 ? gemm_split_kernel<4> : slices == 5 ? gemm_split_kernel<5> : gemm_split_kernel<6>;
+  auto kernel = mixed_widths ? (slices == 4   ? gemm_split_kernel<4, true>
+                                : slices == 5 ? gemm_split_kernel<5, true>
+                                              : gemm_split_kernel<6, true>)
+                             : (slices == 4   ? gemm_split_kernel<4, false>
+                                : slices == 5 ? gemm_split_kernel<5, false>
+                                              : gemm_split_kernel<6, false>);
   const int grid = (int)std::min<int64_t>(ntiles, num_sms);
   kernel<<<grid, kThreads, kSmemBytes, stream>>>(sectors, tiles, (int)ntiles, sa, sb, ea, eb, emax, normsq, wc,
                                                  status);

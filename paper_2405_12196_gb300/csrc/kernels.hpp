@@ -25,11 +25,18 @@ cudaError_t launch_gemm_fp64(const SectorDev *sectors, const GemmTile *tiles, in
                              const double *wa, const double *wb, double *wc, cudaStream_t stream);
 
 // Split-precision path: row exponents and BF16 slices of every sector operand.
-// emax[op] receives each operand's largest row exponent.
+// Staged path (from the FP64 sector matrices wa, wb): row exponents (ea, eb;
+// emax[op] receives each operand's largest), then the slices.
 cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_items, int64_t nexp,
                               const SplitItem *slice_items, int64_t nslice, const double *wa, const double *wb,
                               int32_t *ea, int32_t *eb, int32_t *emax, uint8_t *sa, uint8_t *sb, int slices,
                               cudaStream_t stream);
+
+// Fused path: row exponents, then slices, straight from the tensors' blocks (a, b:
+// the operands' data), two passes over the blocks.
+cudaError_t launch_split_blocks(const SplitOperand *ops, const SliceItem *items, int64_t nitems,
+                                const SliceSeg *segs, const double *a, const double *b, int32_t *ea, int32_t *eb,
+                                int32_t *emax, uint8_t *sa, uint8_t *sb, int slices, cudaStream_t stream);
 
 // Shared-memory opt-in of the split-precision GEMM kernels (once per device).
 cudaError_t configure_split_gemm();
@@ -42,12 +49,14 @@ cudaError_t launch_cscatter(const CScatterJob *jobs, int64_t njobs, const double
 // N(0, 1) numbers: Philox4x32-10 words turned by Box-Muller (see ytn_fill_normal).
 cudaError_t launch_fill_normal(uint64_t seed, int64_t n, double *out, cudaStream_t stream);
 
-// Split-precision grouped GEMM (tcgen05) over 128x128 tiles, FP64 output C_q;
+// Split-precision grouped GEMM (tcgen05) over 128x128 tiles (and 128x64 tiles
+// when mixed_widths: the tile list holds them), FP64 output C_q;
 // the epilogue adds each sector's scaled ||C_q||^2 into normsq (emax: the
 // operands' largest exponents).
 cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles, int64_t ntiles, const uint8_t *sa,
                               const uint8_t *sb, const int32_t *ea, const int32_t *eb, const int32_t *emax,
-                              float *normsq, double *wc, int slices, int *status, int num_sms, cudaStream_t stream);
+                              float *normsq, double *wc, int slices, int *status, int num_sms, bool mixed_widths,
+                              cudaStream_t stream);
 
 // Accuracy check of the split products (one CTA per sector, the last one
 // finalises): per-sector estimates from the exponents and normsq, the list of
@@ -57,8 +66,19 @@ cudaError_t launch_gemm_split(const SplitSector *sectors, const SplitTile *tiles
 // to the row and column scales, per square root of K.
 cudaError_t launch_split_check(const SplitSector *sectors, int64_t nsec, const int32_t *ea, const int32_t *eb,
                                const int32_t *emax, const float *normsq, double *secv, int32_t *flagged,
-                               int32_t *tile_end, SplitRecord *rec, double eta_split, double eta_fp64, double rtol,
-                               int slices, int *status, cudaStream_t stream);
+                               int32_t *tile_end, int32_t *item_end_a, int32_t *item_end_b, SplitRecord *rec,
+                               double eta_split, double eta_fp64, double rtol, int slices, int *status,
+                               cudaStream_t stream);
+
+// FP64 fallback of the fused split path: zero fill (partially populated
+// operands) and gathers of the flagged sectors' FP64 sector matrices only
+// (persistent grids over the flagged sectors' work items; item_end: running item
+// counts per flagged sector, written by the accuracy check).
+cudaError_t launch_gather_flagged(const CopyJob *jobs, const CopyItem *items_a, const CopyItem *items_b,
+                                  const SplitSector *sp_sectors, const SectorDev *sectors, const int32_t *flagged,
+                                  const int32_t *item_end_a, const int32_t *item_end_b, const SplitRecord *rec,
+                                  const double *a, const double *b, double *wa, double *wb, bool zero_a, bool zero_b,
+                                  int num_sms, cudaStream_t stream);
 
 // FP64 recomputation of the flagged sectors (persistent, 64 x 64 DMMA tiles):
 // the sector list and tile counts come from the accuracy check on the device.

@@ -953,6 +953,11 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   p->jobs.clear();
   p->items.clear();
   p->moved = 0;
+  // Where each block lands in its sector matrix, for the fused split: rows
+  // [roff, roff + rlen) and K [koff, koff + klen) of the operand (A_q, or B_q
+  // transposed), with the block's free and contracted dims and their strides.
+  std::vector<SegSource> seg_src[2];
+  std::vector<size_t> sec_jobs[2];   // first job of each sector, per operand
   // Gather A: block (I, x) -> A_q[row_off(I) + i, x_off(x) + k].
   // isA: gather A (free part = rows M) else B (free part = columns N).
   auto gather = [&](const Tensor &T, const std::vector<int> &freeL, const std::vector<int> &conL,
@@ -960,6 +965,7 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
     for (size_t si = 0; si < geo.size(); si++) {
       const SG &g = geo[si];
       const HostSector &h = p->sectors[si];
+      sec_jobs[isA ? 0 : 1].push_back(p->jobs.size());
       for (auto &xk : g.x_off) {
         const auto &blist = isA ? Ax[xk.first] : Bx[xk.first];
         for (int64_t b : blist) {
@@ -992,6 +998,26 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
             dst_off = base + xoff * ldk + foff;
           }
           int64_t src_off = T.off[b];
+          for (int comp = 0; comp < cw; comp++) {
+            SegSource ss;
+            ss.sector = (int64_t)si;
+            ss.roff = foff + comp * (isA ? g.M : g.N);
+            ss.koff = xoff;
+            ss.boff = cw * src_off + comp;
+            ss.rlen = 1;
+            for (size_t i = 0; i < freeL.size(); i++) {
+              ss.fext.push_back(T.dim(b, freeL[i]));
+              ss.fst.push_back(cw * st[freeL[i]]);
+              ss.rlen *= T.dim(b, freeL[i]);
+            }
+            ss.klen = 1;
+            for (size_t i = 0; i < conL.size(); i++) {
+              ss.kext.push_back(T.dim(b, conL[i]));
+              ss.kst.push_back(cw * st[conL[i]]);
+              ss.klen *= T.dim(b, conL[i]);
+            }
+            seg_src[isA ? 0 : 1].push_back(std::move(ss));
+          }
           if (cw == 2) {
             // interleaved (re, im) source: element strides double; the component
             // selects the row block (A) or column block (B) of the sector matrix
@@ -1009,18 +1035,31 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
     }
     return YTN_OK;
   };
+  // Work items per sector (an item never spans two sectors), so that the FP64
+  // fallback of the split path can gather the sectors it recomputes alone.
+  p->sec_gather_items.assign(geo.size(), {0, 0, 0, 0});
+  auto items_per_sector = [&](int which, size_t jend, int64_t base) {
+    const auto &sj = sec_jobs[which];
+    for (size_t si = 0; si < sj.size(); si++) {
+      const size_t a = sj[si], b = si + 1 < sj.size() ? sj[si + 1] : jend;
+      p->sec_gather_items[si][2 * which] = (int64_t)p->items.size() - base;
+      make_items(p, a, b);
+      p->sec_gather_items[si][2 * which + 1] = (int64_t)p->items.size() - base;
+    }
+  };
   size_t j0 = p->jobs.size();
   ytn_status s = gather(A, freeA, axa, true, p->a_kmajor, a_cov);
   if (s != YTN_OK) return s;
   size_t j1 = p->jobs.size();
   p->items_a_begin = (int64_t)p->items.size();
-  make_items(p, j0, j1);
+  (void)j0;
+  items_per_sector(0, j1, p->items_a_begin);
   p->items_a_end = (int64_t)p->items.size();
   s = gather(B, freeB, axb, false, p->b_kmajor, b_cov);
   if (s != YTN_OK) return s;
   size_t j2 = p->jobs.size();
   p->items_b_begin = (int64_t)p->items.size();
-  make_items(p, j1, j2);
+  items_per_sector(1, j2, p->items_b_begin);
   p->items_b_end = (int64_t)p->items.size();
   int64_t a_need = 0, b_need = 0;
   for (auto &g : geo) { a_need += g.M * g.K; b_need += g.K * g.N; }
@@ -1148,24 +1187,28 @@ ytn_status plan_tensordot(ytn_plan_t *p, const Tensor &A, const Tensor &B, int n
   std::stable_sort(p->tiles.begin(), p->tiles.end(), [&](const GemmTile &x, const GemmTile &y) {
     return geo[x.sector].K > geo[y.sector].K;
   });
-  plan_split_tables(p);
+  plan_split_tables(p, seg_src);
   p->kind = Kind::Tensordot;
   p->a_size = A.size;
   p->b_size = B.size;
   return YTN_OK;
 }
 
-// Tables of the split-precision path: per sector, the slice blocks and
-// exponents of A (rows M) and B (rows N), the exponent / slicing work items and
-// the 128 x 128 output tiles (sectors by decreasing K; inside a sector, groups
-// of 8 row tiles with the column tiles innermost, so that CTAs running at the
-// same time share operand slices in L2).
-void plan_split_tables(ytn_plan_t *p) {
+// Tables of the split-precision path: per sector, the slice blocks and exponents
+// of A (rows M) and B (rows N), the exponent / slicing work items and the
+// 128 x 128 output tiles (sectors by decreasing K; inside a sector, groups of 8
+// row tiles with the column tiles innermost, so that CTAs running at the same time
+// share operand slices in L2). When every block's dims fit kFusedDims per side,
+// also the fused path's items and segments (slices straight from the blocks).
+void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src) {
   p->sp_ops.clear();
   p->sp_exp_items.clear();
   p->sp_slice_items.clear();
   p->sp_sectors.clear();
   p->sp_tiles.clear();
+  p->sp_tiles_mix.clear();
+  p->sp_fitems.clear();
+  p->sp_segs.clear();
   int64_t sa = 0, sb = 0, ea = 0, eb = 0;
   const int64_t nsec = (int64_t)p->sectors.size();
   for (int64_t q = 0; q < nsec; q++) {
@@ -1182,6 +1225,12 @@ void plan_split_tables(ytn_plan_t *p) {
     s.N = (int32_t)h.N;
     s.K = (int32_t)h.K;
     s.ks = (int32_t)ks;
+    if ((size_t)q < p->sec_gather_items.size()) {
+      s.ga0 = (int32_t)p->sec_gather_items[q][0];
+      s.ga1 = (int32_t)p->sec_gather_items[q][1];
+      s.gb0 = (int32_t)p->sec_gather_items[q][2];
+      s.gb1 = (int32_t)p->sec_gather_items[q][3];
+    }
     p->sp_sectors.push_back(s);
     SplitOperand oa{h.a_off, ea, sa, (int32_t)h.M, (int32_t)h.K, (int32_t)ks, p->a_kmajor ? 1 : 0};
     SplitOperand ob{h.b_off, eb, sb, (int32_t)h.N, (int32_t)h.K, (int32_t)ks, p->b_kmajor ? 1 : 0};
@@ -1210,14 +1259,133 @@ void plan_split_tables(ytn_plan_t *p) {
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
                    [&](int64_t x, int64_t y) { return p->sectors[x].K > p->sectors[y].K; });
+  // Tile lists: all 128 wide, and the same with the last column tile of a sector 64
+  // wide where the sector's N ends in its first half (N mod 128 in 1..64: half of the
+  // padded products of that tile saved). The first split call on a plan times both
+  // when they differ and keeps the faster.
+  p->sp_tiles_mix.clear();
+  bool any_narrow = false;
   for (int64_t q : order) {
     const HostSector &h = p->sectors[q];
     const int64_t tm = (h.M + kSplitBM - 1) / kSplitBM, tn = (h.N + kSplitBM - 1) / kSplitBM;
+    const bool tail_narrow = h.N % kSplitBM != 0 && h.N % kSplitBM <= kSplitBM / 2;
+    any_narrow = any_narrow || tail_narrow;
     for (int64_t g0 = 0; g0 < tm; g0 += 8)
       for (int64_t n = 0; n < tn; n++)
-        for (int64_t m = g0; m < std::min<int64_t>(g0 + 8, tm); m++)
-          p->sp_tiles.push_back({(int32_t)q, (int32_t)m, (int32_t)n, 0});
+        for (int64_t m = g0; m < std::min<int64_t>(g0 + 8, tm); m++) {
+          p->sp_tiles.push_back({(int32_t)q, (int32_t)m, (int32_t)n, kSplitBM});
+          if (tail_narrow && n == tn - 1)
+            p->sp_tiles_mix.push_back({(int32_t)q, (int32_t)m, (int32_t)(2 * n), kSplitBM / 2});
+          else
+            p->sp_tiles_mix.push_back({(int32_t)q, (int32_t)m, (int32_t)n, kSplitBM});
+        }
   }
+  if (!any_narrow) p->sp_tiles_mix.clear();
+
+  // Fused path: items of 32 rows x 128 of K per operand, each with the parts of
+  // the blocks inside it. Unit dims are dropped and neighbouring dims that are
+  // contiguous in the block merged; a block with more than kFusedDims dims on
+  // either side, or spanning more than 2^31 elements, leaves the fused path off
+  // (the staged path gathers first). Three per side cover the contractions of the
+  // CTM workloads (their free and contracted legs merge to one or two dims each).
+  p->sp_fused = false;
+  if (!src) return;
+  auto squeeze = [](std::vector<int64_t> &ext, std::vector<int64_t> &st) {
+    std::vector<int64_t> e2, s2;
+    for (size_t i = 0; i < ext.size(); i++) {
+      if (ext[i] == 1) continue;
+      if (!e2.empty() && s2.back() == st[i] * ext[i]) {
+        e2.back() *= ext[i];
+        s2.back() = st[i];
+      } else {
+        e2.push_back(ext[i]);
+        s2.push_back(st[i]);
+      }
+    }
+    ext.swap(e2);
+    st.swap(s2);
+  };
+  for (int w = 0; w < 2; w++)
+    for (SegSource &ss : src[w]) {
+      squeeze(ss.fext, ss.fst);
+      squeeze(ss.kext, ss.kst);
+      if (ss.fext.size() > (size_t)kFusedDims || ss.kext.size() > (size_t)kFusedDims) return;
+      int64_t span = 0;   // largest offset of an element inside the block
+      for (size_t i = 0; i < ss.fext.size(); i++) span += (ss.fext[i] - 1) * ss.fst[i];
+      for (size_t i = 0; i < ss.kext.size(); i++) span += (ss.kext[i] - 1) * ss.kst[i];
+      if (span > INT32_MAX) return;
+    }
+  // items: per operand (A of sector q is op 2q, B op 2q + 1), 32-row quarters of
+  // the 128-row tiles x 128 of K
+  std::vector<int64_t> item_base(p->sp_ops.size() + 1, 0);
+  auto nkq = [](const SplitOperand &op) { return ((int64_t)op.ks * kSplitBK + kItemK - 1) / kItemK; };
+  auto nrq = [](const SplitOperand &op) { return (int64_t)((op.rows + kSplitBM - 1) / kSplitBM) * (kSplitBM / kItemRows); };
+  for (size_t o = 0; o < p->sp_ops.size(); o++) item_base[o + 1] = item_base[o] + nrq(p->sp_ops[o]) * nkq(p->sp_ops[o]);
+  const int64_t nitems = item_base.back();
+  std::vector<std::vector<SliceSeg>> per_item(nitems);
+  std::vector<int64_t> covered(nitems, 0);
+  for (int w = 0; w < 2; w++)
+    for (const SegSource &ss : src[w]) {
+      const int64_t o = 2 * ss.sector + w;
+      const SplitOperand &op = p->sp_ops[o];
+      if (ss.rlen <= 0 || ss.klen <= 0) continue;
+      for (int64_t hr = ss.roff / kItemRows; hr <= (ss.roff + ss.rlen - 1) / kItemRows; hr++)
+        for (int64_t c = ss.koff / kItemK; c <= (ss.koff + ss.klen - 1) / kItemK; c++) {
+          const int64_t ra = std::max(ss.roff, hr * kItemRows), rb = std::min(ss.roff + ss.rlen, hr * kItemRows + kItemRows);
+          const int64_t ka = std::max(ss.koff, c * kItemK), kb = std::min(ss.koff + ss.klen, c * kItemK + kItemK);
+          SliceSeg g{};
+          g.boff = ss.boff;
+          g.nf = (uint8_t)ss.fext.size();
+          g.nk = (uint8_t)ss.kext.size();
+          for (size_t i = 0; i < ss.fext.size(); i++) {
+            g.fext[i] = (int32_t)ss.fext[i];
+            g.fst[i] = ss.fst[i];
+          }
+          for (size_t i = 0; i < ss.kext.size(); i++) {
+            g.kext[i] = (int32_t)ss.kext[i];
+            g.kst[i] = ss.kst[i];
+          }
+          g.ibase = (int32_t)(ra - ss.roff);
+          g.kbase = (int32_t)(ka - ss.koff);
+          g.r0 = (int16_t)(ra - hr * kItemRows);
+          g.r1 = (int16_t)(rb - hr * kItemRows);
+          g.k0 = (int16_t)(ka - c * kItemK);
+          g.k1 = (int16_t)(kb - c * kItemK);
+          // rows fastest when the block's innermost free stride is below its
+          // innermost contracted stride (consecutive rows are nearer in memory)
+          const int64_t fs = ss.fst.empty() ? INT64_MAX : ss.fst.back();
+          const int64_t kst = ss.kst.empty() ? INT64_MAX : ss.kst.back();
+          g.rfast = fs < kst ? 1 : 0;
+          division_magic(g.rfast ? rb - ra : kb - ka, g.fmag, g.fshf);
+          const int64_t it = item_base[o] + hr * nkq(op) + c;
+          per_item[it].push_back(g);
+          covered[it] += (rb - ra) * (kb - ka);
+        }
+    }
+  for (size_t o = 0; o < p->sp_ops.size(); o++) {
+    const SplitOperand &op = p->sp_ops[o];
+    for (int64_t hr = 0; hr < nrq(op); hr++)
+      for (int64_t c = 0; c < nkq(op); c++) {
+        const int64_t it = item_base[o] + hr * nkq(op) + c;
+        SliceItem si{};
+        si.op = (int32_t)o;
+        si.rt = (int32_t)(hr / (kSplitBM / kItemRows));
+        si.quarter = (int32_t)(hr % (kSplitBM / kItemRows));
+        si.kq = (int32_t)c;
+        si.seg0 = (int32_t)p->sp_segs.size();
+        si.nseg = (int32_t)per_item[it].size();
+        const int64_t kc = std::min<int64_t>(kItemK, (int64_t)op.ks * kSplitBK - c * kItemK);
+        si.full = covered[it] == kItemRows * kc ? 1 : 0;
+        p->sp_fitems.push_back(si);
+        p->sp_segs.insert(p->sp_segs.end(), per_item[it].begin(), per_item[it].end());
+        if (p->sp_segs.size() > (size_t)INT32_MAX) {
+          p->sp_fitems.clear();
+          p->sp_segs.clear();
+          return;
+        }
+      }
+  }
+  p->sp_fused = true;
 }
 
 // ---------------------------------------------------------------------------

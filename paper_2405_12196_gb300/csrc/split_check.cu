@@ -16,7 +16,8 @@
 // the GEMM epilogue summed (both taken relative to the operands' largest
 // exponents, so nothing overflows). The last CTA to finish:
 //   - lists the sectors with est_q > rtol, in sector order, with the running
-//     count of their 64 x 64 tiles (the FP64 recomputation reads this list);
+//     counts of their 64 x 64 tiles and of their gather work items (the FP64
+//     recomputation reads these lists);
 //   - writes the call's record: the relative error of the whole result before
 //     and after the fallback (sectors weighted by their norms), the largest
 //     per-sector estimate, the number of recomputed sectors and their FLOPs;
@@ -97,8 +98,9 @@ constexpr int kZeroExp = -1021;
 __global__ void __launch_bounds__(kThreads) split_check_kernel(
     const SplitSector *__restrict__ sectors, int nsec, const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
     const int32_t *__restrict__ emax, const float *__restrict__ normsq, double *__restrict__ secv,
-    int32_t *__restrict__ flagged, int32_t *__restrict__ tile_end, SplitRecord *rec, double eta_split,
-    double eta_fp64, double rtol, int slices, int *status) {
+    int32_t *__restrict__ flagged, int32_t *__restrict__ tile_end, int32_t *__restrict__ item_end_a,
+    int32_t *__restrict__ item_end_b, SplitRecord *rec, double eta_split, double eta_fp64, double rtol, int slices,
+    int *status) {
   __shared__ double dred[kThreads / 32];
   __shared__ int ired[kThreads / 32];
   __shared__ int is_last;
@@ -128,10 +130,10 @@ __global__ void __launch_bounds__(kThreads) split_check_kernel(
     if (__ldcg(secv + s) > 0.0 || normsq[s] > 0.0f) g = max(g, emax[2 * s] + emax[2 * s + 1]);
   g = block_max(g, ired);
   double norm = 0.0, err_split = 0.0, err_after = 0.0, flops = 0.0, worst = 0.0;
-  int nflag = 0, ntile = 0;
+  int nflag = 0, ntile = 0, nia = 0, nib = 0;
   for (int base = 0; base < nsec; base += kThreads) {
     const int s = base + tid;
-    int flag = 0, tiles = 0;
+    int flag = 0, tiles = 0, ia = 0, ib = 0;
     if (s < nsec) {
       const double v = __ldcg(secv + s), n2 = (double)normsq[s];
       double est = 0.0;
@@ -147,18 +149,26 @@ __global__ void __launch_bounds__(kThreads) split_check_kernel(
       if (flag) {
         const SplitSector t = sectors[s];
         tiles = ((t.M + 63) / 64) * ((t.N + 63) / 64);
+        ia = t.ga1 - t.ga0;
+        ib = t.gb1 - t.gb0;
         flops += 2.0 * (double)t.M * (double)t.N * (double)t.K;
       }
     }
-    int total_flag, total_tiles;
+    int total_flag, total_tiles, total_ia, total_ib;
     const int pos = block_scan(flag, ired, &total_flag);
     const int tpos = block_scan(tiles, ired, &total_tiles);
+    const int apos = block_scan(ia, ired, &total_ia);
+    const int bpos = block_scan(ib, ired, &total_ib);
     if (flag) {
       flagged[nflag + pos] = s;
       tile_end[nflag + pos] = ntile + tpos + tiles;
+      item_end_a[nflag + pos] = nia + apos + ia;
+      item_end_b[nflag + pos] = nib + bpos + ib;
     }
     nflag += total_flag;
     ntile += total_tiles;
+    nia += total_ia;
+    nib += total_ib;
   }
   norm = block_sum(norm, dred);
   err_split = block_sum(err_split, dred);
@@ -194,13 +204,14 @@ __global__ void __launch_bounds__(kThreads) split_check_kernel(
 
 cudaError_t launch_split_check(const SplitSector *sectors, int64_t nsec, const int32_t *ea, const int32_t *eb,
                                const int32_t *emax, const float *normsq, double *secv, int32_t *flagged,
-                               int32_t *tile_end, SplitRecord *rec, double eta_split, double eta_fp64, double rtol,
-                               int slices, int *status, cudaStream_t stream) {
+                               int32_t *tile_end, int32_t *item_end_a, int32_t *item_end_b, SplitRecord *rec,
+                               double eta_split, double eta_fp64, double rtol, int slices, int *status,
+                               cudaStream_t stream) {
   if (nsec <= 0) return cudaSuccess;
   if (nsec > INT32_MAX) return cudaErrorInvalidValue;
   split_check_kernel<<<(unsigned)nsec, kThreads, 0, stream>>>(sectors, (int)nsec, ea, eb, emax, normsq, secv, flagged,
-                                                              tile_end, rec, eta_split, eta_fp64, rtol, slices,
-                                                              status);
+                                                              tile_end, item_end_a, item_end_b, rec, eta_split,
+                                                              eta_fp64, rtol, slices, status);
   return cudaGetLastError();
 }
 

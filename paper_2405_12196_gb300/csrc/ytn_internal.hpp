@@ -2,6 +2,7 @@
 // (api.cu, copy_kernels.cu, gemm_fp64.cu, gemm_split.cu). Not part of the ABI.
 #pragma once
 
+#include <array>
 #include <atomic>
 #include <cstdint>
 #include <memory>
@@ -139,6 +140,39 @@ struct SplitOperand {
 };
 static_assert(sizeof(SplitOperand) == 40, "SplitOperand layout");
 
+// Fused split (split_blocks.cu): the slices of an operand are built straight from
+// the tensor's blocks. A work item covers 32 rows (a quarter of a 128-row tile)
+// and 128 of K (four K stages); its segments are the parts of the blocks that
+// fall inside it. Element (r, k) of a segment (r0 <= r < r1, k0 <= k < k1,
+// item-relative) is the block's element (i, x) with i = ibase + r - r0 over the
+// free dims fext (row-major) and x = kbase + k - k0 over the contracted dims kext,
+// at boff + sum_d i_d fst_d + sum_d x_d kst_d doubles into the tensor's data.
+// The CTA walks the segment's elements e = 0 .. (r1 - r0)(k1 - k0) - 1 with rows
+// fastest (rfast: r - r0 = e mod (r1 - r0)) or K fastest, whichever is the
+// block's contiguous direction; n / fast extent = (n + umulhi(n, fmag)) >> fshf.
+constexpr int kSegDims = 4;       // dims per side in the table
+constexpr int kFusedDims = 3;     // dims per side the planner puts on the fused path
+constexpr int kItemRows = 32;     // rows per fused work item
+constexpr int kItemK = 128;       // K per fused work item
+struct SliceSeg {
+  int64_t boff;
+  int64_t fst[kSegDims], kst[kSegDims];
+  int32_t fext[kSegDims], kext[kSegDims];
+  int32_t ibase, kbase;
+  uint32_t fmag;
+  uint8_t fshf, nf, nk, rfast;
+  int16_t r0, r1, k0, k1;
+};
+static_assert(sizeof(SliceSeg) == 128, "SliceSeg layout");
+
+struct SliceItem {
+  int32_t op, rt, quarter, kq;  // 128-row tile rt, its 32-row quarter; K from 128 kq
+  int32_t seg0, nseg;
+  int32_t full;                 // the segments cover every element (no zero fill)
+  int32_t pad;
+};
+static_assert(sizeof(SliceItem) == 32, "SliceItem layout");
+
 // Work item of the exponent / slicing kernels: operand, row tile, stage range.
 struct SplitItem {
   int32_t op, rt, kt0, nkt;
@@ -149,11 +183,14 @@ struct SplitSector {
   int64_t ea_off, eb_off;    // int offsets of the row exponents of A and the column exponents of B
   int64_t c_off;             // element offset of C_q in the FP64 workspace
   int32_t M, N, K, ks;
+  int32_t ga0, ga1, gb0, gb1; // the sector's gather items of A and B (FP64 fallback)
 };
-static_assert(sizeof(SplitSector) == 56, "SplitSector layout");
+static_assert(sizeof(SplitSector) == 72, "SplitSector layout");
 
+// One output tile of the split GEMM: 128 rows x bn columns (bn = 128, or 64 for a
+// narrow tile; nt counts tiles of that width).
 struct SplitTile {
-  int32_t sector, mt, nt, pad;
+  int32_t sector, mt, nt, bn;
 };
 
 // Accuracy check of a split-precision call, written into the workspace after the
@@ -357,17 +394,35 @@ struct ytn_plan_s {
   // split-precision tables
   std::vector<ytn::SplitOperand> sp_ops;
   std::vector<ytn::SplitItem> sp_exp_items, sp_slice_items;
+  // fused split: items and segments (empty when a block has more than kSegDims
+  // free or contracted dims: then the staged path gathers first); the tensor
+  // blocks behind them, recorded while the gathers are planned
+  std::vector<ytn::SliceItem> sp_fitems;
+  std::vector<ytn::SliceSeg> sp_segs;
+  bool sp_fused = false;
+  std::vector<std::array<int64_t, 4>> sec_gather_items;   // per sector: A items, B items (relative)
   std::vector<ytn::SplitSector> sp_sectors;
   std::vector<ytn::SplitTile> sp_tiles;
+  std::vector<ytn::SplitTile> sp_tiles_mix;    // with 64-wide sector tails (empty: none)
   int64_t sp_sa_bytes = 0, sp_sb_bytes = 0, sp_ea = 0, sp_eb = 0;
   // YTN_AUTO: per slice count, -1 undecided, 0 FP64, 1 split; the timings (ms)
   std::mutex auto_mu;
   int auto_choice[ytn::kSlices + 1] = {-1, -1, -1, -1, -1, -1, -1};
   float auto_ms[ytn::kSlices + 1][2] = {};
+  // split path variant per slice count: -1 undecided, 0 staged, 1 fused (slices
+  // straight from the blocks); the timings (ms) of the two
+  int split_variant[ytn::kSlices + 1] = {-1, -1, -1, -1, -1, -1, -1};
+  float variant_ms[ytn::kSlices + 1][2] = {};
+  // split GEMM tile list per slice count: -1 undecided, 0 all 128 wide, 1 with the
+  // 64-wide sector tails; the timings (ms)
+  int tile_policy[ytn::kSlices + 1] = {-1, -1, -1, -1, -1, -1, -1};
+  float tile_ms[ytn::kSlices + 1][2] = {};
+  const ytn::SliceItem *d_sp_fitems = nullptr;
+  const ytn::SliceSeg *d_sp_segs = nullptr;
   const ytn::SplitOperand *d_sp_ops = nullptr;
   const ytn::SplitItem *d_sp_exp_items = nullptr, *d_sp_slice_items = nullptr;
   const ytn::SplitSector *d_sp_sectors = nullptr;
-  const ytn::SplitTile *d_sp_tiles = nullptr;
+  const ytn::SplitTile *d_sp_tiles = nullptr, *d_sp_tiles_mix = nullptr;
 };
 
 namespace ytn {
@@ -397,7 +452,14 @@ ytn_status plan_trace(ytn_plan_t *p, const Tensor &A, int naxes, const int *ax1,
                       const int *ax2, std::string &err);
 std::string plan_key(const ytn_op *op);
 void finish_output_view(ytn_plan_t *p);
-void plan_split_tables(ytn_plan_t *p);
+// Where one block of an operand lands in its sector matrix (rows: A's rows or
+// B's columns; K), with the block's free and contracted dims and their strides in
+// doubles (complex data: one entry per component).
+struct SegSource {
+  int64_t sector = 0, roff = 0, rlen = 0, koff = 0, klen = 0, boff = 0;
+  std::vector<int64_t> fext, fst, kext, kst;
+};
+void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src);
 
 // error reporting (api.cu)
 ytn_status fail(ytn_status st, const std::string &msg);

@@ -80,7 +80,8 @@ class ytn_plan_info(C.Structure):
     _fields_ = [("useful_flops", C.c_double), ("nsectors", C.c_int64), ("max_m", C.c_int64),
                 ("max_n", C.c_int64), ("max_k", C.c_int64), ("a_elems", C.c_int64),
                 ("b_elems", C.c_int64), ("c_elems", C.c_int64), ("moved_elems", C.c_int64),
-                ("out_size", C.c_int64), ("njobs", C.c_int64)]
+                ("out_size", C.c_int64), ("njobs", C.c_int64), ("split_fused", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 NPHASES = 8
@@ -93,7 +94,7 @@ class ytn_profile(C.Structure):
 
 class ytn_result(C.Structure):
     _fields_ = [("useful_flops", C.c_double), ("precision", C.c_int32), ("slices", C.c_int32),
-                ("err_est", C.c_double)]
+                ("err_est", C.c_double), ("split_variant", C.c_int32), ("narrow_tiles", C.c_int32)]
 
 
 class ytn_error_report(C.Structure):
@@ -458,7 +459,7 @@ def ytn_tensordot(plan, a, b, c, prec=YTN_FP64, rtol=0.0, workspace=None, worksp
     _check(_lib.ytn_tensordot(plan.handle, _ptr(a), _ptr(b), _ptr(c), prec, float(rtol),
                               _ptr(workspace), int(workspace_bytes), C.byref(res), _stream(stream)))
     return {"useful_flops": res.useful_flops, "precision": res.precision, "slices": res.slices,
-            "err_est": res.err_est}
+            "err_est": res.err_est, "split_variant": res.split_variant, "narrow_tiles": res.narrow_tiles}
 
 
 def ytn_ncon_plan(ctx, records, labels):

@@ -203,3 +203,96 @@ def test_report_needs_a_completed_split_call(ctx):
     with pytest.raises(ytn.YtnError) as e:
         ytn.ytn_tensordot_report(plan, ws)
     assert e.value.name == "YTN_E_INVALID"
+
+
+def test_staged_split_path_for_blocks_with_many_dims(ctx):
+    """Blocks with four free dims that cannot merge (legs free, contracted, free, ...
+    interleaved) are beyond the fused split (three per side): the staged path (FP64
+    sector matrices first) runs, and must meet the tolerance against the oracle."""
+    from gpu_helpers import check_against_oracle, oracle_tensordot
+    l = W.Leg(1, [(0,), (1,)], [2, 2])
+    A = W.random_tensor((0,), [l] * 7, (2,), 21)
+    B = W.random_tensor((0,), [l.conj()] * 3 + [l] * 2, (-1,), 22)
+    axa, axb = (1, 3, 5), (0, 1, 2)
+    got, res, rep, status = _split_run(ctx, A, B, axa, axb)
+    from paper_2405_12196_gb300 import ytn
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    assert plan.info["split_fused"] == 0
+    rec = dict(plan.out)
+    rec["data"] = got
+    check_against_oracle(rec, oracle_tensordot(A, B, axa, axb), rtol=SPLIT_RTOL)
+    assert status == "YTN_OK" and rep["within"] == 1
+
+
+def test_fused_split_path_on_the_environment_contraction(ctx):
+    """The CTM environment contraction X2 . a (U(1)xU(1), D = 12) takes the fused
+    path, and meets the tolerance against the oracle."""
+    from gpu_helpers import check_against_oracle, oracle_tensordot
+    from paper_2405_12196_gb300 import ytn
+    cfg = W.config3()
+    dl = cfg["dleg"]
+    a = W.random_tensor((0, 0), [W.Leg(-1, dl.t, dl.D), W.Leg(1, dl.t, dl.D), W.Leg(1, dl.t, dl.D),
+                                 W.Leg(-1, dl.t, dl.D)], (0, 0), 3999)
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, cfg["X2"], a, (1, 2), (0, 1))
+    assert plan.info["split_fused"] == 1
+    got, res, rep, status = _split_run(ctx, cfg["X2"], a, (1, 2), (0, 1))
+    rec = dict(plan.out)
+    rec["data"] = got
+    check_against_oracle(rec, oracle_tensordot(cfg["X2"], a, (1, 2), (0, 1)), rtol=SPLIT_RTOL)
+    assert status == "YTN_OK" and rep["nfallback"] == 0
+
+
+def test_split_variants_give_identical_bits(ctx):
+    """A plan with fused tables: the first split call times the staged and the fused
+    variant (leaving the fused result) and caches the faster; later calls use the
+    cached one. Both variants build the same slices, so every call gives the same
+    bits."""
+    import torch
+    from paper_2405_12196_gb300 import ytn
+    cfg = W.config3()
+    dl = cfg["dleg"]
+    a = W.random_tensor((0, 0), [W.Leg(-1, dl.t, dl.D), W.Leg(1, dl.t, dl.D), W.Leg(1, dl.t, dl.D),
+                                 W.Leg(-1, dl.t, dl.D)], (0, 0), 4001)
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, cfg["X2"], a, (1, 2), (0, 1))
+    assert plan.info["split_fused"] == 1
+    dev = torch.device("cuda:0")
+    da, db = torch.from_numpy(cfg["X2"]["data"]).to(dev), torch.from_numpy(a["data"]).to(dev)
+    ws = torch.empty(ytn.ytn_workspace_size(plan, ytn.YTN_SPLIT_BF16, SPLIT_RTOL), dtype=torch.uint8, device=dev)
+    outs, variants = [], []
+    for _ in range(3):
+        dc = torch.full((plan.out["size"],), float("nan"), dtype=torch.float64, device=dev)
+        res = ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_SPLIT_BF16, rtol=SPLIT_RTOL, workspace=ws)
+        ytn.ytn_sync(ctx)
+        outs.append(dc.cpu().numpy())
+        variants.append(res["split_variant"])
+    assert variants[0] == 1 and variants[1] == variants[2] and variants[1] in (0, 1)
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[1], outs[2])
+
+
+@pytest.mark.parametrize("dims", [(200, 300, 60), (130, 1000, 190), (64, 96, 1), (257, 513, 129)])
+def test_narrow_sector_tails(ctx, dims):
+    """Sectors whose N ends in the first half of a 128-wide tile get a 128 x 64 last
+    column tile in the second tile list. The first split call runs every candidate
+    and leaves the last one's result, the one with the narrow tails, in C: it must
+    meet the tolerance against the oracle; later calls (the cached choice) too."""
+    import torch
+    from gpu_helpers import check_against_oracle, oracle_tensordot
+    from paper_2405_12196_gb300 import ytn
+    M, K, N = dims
+    rng = np.random.default_rng(M + K + N)
+    A, B, axa, axb = _dense_pair(rng.standard_normal((M, K)), rng.standard_normal((K, N)))
+    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    ref = oracle_tensordot(A, B, axa, axb)
+    dev = torch.device("cuda:0")
+    da, db = torch.from_numpy(A["data"]).to(dev), torch.from_numpy(B["data"]).to(dev)
+    ws = torch.empty(ytn.ytn_workspace_size(plan, ytn.YTN_SPLIT_BF16, SPLIT_RTOL), dtype=torch.uint8, device=dev)
+    for call in range(2):
+        dc = torch.full((plan.out["size"],), float("nan"), dtype=torch.float64, device=dev)
+        res = ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_SPLIT_BF16, rtol=SPLIT_RTOL, workspace=ws)
+        ytn.ytn_sync(ctx)
+        rec = dict(plan.out)
+        rec["data"] = dc.cpu().numpy()
+        check_against_oracle(rec, ref, rtol=SPLIT_RTOL)
+        if call == 0:
+            assert res["narrow_tiles"] == (1 if 0 < N % 128 <= 64 else 0)
