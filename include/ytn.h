@@ -225,10 +225,11 @@ typedef struct {
   double useful_flops;
   int32_t precision;         /* ytn_precision used                              */
   int32_t slices;            /* split path: BF16 slices per operand, else 0     */
-  double err_est;            /* split path: the a-priori bound of the model that
-                                picks the slice count, which does not see the
-                                data; 0 for FP64. The data-aware estimate of the
-                                result is in ytn_tensordot_report            */
+  double err_est;            /* split path: the a-priori forecast that picks the
+                                slice count (the data-aware estimate for data
+                                spread like a normal distribution); 0 for FP64.
+                                The estimate of this result, computed on the
+                                device from its data, is in ytn_tensordot_report */
   int32_t split_variant;     /* split path: 1 when the BF16 slices were built
                                 straight from the blocks (fused), 0 when FP64
                                 sector matrices were gathered first (staged);
@@ -371,12 +372,13 @@ ytn_status ytn_workspace_size_staged(const ytn_plan_t *plan, ytn_precision prec,
  * dims per side (ytn_plan_info.split_fused): slices built straight from the
  * blocks (fused), or from FP64 sector matrices gathered first (staged). The
  * first split-precision call on such a plan (explicit or through YTN_AUTO) times
- * both on the caller's stream in the same way and caches the faster; under graph
- * capture the fused one is taken when the blocks are large (an average of at
- * least 1024 elements per block part). Operands read straight from page-locked
- * host memory (no staging workspace) always take the staged variant, whose
- * gathers read every block linearly over the host link. res->split_variant
- * reports the variant used.
+ * both on the caller's stream in the same way (three times each when a round of
+ * candidates takes under 20 ms, keeping each one's fastest) and caches the
+ * faster; under graph capture the fused one is taken when the blocks are large
+ * (an average of at least 1024 elements per block part). Operands read straight
+ * from page-locked host memory (no staging workspace) always take the staged
+ * variant, whose gathers read every block linearly over the host link.
+ * res->split_variant reports the variant used.
  * Likewise the split GEMM's tile list: 128 x 128 tiles, or the same with a
  * 128 x 64 last column tile for every sector whose N ends in the first half of a
  * 128-wide tile (half of that tile's padded products saved); the first split call
@@ -386,9 +388,11 @@ ytn_status ytn_workspace_size_staged(const ytn_plan_t *plan, ytn_precision prec,
  * ytn_error_report): sectors whose data-aware estimate exceeds rtol are
  * recomputed on the FP64 path before C is written, and when even that leaves
  * the estimate above rtol the next ytn_sync on the context returns
- * YTN_E_TOLERANCE.
+ * YTN_E_TOLERANCE. The slice count comes from an a-priori forecast for typical
+ * data (s = 5 at rtol 1e-10, s = 6 down to about 1.5e-11); the device check makes
+ * every result meet rtol whatever its data.
  * Errors: YTN_E_INVALID (wrong plan kind), YTN_E_WORKSPACE, YTN_E_TOLERANCE
- * (rtol below what the split path can guarantee), YTN_E_CUDA (launch). */
+ * (rtol below what the split path can reach), YTN_E_CUDA (launch). */
 ytn_status ytn_tensordot(ytn_plan_t *plan, const double *a, const double *b, double *c,
                          ytn_precision prec, double rtol, void *workspace,
                          size_t workspace_bytes, ytn_result *res, ytn_stream stream);

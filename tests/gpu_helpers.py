@@ -32,6 +32,8 @@ def run_tensordot(ctx, A, B, axa, axb, prec=None, rtol=0.0):
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device())
     res = ytn.ytn_tensordot(plan, da, db, dc, prec=prec, rtol=rtol, workspace=ws)
     ytn.ytn_sync(ctx)
+    if res["precision"] == ytn.YTN_SPLIT_BF16:
+        res["report"] = ytn.ytn_tensordot_report(plan, ws)   # the device's data-aware estimate
     rec = dict(out)
     rec["data"] = dc[:out["size"]].cpu().numpy()
     return plan, rec, res

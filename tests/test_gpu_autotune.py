@@ -78,7 +78,7 @@ def test_auto_picks_split_on_a_large_contraction(ctx):
     ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_AUTO, rtol=1e-10, workspace=ws)
     r = ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_AUTO, rtol=1e-10, workspace=ws)
     ytn.ytn_sync(ctx)
-    assert r["precision"] == ytn.YTN_SPLIT_BF16 and r["slices"] == 6
+    assert r["precision"] == ytn.YTN_SPLIT_BF16 and r["slices"] == 5   # the forecast 128 eta(s) <= 1e-10 first holds at s = 5
 
 
 def test_auto_under_graph_capture_uses_the_model(ctx):
