@@ -689,11 +689,20 @@ def measure_contraction(args, ytn, ctx, dev, cfg, world, rank, local, prec, step
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            staged_pipelined_call()
-        torch.cuda.synchronize(dev)
-        e2e_value = strong_value(total_flops, e2e_steps, max_over_ranks(time.perf_counter() - t0, dev))
+        # the host link's bandwidth varies from box to box and from run to run (the
+        # page-locked buffers' placement, other jobs on the host): the median of three
+        # timed runs, every run reported
+        e2e_runs = []
+        for _ in range(3):
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                staged_pipelined_call()
+            torch.cuda.synchronize(dev)
+            e2e_runs.append(strong_value(total_flops, e2e_steps, max_over_ranks(time.perf_counter() - t0, dev)))
+        e2e_value = float(np.median(e2e_runs))
         staged_ok = bool(torch.equal(s_hc[(k_s[0] - 1) % nfly], ref_c))
         hbm_reserved = nfly * sbytes
         del s_ws
@@ -703,7 +712,7 @@ def measure_contraction(args, ytn, ctx, dev, cfg, world, rank, local, prec, step
                "path": "ytn_tensordot on page-locked host A, B, C with a staging workspace "
                        f"(ytn_workspace_size_staged): each call copies its inputs in and its result out with "
                        f"the copy engines; {nfly} calls in flight on {nfly} streams",
-               "hbm_reserved_bytes": int(hbm_reserved),
+               "runs": e2e_runs, "hbm_reserved_bytes": int(hbm_reserved),
                "staged_result_equals_device_result": staged_ok, **e2e}
     else:
         del ws, da, db, dc
@@ -730,6 +739,10 @@ def measure_contraction(args, ytn, ctx, dev, cfg, world, rank, local, prec, step
                         "err_est": report["err_est"], "split_err_est": report["split_err_est"],
                         "max_sector_est": report["max_sector_est"], "fp64_fallback_sectors": report["nfallback"],
                         "fp64_fallback_flops": report["fallback_flops"]}
+        # the autotuner's record for this slice count: the candidates' times on the
+        # plan's first call (ms, fastest of its rounds; 0 where not timed)
+        tun = ytn.ytn_plan_tuning(plan, res["slices"])
+        out["split"]["tuning_ms"] = {k: tun[k] for k in ("staged_ms", "fused_ms", "wide_ms", "narrow_ms")}
     return out
 
 

@@ -328,6 +328,23 @@ const ytn_struct *ytn_plan_output(const ytn_plan_t *plan);
 /* Output i of a plan with several (SVD: 0 = U, 1 = S, 2 = V); NULL past the last. */
 const ytn_struct *ytn_plan_output_at(const ytn_plan_t *plan, int32_t i);
 ytn_status ytn_plan_get_info(const ytn_plan_t *plan, ytn_plan_info *info);
+
+/* The choices that a tensordot plan's first split-precision calls made with this
+ * slice count (the autotuner of ytn_tensordot), and the timings behind them.
+ * A choice is -1 while undecided. Timings are in ms: one run of that candidate on
+ * the calling stream, the fastest of the rounds timed. A candidate that was not
+ * timed reads 0, and so do all of them when a cost model decided (graph capture).
+ * YTN_E_INVALID: null plan or out, or slices outside 1..6. */
+typedef struct ytn_tuning {
+  int32_t slices;
+  int32_t auto_choice;     /* YTN_AUTO: 0 FP64, 1 split */
+  int32_t split_variant;   /* 0 staged (FP64 sector matrices first), 1 fused */
+  int32_t tile_policy;     /* 0 128-wide tiles only, 1 with 64-wide sector tails */
+  float fp64_ms, split_ms; /* YTN_AUTO: the FP64 run and the fastest split candidate */
+  float staged_ms, fused_ms;
+  float wide_ms, narrow_ms;
+} ytn_tuning;
+ytn_status ytn_plan_tuning(const ytn_plan_t *plan, int32_t slices, ytn_tuning *out);
 void ytn_plan_release(ytn_plan_t *plan);
 
 /* Device workspace (bytes) a ytn_tensordot call needs for this precision and

@@ -593,6 +593,24 @@ ytn_status ytn_plan_get_info(const ytn_plan_t *p, ytn_plan_info *info) {
   return YTN_OK;
 }
 
+ytn_status ytn_plan_tuning(const ytn_plan_t *p, int32_t slices, ytn_tuning *out) {
+  if (!p || !out) return fail(YTN_E_INVALID, "null argument");
+  if (slices < 1 || slices > kSlices) return fail(YTN_E_INVALID, "slice count out of range");
+  std::lock_guard<std::mutex> lk(const_cast<ytn_plan_t *>(p)->auto_mu);
+  std::memset(out, 0, sizeof(*out));
+  out->slices = slices;
+  out->auto_choice = p->auto_choice[slices];
+  out->split_variant = p->split_variant[slices];
+  out->tile_policy = p->tile_policy[slices];
+  out->fp64_ms = p->auto_ms[slices][0];
+  out->split_ms = p->auto_ms[slices][1];
+  out->staged_ms = p->variant_ms[slices][0];
+  out->fused_ms = p->variant_ms[slices][1];
+  out->wide_ms = p->tile_ms[slices][0];
+  out->narrow_ms = p->tile_ms[slices][1];
+  return YTN_OK;
+}
+
 void ytn_plan_release(ytn_plan_t *plan) {
   if (!plan) return;
   ytn_ctx *ctx = plan->ctx;

@@ -147,9 +147,10 @@ static_assert(sizeof(SplitOperand) == 40, "SplitOperand layout");
 // item-relative) is the block's element (i, x) with i = ibase + r - r0 over the
 // free dims fext (row-major) and x = kbase + k - k0 over the contracted dims kext,
 // at boff + sum_d i_d fst_d + sum_d x_d kst_d doubles into the tensor's data.
-// The CTA walks the segment's elements e = 0 .. (r1 - r0)(k1 - k0) - 1 with rows
-// fastest (rfast: r - r0 = e mod (r1 - r0)) or K fastest, whichever is the
-// block's contiguous direction; n / fast extent = (n + umulhi(n, fmag)) >> fshf.
+// A warp walks a segment with its lanes along the block's contiguous direction
+// (rfast: lanes are rows, the warp steps along K; else lanes are K, the warp steps
+// along rows). fmag / fshf: the division constants of the lanes' extent (r1 - r0
+// when rfast, else k1 - k0); the loader steps its indices and does not use them.
 constexpr int kSegDims = 4;       // dims per side in the table
 constexpr int kFusedDims = 3;     // dims per side the planner puts on the fused path
 constexpr int kItemRows = 32;     // rows per fused work item

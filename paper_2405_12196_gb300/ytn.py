@@ -103,6 +103,13 @@ class ytn_error_report(C.Structure):
                 ("nfallback", C.c_int32), ("within", C.c_int32), ("slices", C.c_int32)]
 
 
+class ytn_tuning(C.Structure):
+    _fields_ = [("slices", C.c_int32), ("auto_choice", C.c_int32), ("split_variant", C.c_int32),
+                ("tile_policy", C.c_int32), ("fp64_ms", C.c_float), ("split_ms", C.c_float),
+                ("staged_ms", C.c_float), ("fused_ms", C.c_float), ("wide_ms", C.c_float),
+                ("narrow_ms", C.c_float)]
+
+
 class ytn_request_info(C.Structure):
     _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("slot", C.c_int32), ("t_arrive", C.c_double),
                 ("t_admit", C.c_double), ("t_done", C.c_double), ("workspace", C.c_size_t)]
@@ -124,6 +131,7 @@ SYMBOLS = {
     "ytn_slice": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ytn_eigh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "ytn_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(ytn_plan_info)]),
+    "ytn_plan_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(ytn_tuning)]),
     "ytn_plan_release": (None, [C.c_void_p]),
     "ytn_workspace_size": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
     "ytn_workspace_size_staged": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_size_t)]),
@@ -504,6 +512,14 @@ def ytn_tensordot_report(plan, workspace, stream=None):
     r = ytn_error_report()
     _check(_lib.ytn_tensordot_report(plan.handle, _ptr(workspace), C.byref(r), _stream(stream)))
     return {k: getattr(r, k) for k, _ in ytn_error_report._fields_}
+
+
+def ytn_plan_tuning(plan, slices):
+    """The split-precision choices the plan's first calls made with ``slices`` slices
+    (-1: undecided) and the candidates' timings in ms (0: not timed)."""
+    t = ytn_tuning()
+    _check(_lib.ytn_plan_tuning(plan.handle, int(slices), C.byref(t)))
+    return {k: getattr(t, k) for k, _ in ytn_tuning._fields_}
 
 
 def ytn_tensordot_noalloc(plan, a, b, c, stream=None):

@@ -414,3 +414,19 @@ def test_blocks_from_legs_errors(hctx):
         with pytest.raises(ytn.YtnError) as ei:
             ytn.ytn_plan_blocks(hctx, (0,), [bad], (0,))
         assert ei.value.name == "YTN_E_INVALID"
+
+
+def test_tuning_of_a_new_plan_is_undecided(hctx):
+    """A plan that has run no split call has no cached choice and no timings; slice
+    counts outside 1..6 are rejected."""
+    cfg = W.config1()
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    for s in range(1, 7):
+        t = ytn.ytn_plan_tuning(plan, s)
+        assert t["slices"] == s
+        assert (t["auto_choice"], t["split_variant"], t["tile_policy"]) == (-1, -1, -1)
+        assert all(t[k] == 0.0 for k in ("fp64_ms", "split_ms", "staged_ms", "fused_ms", "wide_ms", "narrow_ms"))
+    for s in (0, 7):
+        with pytest.raises(ytn.YtnError) as e:
+            ytn.ytn_plan_tuning(plan, s)
+        assert e.value.name == "YTN_E_INVALID"

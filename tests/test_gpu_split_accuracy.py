@@ -253,7 +253,10 @@ def test_split_variants_give_identical_bits(ctx):
     dl = cfg["dleg"]
     a = W.random_tensor((0, 0), [W.Leg(-1, dl.t, dl.D), W.Leg(1, dl.t, dl.D), W.Leg(1, dl.t, dl.D),
                                  W.Leg(-1, dl.t, dl.D)], (0, 0), 4001)
-    plan = ytn.ytn_plan(ctx, ytn.YTN_OP_TENSORDOT, cfg["X2"], a, (1, 2), (0, 1))
+    # a context of its own: plans are cached per context by structure, and this one's
+    # first call must be the one that times the variants
+    fresh = ytn.ytn_ctx_create(0)
+    plan = ytn.ytn_plan(fresh, ytn.YTN_OP_TENSORDOT, cfg["X2"], a, (1, 2), (0, 1))
     assert plan.info["split_fused"] == 1
     dev = torch.device("cuda:0")
     da, db = torch.from_numpy(cfg["X2"]["data"]).to(dev), torch.from_numpy(a["data"]).to(dev)
@@ -262,10 +265,14 @@ def test_split_variants_give_identical_bits(ctx):
     for _ in range(3):
         dc = torch.full((plan.out["size"],), float("nan"), dtype=torch.float64, device=dev)
         res = ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_SPLIT_BF16, rtol=SPLIT_RTOL, workspace=ws)
-        ytn.ytn_sync(ctx)
+        ytn.ytn_sync(fresh)
         outs.append(dc.cpu().numpy())
         variants.append(res["split_variant"])
     assert variants[0] == 1 and variants[1] == variants[2] and variants[1] in (0, 1)
+    # the cached choice is the faster of the two timed runs
+    t = ytn.ytn_plan_tuning(plan, res["slices"])
+    assert t["split_variant"] == variants[1] and t["staged_ms"] > 0 and t["fused_ms"] > 0
+    assert (t["fused_ms"] < t["staged_ms"]) == (variants[1] == 1)
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(outs[1], outs[2])
 
