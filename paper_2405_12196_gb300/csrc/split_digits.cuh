@@ -14,6 +14,21 @@ namespace ytn {
 
 static_assert(kSlices == 6, "the digits are taken from fixed byte positions");
 
+// The float 2^23 + b for 0 <= b < 2^23: b in the low mantissa bits of 2^23.
+__device__ __forceinline__ float biased_int(uint32_t b) { return __uint_as_float(0x4B000000u | b); }
+
+// Byte k of x as the float 2^23 + byte (one byte permute).
+template <int K>
+__device__ __forceinline__ float biased_byte(uint32_t x) {
+  return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7540u | K));
+}
+
+// Two floats with at most 8 significant bits as a BF16 pair (low half: f0). Their
+// BF16 values are exact: the upper 16 bits of each float.
+__device__ __forceinline__ uint32_t pack_exact_bf16(float f0, float f1) {
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632u);
+}
+
 // Eight consecutive elements of one row (raw FP64 bits) -> s slices of 8 BF16
 // values each, packed as 16 bytes per slice (two elements per 32-bit word, the
 // even one in the low half).
@@ -21,7 +36,7 @@ __device__ __forceinline__ void slice_digits8(const unsigned long long *bits8, i
                                               uint32_t (&packed)[kSlices][4]) {
 #pragma unroll
   for (int j = 0; j < 8; j += 2) {
-    float f[2][kSlices];
+    uint32_t lo[2], hi[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       const unsigned long long bits = bits8[j + h];
@@ -37,22 +52,31 @@ __device__ __forceinline__ void slice_digits8(const unsigned long long *bits8, i
       // balanced base-256 digits: with w = u 256^(6-s) + sum_q 128 256^q (q < 6),
       // digit p (most significant first) is byte 5 - p of w minus 128, the leading
       // one taking the carry above byte 5 as well (it lies in [-128, 128]); bytes
-      // below the s kept digits are 128, i.e. digits 0. Each slice value
-      // d_p 2^(-8p) = byte 2^(-8p) - 128 2^(-8p) is one exact FMA.
+      // below the s kept digits are 128, i.e. digits 0.
       const unsigned long long w = ((unsigned long long)u << (8 * (kSlices - s))) + 0x808080808080ull;
-      const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
-      f[h][0] = (float)(hi >> 8) - 128.0f;
-      f[h][1] = fmaf((float)(hi & 255u), 0x1p-8f, -0x1p-1f);
-      f[h][2] = fmaf((float)(lo >> 24), 0x1p-16f, -0x1p-9f);
-      f[h][3] = fmaf((float)((lo >> 16) & 255u), 0x1p-24f, -0x1p-17f);
-      f[h][4] = fmaf((float)((lo >> 8) & 255u), 0x1p-32f, -0x1p-25f);
-      f[h][5] = fmaf((float)(lo & 255u), 0x1p-40f, -0x1p-33f);
+      lo[h] = (uint32_t)w;
+      hi[h] = (uint32_t)(w >> 32);
     }
-#pragma unroll
-    for (int p = 0; p < kSlices; p++) {
-      const __nv_bfloat162 pr = __floats2bfloat162_rn(f[0][p], f[1][p]);
-      packed[p][j >> 1] = *reinterpret_cast<const uint32_t *>(&pr);
-    }
+    // slice p holds d_p 2^(-8p) = (byte - 128) 2^(-8p): from the float 2^23 + byte,
+    // one exact FMA ((2^23 + byte) 2^(-8p) - (2^23 + 128) 2^(-8p), both terms and
+    // the result representable); the leading digit (up to 256 - 128) one exact add
+    constexpr float kBias = 8388608.0f + 128.0f;
+    packed[0][j >> 1] = pack_exact_bf16(biased_int(hi[0] >> 8) - kBias, biased_int(hi[1] >> 8) - kBias);
+    if (s > 1)
+      packed[1][j >> 1] = pack_exact_bf16(fmaf(biased_byte<0>(hi[0]), 0x1p-8f, -kBias * 0x1p-8f),
+                                          fmaf(biased_byte<0>(hi[1]), 0x1p-8f, -kBias * 0x1p-8f));
+    if (s > 2)
+      packed[2][j >> 1] = pack_exact_bf16(fmaf(biased_byte<3>(lo[0]), 0x1p-16f, -kBias * 0x1p-16f),
+                                          fmaf(biased_byte<3>(lo[1]), 0x1p-16f, -kBias * 0x1p-16f));
+    if (s > 3)
+      packed[3][j >> 1] = pack_exact_bf16(fmaf(biased_byte<2>(lo[0]), 0x1p-24f, -kBias * 0x1p-24f),
+                                          fmaf(biased_byte<2>(lo[1]), 0x1p-24f, -kBias * 0x1p-24f));
+    if (s > 4)
+      packed[4][j >> 1] = pack_exact_bf16(fmaf(biased_byte<1>(lo[0]), 0x1p-32f, -kBias * 0x1p-32f),
+                                          fmaf(biased_byte<1>(lo[1]), 0x1p-32f, -kBias * 0x1p-32f));
+    if (s > 5)
+      packed[5][j >> 1] = pack_exact_bf16(fmaf(biased_byte<0>(lo[0]), 0x1p-40f, -kBias * 0x1p-40f),
+                                          fmaf(biased_byte<0>(lo[1]), 0x1p-40f, -kBias * 0x1p-40f));
   }
 }
 

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const SplitOperand *__re
 }
 
 // Slices: one 128 x 32 stage at a time through shared memory (raw FP64 bits).
-__global__ void __launch_bounds__(256) split_slice_kernel(const SplitOperand *__restrict__ ops,
+__global__ void __launch_bounds__(256, 6) split_slice_kernel(const SplitOperand *__restrict__ ops,
                                                           const SplitItem *__restrict__ items,
                                                           const double *__restrict__ wa,
                                                           const double *__restrict__ wb,
