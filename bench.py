@@ -127,6 +127,8 @@ def make_workload(name, rank):
         return W.config5b(seed=5101 + seed_shift)
     if name == "d14":
         return W.config5(seed=5201 + seed_shift, D=14)
+    if name == "cfg5r":
+        return W.config5_sectors(seed=5001 + seed_shift)
     if name == "cfg3":
         c = W.config3(seed=3001 + seed_shift)
         dl = c["dleg"]
@@ -141,6 +143,8 @@ WORKLOAD_DESC = {
     "cfg5b": "U(1)xU(1) iPEPS environment contraction X2.a, D=20 (9 sectors, 25-sector D^2 legs), chi=400",
     "cfg3": "U(1)xU(1) CTMRG X2.a, D=12, chi=144",
     "d14": "U(1)xU(1) iPEPS environment contraction X2.a, D=14, chi=D^2 (profiling size)",
+    "cfg5r": "U(1)xU(1) iPEPS environment contraction X2.a, D=20: the blocks of a random quarter of its "
+             "sectors (the full workload's block and sector sizes; profiling size)",
 }
 
 

@@ -305,6 +305,27 @@ static ytn_status time_runs(cudaStream_t st, const std::vector<std::function<ytn
   return e == cudaSuccess ? YTN_OK : cuda_fail(e, "timing the contraction paths");
 }
 
+// The copy launch of items [b, e) of the plan's job table, with the kernel built for
+// the most dims those items have (cached per range: a range's items never change).
+static cudaError_t copy_range(ytn_plan_t *p, int64_t b, int64_t e, const double *src, double *dst,
+                              cudaStream_t st) {
+  int nd = kMaxCopyDims;
+  if (e > b && e <= (int64_t)p->items.size()) {
+    const int64_t key = (b << 32) + e;
+    std::lock_guard<std::mutex> lk(p->nd_mu);
+    auto it = p->nd_max.find(key);
+    if (it != p->nd_max.end()) {
+      nd = it->second;
+    } else {
+      int m = 1;
+      for (int64_t i = b; i < e; i++) m = std::max(m, p->items[i].kind & 255);
+      p->nd_max.emplace(key, m);
+      nd = m;
+    }
+  }
+  return launch_copy(p->d_jobs, p->d_items + b, e - b, src, dst, st, nd);
+}
+
 }  // namespace ytn
 
 using namespace ytn;
@@ -689,12 +710,12 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
       return cuda_fail(e, "memset B workspace");
     {
       PhaseTimer t(p->ctx, YTN_PHASE_GATHER_A, st);
-      e = launch_copy(p->d_jobs, p->d_items + p->items_a_begin, p->items_a_end - p->items_a_begin, a, wa, st);
+      e = copy_range(p, p->items_a_begin, p->items_a_end, a, wa, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gather A");
     {
       PhaseTimer t(p->ctx, YTN_PHASE_GATHER_B, st);
-      e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, b, wb, st);
+      e = copy_range(p, p->items_b_begin, p->items_b_end, b, wb, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gather B");
   }
@@ -759,7 +780,7 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
     if (p->ca * p->cb > 1)
       e = launch_cscatter(p->d_cs_jobs, (int64_t)p->cs_jobs.size(), wc, c, st);
     else
-      e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, wc, c, st);
+      e = copy_range(p, p->items_c_begin, p->items_c_end, wc, c, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "scatter C");
   return YTN_OK;
@@ -997,7 +1018,7 @@ static ytn_status run_move(ytn_plan_t *p, Kind k, const double *a, double *out, 
       return cuda_fail(e, "trace");
     return YTN_OK;
   }
-  if ((e = launch_copy(p->d_jobs, p->d_items + p->items_a_begin, p->items_a_end - p->items_a_begin, a, out, st)) !=
+  if ((e = copy_range(p, p->items_a_begin, p->items_a_end, a, out, st)) !=
       cudaSuccess)
     return cuda_fail(e, what);
   return YTN_OK;
@@ -1051,22 +1072,22 @@ static ytn_status run_decomp(ytn_plan_t *p, Kind kind, const double *a, double *
   cudaError_t e;
   if (p->svd_zero_m && (e = cudaMemsetAsync(ws, 0, p->svd_m_doubles * sizeof(double), st)) != cudaSuccess)
     return cuda_fail(e, "memset sector matrices");
-  if ((e = launch_copy(p->d_jobs, p->d_items + p->items_a_begin, p->items_a_end - p->items_a_begin, a, ws, st)) !=
+  if ((e = copy_range(p, p->items_a_begin, p->items_a_end, a, ws, st)) !=
       cudaSuccess)
     return cuda_fail(e, "gather sector matrices");
   ytn_status r = svd_factor(p, ws, st);
   if (r != YTN_OK) return r;
   if (p->outs[0].size && (e = cudaMemsetAsync(s, 0, (size_t)p->outs[0].size * sizeof(double), st)) != cudaSuccess)
     return cuda_fail(e, "memset S");
-  if ((e = launch_copy(p->d_jobs, p->d_items + p->items_h_begin, p->items_h_end - p->items_h_begin, ws, ws, st)) !=
+  if ((e = copy_range(p, p->items_h_begin, p->items_h_end, ws, ws, st)) !=
       cudaSuccess)
     return cuda_fail(e, "conjugate a factor");
-  if ((e = launch_copy(p->d_jobs, p->d_items + p->items_b_begin, p->items_b_end - p->items_b_begin, ws, u, st)) !=
+  if ((e = copy_range(p, p->items_b_begin, p->items_b_end, ws, u, st)) !=
           cudaSuccess ||
       (has_v &&
-       (e = launch_copy(p->d_jobs, p->d_items + p->items_c_begin, p->items_c_end - p->items_c_begin, ws, v, st)) !=
+       (e = copy_range(p, p->items_c_begin, p->items_c_end, ws, v, st)) !=
            cudaSuccess) ||
-      (e = launch_copy(p->d_jobs, p->d_items + p->items_s_begin, p->items_s_end - p->items_s_begin, ws, s, st)) !=
+      (e = copy_range(p, p->items_s_begin, p->items_s_end, ws, s, st)) !=
           cudaSuccess)
     return cuda_fail(e, "write the factors");
   return YTN_OK;

@@ -154,12 +154,17 @@ __device__ __forceinline__ void stage_dispatch(bool dense_src, const CopyJob *Js
 }
 
 // One work item: its pieces' parameters into shared memory, then the staged move.
+// MAXND: the most dims an item of the launch has (the host reads it from the job
+// table). Instantiated for at most 4 dims the kernel needs 48 registers instead
+// of 64 and fits five CTAs per SM instead of four.
+template <int MAXND>
 __device__ __forceinline__ void run_item(const CopyJob *__restrict__ jobs, const CopyItem &it,
                                          const double *__restrict__ src, double *__restrict__ dst, CopyJob *Js,
                                          double *stage) {
   const int nj = it.njobs, total = it.total, nd = it.kind & 255, mode = it.kind >> 8;
-  // the planner never makes other items
-  if (nj < 1 || nj > kStageJobs || total < 1 || total > kStageElems || nd < 1 || nd > kMaxCopyDims) return;
+  // the planner never makes other items, and the host never launches an item with
+  // more dims than MAXND
+  if (nj < 1 || nj > kStageJobs || total < 1 || total > kStageElems || nd < 1 || nd > MAXND) return;
   {
     const int32_t *s = reinterpret_cast<const int32_t *>(jobs + it.job);
     int32_t *d = reinterpret_cast<int32_t *>(Js);
@@ -172,20 +177,27 @@ __device__ __forceinline__ void run_item(const CopyJob *__restrict__ jobs, const
     case 2: stage_dispatch<2>(dense_src, Js, nj, total, src, dst, stage); break;
     case 3: stage_dispatch<3>(dense_src, Js, nj, total, src, dst, stage); break;
     case 4: stage_dispatch<4>(dense_src, Js, nj, total, src, dst, stage); break;
-    case 5: stage_dispatch<5>(dense_src, Js, nj, total, src, dst, stage); break;
-    case 6: stage_dispatch<6>(dense_src, Js, nj, total, src, dst, stage); break;
-    case 7: stage_dispatch<7>(dense_src, Js, nj, total, src, dst, stage); break;
-    default: stage_dispatch<8>(dense_src, Js, nj, total, src, dst, stage); break;
+    default:
+      if constexpr (MAXND > 4) {
+        switch (nd) {
+          case 5: stage_dispatch<5>(dense_src, Js, nj, total, src, dst, stage); break;
+          case 6: stage_dispatch<6>(dense_src, Js, nj, total, src, dst, stage); break;
+          case 7: stage_dispatch<7>(dense_src, Js, nj, total, src, dst, stage); break;
+          default: stage_dispatch<8>(dense_src, Js, nj, total, src, dst, stage); break;
+        }
+      }
+      break;
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) copy_kernel(const CopyJob *__restrict__ jobs,
-                                                           const CopyItem *__restrict__ items,
-                                                           const double *__restrict__ src,
-                                                           double *__restrict__ dst) {
+template <int MAXND>
+__global__ void __launch_bounds__(kThreads, MAXND <= 4 ? 5 : 4) copy_kernel(const CopyJob *__restrict__ jobs,
+                                                                           const CopyItem *__restrict__ items,
+                                                                           const double *__restrict__ src,
+                                                                           double *__restrict__ dst) {
   __shared__ CopyJob Js[kStageJobs];
   __shared__ double stage[kStageElems];
-  run_item(jobs, items[blockIdx.x], src, dst, Js, stage);
+  run_item<MAXND>(jobs, items[blockIdx.x], src, dst, Js, stage);
 }
 
 // Gathers of the sectors that the split path's accuracy check flagged (FP64
@@ -216,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 4) copy_flagged_kernel(const CopyJob
     const int first = which == 0 ? sc.ga0 : sc.gb0;
     const int local = t - (lo > 0 ? item_end[lo - 1] : 0);
     __syncthreads();   // the previous item's shared memory is no longer read
-    run_item(jobs, items[first + local], src, dst, Js, stage);
+    run_item<kMaxCopyDims>(jobs, items[first + local], src, dst, Js, stage);
   }
 }
 
@@ -307,10 +319,11 @@ cudaError_t launch_cscatter(const CScatterJob *jobs, int64_t njobs, const double
 }
 
 cudaError_t launch_copy(const CopyJob *jobs, const CopyItem *items, int64_t nitems, const double *src,
-                        double *dst, cudaStream_t stream) {
+                        double *dst, cudaStream_t stream, int max_nd) {
   if (nitems <= 0) return cudaSuccess;
-  if (nitems > INT32_MAX) return cudaErrorInvalidValue;
-  copy_kernel<<<(unsigned)nitems, kThreads, 0, stream>>>(jobs, items, src, dst);
+  if (nitems > INT32_MAX || max_nd < 1 || max_nd > kMaxCopyDims) return cudaErrorInvalidValue;
+  if (max_nd <= 4) copy_kernel<4><<<(unsigned)nitems, kThreads, 0, stream>>>(jobs, items, src, dst);
+  else copy_kernel<kMaxCopyDims><<<(unsigned)nitems, kThreads, 0, stream>>>(jobs, items, src, dst);
   return cudaGetLastError();
 }
 

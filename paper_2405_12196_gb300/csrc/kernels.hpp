@@ -8,8 +8,10 @@
 namespace ytn {
 
 // Move blocks between layouts: items[0..nitems) of the job table, src -> dst.
+// max_nd: the most dims any of these items has (kind & 255); at most 4 selects the
+// kernel with fewer registers.
 cudaError_t launch_copy(const CopyJob *jobs, const CopyItem *items, int64_t nitems, const double *src,
-                        double *dst, cudaStream_t stream);
+                        double *dst, cudaStream_t stream, int max_nd = kMaxCopyDims);
 
 // Trace: one CTA per output block.
 cudaError_t launch_trace(const TraceOut *outs, int64_t nout, const TraceContrib *contribs,

@@ -424,6 +424,10 @@ struct ytn_plan_s {
   const ytn::SplitItem *d_sp_exp_items = nullptr, *d_sp_slice_items = nullptr;
   const ytn::SplitSector *d_sp_sectors = nullptr;
   const ytn::SplitTile *d_sp_tiles = nullptr, *d_sp_tiles_mix = nullptr;
+  // the most dims of any copy item in a range [begin, end) of `items` (selects the
+  // copy kernel built for at most 4 dims), computed on first use
+  std::mutex nd_mu;
+  std::unordered_map<int64_t, int> nd_max;   // key: begin * 2^32 + end
 };
 
 namespace ytn {

@@ -430,3 +430,28 @@ def test_tuning_of_a_new_plan_is_undecided(hctx):
         with pytest.raises(ytn.YtnError) as e:
             ytn.ytn_plan_tuning(plan, s)
         assert e.value.name == "YTN_E_INVALID"
+
+
+def test_sector_subset_workload_keeps_whole_sectors():
+    """The profiling-size workload is every block of a subset of the full contraction's
+    sectors: its blocks and their data are the full tensors', and each kept sector keeps
+    all of its blocks on both sides."""
+    full = W.config5(seed=5001, D=14)
+    part = W.config5_sectors(seed=5001, D=14)
+    for name, legs in (("A", (1, 2)), ("B", (0, 1))):
+        F, P = full[name], part[name]
+        size = np.prod(F["D"], axis=1)
+        off = np.concatenate([[0], np.cumsum(size)])
+        index = {tuple(map(tuple, t)): i for i, t in enumerate(F["t"])}
+        key = lambda t: tuple(t[legs[0]] - t[legs[1]])
+        kept = {key(t) for t in P["t"]}
+        assert 0 < len(kept) < len({key(t) for t in F["t"]})
+        pos = 0
+        for t, d in zip(P["t"], P["D"]):
+            i = index[tuple(map(tuple, t))]
+            np.testing.assert_array_equal(d, F["D"][i])
+            n = int(np.prod(d))
+            np.testing.assert_array_equal(P["data"][pos:pos + n], F["data"][off[i]:off[i + 1]])
+            pos += n
+        assert pos == P["data"].size
+        assert len(P["t"]) == sum(1 for t in F["t"] if key(t) in kept)
