@@ -31,11 +31,13 @@
 //   warp 1     MMA issuer (one thread): tcgen05.mma kind::f16, M = N = 128, K = 16;
 //              the drain of the exact accumulators overlaps a chunk's last R
 //              products, the drain of R the next chunk's first exact products;
-//   warps 2-3  idle;
-//   warps 4-15 epilogue: chunk drains and the FP64 output (three warps per
-//              32-lane quarter of tensor memory, 40, 40 and 48 columns), which
-//              keeps the 64-bit accumulators in registers under the 128-register
-//              budget of a 512-thread CTA.
+//   warps 2-17 epilogue: chunk drains and the FP64 output (four warps per
+//              32-lane quarter of tensor memory, 32 columns each; warp 2 also
+//              allocates and frees tensor memory), which keeps the 64-bit
+//              accumulators in registers under the 96-register budget of a
+//              576-thread CTA. At five slices the drain of the exact accumulators
+//              is not hidden behind the last stage's R products; four warps per
+//              quarter instead of three shorten it.
 // Every wait is bounded; on expiry the kernel records a status code, stops
 // issuing work, waits (bounded) for its own copies and MMAs and frees tensor
 // memory before returning.
@@ -47,9 +49,9 @@ namespace ytn {
 
 namespace {
 
-constexpr int kThreads = 512;     // 16 warps
-constexpr int kFirstEpiWarp = 4;  // warps 4..15: epilogue
-constexpr int kEpiWarps = 12;
+constexpr int kThreads = 576;     // 18 warps
+constexpr int kFirstEpiWarp = 2;  // warps 2..17: epilogue
+constexpr int kEpiWarps = 16;
 constexpr int kStagesRing = 2;
 constexpr int kSlotBytes = 2 * kBlockBytes;
 constexpr int kChunk = 8;         // K stages per exact-accumulation chunk (K 256)
@@ -347,9 +349,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp >= kFirstEpiWarp) {
     // ---------------------------------------------------------------- epilogue
-    // three warps per 32-lane quarter of tensor memory; columns [c0, c0 + w) with
-    // w = 40, 40, 48 in a 128-wide tile and 24, 24, 16 in a 64-wide one
-    const int quarter = warp & 3, third = (warp - kFirstEpiWarp) >> 2;
+    // four warps per 32-lane quarter of tensor memory; columns [c0, c0 + w) with
+    // w = 32 in a 128-wide tile and 16 in a 64-wide one
+    const int quarter = warp & 3, part = (warp - kFirstEpiWarp) >> 2;
     const int rl = quarter * 32 + lane;          // row inside the tile (tensor memory lane)
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     uint32_t cc = 0, tcount = 0;
@@ -358,18 +360,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const SplitTile tl = tiles[t];
       const SplitSector sc = sectors[tl.sector];
       const bool narrow = MIX && tl.bn == 64;
-      const int c0 = narrow ? third * 24 : third * 40;                                  // first column
-      const int ngroups = narrow ? (third == 2 ? 4 : 6) : (third == 2 ? 12 : 10);      // groups of 4 columns
+      const int c0 = narrow ? part * 16 : part * 32;   // first column
+      const int ngroups = narrow ? 4 : 8;              // groups of 4 columns
       const int nchunks = (sc.ks + kChunk - 1) / kChunk;
-      long long acc[48];
+      long long acc[32];
 #pragma unroll
-      for (int j = 0; j < 48; j++) acc[j] = 0;
+      for (int j = 0; j < 32; j++) acc[j] = 0;
       for (int c = 0; c < nchunks && ok; c++, cc++) {
         ok = mbar_wait(bar(kEFull), cc & 1, abort_flag, status, 7);
         if (!ok) break;
         tc_fence_after();
 #pragma unroll
-        for (int g = 0; g < 12; g++) {
+        for (int g = 0; g < 8; g++) {
           if (g < ngroups) {
             uint32_t v2[4], v3[4], v4[4];
             tmem_ld4(lane_addr + kColE2 + c0 + g * 4, v2);
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         tc_fence_after();
 #pragma unroll
-        for (int g = 0; g < 6; g++) {
+        for (int g = 0; g < 4; g++) {
           if (g < ngroups / 2) {
             uint32_t vr[8];
             tmem_ld8(lane_addr + kColR + c0 + g * 8, vr);
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int n0 = tl.nt * (narrow ? 64 : kSplitBM) + c0;
         const int32_t *fcol = eb + sc.eb_off + n0;
 #pragma unroll
-        for (int j = 0; j < 48; j++) {
+        for (int j = 0; j < 32; j++) {
           if (j < ngroups * 4 && n0 + j < sc.N) {
             const int fj = __ldg(fcol + j);
             crow[n0 + j] = scaled_double(acc[j], ei + fj - 40);
