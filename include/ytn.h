@@ -216,7 +216,9 @@ typedef struct {
                                 every block once unit dims are dropped and
                                 contiguous ones merged); 0: it gathers FP64
                                 sector matrices first                          */
-  int32_t reserved;
+  int32_t max_copy_dims;     /* most dims of any piece of the plan's data movers
+                                (after merging contiguous dims); up to 4 runs the
+                                copy kernel built for four, more the one for eight */
 } ytn_plan_info;
 
 /* Per-call result of ytn_tensordot, filled when the call returns (before the

@@ -611,6 +611,9 @@ ytn_status ytn_plan_get_info(const ytn_plan_t *p, ytn_plan_info *info) {
   info->out_size = p->out.size;
   info->njobs = (int64_t)p->jobs.size();
   info->split_fused = p->sp_fused ? 1 : 0;
+  int nd = 0;
+  for (const CopyItem &it : p->items) nd = std::max(nd, it.kind & 255);
+  info->max_copy_dims = nd;
   return YTN_OK;
 }
 

@@ -81,7 +81,7 @@ class ytn_plan_info(C.Structure):
                 ("max_n", C.c_int64), ("max_k", C.c_int64), ("a_elems", C.c_int64),
                 ("b_elems", C.c_int64), ("c_elems", C.c_int64), ("moved_elems", C.c_int64),
                 ("out_size", C.c_int64), ("njobs", C.c_int64), ("split_fused", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("max_copy_dims", C.c_int32)]
 
 
 NPHASES = 8

@@ -455,3 +455,17 @@ def test_sector_subset_workload_keeps_whole_sectors():
             pos += n
         assert pos == P["data"].size
         assert len(P["t"]) == sum(1 for t in F["t"] if key(t) in kept)
+
+
+def test_piece_dims_of_interleaved_and_merged_contractions(hctx):
+    """The copy pieces of a contraction over every other leg of a rank-8 tensor keep
+    eight dims (nothing merges); a contraction of trailing legs merges to at most four."""
+    legs = [W.Leg(s, [(0,), (1,)], [2, 3]) for s in (1, -1, 1, -1, 1, -1, 1, -1)]
+    A = W.random_tensor((0,), legs, (0,), 81)
+    legsB = [legs[1].conj(), legs[3].conj(), legs[5].conj(), legs[7].conj(), W.Leg(1, [(0,)], [3])]
+    B = W.random_tensor((0,), legsB, (2,), 82)
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, A, B, (1, 3, 5, 7), (0, 1, 2, 3))
+    assert plan.info["max_copy_dims"] == 8
+    cfg = W.config1()
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, cfg["A"], cfg["B"], cfg["axa"], cfg["axb"])
+    assert 1 <= plan.info["max_copy_dims"] <= 4

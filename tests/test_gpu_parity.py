@@ -465,3 +465,22 @@ def test_u1u1_tensordot(ctx, case, split):
         _, rec, res = run_tensordot(ctx, A, B, axa, axb)
     assert res["useful_flops"] > 0
     check_against_oracle(rec, oracle_tensordot(A, B, axa, axb), rtol=SPLIT_RTOL if split else FP64_RTOL)
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_interleaved_legs_need_eight_dim_pieces(ctx, split):
+    """Contracting every other leg of a rank-8 tensor (dims 2 or 3 per charge, so no
+    unit dim disappears): in A's gather no two neighbouring dims merge, so its pieces
+    keep eight dims (the copy kernel's instantiation for up to eight dims; the split
+    path takes its staged slicing, the fused tables allowing three dims per side)."""
+    from paper_2405_12196_gb300 import ytn
+    legs = [W.Leg(s, [(0,), (1,)], [2, 3]) for s in (1, -1, 1, -1, 1, -1, 1, -1)]
+    A = W.random_tensor((0,), legs, (0,), 81)
+    legsB = [legs[1].conj(), legs[3].conj(), legs[5].conj(), legs[7].conj(), W.Leg(1, [(0,)], [3])]
+    B = W.random_tensor((0,), legsB, (2,), 82)
+    axa, axb = (1, 3, 5, 7), (0, 1, 2, 3)
+    prec = ytn.YTN_SPLIT_BF16 if split else ytn.YTN_FP64
+    plan, rec, _ = run_tensordot(ctx, A, B, axa, axb, prec=prec, rtol=SPLIT_RTOL if split else 0.0)
+    if split:
+        assert plan.info["split_fused"] == 0
+    check_against_oracle(rec, oracle_tensordot(A, B, axa, axb), rtol=SPLIT_RTOL if split else FP64_RTOL)
