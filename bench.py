@@ -789,10 +789,14 @@ def run_ours(args):
         "latency_ms": m["latency_ms"],
         "clocks": m["head"]["clocks"],
         "e2e": m["e2e"],
-        # kernels of the library per timed region (the split phase launches two, the
-        # accuracy check two)
+        # kernels of the library per timed region: one per phase call, plus the second
+        # kernel of the split phase (exponents and slices, or row maxima and digits)
+        # and the rest of the check phase (the FP64 recomputation; on the fused path
+        # also the gathers of the recomputed sectors, two launches; the workloads here
+        # have every block of a sector, so no zero fill)
         "gpu_launches": int(sum(v["calls"] for v in ph.values()) + ph.get("split", {}).get("calls", 0)
-                            + ph.get("check", {}).get("calls", 0)),
+                            + ph.get("check", {}).get("calls", 0)
+                            * (3 if m["head"]["res"].get("split_variant") == 1 else 1)),
         "roofline": m["roofline"],
         "phases_ms": ph,
         "data_movers": m["data_movers"],
