@@ -269,19 +269,16 @@ static const double kEtaFp64 = std::ldexp(1.0, -52);
 // checks its result on the device (split_check.cu) and recomputes on the FP64
 // path the sectors whose data make the estimate exceed rtol. The slice count is
 // the smallest s >= 4 whose forecast is at most rtol (s = 5 for rtol = 1e-10).
-static double split_error_estimate(int s, int64_t kmax) {
-  (void)kmax;
-  return 128.0 * split_eta(s);
-}
+static double split_error_estimate(int s) { return 128.0 * split_eta(s); }
 
 static ytn_status choose_slices(const ytn_plan_t *p, double rtol, int &s, double &est) {
   if (p->max_k > 16384) return fail(YTN_E_UNSUPPORTED, "split path supports K up to 16384 per sector");
   if (!(rtol > 0.0)) return fail(YTN_E_TOLERANCE, "split path needs rtol > 0");
   for (s = 4; s <= kSlices; s++) {   // orders 0..2 are exact, so at least 4 slices
-    est = split_error_estimate(s, p->max_k);
+    est = split_error_estimate(s);
     if (est <= rtol) return YTN_OK;
   }
-  est = split_error_estimate(kSlices, p->max_k);
+  est = split_error_estimate(kSlices);
   return fail(YTN_E_TOLERANCE, "rtol below what the split path can reach for this plan");
 }
 
