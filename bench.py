@@ -762,6 +762,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     PREC = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}
+    if args.precision not in PREC:
+        raise SystemExit("--precision auto applies to --serving only")
     prec = PREC[args.precision]
     extras = rank == 0 and world == 1 and not args.no_extras and args.workload == "cfg5"
 
@@ -931,7 +933,7 @@ def run_serving(args):
 
     from paper_2405_12196_gb300 import ytn
     dev = torch.device("cuda:0")
-    prec = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16}[args.precision]
+    prec = {"fp64": ytn.YTN_FP64, "split": ytn.YTN_SPLIT_BF16, "auto": ytn.YTN_AUTO}[args.precision]
     ctx = ytn.ytn_ctx_create(0)
     sm = serving_summary(args, ytn, ctx, dev, prec, args.serve_runs, args.serve_requests)
     line = {
@@ -1212,7 +1214,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
+    ap.add_argument("--precision", default="split", choices=["fp64", "split", "auto"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--workload", default="cfg5", choices=sorted(WORKLOAD_DESC))
