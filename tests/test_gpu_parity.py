@@ -298,12 +298,14 @@ def test_split_tiles_chunks_and_ragged_tails(ctx, dims):
 
 
 @pytest.mark.parametrize("sign", [1.0, -1.0])
-def test_split_extreme_digits_fill_the_exact_accumulators(ctx, sign):
-    """Every element just below a power of two has leading digit +-128, so over a
-    full chunk of 256 the order-0 accumulator reaches exactly +-2^22, the end of its
-    exact range; the result must still be right."""
+@pytest.mark.parametrize("K", [512, 1024, 2048])
+def test_split_extreme_digits_fill_the_exact_accumulators(ctx, sign, K):
+    """Every element just below a power of two has leading digit +-128, so every
+    order-0 digit product is 2^14: over each chunk of 256 of K the order-0
+    accumulator reaches exactly +-2^22, the end of the range its drain reads from
+    the bit pattern; over several chunks (K = 1024, 2048) the drains add up exactly.
+    The result must still be right."""
     x = 2.0 - 2.0 ** -40
-    K = 512
     l_m, l_k, l_n = W.Leg(1, [(0,)], [130]), W.Leg(1, [(0,)], [K]), W.Leg(1, [(0,)], [129])
     A = W.random_tensor((0,), [l_m, l_k], (0,), 1)
     B = W.random_tensor((0,), [l_k.conj(), l_n], (0,), 2)
