@@ -79,11 +79,17 @@ def test_auto_picks_split_on_a_large_contraction(ctx):
     r = ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_AUTO, rtol=1e-10, workspace=ws)
     ytn.ytn_sync(ctx)
     assert r["precision"] == ytn.YTN_SPLIT_BF16 and r["slices"] == 5   # the forecast 128 eta(s) <= 1e-10 first holds at s = 5
+    # the first call timed both paths and kept the faster
+    t = ytn.ytn_plan_tuning(plan, 5)
+    assert t["auto_choice"] == 1 and 0 < t["split_ms"] < t["fp64_ms"]
 
 
 def test_auto_under_graph_capture_uses_the_model(ctx):
     import torch
     from paper_2405_12196_gb300 import ytn
+    # a context of its own: plans are cached per context, and this plan's choices
+    # must still be undecided when the capture starts
+    ctx = ytn.ytn_ctx_create(0)
     cfg = W.config3()
     X2 = cfg["X2"]
     dl = cfg["dleg"]
@@ -100,4 +106,7 @@ def test_auto_under_graph_capture_uses_the_model(ctx):
     ytn.ytn_sync(ctx, stream)
     ref = O.to_record(O.tensordot(O.from_record(X2), O.from_record(a), (1, 2), (0, 1)))
     assert rel_frobenius(dc[:n].cpu().numpy(), ref["data"]) <= 1e-10
+    # the cost model decided: a choice, no timings
+    t = ytn.ytn_plan_tuning(plan, 5)
+    assert t["auto_choice"] in (0, 1) and t["fp64_ms"] == 0.0 and t["split_ms"] == 0.0
     g.close()
