@@ -1285,7 +1285,7 @@ void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src) {
   // Fused path: items of 32 rows x 128 of K per operand, each with the parts of
   // the blocks inside it. Unit dims are dropped and neighbouring dims that are
   // contiguous in the block merged; a block with more than kFusedDims dims on
-  // either side, or spanning more than 2^31 elements, leaves the fused path off
+  // either side, or spanning more than 2^30 elements, leaves the fused path off
   // (the staged path gathers first). Three per side cover the contractions of the
   // CTM workloads (their free and contracted legs merge to one or two dims each).
   p->sp_fused = false;
@@ -1313,7 +1313,7 @@ void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src) {
       int64_t span = 0;   // largest offset of an element inside the block
       for (size_t i = 0; i < ss.fext.size(); i++) span += (ss.fext[i] - 1) * ss.fst[i];
       for (size_t i = 0; i < ss.kext.size(); i++) span += (ss.kext[i] - 1) * ss.kst[i];
-      if (span > INT32_MAX) return;
+      if (span > INT32_MAX / 2) return;   // 32-bit offsets, one step past the end included
     }
   // items: per operand (A of sector q is op 2q, B op 2q + 1), 32-row quarters of
   // the 128-row tiles x 128 of K
@@ -1356,7 +1356,6 @@ void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src) {
           const int64_t fs = ss.fst.empty() ? INT64_MAX : ss.fst.back();
           const int64_t kst = ss.kst.empty() ? INT64_MAX : ss.kst.back();
           g.rfast = fs < kst ? 1 : 0;
-          division_magic(g.rfast ? rb - ra : kb - ka, g.fmag, g.fshf);
           const int64_t it = item_base[o] + hr * nkq(op) + c;
           per_item[it].push_back(g);
           covered[it] += (rb - ra) * (kb - ka);
@@ -1376,6 +1375,13 @@ void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src) {
         si.nseg = (int32_t)per_item[it].size();
         const int64_t kc = std::min<int64_t>(kItemK, (int64_t)op.ks * kSplitBK - c * kItemK);
         si.full = covered[it] == kItemRows * kc ? 1 : 0;
+        int32_t cost = 0;   // warp-wide copy steps (at most 32 rows x 128 of K)
+        for (SliceSeg &g : per_item[it]) {
+          g.cost0 = cost;
+          const int32_t nr = g.r1 - g.r0, nk = g.k1 - g.k0;
+          cost += g.rfast ? nk : nr * ((nk + 31) / 32);
+        }
+        si.cost = cost;
         p->sp_fitems.push_back(si);
         p->sp_segs.insert(p->sp_segs.end(), per_item[it].begin(), per_item[it].end());
         if (p->sp_segs.size() > (size_t)INT32_MAX) {

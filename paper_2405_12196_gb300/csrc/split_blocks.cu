@@ -16,7 +16,8 @@
 // staged path moves 8 bytes in and out of an FP64 sector matrix first, then reads
 // it twice).
 //
-// Warps take whole segments. The walk follows the block's contiguous direction:
+// Every warp copies an equal share of the item: its segments are cut along the
+// direction the walk steps in. The walk follows the block's contiguous direction:
 // when its innermost free stride is the smaller the lanes are rows and the warp
 // steps along K, else the lanes are K and the warp steps along the rows. A lane's
 // offset is decomposed once (mixed radix over the block's free or contracted dims)
@@ -49,13 +50,14 @@ struct Smem {
 };
 
 // A mixed-radix index over up to kFusedDims dims (row-major, outer first) and its
-// element offset, stepped by one with carries (no division). The dims sit in the
-// last slots (unused outer slots: extent 1, stride 0), so that every index below is
-// a constant and the walker lives in registers.
+// element offset inside the block, stepped by one with carries (no division). The
+// dims sit in the last slots (unused outer slots: extent 1, stride 0), so that every
+// index below is a constant and the walker lives in registers. Offsets inside a
+// block fit 32 bits, one step past its last element included (the planner keeps
+// blocks spanning more than 2^30 elements off the fused path).
 struct Walker {
-  int32_t ext[kFusedDims], idx[kFusedDims];
-  int64_t st[kFusedDims];
-  int64_t off;
+  int32_t ext[kFusedDims], idx[kFusedDims], st[kFusedDims];
+  int32_t off;
 
   __device__ __forceinline__ void start(int i, int nd, const int32_t *e, const int64_t *s) {
     off = 0;
@@ -63,10 +65,10 @@ struct Walker {
     for (int d = kFusedDims - 1; d >= 0; d--) {
       const int k = d - (kFusedDims - nd);   // the dim in this slot, if any
       ext[d] = k >= 0 ? e[k] : 1;
-      st[d] = k >= 0 ? s[k] : 0;
+      st[d] = k >= 0 ? (int32_t)s[k] : 0;
       const int q = i / ext[d];
       idx[d] = i - q * ext[d];
-      off += (int64_t)idx[d] * st[d];
+      off += idx[d] * st[d];
       i = q;
     }
   }
@@ -79,7 +81,7 @@ struct Walker {
     for (int t = kFusedDims - 1; t > 0; t--) {
       if (idx[t] == ext[t]) {
         idx[t] = 0;
-        off -= (int64_t)ext[t] * st[t];
+        off -= ext[t] * st[t];
         idx[t - 1]++;
         off += st[t - 1];
       }
@@ -87,54 +89,87 @@ struct Walker {
   }
 };
 
-// The item's 32 x 128 elements into the tile (zero where no block lies). Warps take
-// whole segments; in a segment whose rows are the contiguous direction the lanes are
-// rows and the warp steps along K, else the lanes are K (four per lane) and the warp
-// steps along the rows. Offsets are decomposed once per lane and stepped after that.
+// Units [u0, u1) of a segment into the tile. rfast: a unit is one column of K, the
+// lanes its rows; else a unit is one row, the lanes its K (four per lane).
+__device__ __forceinline__ void load_units(Smem &sm, const SliceSeg &g, int u0, int u1, int lane,
+                                           const double *__restrict__ X) {
+  const int r0 = g.r0, nr = g.r1 - g.r0, k0 = g.k0, kc = g.k1 - g.k0;
+  const double *base = X + g.boff;
+  if (g.rfast) {
+    Walker kw;
+    kw.start(g.kbase + u0, g.nk, g.kext, g.kst);
+    const double *rb = base;
+    if (lane < nr) {
+      Walker rw;
+      rw.start(g.ibase + lane, g.nf, g.fext, g.fst);
+      rb += rw.off;
+    }
+    for (int k = u0; k < u1; k++) {
+      if (lane < nr) cp_async8(&sm.tile[r0 + lane][k0 + k], rb + kw.off);
+      kw.step();
+    }
+  } else {
+    int32_t ko[kItemK / 32];
+#pragma unroll
+    for (int q = 0; q < kItemK / 32; q++) {
+      ko[q] = 0;
+      if (lane + 32 * q < kc) {
+        Walker kw;
+        kw.start(g.kbase + lane + 32 * q, g.nk, g.kext, g.kst);
+        ko[q] = kw.off;
+      }
+    }
+    Walker rw;
+    rw.start(g.ibase + u0, g.nf, g.fext, g.fst);
+    for (int r = u0; r < u1; r++) {
+#pragma unroll
+      for (int q = 0; q < kItemK / 32; q++)
+        if (lane + 32 * q < kc) cp_async8(&sm.tile[r0 + r][k0 + lane + 32 * q], base + rw.off + ko[q]);
+      rw.step();
+    }
+  }
+}
+
+// The item's 32 x 128 elements into the tile (zero where no block lies). Each warp
+// takes an equal share [lo, hi) of the item's cost (warp-wide copy steps, summed
+// over the segments in order): the units of a segment whose starting cost falls in
+// that share. A unit u of a segment with starting cost c0 and unit cost w starts at
+// c0 + u w, so the warp's units are those with ceil((lo - c0) / w) <= u <
+// ceil((hi - c0) / w), and every unit goes to exactly one warp. Each lane looks at
+// one segment of a group of 32 and the warp takes the ones that meet its share in
+// order; offsets are decomposed once per lane and part, and stepped after that.
 __device__ __forceinline__ void load_item(Smem &sm, const SliceItem &it, const SliceSeg *__restrict__ segs,
                                           const double *__restrict__ X) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kThreads / 32;
   if (!it.full) {
     for (int w = tid; w < kItemRows * kItemK; w += kThreads) sm.tile[w / kItemK][w % kItemK] = 0ull;
     __syncthreads();   // zero fill before the copies land
   }
-  for (int j = warp; j < it.nseg; j += kThreads / 32) {
-    const SliceSeg &g = segs[it.seg0 + j];
-    const int r0 = g.r0, nr = g.r1 - g.r0, k0 = g.k0, kc = g.k1 - g.k0;
-    const double *base = X + g.boff;
-    if (g.rfast) {
-      Walker kw;
-      kw.start(g.kbase, g.nk, g.kext, g.kst);
-      int64_t ro = 0;
-      if (lane < nr) {
-        Walker rw;
-        rw.start(g.ibase + lane, g.nf, g.fext, g.fst);
-        ro = rw.off;
-      }
-      for (int k = 0; k < kc; k++) {
-        if (lane < nr) cp_async8(&sm.tile[r0 + lane][k0 + k], base + ro + kw.off);
-        kw.step();
-      }
-    } else {
-      int64_t ko[kItemK / 32];
-#pragma unroll
-      for (int q = 0; q < kItemK / 32; q++) {
-        ko[q] = 0;
-        if (lane + 32 * q < kc) {
-          Walker kw;
-          kw.start(g.kbase + lane + 32 * q, g.nk, g.kext, g.kst);
-          ko[q] = kw.off;
-        }
-      }
-      Walker rw;
-      rw.start(g.ibase, g.nf, g.fext, g.fst);
-      for (int r = 0; r < nr; r++) {
-#pragma unroll
-        for (int q = 0; q < kItemK / 32; q++)
-          if (lane + 32 * q < kc) cp_async8(&sm.tile[r0 + r][k0 + lane + 32 * q], base + rw.off + ko[q]);
-        rw.step();
-      }
+  const int lo = (warp * it.cost) / kWarps, hi = ((warp + 1) * it.cost) / kWarps;
+  const SliceSeg *sg = segs + it.seg0;
+  for (int j0 = 0; j0 < it.nseg && hi > lo; j0 += 32) {
+    const int j = j0 + lane;
+    int c0 = INT_MAX, c1 = INT_MAX;
+    if (j < it.nseg) {
+      c0 = sg[j].cost0;
+      c1 = j + 1 < it.nseg ? sg[j + 1].cost0 : it.cost;
     }
+    uint32_t meet = __ballot_sync(0xffffffffu, c0 < hi && c1 > lo);
+    const bool past = __any_sync(0xffffffffu, j < it.nseg && c1 >= hi);
+    while (meet) {
+      const int b = __ffs(meet) - 1;
+      meet &= meet - 1;
+      const int s0 = __shfl_sync(0xffffffffu, c0, b);
+      const SliceSeg &g = sg[j0 + b];
+      const int nr = g.r1 - g.r0, kc = g.k1 - g.k0;
+      const int w = g.rfast ? 1 : (kc + 31) / 32;
+      const int nu = g.rfast ? kc : nr;
+      const int u0 = lo > s0 ? (lo - s0 + w - 1) / w : 0;
+      const int u1 = min(nu, (hi - s0 + w - 1) / w);
+      if (u0 < u1) load_units(sm, g, u0, u1, lane, X);
+    }
+    if (past) break;   // later segments start at or beyond hi
   }
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();

@@ -147,10 +147,13 @@ static_assert(sizeof(SplitOperand) == 40, "SplitOperand layout");
 // item-relative) is the block's element (i, x) with i = ibase + r - r0 over the
 // free dims fext (row-major) and x = kbase + k - k0 over the contracted dims kext,
 // at boff + sum_d i_d fst_d + sum_d x_d kst_d doubles into the tensor's data.
-// A warp walks a segment with its lanes along the block's contiguous direction
-// (rfast: lanes are rows, the warp steps along K; else lanes are K, the warp steps
-// along rows). fmag / fshf: the division constants of the lanes' extent (r1 - r0
-// when rfast, else k1 - k0); the loader steps its indices and does not use them.
+// A segment is walked with the lanes along the block's contiguous direction
+// (rfast: lanes are rows and the walk steps along K; else lanes are K, four per
+// lane, and the walk steps along rows). Its cost is the number of warp-wide copy
+// steps: k1 - k0 when rfast, else (r1 - r0) * ceil((k1 - k0) / 32). cost0: the
+// summed cost of the item's segments before it; the loader gives each warp an
+// equal share of the item's total cost (SliceItem::cost), cutting segments along
+// their stepped direction.
 constexpr int kSegDims = 4;       // dims per side in the table
 constexpr int kFusedDims = 3;     // dims per side the planner puts on the fused path
 constexpr int kItemRows = 32;     // rows per fused work item
@@ -160,8 +163,8 @@ struct SliceSeg {
   int64_t fst[kSegDims], kst[kSegDims];
   int32_t fext[kSegDims], kext[kSegDims];
   int32_t ibase, kbase;
-  uint32_t fmag;
-  uint8_t fshf, nf, nk, rfast;
+  int32_t cost0;
+  uint8_t pad0, nf, nk, rfast;
   int16_t r0, r1, k0, k1;
 };
 static_assert(sizeof(SliceSeg) == 128, "SliceSeg layout");
@@ -170,7 +173,7 @@ struct SliceItem {
   int32_t op, rt, quarter, kq;  // 128-row tile rt, its 32-row quarter; K from 128 kq
   int32_t seg0, nseg;
   int32_t full;                 // the segments cover every element (no zero fill)
-  int32_t pad;
+  int32_t cost;                 // summed cost of the segments (warp-wide copy steps)
 };
 static_assert(sizeof(SliceItem) == 32, "SliceItem layout");
 
