@@ -43,42 +43,60 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
                : "memory");
 }
 
-struct Smem {
+struct __align__(16) Smem {
   unsigned long long tile[kItemRows][kPitch];
   int red[kThreads / 32][kItemRows];
   int rexp[kItemRows];
 };
 
-// A mixed-radix index over up to kFusedDims dims (row-major, outer first) and its
-// element offset inside the block, stepped by one with carries (no division). The
-// dims sit in the last slots (unused outer slots: extent 1, stride 0), so that every
-// index below is a constant and the walker lives in registers. Offsets inside a
-// block fit 32 bits, one step past its last element included (the planner keeps
-// blocks spanning more than 2^30 elements off the fused path).
-struct Walker {
-  int32_t ext[kFusedDims], idx[kFusedDims], st[kFusedDims];
+// Offset of index i over the nd dims of one side of a block (extents e and strides
+// s, outer first; nd <= kFusedDims): nd - 1 divisions. Offsets inside a block fit
+// 32 bits, one step past its last element included (the planner keeps blocks
+// spanning more than 2^30 elements off the fused path).
+__device__ __forceinline__ int32_t side_offset(int i, int nd, const int32_t *e, const int64_t *s) {
+  int32_t off = 0;
+#pragma unroll
+  for (int d = kFusedDims - 1; d >= 1; d--)
+    if (d < nd) {
+      const int q = i / e[d];
+      off += (i - q * e[d]) * (int32_t)s[d];
+      i = q;
+    }
+  return nd >= 1 ? off + i * (int32_t)s[0] : 0;
+}
+
+// A mixed-radix index over the ND dims of one side of a block (row-major, outer
+// first) and its offset, stepped by one with carries (no division).
+template <int ND>
+struct Stepper {
+  static constexpr int kN = ND > 0 ? ND : 1;
+  int32_t ext[kN], idx[kN], st[kN];
   int32_t off;
 
-  __device__ __forceinline__ void start(int i, int nd, const int32_t *e, const int64_t *s) {
+  __device__ __forceinline__ void start(int i, const int32_t *e, const int64_t *s) {
     off = 0;
 #pragma unroll
-    for (int d = kFusedDims - 1; d >= 0; d--) {
-      const int k = d - (kFusedDims - nd);   // the dim in this slot, if any
-      ext[d] = k >= 0 ? e[k] : 1;
-      st[d] = k >= 0 ? (int32_t)s[k] : 0;
-      const int q = i / ext[d];
-      idx[d] = i - q * ext[d];
+    for (int d = ND - 1; d >= 0; d--) {
+      ext[d] = e[d];
+      st[d] = (int32_t)s[d];
+      if (d > 0) {
+        const int q = i / ext[d];
+        idx[d] = i - q * ext[d];
+        i = q;
+      } else {
+        idx[d] = i;
+      }
       off += idx[d] * st[d];
-      i = q;
     }
   }
   // the next index (carries past the last valid index are harmless: the offset is
   // not used any more)
   __device__ __forceinline__ void step() {
-    idx[kFusedDims - 1]++;
-    off += st[kFusedDims - 1];
+    if (ND == 0) return;
+    idx[ND - 1]++;
+    off += st[ND - 1];
 #pragma unroll
-    for (int t = kFusedDims - 1; t > 0; t--) {
+    for (int t = ND - 1; t > 0; t--) {
       if (idx[t] == ext[t]) {
         idx[t] = 0;
         off -= ext[t] * st[t];
@@ -90,62 +108,63 @@ struct Walker {
 };
 
 // Units [u0, u1) of a segment into the tile. rfast: a unit is one column of K, the
-// lanes its rows; else a unit is one row, the lanes its K (four per lane).
+// lanes its rows; else a unit is one row, the lanes its K (four per lane). ND: the
+// dims of the stepped side (K when rfast, else the rows).
+template <int ND>
 __device__ __forceinline__ void load_units(Smem &sm, const SliceSeg &g, int u0, int u1, int lane,
                                            const double *__restrict__ X) {
   const int r0 = g.r0, nr = g.r1 - g.r0, k0 = g.k0, kc = g.k1 - g.k0;
   const double *base = X + g.boff;
   if (g.rfast) {
-    Walker kw;
-    kw.start(g.kbase + u0, g.nk, g.kext, g.kst);
+    Stepper<ND> kw;
+    kw.start(g.kbase + u0, g.kext, g.kst);
     const double *rb = base;
-    if (lane < nr) {
-      Walker rw;
-      rw.start(g.ibase + lane, g.nf, g.fext, g.fst);
-      rb += rw.off;
-    }
+    if (lane < nr) rb += side_offset(g.ibase + lane, g.nf, g.fext, g.fst);
+    unsigned long long *t = &sm.tile[r0 + lane][k0];
     for (int k = u0; k < u1; k++) {
-      if (lane < nr) cp_async8(&sm.tile[r0 + lane][k0 + k], rb + kw.off);
+      if (lane < nr) cp_async8(t + k, rb + kw.off);
       kw.step();
     }
   } else {
     int32_t ko[kItemK / 32];
 #pragma unroll
-    for (int q = 0; q < kItemK / 32; q++) {
-      ko[q] = 0;
-      if (lane + 32 * q < kc) {
-        Walker kw;
-        kw.start(g.kbase + lane + 32 * q, g.nk, g.kext, g.kst);
-        ko[q] = kw.off;
-      }
-    }
-    Walker rw;
-    rw.start(g.ibase + u0, g.nf, g.fext, g.fst);
+    for (int q = 0; q < kItemK / 32; q++)
+      ko[q] = lane + 32 * q < kc ? side_offset(g.kbase + lane + 32 * q, g.nk, g.kext, g.kst) : 0;
+    Stepper<ND> rw;
+    rw.start(g.ibase + u0, g.fext, g.fst);
     for (int r = u0; r < u1; r++) {
+      const double *rb = base + rw.off;
+      unsigned long long *t = &sm.tile[r0 + r][k0 + lane];
 #pragma unroll
       for (int q = 0; q < kItemK / 32; q++)
-        if (lane + 32 * q < kc) cp_async8(&sm.tile[r0 + r][k0 + lane + 32 * q], base + rw.off + ko[q]);
+        if (lane + 32 * q < kc) cp_async8(t + 32 * q, rb + ko[q]);
       rw.step();
     }
   }
 }
 
-// The item's 32 x 128 elements into the tile (zero where no block lies). Each warp
-// takes an equal share [lo, hi) of the item's cost (warp-wide copy steps, summed
-// over the segments in order): the units of a segment whose starting cost falls in
-// that share. A unit u of a segment with starting cost c0 and unit cost w starts at
-// c0 + u w, so the warp's units are those with ceil((lo - c0) / w) <= u <
-// ceil((hi - c0) / w), and every unit goes to exactly one warp. Each lane looks at
-// one segment of a group of 32 and the warp takes the ones that meet its share in
-// order; offsets are decomposed once per lane and part, and stepped after that.
-__device__ __forceinline__ void load_item(Smem &sm, const SliceItem &it, const SliceSeg *__restrict__ segs,
-                                          const double *__restrict__ X) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kWarps = kThreads / 32;
-  if (!it.full) {
-    for (int w = tid; w < kItemRows * kItemK; w += kThreads) sm.tile[w / kItemK][w % kItemK] = 0ull;
-    __syncthreads();   // zero fill before the copies land
+__device__ __forceinline__ void load_units_any(Smem &sm, const SliceSeg &g, int u0, int u1, int lane,
+                                               const double *__restrict__ X) {
+  switch (g.rfast ? g.nk : g.nf) {
+    case 0: load_units<0>(sm, g, u0, u1, lane, X); break;
+    case 1: load_units<1>(sm, g, u0, u1, lane, X); break;
+    case 2: load_units<2>(sm, g, u0, u1, lane, X); break;
+    default: load_units<3>(sm, g, u0, u1, lane, X); break;
   }
+}
+
+// This warp's share of an item: f(g, u0, u1) for the units [u0, u1) of each segment
+// g it takes. Each warp takes an equal share [lo, hi) of the item's cost (warp-wide
+// copy steps, summed over the segments in order): the units of a segment whose
+// starting cost falls in that share. A unit u of a segment with starting cost c0
+// and unit cost w starts at c0 + u w, so the warp's units are those with
+// ceil((lo - c0) / w) <= u < ceil((hi - c0) / w), and every unit goes to exactly one
+// warp. Each lane looks at one segment of a group of 32 and the warp takes the ones
+// that meet its share in order.
+template <class F>
+__device__ __forceinline__ void for_warp_share(const SliceItem &it, const SliceSeg *__restrict__ segs, F f) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kThreads / 32;
   const int lo = (warp * it.cost) / kWarps, hi = ((warp + 1) * it.cost) / kWarps;
   const SliceSeg *sg = segs + it.seg0;
   for (int j0 = 0; j0 < it.nseg && hi > lo; j0 += 32) {
@@ -167,44 +186,119 @@ __device__ __forceinline__ void load_item(Smem &sm, const SliceItem &it, const S
       const int nu = g.rfast ? kc : nr;
       const int u0 = lo > s0 ? (lo - s0 + w - 1) / w : 0;
       const int u1 = min(nu, (hi - s0 + w - 1) / w);
-      if (u0 < u1) load_units(sm, g, u0, u1, lane, X);
+      if (u0 < u1) f(g, u0, u1);
     }
     if (past) break;   // later segments start at or beyond hi
   }
+}
+
+// The item's 32 x 128 elements into the tile (zero where no block lies), offsets
+// decomposed once per lane and part and stepped after that.
+__device__ __forceinline__ void load_item(Smem &sm, const SliceItem &it, const SliceSeg *__restrict__ segs,
+                                          const double *__restrict__ X) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (!it.full) {   // the whole tile, pitch padding included, in 16-byte stores
+    uint4 *z = reinterpret_cast<uint4 *>(&sm.tile[0][0]);
+    for (int w = tid; w < (int)(sizeof(sm.tile) / 16); w += kThreads) z[w] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();   // zero fill before the copies land
+  }
+  for_warp_share(it, segs, [&](const SliceSeg &g, int u0, int u1) { load_units_any(sm, g, u0, u1, lane, X); });
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) split_rowmax_kernel(const SplitOperand *__restrict__ ops,
+// The biased exponent of the double at p, from its upper word.
+__device__ __forceinline__ int biased_exp_at(const double *p) {
+  return (int)((__ldg(reinterpret_cast<const unsigned int *>(p) + 1) >> 20) & 0x7FF);
+}
+
+// Row maxima of the biased exponent over units [u0, u1) of a segment, combined into
+// rmax (shared memory, one per row of the item). rfast: each lane keeps its row's
+// maximum over the K columns it steps through, eight loads in flight; else each row
+// is one step, its maximum reduced over the warp. ND: the dims of the stepped side.
+template <int ND>
+__device__ __forceinline__ void rowmax_units(int *rmax, const SliceSeg &g, int u0, int u1, int lane,
+                                             const double *__restrict__ X) {
+  const int r0 = g.r0, nr = g.r1 - g.r0, kc = g.k1 - g.k0;
+  const double *base = X + g.boff;
+  if (g.rfast) {
+    const bool act = lane < nr;
+    Stepper<ND> kw;
+    kw.start(g.kbase + u0, g.kext, g.kst);
+    const double *rb = base;
+    if (act) rb += side_offset(g.ibase + lane, g.nf, g.fext, g.fst);
+    int m = 0;
+    int k = u0;
+    for (; k + 8 <= u1; k += 8) {
+      int x[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        x[q] = act ? biased_exp_at(rb + kw.off) : 0;
+        kw.step();
+      }
+#pragma unroll
+      for (int q = 0; q < 8; q++) m = max(m, x[q]);
+    }
+    for (; k < u1; k++) {
+      if (act) m = max(m, biased_exp_at(rb + kw.off));
+      kw.step();
+    }
+    if (act) atomicMax(rmax + r0 + lane, m);
+  } else {
+    int32_t ko[kItemK / 32];
+#pragma unroll
+    for (int q = 0; q < kItemK / 32; q++)
+      ko[q] = lane + 32 * q < kc ? side_offset(g.kbase + lane + 32 * q, g.nk, g.kext, g.kst) : 0;
+    Stepper<ND> rw;
+    rw.start(g.ibase + u0, g.fext, g.fst);
+    for (int r = u0; r < u1; r++) {
+      const double *rb = base + rw.off;
+      int m = 0;
+#pragma unroll
+      for (int q = 0; q < kItemK / 32; q++)
+        if (lane + 32 * q < kc) m = max(m, biased_exp_at(rb + ko[q]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) atomicMax(rmax + r0 + r, m);
+      rw.step();
+    }
+  }
+}
+
+// Row maxima of the biased exponent over each item's elements, combined over the
+// row's items into its scale exponent (E = max - 1021, so that |x| < 2^(E - 1))
+// with atomicMax, and into the operand's largest. Rows without elements in the item
+// count as 0 (as zeros do). No staging: the elements are read straight into
+// registers, each warp taking its share of the item.
+__global__ void __launch_bounds__(kThreads, 6) split_rowmax_kernel(const SplitOperand *__restrict__ ops,
                                                                 const SliceItem *__restrict__ items,
                                                                 const SliceSeg *__restrict__ segs,
                                                                 const double *__restrict__ a,
                                                                 const double *__restrict__ b,
                                                                 int32_t *__restrict__ ea, int32_t *__restrict__ eb,
                                                                 int32_t *__restrict__ emax) {
-  __shared__ Smem sm;
+  __shared__ int rmax[kItemRows];
   const SliceItem it = items[blockIdx.x];
-  const SplitOperand o = ops[it.op];
   const bool isA = (it.op & 1) == 0;
-  load_item(sm, it, segs, isA ? a : b);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // lanes are rows (bank-friendly), warps take 16 elements each of the row; K
-  // stages past the operand's last are not in the tile (a multiple of 32 of K)
-  const int kcv = min(kItemK, o.ks * kSplitBK - it.kq * kItemK);
-  int m = 0;
-  if (warp * (kItemK / 8) < kcv)
-#pragma unroll
-    for (int j = 0; j < kItemK / 8; j++)
-      m = max(m, biased_exp(__longlong_as_double((long long)sm.tile[lane][warp * (kItemK / 8) + j])));
-  sm.red[warp][lane] = m;
+  const double *X = isA ? a : b;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < kItemRows) rmax[tid] = 0;
   __syncthreads();
-  if (warp == 0) {
-    int r = sm.red[0][lane];
-#pragma unroll
-    for (int w = 1; w < kThreads / 32; w++) r = max(r, sm.red[w][lane]);
+  for_warp_share(it, segs, [&](const SliceSeg &g, int u0, int u1) {
+    switch (g.rfast ? g.nk : g.nf) {
+      case 0: rowmax_units<0>(rmax, g, u0, u1, lane, X); break;
+      case 1: rowmax_units<1>(rmax, g, u0, u1, lane, X); break;
+      case 2: rowmax_units<2>(rmax, g, u0, u1, lane, X); break;
+      default: rowmax_units<3>(rmax, g, u0, u1, lane, X); break;
+    }
+  });
+  __syncthreads();
+  if (tid < 32) {
+    const SplitOperand &o = ops[it.op];
     const int row = it.rt * kSplitBM + it.quarter * kItemRows + lane;
     int mine = INT_MIN;
     if (row < o.rows) {
+      const int r = rmax[lane];
       atomicMax((isA ? ea : eb) + o.exp_off + row, r - 1021);
       mine = r - 1021;
     }
