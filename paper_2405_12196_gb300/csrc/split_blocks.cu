@@ -269,8 +269,9 @@ __device__ __forceinline__ void rowmax_units(int *rmax, const SliceSeg &g, int u
 // row's items into its scale exponent (E = max - 1021, so that |x| < 2^(E - 1))
 // with atomicMax, and into the operand's largest. Rows without elements in the item
 // count as 0 (as zeros do). No staging: the elements are read straight into
-// registers, each warp taking its share of the item.
-__global__ void __launch_bounds__(kThreads, 6) split_rowmax_kernel(const SplitOperand *__restrict__ ops,
+// registers, each warp taking its share of the item; eight CTAs per SM (32
+// registers) keep the most loads in flight (measured against six and four).
+__global__ void __launch_bounds__(kThreads, 8) split_rowmax_kernel(const SplitOperand *__restrict__ ops,
                                                                 const SliceItem *__restrict__ items,
                                                                 const SliceSeg *__restrict__ segs,
                                                                 const double *__restrict__ a,
