@@ -153,19 +153,18 @@ __device__ __forceinline__ void load_units_any(Smem &sm, const SliceSeg &g, int 
   }
 }
 
-// This warp's share of an item: f(g, u0, u1) for the units [u0, u1) of each segment
-// g it takes. Each warp takes an equal share [lo, hi) of the item's cost (warp-wide
-// copy steps, summed over the segments in order): the units of a segment whose
-// starting cost falls in that share. A unit u of a segment with starting cost c0
+// A warp's share of an item: f(g, u0, u1) for the units [u0, u1) of each segment g
+// whose units start inside the cost range [lo, hi) (for_warp_share: an equal share
+// of the item's cost, warp-wide copy steps summed over the segments in order, per
+// warp). A unit u of a segment with starting cost c0
 // and unit cost w starts at c0 + u w, so the warp's units are those with
 // ceil((lo - c0) / w) <= u < ceil((hi - c0) / w), and every unit goes to exactly one
 // warp. Each lane looks at one segment of a group of 32 and the warp takes the ones
 // that meet its share in order.
 template <class F>
-__device__ __forceinline__ void for_warp_share(const SliceItem &it, const SliceSeg *__restrict__ segs, F f) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kWarps = kThreads / 32;
-  const int lo = (warp * it.cost) / kWarps, hi = ((warp + 1) * it.cost) / kWarps;
+__device__ __forceinline__ void for_cost_range(const SliceItem &it, const SliceSeg *__restrict__ segs, int lo, int hi,
+                                               F f) {
+  const int lane = threadIdx.x & 31;
   const SliceSeg *sg = segs + it.seg0;
   for (int j0 = 0; j0 < it.nseg && hi > lo; j0 += 32) {
     const int j = j0 + lane;
@@ -190,6 +189,13 @@ __device__ __forceinline__ void for_warp_share(const SliceItem &it, const SliceS
     }
     if (past) break;   // later segments start at or beyond hi
   }
+}
+
+template <class F>
+__device__ __forceinline__ void for_warp_share(const SliceItem &it, const SliceSeg *__restrict__ segs, F f) {
+  const int warp = threadIdx.x >> 5;
+  constexpr int kWarps = kThreads / 32;
+  for_cost_range(it, segs, (warp * it.cost) / kWarps, ((warp + 1) * it.cost) / kWarps, f);
 }
 
 // The item's 32 x 128 elements into the tile (zero where no block lies), offsets
@@ -269,37 +275,57 @@ __device__ __forceinline__ void rowmax_units(int *rmax, const SliceSeg &g, int u
 // row's items into its scale exponent (E = max - 1021, so that |x| < 2^(E - 1))
 // with atomicMax, and into the operand's largest. Rows without elements in the item
 // count as 0 (as zeros do). No staging: the elements are read straight into
-// registers, each warp taking its share of the item; eight CTAs per SM (32
+// registers. A CTA takes two consecutive items (their records and segment tables
+// read together), its warps equal shares of their summed cost; eight CTAs per SM (32
 // registers) keep the most loads in flight (measured against six and four).
+constexpr int kRowmaxItems = 2;
+
 __global__ void __launch_bounds__(kThreads, 8) split_rowmax_kernel(const SplitOperand *__restrict__ ops,
-                                                                const SliceItem *__restrict__ items,
-                                                                const SliceSeg *__restrict__ segs,
-                                                                const double *__restrict__ a,
-                                                                const double *__restrict__ b,
-                                                                int32_t *__restrict__ ea, int32_t *__restrict__ eb,
-                                                                int32_t *__restrict__ emax) {
-  __shared__ int rmax[kItemRows];
-  const SliceItem it = items[blockIdx.x];
-  const bool isA = (it.op & 1) == 0;
-  const double *X = isA ? a : b;
-  const int tid = threadIdx.x, lane = tid & 31;
-  if (tid < kItemRows) rmax[tid] = 0;
+                                                                   const SliceItem *__restrict__ items, int nitems,
+                                                                   const SliceSeg *__restrict__ segs,
+                                                                   const double *__restrict__ a,
+                                                                   const double *__restrict__ b,
+                                                                   int32_t *__restrict__ ea, int32_t *__restrict__ eb,
+                                                                   int32_t *__restrict__ emax) {
+  __shared__ int rmax[kRowmaxItems][kItemRows];
+  __shared__ SliceItem rec[kRowmaxItems];
+  const int i0 = blockIdx.x * kRowmaxItems, ni = min(kRowmaxItems, nitems - i0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < kRowmaxItems * kItemRows) rmax[tid / kItemRows][tid % kItemRows] = 0;
+  if (tid < ni * (int)(sizeof(SliceItem) / 4))
+    reinterpret_cast<int32_t *>(rec)[tid] = reinterpret_cast<const int32_t *>(items + i0)[tid];
   __syncthreads();
-  for_warp_share(it, segs, [&](const SliceSeg &g, int u0, int u1) {
-    switch (g.rfast ? g.nk : g.nf) {
-      case 0: rowmax_units<0>(rmax, g, u0, u1, lane, X); break;
-      case 1: rowmax_units<1>(rmax, g, u0, u1, lane, X); break;
-      case 2: rowmax_units<2>(rmax, g, u0, u1, lane, X); break;
-      default: rowmax_units<3>(rmax, g, u0, u1, lane, X); break;
-    }
-  });
+  const SliceItem &it0 = rec[0], &it1 = rec[ni > 1 ? 1 : 0];
+  const int c0 = it0.cost, total = c0 + (ni > 1 ? it1.cost : 0);
+  constexpr int kWarps = kThreads / 32;
+  const int lo = (warp * total) / kWarps, hi = ((warp + 1) * total) / kWarps;
+#pragma unroll 1
+  for (int t = 0; t < kRowmaxItems; t++) {
+    if (t >= ni) break;
+    const SliceItem &it = t == 0 ? it0 : it1;
+    const int base = t == 0 ? 0 : c0;
+    const int l = max(lo - base, 0), h = min(hi - base, it.cost);
+    if (l >= h) continue;
+    const double *X = (it.op & 1) == 0 ? a : b;
+    int *rm = rmax[t];
+    for_cost_range(it, segs, l, h, [&](const SliceSeg &g, int u0, int u1) {
+      switch (g.rfast ? g.nk : g.nf) {
+        case 0: rowmax_units<0>(rm, g, u0, u1, lane, X); break;
+        case 1: rowmax_units<1>(rm, g, u0, u1, lane, X); break;
+        case 2: rowmax_units<2>(rm, g, u0, u1, lane, X); break;
+        default: rowmax_units<3>(rm, g, u0, u1, lane, X); break;
+      }
+    });
+  }
   __syncthreads();
-  if (tid < 32) {
+  if (warp < ni) {   // warp t flushes item t's rows
+    const SliceItem &it = warp == 0 ? it0 : it1;
+    const bool isA = (it.op & 1) == 0;
     const SplitOperand &o = ops[it.op];
     const int row = it.rt * kSplitBM + it.quarter * kItemRows + lane;
     int mine = INT_MIN;
     if (row < o.rows) {
-      const int r = rmax[lane];
+      const int r = rmax[warp][lane];
       atomicMax((isA ? ea : eb) + o.exp_off + row, r - 1021);
       mine = r - 1021;
     }
@@ -347,7 +373,8 @@ cudaError_t launch_split_blocks(const SplitOperand *ops, const SliceItem *items,
                                 int32_t *emax, uint8_t *sa, uint8_t *sb, int slices, cudaStream_t stream) {
   if (nitems <= 0) return cudaSuccess;
   if (nitems > INT32_MAX || slices < 1 || slices > kSlices) return cudaErrorInvalidValue;
-  split_rowmax_kernel<<<(unsigned)nitems, kThreads, 0, stream>>>(ops, items, segs, a, b, ea, eb, emax);
+  split_rowmax_kernel<<<(unsigned)((nitems + kRowmaxItems - 1) / kRowmaxItems), kThreads, 0, stream>>>(
+      ops, items, (int)nitems, segs, a, b, ea, eb, emax);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   split_digits_kernel<<<(unsigned)nitems, kThreads, 0, stream>>>(ops, items, segs, a, b, ea, eb, sa, sb, slices);

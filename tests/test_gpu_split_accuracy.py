@@ -242,6 +242,51 @@ def test_fused_split_path_on_the_environment_contraction(ctx):
     assert status == "YTN_OK" and rep["nfallback"] == 0
 
 
+def _interleaved_pair(pattern, seed):
+    """U(1) tensors whose contracted legs ('k') and free legs ('f') alternate as in
+    `pattern`, in both operands: no two neighbouring legs of a side merge, so each
+    side keeps two or three dims per block."""
+    lk = W.Leg(1, [(-1,), (0,), (1,)], [2, 3, 2])
+    lf = W.Leg(1, [(-1,), (0,), (1,)], [3, 2, 3])
+    A = W.random_tensor((0,), [lk if ch == "k" else lf for ch in pattern], (0,), seed)
+    B = W.random_tensor((0,), [lk.conj() if ch == "k" else W.Leg(-1, lf.t, [2, 2, 2]) for ch in pattern],
+                        (0,), seed + 1)
+    ax = tuple(i for i, ch in enumerate(pattern) if ch == "k")
+    return A, B, ax, ax
+
+
+@pytest.mark.parametrize("pattern", ["kfkf", "kfkfkf", "fkfk", "fkfkfk"])
+def test_fused_split_walks_unmerged_dims(pattern):
+    """The fused slicing walks a block side of two or three dims with its stepped
+    index: K when the block's rows are its contiguous direction (free leg last),
+    else the rows (contracted leg last). The first split call on a plan leaves the
+    fused candidate's result in C; it must meet the tolerance against the oracle,
+    and a later call (the autotuner's choice) must give the same bits."""
+    import torch
+    from gpu_helpers import check_against_oracle, oracle_tensordot
+    from paper_2405_12196_gb300 import ytn
+    A, B, axa, axb = _interleaved_pair(pattern, 31 + len(pattern))
+    fresh = ytn.ytn_ctx_create(0)   # the first call on this structure must be the timing one
+    plan = ytn.ytn_plan(fresh, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    assert plan.info["split_fused"] == 1
+    dev = torch.device("cuda:0")
+    da, db = torch.from_numpy(A["data"]).to(dev), torch.from_numpy(B["data"]).to(dev)
+    ws = torch.empty(ytn.ytn_workspace_size(plan, ytn.YTN_SPLIT_BF16, SPLIT_RTOL), dtype=torch.uint8, device=dev)
+    ref = oracle_tensordot(A, B, axa, axb)
+    outs = []
+    for call in range(2):
+        dc = torch.full((plan.out["size"],), float("nan"), dtype=torch.float64, device=dev)
+        res = ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_SPLIT_BF16, rtol=SPLIT_RTOL, workspace=ws)
+        ytn.ytn_sync(fresh)
+        if call == 0:
+            assert res["split_variant"] == 1
+        rec = dict(plan.out)
+        rec["data"] = dc.cpu().numpy()
+        check_against_oracle(rec, ref, rtol=SPLIT_RTOL)
+        outs.append(rec["data"])
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 def test_split_variants_give_identical_bits(ctx):
     """A plan with fused tables: the first split call times the staged and the fused
     variant (leaving the fused result) and caches the faster; later calls use the
