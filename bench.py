@@ -736,8 +736,11 @@ def measure_contraction(args, ytn, ctx, dev, cfg, world, rank, local, prec, step
     }
     if prec != ytn.YTN_FP64:
         out["split"] = {"slices": res["slices"],
-                        "variant": {1: "fused: slices straight from the blocks",
+                        "variant": {2: "fused and pipelined: slices straight from the blocks, each sector "
+                                       "group's slicing beside the previous group's GEMM",
+                                    1: "fused: slices straight from the blocks",
                                     0: "staged: FP64 sector matrices gathered first"}.get(res["split_variant"]),
+                        "pipe_groups": plan.info["split_pipe_groups"],
                         "narrow_sector_tails": bool(res.get("narrow_tiles", 0)),
                         "a_priori_err_est": res["err_est"],
                         "err_est": report["err_est"], "split_err_est": report["split_err_est"],
@@ -746,7 +749,8 @@ def measure_contraction(args, ytn, ctx, dev, cfg, world, rank, local, prec, step
         # the autotuner's record for this slice count: the candidates' times on the
         # plan's first call (ms, fastest of its rounds; 0 where not timed)
         tun = ytn.ytn_plan_tuning(plan, res["slices"])
-        out["split"]["tuning_ms"] = {k: tun[k] for k in ("staged_ms", "fused_ms", "wide_ms", "narrow_ms")}
+        out["split"]["tuning_ms"] = {k: tun[k] for k in ("staged_ms", "fused_ms", "pipelined_ms", "wide_ms",
+                                                         "narrow_ms")}
     return out
 
 
@@ -795,10 +799,13 @@ def run_ours(args):
         # kernel of the split phase (exponents and slices, or row maxima and digits)
         # and the rest of the check phase (the FP64 recomputation; on the fused path
         # also the gathers of the recomputed sectors, two launches; the workloads here
-        # have every block of a sector, so no zero fill)
+        # have every block of a sector, so no zero fill); the pipelined variant adds,
+        # inside its GEMM phase, one GEMM and two slicing launches per further group
         "gpu_launches": int(sum(v["calls"] for v in ph.values()) + ph.get("split", {}).get("calls", 0)
                             + ph.get("check", {}).get("calls", 0)
-                            * (3 if m["head"]["res"].get("split_variant") == 1 else 1)),
+                            * (3 if m["head"]["res"].get("split_variant") in (1, 2) else 1)
+                            + (ph.get("gemm", {}).get("calls", 0) * 3 * (m["split"]["pipe_groups"] - 1)
+                               if m["head"]["res"].get("split_variant") == 2 else 0)),
         "roofline": m["roofline"],
         "phases_ms": ph,
         "data_movers": m["data_movers"],

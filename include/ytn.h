@@ -219,6 +219,8 @@ typedef struct {
   int32_t max_copy_dims;     /* most dims of any piece of the plan's data movers
                                 (after merging contiguous dims); up to 4 runs the
                                 copy kernel built for four, more the one for eight */
+  int32_t split_pipe_groups; /* sector groups of the pipelined fused split (see
+                                ytn_tensordot), 0 when the plan has none       */
 } ytn_plan_info;
 
 /* Per-call result of ytn_tensordot, filled when the call returns (before the
@@ -233,9 +235,10 @@ typedef struct {
                                 The estimate of this result, computed on the
                                 device from its data, is in ytn_tensordot_report */
   int32_t split_variant;     /* split path: 1 when the BF16 slices were built
-                                straight from the blocks (fused), 0 when FP64
-                                sector matrices were gathered first (staged);
-                                -1 for FP64                                    */
+                                straight from the blocks (fused), 2 the same
+                                pipelined with the GEMM, 0 when FP64 sector
+                                matrices were gathered first (staged); -1 for
+                                FP64                                           */
   int32_t narrow_tiles;      /* split path: 1 when sectors whose N ends in the
                                 first half of a 128-wide tile had a 64-wide last
                                 column tile, else 0                            */
@@ -340,11 +343,13 @@ ytn_status ytn_plan_get_info(const ytn_plan_t *plan, ytn_plan_info *info);
 typedef struct ytn_tuning {
   int32_t slices;
   int32_t auto_choice;     /* YTN_AUTO: 0 FP64, 1 split */
-  int32_t split_variant;   /* 0 staged (FP64 sector matrices first), 1 fused */
+  int32_t split_variant;   /* 0 staged (FP64 sector matrices first), 1 fused,
+                              2 fused and pipelined with the GEMM */
   int32_t tile_policy;     /* 0 128-wide tiles only, 1 with 64-wide sector tails */
   float fp64_ms, split_ms; /* YTN_AUTO: the FP64 run and the fastest split candidate */
   float staged_ms, fused_ms;
   float wide_ms, narrow_ms;
+  float pipelined_ms;      /* the fused variant pipelined with the GEMM */
 } ytn_tuning;
 ytn_status ytn_plan_tuning(const ytn_plan_t *plan, int32_t slices, ytn_tuning *out);
 void ytn_plan_release(ytn_plan_t *plan);
@@ -397,7 +402,14 @@ ytn_status ytn_workspace_size_staged(const ytn_plan_t *plan, ytn_precision prec,
  * (an average of at least 1024 elements per block part). Operands read straight
  * from page-locked host memory (no staging workspace) always take the staged
  * variant, whose gathers read every block linearly over the host link.
- * res->split_variant reports the variant used.
+ * A large plan (sectors enough for at least two groups of about an eighth of the
+ * useful FLOPs and two waves of 128-wide tiles each) also times the fused variant
+ * pipelined with the GEMM: the sectors in groups, each group's slices built on
+ * the lowest-priority stream of the context while the previous group's GEMM runs
+ * on its highest-priority stream (a slicing CTA shares each SM with a GEMM CTA),
+ * forked from and joined to the caller's stream; one pipelined call is enqueued
+ * at a time per context, and a call on a stream being captured into a graph does
+ * not pipeline. res->split_variant reports the variant used.
  * Likewise the split GEMM's tile list: 128 x 128 tiles, or the same with a
  * 128 x 64 last column tile for every sector whose N ends in the first half of a
  * 128-wide tile (half of that tile's padded products saved); the first split call

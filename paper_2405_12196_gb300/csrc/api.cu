@@ -361,6 +361,7 @@ ytn_status ytn_ctx_create(ytn_ctx **ctx, int device) {
     return cuda_fail(e, "cudaDeviceGetAttribute");
   }
   e = configure_split_gemm();
+  if (e == cudaSuccess) e = configure_split_blocks();
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(e, "configure split-precision GEMM");
@@ -375,6 +376,30 @@ ytn_status ytn_ctx_create(ytn_ctx **ctx, int device) {
     cudaFree(c->status_dev);
     delete c;
     return cuda_fail(e, "cudaMemset status word");
+  }
+  // pipelined fused split: the GEMM chain on the highest-priority stream, so that
+  // its CTAs take the SMs before the slicing that runs beside them
+  {
+    int least = 0, greatest = 0;
+    cudaStream_t hi = nullptr, lo = nullptr;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&lo, cudaStreamNonBlocking, least);
+    for (int i = 0; e == cudaSuccess && i < kPipeGroups + 2; i++) {
+      cudaEvent_t ev = nullptr;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) c->pipe_ev.push_back(ev);
+    }
+    c->pipe_hi = hi;
+    c->pipe_lo = lo;
+    if (e != cudaSuccess) {
+      for (void *ev : c->pipe_ev) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
+      if (hi) cudaStreamDestroy(hi);
+      if (lo) cudaStreamDestroy(lo);
+      cudaFree(c->status_dev);
+      delete c;
+      return cuda_fail(e, "pipeline streams and events");
+    }
   }
   *ctx = c;
   return YTN_OK;
@@ -393,6 +418,9 @@ void ytn_ctx_destroy(ytn_ctx *ctx) {
   if (ctx->device >= 0) {
     DeviceGuard g(ctx->device);
     for (void *ev : ctx->ev_pool) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
+    for (void *ev : ctx->pipe_ev) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
+    if (ctx->pipe_hi) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->pipe_hi));
+    if (ctx->pipe_lo) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->pipe_lo));
     if (ctx->status_dev) cudaFree(ctx->status_dev);
     svd_release(ctx);
   }
@@ -611,6 +639,7 @@ ytn_status ytn_plan_get_info(const ytn_plan_t *p, ytn_plan_info *info) {
   int nd = 0;
   for (const CopyItem &it : p->items) nd = std::max(nd, it.kind & 255);
   info->max_copy_dims = nd;
+  info->split_pipe_groups = (int32_t)p->sp_pipe_tile_end.size();
   return YTN_OK;
 }
 
@@ -627,6 +656,7 @@ ytn_status ytn_plan_tuning(const ytn_plan_t *p, int32_t slices, ytn_tuning *out)
   out->split_ms = p->auto_ms[slices][1];
   out->staged_ms = p->variant_ms[slices][0];
   out->fused_ms = p->variant_ms[slices][1];
+  out->pipelined_ms = p->variant_ms[slices][2];
   out->wide_ms = p->tile_ms[slices][0];
   out->narrow_ms = p->tile_ms[slices][1];
   return YTN_OK;
@@ -693,7 +723,7 @@ ytn_status ytn_workspace_size(const ytn_plan_t *p, ytn_precision prec, double rt
 // One contraction on the chosen path; arguments already checked and mapped.
 static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b, double *c, bool split, int slices,
                                  double rtol, void *workspace, cudaStream_t st, bool fused_variant = false,
-                                 bool narrow_tails = false) {
+                                 bool narrow_tails = false, bool pipelined = false) {
   WsLayout w;
   workspace_layout(p, split, w);
   char *ws = static_cast<char *>(workspace);
@@ -729,33 +759,79 @@ static ytn_status exec_tensordot(ytn_plan_t *p, const double *a, const double *b
     float *normsq = reinterpret_cast<float *>(ws + w.normsq);
     SplitRecord *rec = reinterpret_cast<SplitRecord *>(ws + w.rec);
     uint8_t *sa = reinterpret_cast<uint8_t *>(ws + w.sa), *sb = reinterpret_cast<uint8_t *>(ws + w.sb);
-    {
-      PhaseTimer t(p->ctx, YTN_PHASE_SPLIT, st);
-      // the exponent kernels max-combine into EA, EB and EMAX: start from a value
-      // below every exponent (bytes 0x80: 0x80808080 as int32); the epilogue sums
-      // into NORMSQ and the check counts in the record: start from zero
-      e = cudaMemsetAsync(ea, 0x80, w.emax_end - w.ea, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(normsq, 0, w.rec_end - w.normsq, st);
-      if (e == cudaSuccess) {
-        if (fused)
-          e = launch_split_blocks(p->d_sp_ops, p->d_sp_fitems, (int64_t)p->sp_fitems.size(), p->d_sp_segs, a, b,
-                                  ea, eb, emax, sa, sb, slices, st);
-        else
-          e = launch_split_prep(p->d_sp_ops, p->d_sp_exp_items, (int64_t)p->sp_exp_items.size(),
-                                p->d_sp_slice_items, (int64_t)p->sp_slice_items.size(), wa, wb, ea, eb, emax, sa,
-                                sb, slices, st);
-      }
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "split into slices");
     const int sms = p->ctx->gemm_sms.load() > 0 ? p->ctx->gemm_sms.load() : p->ctx->num_sms;
-    {
-      PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
-      const bool mix = narrow_tails && !p->sp_tiles_mix.empty();
-      e = launch_gemm_split(p->d_sp_sectors, mix ? p->d_sp_tiles_mix : p->d_sp_tiles,
-                            (int64_t)(mix ? p->sp_tiles_mix.size() : p->sp_tiles.size()), sa, sb, ea, eb, emax,
-                            normsq, wc, slices, p->ctx->status_dev, sms, mix, st);
+    const size_t ngroups = p->sp_pipe_tile_end.size();
+    if (fused && pipelined && ngroups >= 2 && ngroups <= (size_t)kPipeGroups && p->ctx->pipe_hi) {
+      // Pipelined: the sectors in groups (the GEMM's order). Group 0 is sliced
+      // alone; then each group's GEMM runs while the next groups are sliced beside
+      // it on the same SMs (a slicing CTA fits next to a GEMM CTA), and each group's
+      // GEMM waits for its slices. The GEMM chain runs on the highest-priority
+      // stream, the slicing on the lowest, both forked from and joined to st.
+      std::lock_guard<std::mutex> lk(p->ctx->pipe_mu);
+      cudaStream_t hi = static_cast<cudaStream_t>(p->ctx->pipe_hi), lo = static_cast<cudaStream_t>(p->ctx->pipe_lo);
+      auto ev = [&](size_t i) { return static_cast<cudaEvent_t>(p->ctx->pipe_ev[i]); };
+      const std::vector<int64_t> &te = p->sp_pipe_tile_end, &ie = p->sp_pipe_item_end;
+      e = cudaEventRecord(ev(0), st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(hi, ev(0), 0);
+      if (e == cudaSuccess) {
+        PhaseTimer t(p->ctx, YTN_PHASE_SPLIT, hi);
+        e = cudaMemsetAsync(ea, 0x80, w.emax_end - w.ea, hi);
+        if (e == cudaSuccess) e = cudaMemsetAsync(normsq, 0, w.rec_end - w.normsq, hi);
+        if (e == cudaSuccess)
+          e = launch_split_blocks(p->d_sp_ops, p->d_sp_fitems, ie[0], p->d_sp_segs, a, b, ea, eb, emax, sa, sb, slices,
+                                  false, hi);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev(1), hi);
+      if (e != cudaSuccess) return cuda_fail(e, "split into slices");
+      {
+        PhaseTimer t(p->ctx, YTN_PHASE_GEMM, hi);
+        e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles, te[0], sa, sb, ea, eb, emax, normsq, wc, slices,
+                              p->ctx->status_dev, sms, false, hi);
+        // enqueued after group 0's GEMM, so that its CTAs are dispatched first
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(lo, ev(1), 0);
+        for (size_t g = 1; g < ngroups && e == cudaSuccess; g++) {
+          e = launch_split_blocks(p->d_sp_ops, p->d_sp_fitems + ie[g - 1], ie[g] - ie[g - 1], p->d_sp_segs, a, b, ea,
+                                  eb, emax, sa, sb, slices, true, lo);
+          if (e == cudaSuccess) e = cudaEventRecord(ev(g + 1), lo);
+        }
+        for (size_t g = 1; g < ngroups && e == cudaSuccess; g++) {
+          e = cudaStreamWaitEvent(hi, ev(g + 1), 0);
+          if (e == cudaSuccess)
+            e = launch_gemm_split(p->d_sp_sectors, p->d_sp_tiles + te[g - 1], te[g] - te[g - 1], sa, sb, ea, eb, emax,
+                                  normsq, wc, slices, p->ctx->status_dev, sms, false, hi);
+        }
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev(ngroups + 1), hi);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev(ngroups + 1), 0);
+      if (e != cudaSuccess) return cuda_fail(e, "pipelined split-precision GEMM");
+    } else {
+      {
+        PhaseTimer t(p->ctx, YTN_PHASE_SPLIT, st);
+        // the exponent kernels max-combine into EA, EB and EMAX: start from a value
+        // below every exponent (bytes 0x80: 0x80808080 as int32); the epilogue sums
+        // into NORMSQ and the check counts in the record: start from zero
+        e = cudaMemsetAsync(ea, 0x80, w.emax_end - w.ea, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(normsq, 0, w.rec_end - w.normsq, st);
+        if (e == cudaSuccess) {
+          if (fused)
+            e = launch_split_blocks(p->d_sp_ops, p->d_sp_fitems, (int64_t)p->sp_fitems.size(), p->d_sp_segs, a, b,
+                                    ea, eb, emax, sa, sb, slices, false, st);
+          else
+            e = launch_split_prep(p->d_sp_ops, p->d_sp_exp_items, (int64_t)p->sp_exp_items.size(),
+                                  p->d_sp_slice_items, (int64_t)p->sp_slice_items.size(), wa, wb, ea, eb, emax, sa,
+                                  sb, slices, st);
+        }
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "split into slices");
+      {
+        PhaseTimer t(p->ctx, YTN_PHASE_GEMM, st);
+        const bool mix = narrow_tails && !p->sp_tiles_mix.empty();
+        e = launch_gemm_split(p->d_sp_sectors, mix ? p->d_sp_tiles_mix : p->d_sp_tiles,
+                              (int64_t)(mix ? p->sp_tiles_mix.size() : p->sp_tiles.size()), sa, sb, ea, eb, emax,
+                              normsq, wc, slices, p->ctx->status_dev, sms, mix, st);
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "grouped split-precision GEMM");
     }
-    if (e != cudaSuccess) return cuda_fail(e, "grouped split-precision GEMM");
     {
       // data-aware error estimate per sector; sectors above rtol recomputed in FP64
       PhaseTimer t(p->ctx, YTN_PHASE_CHECK, st);
@@ -928,11 +1004,15 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     // candidates in a fixed order: FP64 (YTN_AUTO), staged split, fused split (128
     // wide tiles), then the variant of the previous run with 64-wide tails
     const bool with64 = need_choice, withfused = p->sp_fused && !((ha || hb) && !staged), withmix = has_mix;
+    const bool withpipe = withfused && p->sp_pipe_tile_end.size() >= 2;
     std::vector<std::function<ytn_status()>> runs;
     if (with64) runs.push_back([&]() { return exec_tensordot(p, a, b, c, false, 0, rtol, workspace, st); });
     runs.push_back([&]() { return exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st, false, false); });
     if (withfused)
       runs.push_back([&]() { return exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st, true, false); });
+    if (withpipe)
+      runs.push_back(
+          [&]() { return exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st, true, false, true); });
     if (withmix)
       runs.push_back(
           [&]() { return exec_tensordot(p, a, b, c, true, slices, rtol, workspace, st, withfused, true); });
@@ -952,29 +1032,35 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
     const float t64 = with64 ? ms[k++] : 0.f;
     const float tst = ms[k++];
     const float tfu = withfused ? ms[k++] : tst;
+    const float tpi = withpipe ? ms[k++] : 0.f;
     const float tmx = withmix ? ms[k++] : 0.f;
     const float t128 = withfused ? tfu : tst;   // the 128-wide run of the variant tried with tails
+    // the pipelined variant (128-wide tiles) is kept when it beats every other run
+    const bool pipe_best = withpipe && tpi < std::min(tst, tfu) && (!withmix || tpi <= tmx);
     {
       std::lock_guard<std::mutex> lk(p->auto_mu);
       if (withfused && p->split_variant[slices] < 0) {
-        p->split_variant[slices] = tfu < tst ? 1 : 0;
+        p->split_variant[slices] = pipe_best ? 2 : tfu < tst ? 1 : 0;
         p->variant_ms[slices][0] = tst;
         p->variant_ms[slices][1] = tfu;
+        p->variant_ms[slices][2] = tpi;
       }
       if (withmix) {
-        p->tile_policy[slices] = tmx < t128 ? 1 : 0;
+        p->tile_policy[slices] = !pipe_best && tmx < t128 ? 1 : 0;
         p->tile_ms[slices][0] = t128;
         p->tile_ms[slices][1] = tmx;
       }
       if (with64) {
         float best = std::min(tst, tfu);
+        if (withpipe) best = std::min(best, tpi);
         if (withmix) best = std::min(best, tmx);
         p->auto_choice[slices] = best < t64 ? 1 : 0;
         p->auto_ms[slices][0] = t64;
         p->auto_ms[slices][1] = best;
       }
     }
-    fill_res(true, withfused ? 1 : 0);
+    // C holds the last candidate's result
+    fill_res(true, withmix ? (withfused ? 1 : 0) : withpipe ? 2 : withfused ? 1 : 0);
     if (res) res->narrow_tiles = withmix ? 1 : 0;
     return unstage();
   }
@@ -983,12 +1069,16 @@ ytn_status ytn_tensordot(ytn_plan_t *p, const double *a, const double *b, double
   // read every block linearly over the host link (the fused kernels read blocks in
   // runs, twice)
   const bool host_direct = (ha || hb) && !staged;
-  const bool use_fused = split && p->sp_fused && variant == 1 && !host_direct;
-  const bool use_mix = split && has_mix && tiles == 1;
-  ytn_status r = exec_tensordot(p, a, b, c, split, split ? slices : 0, rtol, workspace, st, use_fused, use_mix);
+  const bool use_fused = split && p->sp_fused && variant >= 1 && !host_direct;
+  // a stream being captured into a graph takes the fused variant unpipelined (the
+  // pipeline's streams are shared by the context's calls)
+  const bool use_pipe = use_fused && variant == 2 && !capturing;
+  const bool use_mix = split && has_mix && tiles == 1 && !use_pipe;
+  ytn_status r =
+      exec_tensordot(p, a, b, c, split, split ? slices : 0, rtol, workspace, st, use_fused, use_mix, use_pipe);
   if (r != YTN_OK) return r;
   if ((r = unstage()) != YTN_OK) return r;
-  fill_res(split, use_fused ? 1 : 0);
+  fill_res(split, use_pipe ? 2 : use_fused ? 1 : 0);
   if (res) res->narrow_tiles = use_mix ? 1 : 0;
   return YTN_OK;
 }

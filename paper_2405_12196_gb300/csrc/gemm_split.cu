@@ -460,6 +460,11 @@ cudaError_t configure_split_gemm() {
                       gemm_split_kernel<4, true>, gemm_split_kernel<5, true>, gemm_split_kernel<6, true>}) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
+    // all of the SM's unified memory as shared memory, so that a slicing CTA of the
+    // pipelined split fits beside this kernel's CTA (the L1 share it leaves unused
+    // is not read by this kernel: operands arrive by bulk copies)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

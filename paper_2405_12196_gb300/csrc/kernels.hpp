@@ -35,13 +35,18 @@ cudaError_t launch_split_prep(const SplitOperand *ops, const SplitItem *exp_item
                               cudaStream_t stream);
 
 // Fused path: row exponents, then slices, straight from the tensors' blocks (a, b:
-// the operands' data), two passes over the blocks.
+// the operands' data), two passes over the blocks, for the items [items, items +
+// nitems). beside_gemm: the digits kernel sized to share each SM with a
+// split-GEMM CTA (pipelined variant).
 cudaError_t launch_split_blocks(const SplitOperand *ops, const SliceItem *items, int64_t nitems,
                                 const SliceSeg *segs, const double *a, const double *b, int32_t *ea, int32_t *eb,
-                                int32_t *emax, uint8_t *sa, uint8_t *sb, int slices, cudaStream_t stream);
+                                int32_t *emax, uint8_t *sa, uint8_t *sb, int slices, bool beside_gemm,
+                                cudaStream_t stream);
 
 // Shared-memory opt-in of the split-precision GEMM kernels (once per device).
 cudaError_t configure_split_gemm();
+// Shared-memory carveout of the slicing kernels that run beside the split GEMM.
+cudaError_t configure_split_blocks();
 
 // Scatter-combine of complex products: C blocks (interleaved complex) from the
 // quadrants of the doubled real C_q (one CTA per job).

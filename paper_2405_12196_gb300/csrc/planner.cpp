@@ -1209,6 +1209,8 @@ void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src) {
   p->sp_tiles_mix.clear();
   p->sp_fitems.clear();
   p->sp_segs.clear();
+  p->sp_pipe_tile_end.clear();
+  p->sp_pipe_item_end.clear();
   int64_t sa = 0, sb = 0, ea = 0, eb = 0;
   const int64_t nsec = (int64_t)p->sectors.size();
   for (int64_t q = 0; q < nsec; q++) {
@@ -1361,7 +1363,11 @@ void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src) {
           covered[it] += (rb - ra) * (kb - ka);
         }
     }
-  for (size_t o = 0; o < p->sp_ops.size(); o++) {
+  // items in the GEMM's sector order (decreasing K), A's before B's per sector, so
+  // that a run of sectors in that order is a run of items (pipelined slicing)
+  std::vector<int64_t> sec_item_end;
+  for (int64_t oq = 0; oq < 2 * nsec; oq++) {
+    const size_t o = (size_t)(2 * order[oq / 2] + oq % 2);
     const SplitOperand &op = p->sp_ops[o];
     for (int64_t hr = 0; hr < nrq(op); hr++)
       for (int64_t c = 0; c < nkq(op); c++) {
@@ -1390,8 +1396,42 @@ void plan_split_tables(ytn_plan_t *p, std::vector<SegSource> *src) {
           return;
         }
       }
+    if (oq % 2 == 1) sec_item_end.push_back((int64_t)p->sp_fitems.size());
   }
   p->sp_fused = true;
+
+  // Pipeline groups: runs of sectors in the GEMM's order of about an eighth of the
+  // useful FLOPs each, every group holding at least two waves of 128-wide tiles
+  // (one CTA per SM), so that each group's GEMM launch fills the GPU; the last run
+  // joins its predecessor when it is shorter. Fewer than two groups: no pipeline.
+  const int64_t min_tiles = 2 * (int64_t)std::max(1, p->ctx ? p->ctx->num_sms : 0);
+  double total = 0.0;
+  for (int64_t q : order) total += 2.0 * p->sectors[q].M * p->sectors[q].N * p->sectors[q].K;
+  int64_t tile_end = 0, gt = 0;
+  double gf = 0.0;
+  for (int64_t oi = 0; oi < nsec; oi++) {
+    const HostSector &h = p->sectors[order[oi]];
+    const int64_t nt = ((h.M + kSplitBM - 1) / kSplitBM) * ((h.N + kSplitBM - 1) / kSplitBM);
+    tile_end += nt;
+    gt += nt;
+    gf += 2.0 * h.M * h.N * h.K;
+    const bool last = oi == nsec - 1;
+    if ((gf >= total / kPipeGroups && gt >= min_tiles) || last) {
+      if (last && gt < min_tiles && !p->sp_pipe_tile_end.empty()) {
+        p->sp_pipe_tile_end.back() = tile_end;
+        p->sp_pipe_item_end.back() = sec_item_end[oi];
+      } else {
+        p->sp_pipe_tile_end.push_back(tile_end);
+        p->sp_pipe_item_end.push_back(sec_item_end[oi]);
+      }
+      gt = 0;
+      gf = 0.0;
+    }
+  }
+  if (p->sp_pipe_tile_end.size() < 2 || p->ctx == nullptr || p->ctx->device < 0) {
+    p->sp_pipe_tile_end.clear();
+    p->sp_pipe_item_end.clear();
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -43,9 +43,10 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
                : "memory");
 }
 
+// The digits kernel's shared memory: the item's tile of raw FP64 bits and its
+// rows' scale exponents (33.2 KB).
 struct __align__(16) Smem {
   unsigned long long tile[kItemRows][kPitch];
-  int red[kThreads / 32][kItemRows];
   int rexp[kItemRows];
 };
 
@@ -278,8 +279,12 @@ __device__ __forceinline__ void rowmax_units(int *rmax, const SliceSeg &g, int u
 // registers. A CTA takes two consecutive items (their records and segment tables
 // read together), its warps equal shares of their summed cost; eight CTAs per SM (32
 // registers) keep the most loads in flight (measured against six and four).
+// BESIDE: the instance launched beside the split GEMM (pipelined variant), the same
+// code with the SM's shared-memory carveout at its maximum (set at context
+// creation), so that the SMs it runs on stay configured for the GEMM's CTAs.
 constexpr int kRowmaxItems = 2;
 
+template <bool BESIDE>
 __global__ void __launch_bounds__(kThreads, 8) split_rowmax_kernel(const SplitOperand *__restrict__ ops,
                                                                    const SliceItem *__restrict__ items, int nitems,
                                                                    const SliceSeg *__restrict__ segs,
@@ -335,15 +340,22 @@ __global__ void __launch_bounds__(kThreads, 8) split_rowmax_kernel(const SplitOp
   }
 }
 
-__global__ void __launch_bounds__(kThreads) split_digits_kernel(const SplitOperand *__restrict__ ops,
-                                                                const SliceItem *__restrict__ items,
-                                                                const SliceSeg *__restrict__ segs,
-                                                                const double *__restrict__ a,
-                                                                const double *__restrict__ b,
-                                                                const int32_t *__restrict__ ea,
-                                                                const int32_t *__restrict__ eb,
-                                                                uint8_t *__restrict__ sa, uint8_t *__restrict__ sb,
-                                                                int s) {
+// MINB: CTAs per SM the launch bounds ask for. 5: 48 registers (five CTAs per SM,
+// as shared memory allows), the fastest alone; 6: 40
+// registers, so that one CTA fits beside a split-GEMM CTA (576 threads x 96
+// registers + 256 x 40 = 65,536; shared memory 198,912 + 34,176 bytes with the
+// per-CTA reserve, within the SM's 233,472), for the slicing that runs beside the
+// GEMM in the pipelined variant.
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) split_digits_kernel(const SplitOperand *__restrict__ ops,
+                                                                      const SliceItem *__restrict__ items,
+                                                                      const SliceSeg *__restrict__ segs,
+                                                                      const double *__restrict__ a,
+                                                                      const double *__restrict__ b,
+                                                                      const int32_t *__restrict__ ea,
+                                                                      const int32_t *__restrict__ eb,
+                                                                      uint8_t *__restrict__ sa,
+                                                                      uint8_t *__restrict__ sb, int s) {
   __shared__ Smem sm;
   const SliceItem it = items[blockIdx.x];
   const SplitOperand o = ops[it.op];
@@ -368,16 +380,31 @@ __global__ void __launch_bounds__(kThreads) split_digits_kernel(const SplitOpera
 
 }  // namespace
 
+cudaError_t configure_split_blocks() {
+  cudaError_t e = cudaFuncSetAttribute(split_rowmax_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(split_digits_kernel<6>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
+}
+
 cudaError_t launch_split_blocks(const SplitOperand *ops, const SliceItem *items, int64_t nitems,
                                 const SliceSeg *segs, const double *a, const double *b, int32_t *ea, int32_t *eb,
-                                int32_t *emax, uint8_t *sa, uint8_t *sb, int slices, cudaStream_t stream) {
+                                int32_t *emax, uint8_t *sa, uint8_t *sb, int slices, bool beside_gemm,
+                                cudaStream_t stream) {
   if (nitems <= 0) return cudaSuccess;
   if (nitems > INT32_MAX || slices < 1 || slices > kSlices) return cudaErrorInvalidValue;
-  split_rowmax_kernel<<<(unsigned)((nitems + kRowmaxItems - 1) / kRowmaxItems), kThreads, 0, stream>>>(
-      ops, items, (int)nitems, segs, a, b, ea, eb, emax);
+  const unsigned g0 = (unsigned)((nitems + kRowmaxItems - 1) / kRowmaxItems);
+  if (beside_gemm)
+    split_rowmax_kernel<true><<<g0, kThreads, 0, stream>>>(ops, items, (int)nitems, segs, a, b, ea, eb, emax);
+  else
+    split_rowmax_kernel<false><<<g0, kThreads, 0, stream>>>(ops, items, (int)nitems, segs, a, b, ea, eb, emax);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  split_digits_kernel<<<(unsigned)nitems, kThreads, 0, stream>>>(ops, items, segs, a, b, ea, eb, sa, sb, slices);
+  if (beside_gemm)
+    split_digits_kernel<6><<<(unsigned)nitems, kThreads, 0, stream>>>(ops, items, segs, a, b, ea, eb, sa, sb, slices);
+  else
+    split_digits_kernel<5><<<(unsigned)nitems, kThreads, 0, stream>>>(ops, items, segs, a, b, ea, eb, sa, sb, slices);
   return cudaGetLastError();
 }
 

@@ -158,6 +158,7 @@ constexpr int kSegDims = 4;       // dims per side in the table
 constexpr int kFusedDims = 3;     // dims per side the planner puts on the fused path
 constexpr int kItemRows = 32;     // rows per fused work item
 constexpr int kItemK = 128;       // K per fused work item
+constexpr int kPipeGroups = 8;    // most sector groups of the pipelined fused split
 struct SliceSeg {
   int64_t boff;
   int64_t fst[kSegDims], kst[kSegDims];
@@ -324,6 +325,12 @@ struct ytn_ctx {
   // (created by the first SVD / eigh plan); sectors are factored concurrently
   std::vector<void *> solvers, solver_params, solver_streams, solver_events;
   std::mutex solver_mu;
+  // pipelined fused split: the GEMM chain's stream (highest priority), the
+  // slicing stream (lowest) and their events (created with the context); one
+  // call's enqueue at a time
+  void *pipe_hi = nullptr, *pipe_lo = nullptr;
+  std::vector<void *> pipe_ev;
+  std::mutex pipe_mu;
 };
 
 struct ytn_plan_s {
@@ -404,6 +411,10 @@ struct ytn_plan_s {
   std::vector<ytn::SliceItem> sp_fitems;
   std::vector<ytn::SliceSeg> sp_segs;
   bool sp_fused = false;
+  // pipelined fused split: the sectors in the GEMM's order cut into groups; per
+  // group the end of its tiles in sp_tiles and of its items in sp_fitems (empty:
+  // fewer than two groups). Group g's slicing runs beside group g - 1's GEMM.
+  std::vector<int64_t> sp_pipe_tile_end, sp_pipe_item_end;
   std::vector<std::array<int64_t, 4>> sec_gather_items;   // per sector: A items, B items (relative)
   std::vector<ytn::SplitSector> sp_sectors;
   std::vector<ytn::SplitTile> sp_tiles;
@@ -414,9 +425,10 @@ struct ytn_plan_s {
   int auto_choice[ytn::kSlices + 1] = {-1, -1, -1, -1, -1, -1, -1};
   float auto_ms[ytn::kSlices + 1][2] = {};
   // split path variant per slice count: -1 undecided, 0 staged, 1 fused (slices
-  // straight from the blocks); the timings (ms) of the two
+  // straight from the blocks), 2 fused and pipelined with the GEMM; the timings
+  // (ms) of the three
   int split_variant[ytn::kSlices + 1] = {-1, -1, -1, -1, -1, -1, -1};
-  float variant_ms[ytn::kSlices + 1][2] = {};
+  float variant_ms[ytn::kSlices + 1][3] = {};
   // split GEMM tile list per slice count: -1 undecided, 0 all 128 wide, 1 with the
   // 64-wide sector tails; the timings (ms)
   int tile_policy[ytn::kSlices + 1] = {-1, -1, -1, -1, -1, -1, -1};

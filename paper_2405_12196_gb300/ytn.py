@@ -81,7 +81,7 @@ class ytn_plan_info(C.Structure):
                 ("max_n", C.c_int64), ("max_k", C.c_int64), ("a_elems", C.c_int64),
                 ("b_elems", C.c_int64), ("c_elems", C.c_int64), ("moved_elems", C.c_int64),
                 ("out_size", C.c_int64), ("njobs", C.c_int64), ("split_fused", C.c_int32),
-                ("max_copy_dims", C.c_int32)]
+                ("max_copy_dims", C.c_int32), ("split_pipe_groups", C.c_int32)]
 
 
 NPHASES = 8
@@ -107,7 +107,7 @@ class ytn_tuning(C.Structure):
     _fields_ = [("slices", C.c_int32), ("auto_choice", C.c_int32), ("split_variant", C.c_int32),
                 ("tile_policy", C.c_int32), ("fp64_ms", C.c_float), ("split_ms", C.c_float),
                 ("staged_ms", C.c_float), ("fused_ms", C.c_float), ("wide_ms", C.c_float),
-                ("narrow_ms", C.c_float)]
+                ("narrow_ms", C.c_float), ("pipelined_ms", C.c_float)]
 
 
 class ytn_request_info(C.Structure):

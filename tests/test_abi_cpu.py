@@ -416,6 +416,17 @@ def test_blocks_from_legs_errors(hctx):
         assert ei.value.name == "YTN_E_INVALID"
 
 
+def test_host_only_plans_have_no_pipeline_groups(hctx):
+    """The pipelined fused split needs the device's SM count and streams: a plan of a
+    host-only context reports no pipeline groups, even one large enough to have
+    them on a GPU."""
+    q = [(c,) for c in range(10)]
+    A = W.random_tensor((0,), [W.Leg(1, q, [1024] * 10), W.Leg(-1, q, [256] * 10)], (0,), 1, fill="ones")
+    B = W.random_tensor((0,), [W.Leg(1, q, [256] * 10), W.Leg(-1, q, [1024] * 10)], (0,), 2, fill="ones")
+    plan = ytn.ytn_plan(hctx, ytn.YTN_OP_TENSORDOT, A, B, (1,), (0,))
+    assert plan.info["split_fused"] == 1 and plan.info["split_pipe_groups"] == 0
+
+
 def test_tuning_of_a_new_plan_is_undecided(hctx):
     """A plan that has run no split call has no cached choice and no timings; slice
     counts outside 1..6 are rejected."""
@@ -425,7 +436,8 @@ def test_tuning_of_a_new_plan_is_undecided(hctx):
         t = ytn.ytn_plan_tuning(plan, s)
         assert t["slices"] == s
         assert (t["auto_choice"], t["split_variant"], t["tile_policy"]) == (-1, -1, -1)
-        assert all(t[k] == 0.0 for k in ("fp64_ms", "split_ms", "staged_ms", "fused_ms", "wide_ms", "narrow_ms"))
+        assert all(t[k] == 0.0 for k in ("fp64_ms", "split_ms", "staged_ms", "fused_ms", "wide_ms", "narrow_ms",
+                                         "pipelined_ms"))
     for s in (0, 7):
         with pytest.raises(ytn.YtnError) as e:
             ytn.ytn_plan_tuning(plan, s)

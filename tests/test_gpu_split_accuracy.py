@@ -287,6 +287,49 @@ def test_fused_split_walks_unmerged_dims(pattern):
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
+def _many_sector_pair(nsec=10, m=1024, k=256, n=1024, seed=77):
+    """U(1) matrices with `nsec` charge sectors of m x k times k x n each."""
+    q = [(c,) for c in range(nsec)]
+    A = W.random_tensor((0,), [W.Leg(1, q, [m] * nsec), W.Leg(-1, q, [k] * nsec)], (0,), seed)
+    B = W.random_tensor((0,), [W.Leg(1, q, [k] * nsec), W.Leg(-1, q, [n] * nsec)], (0,), seed + 1)
+    return A, B, (1,), (0,)
+
+
+def test_pipelined_fused_split():
+    """Ten sectors of 1024 x 256 x 1024 (640 tiles of 128 x 128) make two pipeline
+    groups. The first split call times the staged, fused and pipelined variants in
+    that order and leaves the pipelined run's result in C (no sector has a 64-wide
+    tail to try): it must meet the tolerance against the oracle, and a later call
+    (the autotuner's choice, whichever it is) must give the same bits."""
+    import torch
+    from gpu_helpers import check_against_oracle, oracle_tensordot
+    from paper_2405_12196_gb300 import ytn
+    A, B, axa, axb = _many_sector_pair()
+    fresh = ytn.ytn_ctx_create(0)
+    plan = ytn.ytn_plan(fresh, ytn.YTN_OP_TENSORDOT, A, B, axa, axb)
+    assert plan.info["split_fused"] == 1 and plan.info["split_pipe_groups"] == 2
+    dev = torch.device("cuda:0")
+    da, db = torch.from_numpy(A["data"]).to(dev), torch.from_numpy(B["data"]).to(dev)
+    ws = torch.empty(ytn.ytn_workspace_size(plan, ytn.YTN_SPLIT_BF16, SPLIT_RTOL), dtype=torch.uint8, device=dev)
+    ref = oracle_tensordot(A, B, axa, axb)
+    outs, variants = [], []
+    for call in range(2):
+        dc = torch.full((plan.out["size"],), float("nan"), dtype=torch.float64, device=dev)
+        res = ytn.ytn_tensordot(plan, da, db, dc, prec=ytn.YTN_SPLIT_BF16, rtol=SPLIT_RTOL, workspace=ws)
+        ytn.ytn_sync(fresh)
+        variants.append(res["split_variant"])
+        rec = dict(plan.out)
+        rec["data"] = dc.cpu().numpy()
+        check_against_oracle(rec, ref, rtol=SPLIT_RTOL)
+        outs.append(rec["data"])
+    assert variants[0] == 2
+    t = ytn.ytn_plan_tuning(plan, res["slices"])
+    assert t["pipelined_ms"] > 0 and t["fused_ms"] > 0 and t["staged_ms"] > 0
+    assert t["split_variant"] == variants[1]
+    assert (t["split_variant"] == 2) == (t["pipelined_ms"] < min(t["fused_ms"], t["staged_ms"]))
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 def test_split_variants_give_identical_bits(ctx):
     """A plan with fused tables: the first split call times the staged and the fused
     variant (leaving the fused result) and caches the faster; later calls use the
