@@ -5,13 +5,19 @@
 //
 // A work item is 32 rows of one operand (a quarter of a 128-row slice tile) and
 // 128 of K (four K stages). Its segments (planner: SliceSeg) are the parts of the
-// blocks that fall inside it. Both kernels load the whole item into a shared-memory
-// tile of raw FP64 bits with asynchronous copies, every element in flight at once:
-//   split_rowmax_kernel: the item's row maxima of the biased exponent, combined
+// blocks that fall inside it.
+//   split_rowmax_kernel: the item's row maxima of the biased exponent, read
+//                        straight into registers (two items per CTA), combined
 //                        over the row's items into its scale exponent with
 //                        atomicMax (and into the operand's largest);
-//   split_digits_kernel: the balanced digits at that scale, written as s BF16
-//                        slices in the tensor cores' swizzled layout.
+//   split_digits_kernel: the whole item loaded into a shared-memory tile of raw
+//                        FP64 bits with asynchronous copies, every element in
+//                        flight at once, then the balanced digits at the row
+//                        scales, written as s BF16 slices in the tensor cores'
+//                        swizzled layout.
+// Both take the items of a range [items, items + nitems): the whole list, or one
+// sector group of the pipelined variant (its instances launched beside the split
+// GEMM are sized to share an SM with a GEMM CTA).
 // HBM traffic per operand element: 8 bytes read twice and 2 s bytes written (the
 // staged path moves 8 bytes in and out of an FP64 sector matrix first, then reads
 // it twice).
@@ -22,7 +28,7 @@
 // steps along K, else the lanes are K and the warp steps along the rows. A lane's
 // offset is decomposed once (mixed radix over the block's free or contracted dims)
 // and the stepped one is carried from index to index, so that an element costs one
-// asynchronous copy and an add.
+// load (or asynchronous copy) and an add.
 #include <cuda_runtime.h>
 
 #include <climits>
